@@ -1,0 +1,151 @@
+/*
+ * fks.h -- C ABI of the GB300 Fast Kinetic Scheme library (libfks.so).
+ *
+ * Method: J. Narski, "Fast Kinetic Scheme: efficient MPI parallelization
+ * strategy for 3D Boltzmann equation", arXiv 1701.01608.
+ *   - phase space: N_s spatial cells x N_v = n^3 discrete velocities (Sec. 2.1,
+ *     "Let us start by truncating a velocity space"), velocity grid cell-centred
+ *     on [-L, L]^3: v_i = (i + 1/2 - n/2) * 2L/n;
+ *   - transport: exact shift of the generic-cell particles (Sec. 2.1
+ *     "Transport step", Sec. 3);
+ *   - collision: explicit Euler f = f* + dt Q(f*) (Eq. disc_relax) with the
+ *     fast spectral Boltzmann operator Q (Appendix A);
+ *   - moments U = (rho, rho u, E) = sum_k phi(v_k) f_k dv^3 (Sec. 3).
+ *
+ * Data layout of every distribution array: f[cell][ix][iy][iz] (iz fastest),
+ * cell = (cx*ny + cy)*nz + cz, element type double for FKS_FP64 and float
+ * for FKS_FP32.  All distribution / moment pointers are DEVICE pointers owned
+ * by the caller, 16-byte aligned, and must not alias unless stated.  The
+ * library owns its tables, offsets and flags.  `stream` is a cudaStream_t
+ * (NULL = legacy default stream); every call only enqueues work on it.
+ *
+ * Errors: every call returns an fks_status; nothing throws across the ABI.
+ * Invalid arguments are rejected before any work is enqueued.  Kernel health
+ * bits (non-finite result, negative f after a step) are read by fks_check.
+ * fks_last_error() gives a message for the last failing call on a context.
+ * One context per stream: calls on one context are not thread-safe.
+ */
+#ifndef FKS_H
+#define FKS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fks_ctx fks_ctx;
+
+typedef enum {
+    FKS_OK = 0,
+    FKS_ERR_INVALID_ARG = 1,
+    FKS_ERR_UNSUPPORTED = 2,
+    FKS_ERR_OOM = 3,
+    FKS_ERR_CUDA = 4,
+    FKS_ERR_NUMERIC = 5,
+    FKS_ERR_TIMEOUT = 6
+} fks_status;
+
+enum { FKS_BC_PERIODIC = 0, FKS_BC_SPECULAR = 1 };
+enum { FKS_FP64 = 0, FKS_FP32 = 1 };
+enum { FKS_HARD_SPHERE = 0, FKS_MAXWELL = 1 };
+
+/* Spatial grid: nx*ny*nz cells on the box [x0, x1]; bc[a] applies to both
+ * walls of axis a.  nx = ny = nz = 1 is the space-homogeneous problem. */
+typedef struct {
+    int nx, ny, nz;
+    double x0[3], x1[3];
+    int bc[3];
+} fks_grid;
+
+/* Velocity box: n^3 points on [-L, L]^3; n in {8, 16, 24, 32}. */
+typedef struct {
+    int n;
+    double L;
+} fks_vbox;
+
+/* Collision kernel (Appendix A, Eq. Btilde_pl):
+ *   FKS_HARD_SPHERE: B~(|x|,|y|) = 4C             (C = 1/4 gives B~ = 1)
+ *   FKS_MAXWELL:     B~(|x|,|y|) = 4C (|x||y|)^-1/2, a separable kernel whose
+ *                    collision kernel B = C (sin(theta)/2)^-1/2 does not
+ *                    depend on |g| (Maxwell type).
+ * The operator returned is Q / knudsen. */
+typedef struct {
+    int type;
+    double C;
+    double knudsen;
+} fks_kernel;
+
+/* Collision directions (Appendix A): M = A1*A2 half-sphere directions
+ * e = (sin t cos f, sin t sin f, cos t), f_q = q pi/A2, weight
+ * pi^2/(A1 A2) sin t_p;  rule 0: t_p = (p + 1/2) pi/A1, rule 1: t_p = p pi/A1. */
+typedef struct {
+    int A1, A2;
+    int rule;
+} fks_dirs;
+
+/* Create a context: validates the arguments, builds the spectral tables on
+ * the current device (FP64 arithmetic, stored in the working precision),
+ * and allocates the per-context state (sub-cell offsets, shift table,
+ * flags).  precision: FKS_FP64 or FKS_FP32.  On failure *out is NULL. */
+fks_status fks_init(const fks_grid *grid, const fks_vbox *vbox, const fks_kernel *kernel,
+                    const fks_dirs *dirs, int precision, fks_ctx **out);
+
+/* Q[cell] = Q(f[cell]) / Kn for every cell (Appendix A), followed by the
+ * FP64 conservation projection Q <- Q - C^T (C C^T)^-1 C Q onto the space
+ * orthogonal to the collision invariants (1, v, |v|^2/2).
+ * f, Q: device arrays of ncells * n^3 elements; f and Q must not overlap. */
+fks_status fks_collide(fks_ctx *ctx, const void *f, void *Q, void *stream);
+
+/* Exact shift transport over time dt (Sec. 2.1): advances the generic-cell
+ * particle offsets (FP64, s <- s + v dt, cell shift delta = floor((s + dx/2)/dx))
+ * and writes f_out[j][k] = f[j - delta_k][k'] (k' = k mirrored along an axis
+ * whose specular wall was crossed).  A permutation of the values: bit-exact.
+ * f and f_out must not overlap. */
+fks_status fks_transport(fks_ctx *ctx, const void *f, void *f_out, double dt, void *stream);
+
+/* One FKS step (Sec. 2.1, Eq. disc_relax): transport over dt, then the
+ * collision step f_out = f* + dt Q(f*) with the projected Q, fused in one
+ * kernel per cell (f* never goes to memory).  f and f_out must not overlap. */
+fks_status fks_step(fks_ctx *ctx, const void *f, void *f_out, double dt, void *stream);
+
+/* U[cell][0..4] = sum_k (1, vx, vy, vz, |v|^2/2) f[cell][k] dv^3, accumulated
+ * in FP64 (Sec. 3).  U: device array of ncells * 5 doubles. */
+fks_status fks_moments(fks_ctx *ctx, const void *f, double *U, void *stream);
+
+/* Synchronises `stream`, reads and clears the health bits of the kernels
+ * launched so far: bit 0 = non-finite value written, bit 1 = negative f
+ * after a step.  Returns FKS_ERR_NUMERIC if bit 0 was set, and stores the
+ * bits in *bits if bits != NULL. */
+fks_status fks_check(fks_ctx *ctx, void *stream, int *bits);
+
+/* Host copies of the per-axis sub-cell offsets s[3][n] (FP64).  get
+ * synchronises the device; set is synchronous too. */
+fks_status fks_get_offsets(fks_ctx *ctx, double *s);
+fks_status fks_set_offsets(fks_ctx *ctx, const double *s);
+
+/* Number of cells, velocity points per cell, and the thread-block cluster
+ * size the collision kernel runs with. */
+long fks_ncells(const fks_ctx *ctx);
+int fks_nv(const fks_ctx *ctx);
+int fks_cluster_size(const fks_ctx *ctx);
+
+/* Override the cluster size (a divisor of n for which a kernel exists);
+ * used by the autotuner.  Returns FKS_ERR_UNSUPPORTED if there is none. */
+fks_status fks_set_cluster_size(fks_ctx *ctx, int C);
+
+/* Kernel launches enqueued by this context since creation (for accounting). */
+long fks_launch_count(const fks_ctx *ctx);
+
+/* Diagnostic: the kernel transforms phi_R(s) and psi_R(s) of Appendix A
+ * (R = 2L/(3+sqrt 2)) evaluated on the host by the same code the table
+ * kernel runs on the device.  Needs no GPU. */
+fks_status fks_kernel_transform(int ktype, double C, double L, double s, double *phi, double *psi);
+
+void fks_destroy(fks_ctx *ctx);
+const char *fks_last_error(const fks_ctx *ctx);
+const char *fks_status_string(fks_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FKS_H */

@@ -1,0 +1,703 @@
+// fks_capi.cu -- C ABI of libfks: context, spectral tables, transport,
+// moments and the launch of the fused collision kernel.
+//
+// Method: arXiv 1701.01608 (Fast Kinetic Scheme), Sec. 2.1 (transport and
+// explicit Euler collision step, Eq. disc_relax), Sec. 3 (generic-cell
+// particles, moments), Appendix A (fast spectral Boltzmann operator).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fks.h"
+#include "fks_internal.h"
+
+namespace fks {
+
+// ------------------------------------------------------------------ tables
+//
+// Carleman form with a separable kernel B~ = a(|x|) b(|y|) (Appendix A):
+//   alpha_p(k)  = phi(xi_k . e_p),   phi(s) = int_{-R}^{R} |r| a(|r|) e^{i r s} dr
+//   alphap_p(k) = psi(|xi_k - (xi_k . e_p) e_p|),
+//                 psi(s) = int_0^pi phi_b(s cos t) dt  (disc integral in the plane
+//                 orthogonal to e_p, written in polar form)
+// with xi_k = (pi/L) kappa(k), cut-off R = lam L, lam = 2/(3+sqrt 2).
+// Hard spheres: a = b = sqrt(4C); pseudo-Maxwell: a = b = sqrt(4C) r^-1/2.
+
+constexpr int kGL = 64;
+
+struct TableParams {
+    int n, M, ktype, HF;
+    double L, R, c4;               // c4 = sqrt(4C)
+    const double* e;               // [M][3]
+    const double* w;               // [M]
+    const double* glt_x;           // Gauss-Legendre on [0, pi/2]: nodes
+    const double* glt_w;           //                               weights
+    const double* glu_x;           // Gauss-Legendre on [0, sqrt(R)]: nodes
+    const double* glu_w;           //                                  weights
+};
+
+// phi for hard spheres in closed form: 2 c4 [R sin(Rs)/s + (cos(Rs) - 1)/s^2]
+__host__ __device__ inline double phi_hs(double c4, double R, double s) {
+    s = fabs(s);
+    const double x = R * s;
+    if (x < 1e-3) {
+        const double x2 = x * x;
+        return c4 * R * R * (1.0 - x2 * (1.0 / 4.0) + x2 * x2 * (1.0 / 72.0) - x2 * x2 * x2 * (1.0 / 2880.0));
+    }
+    const double sh = sin(0.5 * x);
+    return c4 * 2.0 * (R * sin(x) / s - 2.0 * sh * sh / (s * s));
+}
+
+// phi for the pseudo-Maxwell kernel: 2 c4 int_0^R sqrt(r) cos(r s) dr,
+// r = u^2:  4 c4 int_0^sqrt(R) u^2 cos(u^2 s) du, Gauss-Legendre in u
+__host__ __device__ inline double phi_pm(double c4, double s, const double* gx, const double* gw) {
+    double acc = 0.0;
+    for (int i = 0; i < kGL; ++i) acc += gw[i] * gx[i] * gx[i] * cos(gx[i] * gx[i] * s);
+    return 4.0 * c4 * acc;
+}
+
+__host__ __device__ inline double phi_any(const TableParams& tp, double s) {
+    return tp.ktype == 0 ? phi_hs(tp.c4, tp.R, s) : phi_pm(tp.c4, s, tp.glu_x, tp.glu_w);
+}
+
+// psi(s) = 2 int_0^{pi/2} phi(s cos t) dt  (phi is even), Gauss-Legendre in t
+__host__ __device__ inline double psi_any(const TableParams& tp, double s) {
+    double acc = 0.0;
+    for (int i = 0; i < kGL; ++i) acc += tp.glt_w[i] * phi_any(tp, s * cos(tp.glt_x[i]));
+    return 2.0 * acc;
+}
+
+__host__ __device__ inline int signed_freq(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
+
+// alpha and alphap of mode (kx, ky, kz) for direction p, averaged over the
+// sign choices of Nyquist components (each stands for +-n/2 with half weight)
+__host__ __device__ inline void mode_tables(const TableParams& tp, int p, int kx, int ky, int kz,
+                                            double* a_out, double* b_out) {
+    const int n = tp.n;
+    const int kk[3] = {kx, ky, kz};
+    const double h = 3.14159265358979323846 / tp.L;
+    int nyq_axes[3], nnyq = 0;
+    for (int a = 0; a < 3; ++a)
+        if ((n % 2 == 0) && kk[a] == n / 2) nyq_axes[nnyq++] = a;
+    const double ex = tp.e[3 * p], ey = tp.e[3 * p + 1], ez = tp.e[3 * p + 2];
+    double sa = 0.0, sb = 0.0;
+    const int ncomb = 1 << nnyq;
+    for (int c = 0; c < ncomb; ++c) {
+        double xi[3];
+        for (int a = 0; a < 3; ++a) xi[a] = h * signed_freq(kk[a], n);
+        for (int b = 0; b < nnyq; ++b)
+            if (c & (1 << b)) xi[nyq_axes[b]] = -xi[nyq_axes[b]];
+        const double d = xi[0] * ex + xi[1] * ey + xi[2] * ez;
+        const double q2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2] - d * d;
+        sa += phi_any(tp, d);
+        sb += psi_any(tp, sqrt(q2 > 0.0 ? q2 : 0.0));
+    }
+    *a_out = sa / ncomb;
+    *b_out = sb / ncomb;
+}
+
+// FP64 tables on the half spectrum kz in [0, n/2]: A, B = [M][n][n][HF]
+__global__ void tables_kernel(TableParams tp, double* A, double* B) {
+    const long total = (long)tp.M * tp.n * tp.n * tp.HF;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(i % tp.HF);
+        const int ky = (int)((i / tp.HF) % tp.n);
+        const int kx = (int)((i / ((long)tp.HF * tp.n)) % tp.n);
+        const int p = (int)(i / ((long)tp.HF * tp.n * tp.n));
+        double a, b;
+        mode_tables(tp, p, kx, ky, kz, &a, &b);
+        A[i] = a;
+        B[i] = b;
+    }
+}
+
+// Pack into the collision kernel's layout [M+1][C][2][n kx][NS kyl][HF]:
+// table 0 = alpha N^-3, table 1 = w_p alphap N^-3; slot M holds betaL N^-3
+// (betaL = sum_p w_p alpha_p alphap_p) and zeros.
+template <typename T>
+__global__ void pack_tables_kernel(int n, int M, int C, int HF, const double* A, const double* B,
+                                   const double* w, T* out) {
+    const int NS = n / C;
+    const double s3 = 1.0 / ((double)n * n * n);
+    const long per = (long)n * NS * HF;
+    const long total = (long)(M + 1) * C * 2 * per;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(i % HF);
+        const int kyl = (int)((i / HF) % NS);
+        const int kx = (int)((i / ((long)HF * NS)) % n);
+        const int tab = (int)((i / per) % 2);
+        const int r = (int)((i / (per * 2)) % C);
+        const int p = (int)(i / (per * 2 * C));
+        const int ky = r * NS + kyl;
+        const long src = ((long)kx * n + ky) * HF + kz;
+        const long plane = (long)n * n * HF;
+        double v;
+        if (p < M) {
+            v = tab == 0 ? A[p * plane + src] * s3 : w[p] * B[p * plane + src] * s3;
+        } else if (tab == 0) {
+            double acc = 0.0;
+            for (int q = 0; q < M; ++q) acc += w[q] * A[q * plane + src] * B[q * plane + src];
+            v = acc * s3;
+        } else {
+            v = 0.0;
+        }
+        out[i] = (T)v;
+    }
+}
+
+// ------------------------------------------------------------------ offsets
+// Generic-cell particle offsets (Sec. 3), one axis per blockIdx.y:
+//   s <- s + v dt;  delta = floor((s + dx/2)/dx);  s <- s - delta dx
+// computed for v > 0 and mirrored for -v.  Explicit roundings (no
+// contraction) keep the result identical to a plain IEEE evaluation.
+__global__ void offsets_kernel(int n, double L, double3 dx3, double dt, double* s, signed char* delta, int* flags) {
+    const int a = blockIdx.y;
+    const int i = n / 2 + threadIdx.x;
+    if (i >= n) return;
+    const double dx = a == 0 ? dx3.x : (a == 1 ? dx3.y : dx3.z);
+    const double dv = __ddiv_rn(2.0 * L, (double)n);
+    const double v = __dmul_rn((double)i + 0.5 - 0.5 * n, dv);
+    const double sn = __dadd_rn(s[a * n + i], __dmul_rn(v, dt));
+    const double d = floor(__ddiv_rn(__dadd_rn(sn, __dmul_rn(0.5, dx)), dx));
+    const double snew = __dsub_rn(sn, __dmul_rn(d, dx));
+    const int im = n - 1 - i;
+    s[a * n + i] = snew;
+    s[a * n + im] = -snew;
+    if (fabs(d) > 120.0) atomicOr(flags, 4);
+    const int di = (int)d;
+    delta[a * n + i] = (signed char)di;
+    delta[a * n + im] = (signed char)(-di);
+}
+
+// ------------------------------------------------------------------ transport
+// f_out[j][k] = f[j - delta_k][k'] : one thread per output element
+template <typename T>
+__global__ void transport_kernel(int n, int ncx, int ncy, int ncz, int bcx, int bcy, int bcz,
+                                 const signed char* __restrict__ delta, const T* __restrict__ f,
+                                 T* __restrict__ out, long total) {
+    const long n3 = (long)n * n * n;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const long cell = i / n3;
+        const int k = (int)(i - cell * n3);
+        const int kz = k % n, ky = (k / n) % n, kx = k / (n * n);
+        const int cz = (int)(cell % ncz);
+        const int cy = (int)((cell / ncz) % ncy);
+        const int cx = (int)(cell / ((long)ncy * ncz));
+        int fx, fy, fz;
+        const int sx = fold_cell(cx - delta[kx], ncx, bcx, fx);
+        const int sy = fold_cell(cy - delta[n + ky], ncy, bcy, fy);
+        const int sz = fold_cell(cz - delta[2 * n + kz], ncz, bcz, fz);
+        const int qx = fx ? n - 1 - kx : kx;
+        const int qy = fy ? n - 1 - ky : ky;
+        const int qz = fz ? n - 1 - kz : kz;
+        out[i] = f[(((long)sx * ncy + sy) * ncz + sz) * n3 + ((long)qx * n + qy) * n + qz];
+    }
+}
+
+// ------------------------------------------------------------------ moments
+template <typename T, int BS>
+__global__ void __launch_bounds__(BS) moments_kernel(int n, double L, long ncells, const T* __restrict__ f,
+                                                     double* __restrict__ U) {
+    __shared__ double red[BS / 32][5];
+    const long n3 = (long)n * n * n;
+    const double dv = 2.0 * L / n;
+    const double dv3 = dv * dv * dv;
+    for (long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
+        const T* fc = f + cell * n3;
+        double s[5] = {0, 0, 0, 0, 0};
+        for (long k = threadIdx.x; k < n3; k += BS) {
+            const int kz = (int)(k % n), ky = (int)((k / n) % n), kx = (int)(k / ((long)n * n));
+            const double vx = ((double)kx + 0.5 - 0.5 * n) * dv;
+            const double vy = ((double)ky + 0.5 - 0.5 * n) * dv;
+            const double vz = ((double)kz + 0.5 - 0.5 * n) * dv;
+            const double m = (double)fc[k];
+            s[0] += m;
+            s[1] += m * vx;
+            s[2] += m * vy;
+            s[3] += m * vz;
+            s[4] += m * 0.5 * (vx * vx + vy * vy + vz * vz);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s[i] += __shfl_xor_sync(0xffffffffu, s[i], off);
+        const int warp = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0)
+            for (int i = 0; i < 5; ++i) red[warp][i] = s[i];
+        __syncthreads();
+        if (threadIdx.x < 5) {
+            double acc = 0.0;
+            for (int w = 0; w < BS / 32; ++w) acc += red[w][threadIdx.x];
+            U[cell * 5 + threadIdx.x] = acc * dv3;
+        }
+        __syncthreads();
+    }
+}
+
+int default_cluster_size(bool fp64, int N) {
+    if (!fp64) return N == 32 ? 4 : (N == 24 ? 2 : 1);
+    return N == 32 ? 8 : (N == 24 ? 4 : (N == 16 ? 2 : 1));
+}
+
+bool find_collide_variant(bool fp64, int N, int C, CollideVariant* out) {
+    return fp64 ? find_collide_variant_f64(N, C, out) : find_collide_variant_f32(N, C, out);
+}
+
+// Gauss-Legendre rule on [a, b] by Newton iteration on the Legendre recurrence
+static void gl_rule(int m, double a, double b, double* x, double* w) {
+    for (int i = 0; i < m; ++i) {
+        double z = std::cos(3.14159265358979323846 * (i + 0.75) / (m + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= m; ++k) {
+                const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = m * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = 0.5 * (b - a) * z + 0.5 * (b + a);
+        w[i] = (b - a) / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+}  // namespace fks
+
+using namespace fks;
+
+struct fks_ctx {
+    fks_grid grid;
+    fks_vbox vbox;
+    fks_kernel kern;
+    fks_dirs dirs;
+    bool fp64;
+    int n, M, C;
+    long ncells;
+    double dx[3];
+    void* tables = nullptr;     // collision-kernel layout, element T
+    double* d_s = nullptr;      // [3][n] offsets
+    signed char* d_delta = nullptr;
+    int* d_flags = nullptr;
+    double P[25];
+    CollideVariant var;
+    int max_clusters = 0;
+    long launches = 0;
+    std::string err;
+    int device = 0;
+};
+
+static fks_status fail(fks_ctx* c, fks_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+static fks_status cuda_fail(fks_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, FKS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define FKS_CUDA(call)                                     \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+static fks_status configure_variant(fks_ctx* c, int C) {
+    CollideVariant v;
+    if (!find_collide_variant(c->fp64, c->n, C, &v))
+        return fail(c, FKS_ERR_UNSUPPORTED, "no collision kernel for this (precision, n, cluster size)");
+    FKS_CUDA(cudaFuncSetAttribute(v.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(v.NT, 1, 1);
+    cfg.dynamicSmemBytes = v.smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclus = 0;
+    FKS_CUDA(cudaOccupancyMaxActiveClusters(&nclus, v.func, &cfg));
+    if (nclus <= 0) return fail(c, FKS_ERR_UNSUPPORTED, "collision kernel cannot be resident on this device");
+    c->var = v;
+    c->C = C;
+    c->max_clusters = nclus;
+    return FKS_OK;
+}
+
+static fks_status build_tables(fks_ctx* c) {
+    const int n = c->n, M = c->M, HF = n / 2 + 1;
+    const double pi = 3.14159265358979323846;
+    std::vector<double> e(3 * M), w(M);
+    for (int p = 0; p < c->dirs.A1; ++p) {
+        const double t = (c->dirs.rule == 0 ? (p + 0.5) : (double)p) * pi / c->dirs.A1;
+        for (int q = 0; q < c->dirs.A2; ++q) {
+            const double fi = q * pi / c->dirs.A2;
+            const int m = p * c->dirs.A2 + q;
+            e[3 * m] = std::sin(t) * std::cos(fi);
+            e[3 * m + 1] = std::sin(t) * std::sin(fi);
+            e[3 * m + 2] = std::cos(t);
+            w[m] = pi * pi / ((double)c->dirs.A1 * c->dirs.A2) * std::sin(t);
+        }
+    }
+    const double R = 2.0 / (3.0 + std::sqrt(2.0)) * c->vbox.L;
+    std::vector<double> gl(4 * kGL);
+    gl_rule(kGL, 0.0, 0.5 * pi, gl.data(), gl.data() + kGL);
+    gl_rule(kGL, 0.0, std::sqrt(R), gl.data() + 2 * kGL, gl.data() + 3 * kGL);
+
+    double *d_e = nullptr, *d_gl = nullptr, *d_A = nullptr, *d_B = nullptr, *d_w = nullptr;
+    const long half = (long)M * n * n * HF;
+    const long packed = (long)(M + 1) * c->C * 2 * n * (n / c->C) * HF;
+    const size_t esz = c->fp64 ? 8 : 4;
+    fks_status st = FKS_OK;
+    cudaError_t e1 = cudaMalloc(&d_e, sizeof(double) * (3 * M + M));
+    cudaError_t e2 = cudaMalloc(&d_gl, sizeof(double) * 4 * kGL);
+    cudaError_t e3 = cudaMalloc(&d_A, sizeof(double) * half);
+    cudaError_t e4 = cudaMalloc(&d_B, sizeof(double) * half);
+    cudaError_t e5 = cudaMalloc(&c->tables, esz * packed);
+    if (e1 || e2 || e3 || e4 || e5) {
+        st = fail(c, FKS_ERR_OOM, "cudaMalloc of spectral tables failed");
+    } else {
+        d_w = d_e + 3 * M;
+        cudaMemcpy(d_e, e.data(), sizeof(double) * 3 * M, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_w, w.data(), sizeof(double) * M, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_gl, gl.data(), sizeof(double) * 4 * kGL, cudaMemcpyHostToDevice);
+        TableParams tp;
+        tp.n = n;
+        tp.M = M;
+        tp.ktype = c->kern.type;
+        tp.HF = HF;
+        tp.L = c->vbox.L;
+        tp.R = R;
+        tp.c4 = std::sqrt(4.0 * c->kern.C);
+        tp.e = d_e;
+        tp.w = d_w;
+        tp.glt_x = d_gl;
+        tp.glt_w = d_gl + kGL;
+        tp.glu_x = d_gl + 2 * kGL;
+        tp.glu_w = d_gl + 3 * kGL;
+        tables_kernel<<<1024, 128>>>(tp, d_A, d_B);
+        if (c->fp64)
+            pack_tables_kernel<double><<<1024, 256>>>(n, M, c->C, HF, d_A, d_B, d_w, (double*)c->tables);
+        else
+            pack_tables_kernel<float><<<1024, 256>>>(n, M, c->C, HF, d_A, d_B, d_w, (float*)c->tables);
+        c->launches += 2;
+        cudaError_t es = cudaDeviceSynchronize();
+        if (es != cudaSuccess) st = cuda_fail(c, es, "table construction");
+    }
+    cudaFree(d_e);
+    cudaFree(d_gl);
+    cudaFree(d_A);
+    cudaFree(d_B);
+    return st;
+}
+
+// P = (sum_k phi(v_k) phi(v_k)^T)^-1, phi = (1, v, |v|^2/2): the projection
+// Q -= C^T (C C^T)^-1 C Q with C = dv^3 phi^T becomes Q -= phi^T P (phi^T Q)
+static void projection_matrix(int n, double L, double* P) {
+    const double dv = 2.0 * L / n;
+    double A[5][10];
+    std::memset(A, 0, sizeof(A));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < n; ++k) {
+                const double vx = (i + 0.5 - 0.5 * n) * dv, vy = (j + 0.5 - 0.5 * n) * dv, vz = (k + 0.5 - 0.5 * n) * dv;
+                const double ph[5] = {1.0, vx, vy, vz, 0.5 * (vx * vx + vy * vy + vz * vz)};
+                for (int a = 0; a < 5; ++a)
+                    for (int b = 0; b < 5; ++b) A[a][b] += ph[a] * ph[b];
+            }
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) A[a][5 + b] = (a == b) ? 1.0 : 0.0;
+    for (int col = 0; col < 5; ++col) {   // Gauss-Jordan with partial pivoting
+        int piv = col;
+        for (int r = col + 1; r < 5; ++r)
+            if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+        if (piv != col)
+            for (int t = 0; t < 10; ++t) std::swap(A[col][t], A[piv][t]);
+        const double d = A[col][col];
+        for (int t = 0; t < 10; ++t) A[col][t] /= d;
+        for (int r = 0; r < 5; ++r) {
+            if (r == col) continue;
+            const double fct = A[r][col];
+            for (int t = 0; t < 10; ++t) A[r][t] -= fct * A[col][t];
+        }
+    }
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) P[a * 5 + b] = A[a][5 + b];
+}
+
+extern "C" {
+
+const char* fks_status_string(fks_status s) {
+    switch (s) {
+        case FKS_OK: return "ok";
+        case FKS_ERR_INVALID_ARG: return "invalid argument";
+        case FKS_ERR_UNSUPPORTED: return "unsupported configuration";
+        case FKS_ERR_OOM: return "out of device memory";
+        case FKS_ERR_CUDA: return "CUDA error";
+        case FKS_ERR_NUMERIC: return "numerical health check failed";
+        case FKS_ERR_TIMEOUT: return "timeout";
+    }
+    return "unknown";
+}
+
+fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel* kernel, const fks_dirs* dirs,
+                    int precision, fks_ctx** out) {
+    if (out) *out = nullptr;
+    if (!grid || !vbox || !kernel || !dirs || !out) return FKS_ERR_INVALID_ARG;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return FKS_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) {
+        if (!(grid->x1[a] > grid->x0[a])) return FKS_ERR_INVALID_ARG;
+        if (grid->bc[a] != FKS_BC_PERIODIC && grid->bc[a] != FKS_BC_SPECULAR) return FKS_ERR_INVALID_ARG;
+    }
+    if (!(vbox->L > 0.0) || !std::isfinite(vbox->L)) return FKS_ERR_INVALID_ARG;
+    if (vbox->n != 8 && vbox->n != 16 && vbox->n != 24 && vbox->n != 32) return FKS_ERR_UNSUPPORTED;
+    if (kernel->type != FKS_HARD_SPHERE && kernel->type != FKS_MAXWELL) return FKS_ERR_INVALID_ARG;
+    if (!(kernel->C > 0.0) || !(kernel->knudsen > 0.0)) return FKS_ERR_INVALID_ARG;
+    if (dirs->A1 < 1 || dirs->A2 < 1 || dirs->A1 * dirs->A2 > 4096 || (dirs->rule != 0 && dirs->rule != 1))
+        return FKS_ERR_INVALID_ARG;
+    if (precision != FKS_FP64 && precision != FKS_FP32) return FKS_ERR_UNSUPPORTED;
+
+    fks_ctx* c = new (std::nothrow) fks_ctx();
+    if (!c) return FKS_ERR_OOM;
+    c->grid = *grid;
+    c->vbox = *vbox;
+    c->kern = *kernel;
+    c->dirs = *dirs;
+    c->fp64 = precision == FKS_FP64;
+    c->n = vbox->n;
+    c->M = dirs->A1 * dirs->A2;
+    c->ncells = (long)grid->nx * grid->ny * grid->nz;
+    const int nca[3] = {grid->nx, grid->ny, grid->nz};
+    for (int a = 0; a < 3; ++a) c->dx[a] = (grid->x1[a] - grid->x0[a]) / nca[a];
+    cudaGetDevice(&c->device);
+    fks_status st = configure_variant(c, default_cluster_size(c->fp64, c->n));
+    if (st == FKS_OK) st = build_tables(c);
+    if (st == FKS_OK) {
+        if (cudaMalloc(&c->d_s, sizeof(double) * 3 * c->n) != cudaSuccess ||
+            cudaMalloc(&c->d_delta, 3 * c->n) != cudaSuccess || cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess)
+            st = FKS_ERR_OOM;
+        else if (cudaMemset(c->d_s, 0, sizeof(double) * 3 * c->n) != cudaSuccess ||
+                 cudaMemset(c->d_delta, 0, 3 * c->n) != cudaSuccess || cudaMemset(c->d_flags, 0, sizeof(int)) != cudaSuccess)
+            st = FKS_ERR_CUDA;
+    }
+    if (st != FKS_OK) {
+        std::fprintf(stderr, "fks_init: %s\n", c->err.c_str());
+        fks_destroy(c);
+        return st;
+    }
+    projection_matrix(c->n, c->vbox.L, c->P);
+    *out = c;
+    return FKS_OK;
+}
+
+void fks_destroy(fks_ctx* c) {
+    if (!c) return;
+    cudaFree(c->tables);
+    cudaFree(c->d_s);
+    cudaFree(c->d_delta);
+    cudaFree(c->d_flags);
+    delete c;
+}
+
+const char* fks_last_error(const fks_ctx* c) { return c ? c->err.c_str() : "null context"; }
+long fks_ncells(const fks_ctx* c) { return c ? c->ncells : -1; }
+int fks_nv(const fks_ctx* c) { return c ? c->n * c->n * c->n : -1; }
+int fks_cluster_size(const fks_ctx* c) { return c ? c->C : -1; }
+long fks_launch_count(const fks_ctx* c) { return c ? c->launches : -1; }
+
+fks_status fks_set_cluster_size(fks_ctx* c, int C) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (C == c->C) return FKS_OK;
+    // tables are laid out per cluster rank: rebuild them for the new size
+    CollideVariant v;
+    if (!find_collide_variant(c->fp64, c->n, C, &v)) return fail(c, FKS_ERR_UNSUPPORTED, "no kernel for this cluster size");
+    cudaDeviceSynchronize();
+    cudaFree(c->tables);
+    c->tables = nullptr;
+    fks_status st = configure_variant(c, C);
+    if (st == FKS_OK) st = build_tables(c);
+    return st;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
+                                 cudaStream_t s) {
+    CollideArgs a;
+    a.f = f;
+    a.out = out;
+    a.tables = c->tables;
+    a.delta = delta;
+    a.flags = c->d_flags;
+    a.ncells = c->ncells;
+    a.nc[0] = c->grid.nx;
+    a.nc[1] = c->grid.ny;
+    a.nc[2] = c->grid.nz;
+    for (int i = 0; i < 3; ++i) a.bc[i] = c->grid.bc[i];
+    a.M = c->M;
+    a.L = c->vbox.L;
+    a.inv_kn = 1.0 / c->kern.knudsen;
+    a.dt = dt;
+    a.mode = mode;
+    std::memcpy(a.P, c->P, sizeof(a.P));
+    const long nclus = c->ncells < c->max_clusters ? c->ncells : c->max_clusters;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c->C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(nclus * c->C), 1, 1);
+    cfg.blockDim = dim3(c->var.NT, 1, 1);
+    cfg.dynamicSmemBytes = c->var.smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {&a};
+    cudaError_t e = cudaLaunchKernelExC(&cfg, c->var.func, args);
+    if (e != cudaSuccess) return cuda_fail(c, e, "collision kernel launch");
+    c->launches += 1;
+    return FKS_OK;
+}
+
+static fks_status launch_offsets(fks_ctx* c, double dt, cudaStream_t s) {
+    if (!std::isfinite(dt)) return fail(c, FKS_ERR_INVALID_ARG, "dt must be finite");
+    const double vmax = c->vbox.L;
+    for (int a = 0; a < 3; ++a)
+        if (std::fabs(vmax * dt) > 100.0 * c->dx[a]) return fail(c, FKS_ERR_INVALID_ARG, "dt moves particles more than 100 cells");
+    offsets_kernel<<<dim3(1, 3), c->n / 2, 0, s>>>(c->n, c->vbox.L, make_double3(c->dx[0], c->dx[1], c->dx[2]), dt, c->d_s,
+                                                 c->d_delta, c->d_flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "offsets kernel launch");
+    c->launches += 1;
+    return FKS_OK;
+}
+
+fks_status fks_collide(fks_ctx* c, const void* f, void* Q, void* stream) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (!f || !Q || !aligned16(f) || !aligned16(Q)) return fail(c, FKS_ERR_INVALID_ARG, "f and Q must be 16-byte aligned device pointers");
+    if (f == Q) return fail(c, FKS_ERR_INVALID_ARG, "f and Q must not alias");
+    if (c->ncells == 0) return FKS_OK;
+    return launch_collide(c, f, Q, nullptr, 0.0, 0, (cudaStream_t)stream);
+}
+
+fks_status fks_transport(fks_ctx* c, const void* f, void* f_out, double dt, void* stream) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (!f || !f_out || f == f_out) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must be distinct device pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    fks_status st = launch_offsets(c, dt, s);
+    if (st != FKS_OK) return st;
+    const long total = c->ncells * (long)c->n * c->n * c->n;
+    const int bs = 256;
+    long blocks = (total + bs - 1) / bs;
+    if (blocks > 152L * 64) blocks = 152L * 64;
+    if (c->fp64)
+        transport_kernel<double><<<(unsigned)blocks, bs, 0, s>>>(c->n, c->grid.nx, c->grid.ny, c->grid.nz, c->grid.bc[0],
+                                                               c->grid.bc[1], c->grid.bc[2], c->d_delta,
+                                                               (const double*)f, (double*)f_out, total);
+    else
+        transport_kernel<float><<<(unsigned)blocks, bs, 0, s>>>(c->n, c->grid.nx, c->grid.ny, c->grid.nz, c->grid.bc[0],
+                                                              c->grid.bc[1], c->grid.bc[2], c->d_delta,
+                                                              (const float*)f, (float*)f_out, total);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "transport kernel launch");
+    c->launches += 1;
+    return FKS_OK;
+}
+
+fks_status fks_step(fks_ctx* c, const void* f, void* f_out, double dt, void* stream) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (!f || !f_out || !aligned16(f) || !aligned16(f_out)) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must be 16-byte aligned device pointers");
+    if (f == f_out) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must not alias");
+    cudaStream_t s = (cudaStream_t)stream;
+    fks_status st = launch_offsets(c, dt, s);
+    if (st != FKS_OK) return st;
+    if (c->ncells == 0) return FKS_OK;
+    return launch_collide(c, f, f_out, c->d_delta, dt, 1, s);
+}
+
+fks_status fks_moments(fks_ctx* c, const void* f, double* U, void* stream) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (!f || !U) return fail(c, FKS_ERR_INVALID_ARG, "null pointer");
+    if (c->ncells == 0) return FKS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    long blocks = c->ncells < 152L * 16 ? c->ncells : 152L * 16;
+    if (c->fp64)
+        moments_kernel<double, 256><<<(unsigned)blocks, 256, 0, s>>>(c->n, c->vbox.L, c->ncells, (const double*)f, U);
+    else
+        moments_kernel<float, 256><<<(unsigned)blocks, 256, 0, s>>>(c->n, c->vbox.L, c->ncells, (const float*)f, U);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel launch");
+    c->launches += 1;
+    return FKS_OK;
+}
+
+fks_status fks_check(fks_ctx* c, void* stream, int* bits) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    e = cudaMemcpy(&h, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "flag read");
+    e = cudaMemset(c->d_flags, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(c, e, "flag reset");
+    if (bits) *bits = h;
+    if (h & 1) return fail(c, FKS_ERR_NUMERIC, "non-finite value written");
+    if (h & 4) return fail(c, FKS_ERR_NUMERIC, "cell shift out of range");
+    return FKS_OK;
+}
+
+fks_status fks_get_offsets(fks_ctx* c, double* s) {
+    if (!c || !s) return FKS_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpy(s, c->d_s, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "offset read");
+    return FKS_OK;
+}
+
+fks_status fks_set_offsets(fks_ctx* c, const double* s) {
+    if (!c || !s) return FKS_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpy(c->d_s, s, sizeof(double) * 3 * c->n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "offset write");
+    return FKS_OK;
+}
+
+// Host evaluation of the kernel transforms phi_R(s), psi_R(s) with the same
+// code the table kernel runs on the device (a diagnostic: no GPU needed).
+fks_status fks_kernel_transform(int ktype, double C, double L, double s, double* phi, double* psi) {
+    if (!phi || !psi || (ktype != 0 && ktype != 1) || !(C > 0) || !(L > 0)) return FKS_ERR_INVALID_ARG;
+    const double R = 2.0 / (3.0 + std::sqrt(2.0)) * L;
+    std::vector<double> gl(4 * kGL);
+    gl_rule(kGL, 0.0, 0.5 * 3.14159265358979323846, gl.data(), gl.data() + kGL);
+    gl_rule(kGL, 0.0, std::sqrt(R), gl.data() + 2 * kGL, gl.data() + 3 * kGL);
+    TableParams tp;
+    tp.n = 0;
+    tp.M = 0;
+    tp.ktype = ktype;
+    tp.HF = 0;
+    tp.L = L;
+    tp.R = R;
+    tp.c4 = std::sqrt(4.0 * C);
+    tp.e = nullptr;
+    tp.w = nullptr;
+    tp.glt_x = gl.data();
+    tp.glt_w = gl.data() + kGL;
+    tp.glu_x = gl.data() + 2 * kGL;
+    tp.glu_w = gl.data() + 3 * kGL;
+    *phi = phi_any(tp, s);
+    *psi = psi_any(tp, s);
+    return FKS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,390 @@
+// fks_collide.cuh -- per-cell fast spectral collision operator (Appendix A of
+// arXiv 1701.01608) with the FKS transport gather and the explicit Euler step
+// (Eq. disc_relax) fused around it.
+//
+// One cell is processed by one thread-block cluster of C CTAs.  The
+// half-spectrum f^ (kz' = 0..N/2) is distributed over the cluster by ky slab;
+// each inverse transform runs x-pass (local) -> DSMEM exchange -> y-pass ->
+// z-pass (C2R, local), so the whole per-cell working set stays on chip and f^
+// is read from shared memory 2M+1 times instead of from HBM.
+//
+// Per cell:
+//   f*  = gather of f over the transport shifts delta_k (identity for collide)
+//   F   = DFT(f*)                                   forward R2C, 3 passes
+//   for p < M:  a = IDFT(alpha_p F) / N^3,  b = IDFT(w_p alphap_p F) / N^3,
+//               G += a b                            (gain, Appendix A)
+//   l   = IDFT(betaL F) / N^3,  L = f* l             (loss: the B_F(m,m) term)
+//   Q   = (G - L) / Kn                               (difference in FP64)
+//   Q  -= C^T (C C^T)^-1 C Q                         (FP64 conservation projection)
+//   out = Q  or  f* + dt Q
+//
+// Inverse-pass packing: the kz' = 0 and kz' = N/2 planes of a real field are
+// each 2-D Hermitian, so they travel together as one complex plane
+// (plane 0 = P_0 + i P_{N/2}); every pass then has exactly N/2 planes.
+#pragma once
+#include <cooperative_groups.h>
+#include <cstdint>
+
+#include "fks_fft.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace fks {
+
+struct CollideArgs {
+    const void* f;          // input distribution, ncells * N^3 (element type T)
+    void* out;              // Q or f^{n+1}
+    const void* tables;     // [M+1][C][2][N kx][NS kyl][H+1 kz'] of T
+    const signed char* delta;  // [3][N] cell shifts for this step (transport) or nullptr
+    int* flags;             // health bits (atomicOr)
+    long ncells;
+    int nc[3];              // spatial cells per axis
+    int bc[3];              // 0 periodic, 1 specular
+    int M;                  // number of directions
+    double L;               // velocity box half width
+    double inv_kn;
+    double dt;              // Euler step (step mode)
+    int mode;               // 0 collide (out = Q), 1 step (out = f* + dt Q)
+    double P[25];           // dv^6 (C C^T)^-1 over the rows phi = (1, v, |v|^2/2)
+};
+
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    cluster_arrive();
+    cluster_wait();
+}
+
+// 32-bit shared-window addresses and stores into a peer CTA's shared memory
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, cpx<float> v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, cpx<double> v) {
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};\n" ::"r"(addr), "d"(v.x), "d"(v.y) : "memory");
+}
+
+// fold a source cell coordinate: periodic wrap or specular reflection
+__device__ __forceinline__ int fold_cell(int u, int len, int specular, int& flip) {
+    if (!specular) {
+        int r = u % len;
+        if (r < 0) r += len;
+        flip = 0;
+        return r;
+    }
+    int per = 2 * len;
+    int r = u % per;
+    if (r < 0) r += per;
+    if (r >= len) { flip = 1; return per - 1 - r; }
+    flip = 0;
+    return r;
+}
+
+template <typename T, int N, int C>
+struct CollideCfg {
+    static constexpr int NS = N / C;          // slab width (ky for f^, x for W)
+    static constexpr int H = N / 2;           // packed planes per inverse transform
+    static constexpr int HF = H + 1;          // kz' planes of f^
+    static constexpr int HP = H + 1;          // padded plane stride of W
+    static constexpr int NTASK = N * N / C;   // pencils / columns per pass per CTA
+    static constexpr int NT = (NTASK + 31) / 32 * 32;   // threads per CTA (whole warps)
+    // shared memory: Fh, W (cpx<T>); G, f* (T, one column of N per task)
+    static constexpr long FH_ELEMS = (long)N * NS * HF;
+    static constexpr long W_ELEMS = 2L * NS * N * HP;
+    static constexpr long COL_ELEMS = (long)NS * N * N;
+    static constexpr size_t SMEM_BYTES = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS) + sizeof(T) * 2 * COL_ELEMS +
+                                         sizeof(double) * (8 + (NT / 32) * 5 + 8) + 3 * N + 16;
+    static_assert(N % C == 0, "cluster size must divide N");
+};
+
+template <typename T, int N, int C>
+__global__ void __launch_bounds__(CollideCfg<T, N, C>::NT, 1)
+collide_kernel(CollideArgs args) {
+    using Cfg = CollideCfg<T, N, C>;
+    constexpr int NS = Cfg::NS, H = Cfg::H, HF = Cfg::HF, HP = Cfg::HP, NT = Cfg::NT, NTASK = Cfg::NTASK;
+    constexpr long N3 = (long)N * N * N;
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x;
+    const long cluster_id = blockIdx.x / C;
+    const long nclusters = gridDim.x / C;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* Fh = reinterpret_cast<cpx<T>*>(smem_raw);                 // [N kx][NS kyl][HF]
+    cpx<T>* W = Fh + Cfg::FH_ELEMS;                                    // [2][NS xl][N ky][HP]
+    T* Gs = reinterpret_cast<T*>(W + Cfg::W_ELEMS);                   // [NS xl][N y][N z] gain
+    T* Fs = Gs + Cfg::COL_ELEMS;                                       // [NS xl][N y][N z] f*
+    double* red = reinterpret_cast<double*>(Fs + Cfg::COL_ELEMS);     // [8] own partials
+    double* redw = red + 8;                                            // [NT/32][5]
+    double* mu = redw + (NT / 32) * 5;                                 // [8] correction coefficients
+    signed char* dsm = reinterpret_cast<signed char*>(mu + 8);        // [3][N] shifts
+
+    // shared-window addresses of W and Fh (mapped to a peer rank when stored)
+    const uint32_t W_u32 = smem_addr(W);
+    const uint32_t F_u32 = smem_addr(Fh);
+    // store v at element `idx` of buffer `base` (W_u32 or F_u32) in CTA `dst`
+    auto put = [&](uint32_t base, cpx<T>* local, int dst, long idx, cpx<T> v) {
+        if constexpr (C == 1) {
+            local[idx] = v;
+        } else {
+            st_cluster(map_rank(base + (uint32_t)(idx * (long)sizeof(cpx<T>)), dst), v);
+        }
+    };
+
+    const T* __restrict__ fin = static_cast<const T*>(args.f);
+    T* __restrict__ fout = static_cast<T*>(args.out);
+    const T* __restrict__ tab = static_cast<const T*>(args.tables);
+    const bool transport = args.delta != nullptr;
+    for (int i = tid; i < 3 * N; i += NT) dsm[i] = transport ? args.delta[i] : 0;
+    // every CTA of the cluster is running before any distributed-shared access
+    cluster_sync_all();
+
+    const double dv = 2.0 * args.L / N;
+    // velocity of grid index i: (i + 1/2 - N/2) dv
+    auto vel = [dv](int i) { return ((double)i + 0.5 - 0.5 * N) * dv; };
+    const int ncx = args.nc[0], ncy = args.nc[1], ncz = args.nc[2];
+
+    // z-pass ownership: column (xl, y), x = rank*NS + xl (threads >= NTASK idle)
+    const bool has_col = tid < NTASK;
+    const int zl_x = has_col ? tid / N : 0, zl_y = tid % N;
+    const int zx = rank * NS + zl_x;
+    T* Gcol = Gs + ((long)zl_x * N + zl_y) * N;
+    T* Fcol = Fs + ((long)zl_x * N + zl_y) * N;
+
+    // x/y task coordinates
+    const int t_tab = tid / (NS * H);
+    const int t_rem = tid % (NS * H);
+    const int t_a = t_rem / H;     // kyl (x-pass) or xl (y-pass)
+    const int t_pp = t_rem % H;
+
+    for (long cell = cluster_id; cell < args.ncells; cell += nclusters) {
+        const int cx = (int)(cell / ((long)ncy * ncz));
+        const int cy = (int)((cell / ncz) % ncy);
+        const int cz = (int)(cell % ncz);
+
+        // ---------------- forward transform -----------------------------
+        // F1: gather the f* column (x, y, :) of the transported cell into
+        // shared memory, z-R2C; staging S = W[0] as [xl][y][HP]
+        if (has_col) {
+            if (!transport) {
+                const T* src = fin + cell * N3 + ((long)zx * N + zl_y) * N;
+#pragma unroll 4
+                for (int z = 0; z < N; ++z) Fcol[z] = src[z];
+            } else {
+                int fx, fy;
+                const int sx = fold_cell(cx - dsm[zx], ncx, args.bc[0], fx);
+                const int sy = fold_cell(cy - dsm[N + zl_y], ncy, args.bc[1], fy);
+                const int qx = fx ? N - 1 - zx : zx;
+                const int qy = fy ? N - 1 - zl_y : zl_y;
+                const T* base_xy = fin + ((long)sx * ncy + sy) * ncz * N3 + ((long)qx * N + qy) * N;
+#pragma unroll 4
+                for (int z = 0; z < N; ++z) {
+                    int fz;
+                    const int sz = fold_cell(cz - dsm[2 * N + z], ncz, args.bc[2], fz);
+                    const int qz = fz ? N - 1 - z : z;
+                    Fcol[z] = base_xy[(long)sz * N3 + qz];
+                }
+            }
+            cpx<T> a[N];
+#pragma unroll
+            for (int z = 0; z < N; ++z) a[z] = {Fcol[z], T(0)};
+            fft<N, -1>(a);
+            cpx<T>* S = W + ((long)zl_x * N + zl_y) * HP;
+#pragma unroll
+            for (int k = 0; k < HF; ++k) S[k] = a[k];
+#pragma unroll
+            for (int z = 0; z < N; ++z) Gcol[z] = T(0);
+        }
+        __syncthreads();
+        // F2 + F3: y-FFT of (xl, kz') pencils, scatter to the ky owner as Fh[x][kyl][kz']
+        if (tid < NS * HF) {
+            const int xl = tid / HF, kz = tid % HF;
+            cpx<T> a[N];
+#pragma unroll
+            for (int y = 0; y < N; ++y) a[y] = W[((long)xl * N + y) * HP + kz];
+            fft<N, -1>(a);
+            const int x = rank * NS + xl;
+#pragma unroll
+            for (int ky = 0; ky < N; ++ky) put(F_u32, Fh, ky / NS, ((long)x * NS + ky % NS) * HF + kz, a[ky]);
+        }
+        cluster_sync_all();
+        // F4: x-FFT of (kyl, kz') pencils in place
+        if (tid < NS * HF) {
+            const int kyl = tid / HF, kz = tid % HF;
+            cpx<T> a[N];
+#pragma unroll
+            for (int x = 0; x < N; ++x) a[x] = Fh[((long)x * NS + kyl) * HF + kz];
+            fft<N, -1>(a);
+#pragma unroll
+            for (int kx = 0; kx < N; ++kx) Fh[((long)kx * NS + kyl) * HF + kz] = a[kx];
+        }
+        __syncthreads();
+
+        // ---------------- gain and loss ---------------------------------
+        cluster_arrive();   // matches the wait before the first x-pass scatter
+        for (int p = 0; p <= args.M; ++p) {
+            const bool loss = (p == args.M);
+            // ---- x-pass: table product, pack kz'=0 with kz'=N/2, inverse FFT along kx
+            const bool active = has_col && (!loss || t_tab == 0);
+            cpx<T> a[N];
+            if (active) {
+                const T* tb = tab + ((((long)p * C + rank) * 2 + t_tab) * N) * NS * HF + (long)t_a * HF;
+                const cpx<T>* fb = Fh + (long)t_a * HF;
+                if (t_pp == 0) {
+#pragma unroll
+                    for (int kx = 0; kx < N; ++kx) {
+                        const long o = (long)kx * NS * HF;
+                        const cpx<T> fv = fb[o], fn = fb[o + H];
+                        const T tv = __ldg(tb + o), tn = __ldg(tb + o + H);
+                        a[kx] = {tv * fv.x - tn * fn.y, tv * fv.y + tn * fn.x};   // tv fv + i tn fn
+                    }
+                } else {
+#pragma unroll
+                    for (int kx = 0; kx < N; ++kx) {
+                        const long o = (long)kx * NS * HF + t_pp;
+                        const cpx<T> fv = fb[o];
+                        const T tv = __ldg(tb + o);
+                        a[kx] = {tv * fv.x, tv * fv.y};
+                    }
+                }
+                fft<N, +1>(a);
+            }
+            cluster_wait();   // every CTA has finished reading its W (previous z-pass)
+            if (active) {
+                const int ky = rank * NS + t_a;
+#pragma unroll
+                for (int x = 0; x < N; ++x)
+                    put(W_u32, W, x / NS, (((long)t_tab * NS + x % NS) * N + ky) * HP + t_pp, a[x]);
+            }
+            cluster_sync_all();
+            // ---- y-pass in place
+            if (active) {
+                cpx<T>* base = W + ((long)t_tab * NS + t_a) * N * HP + t_pp;
+#pragma unroll
+                for (int y = 0; y < N; ++y) a[y] = base[(long)y * HP];
+                fft<N, +1>(a);
+#pragma unroll
+                for (int y = 0; y < N; ++y) base[(long)y * HP] = a[y];
+            }
+            __syncthreads();
+            // ---- z-pass: C2R along z, products
+            T av[N];
+            if (has_col) {
+                const cpx<T>* c0 = W + ((long)zl_x * N + zl_y) * HP;          // table 0
+                cpx<T> h[H];
+#pragma unroll
+                for (int k = 0; k < H; ++k) h[k] = c0[k];
+                c2r<N>(h, av);
+            }
+            if (!loss) {
+                if (has_col) {
+                    const cpx<T>* c1 = W + ((long)(NS + zl_x) * N + zl_y) * HP;   // table 1
+                    cpx<T> h[H];
+#pragma unroll
+                    for (int k = 0; k < H; ++k) h[k] = c1[k];
+                    T bv[N];
+                    c2r<N>(h, bv);
+#pragma unroll
+                    for (int z = 0; z < N; ++z) Gcol[z] += av[z] * bv[z];
+                }
+                cluster_arrive();   // this CTA has finished reading W
+            } else {
+                // loss: Q = (G - f* l) / Kn in FP64, projection moments
+                double s5[5] = {0, 0, 0, 0, 0};
+                const double vx = vel(zx), vy = vel(zl_y);
+                const double v2xy = vx * vx + vy * vy;
+                if (has_col) {
+#pragma unroll
+                    for (int z = 0; z < N; ++z) {
+                        const double q = ((double)Gcol[z] - (double)Fcol[z] * (double)av[z]) * args.inv_kn;
+                        const double vz = vel(z);
+                        s5[0] += q;
+                        s5[1] += q * vx;
+                        s5[2] += q * vy;
+                        s5[3] += q * vz;
+                        s5[4] += q * 0.5 * (v2xy + vz * vz);
+                    }
+                }
+                // block reduction of the five moments (fixed order: deterministic)
+#pragma unroll
+                for (int i = 0; i < 5; ++i) {
+                    double v = s5[i];
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                    s5[i] = v;
+                }
+                const int warp = tid >> 5, lane = tid & 31;
+                if (lane == 0) {
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) redw[warp * 5 + i] = s5[i];
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    for (int i = 0; i < 5; ++i) {
+                        double acc = 0.0;
+                        for (int w = 0; w < NT / 32; ++w) acc += redw[w * 5 + i];
+                        red[i] = acc;
+                    }
+                }
+                cluster_sync_all();
+                if (tid == 0) {
+                    double tot[5] = {0, 0, 0, 0, 0};
+                    for (int r = 0; r < C; ++r) {
+                        const double* rr = cluster.map_shared_rank(red, r);
+                        for (int i = 0; i < 5; ++i) tot[i] += rr[i];
+                    }
+                    for (int i = 0; i < 5; ++i) {
+                        double acc = 0.0;
+                        for (int j = 0; j < 5; ++j) acc += args.P[i * 5 + j] * tot[j];
+                        mu[i] = acc;
+                    }
+                }
+                cluster_sync_all();   // every CTA has read the partials; mu is visible
+                if (has_col) {
+                    const double m0 = mu[0], m1 = mu[1], m2 = mu[2], m3 = mu[3], m4 = mu[4];
+                    const double cxy = m0 + m1 * vx + m2 * vy + m4 * 0.5 * v2xy;
+                    T* dst = fout + cell * N3 + ((long)zx * N + zl_y) * N;
+                    bool bad = false, neg = false;
+                    constexpr int V = 16 / sizeof(T);
+                    static_assert((N * sizeof(T)) % 16 == 0, "rows are whole 16-byte vectors");
+#pragma unroll
+                    for (int z0 = 0; z0 < N; z0 += V) {
+                        T res[V];
+#pragma unroll
+                        for (int j = 0; j < V; ++j) {
+                            const int z = z0 + j;
+                            const double vz = vel(z);
+                            const double q = ((double)Gcol[z] - (double)Fcol[z] * (double)av[z]) * args.inv_kn -
+                                             (cxy + m3 * vz + m4 * 0.5 * vz * vz);
+                            const double o = args.mode == 1 ? (double)Fcol[z] + args.dt * q : q;
+                            bad |= !isfinite(o);
+                            neg |= (args.mode == 1) && (o < 0.0);
+                            res[j] = (T)o;
+                        }
+                        if constexpr (sizeof(T) == 4)
+                            *reinterpret_cast<float4*>(dst + z0) = make_float4(res[0], res[1], res[2], res[3]);
+                        else
+                            *reinterpret_cast<double2*>(dst + z0) = make_double2(res[0], res[1]);
+                    }
+                    if (bad) atomicOr(args.flags, 1);
+                    if (neg) atomicOr(args.flags, 2);
+                }
+            }
+        }
+        // the loss pass ended with a full cluster sync: W, Fh and red are free
+    }
+}
+
+}  // namespace fks

@@ -1,0 +1,27 @@
+// fks_internal.h -- declarations shared by the translation units of libfks.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "fks_collide.cuh"
+
+namespace fks {
+
+// One instantiation of collide_kernel<T, N, C>.
+struct CollideVariant {
+    const void* func;     // host stub of the kernel
+    int N, C, NT;
+    size_t smem;
+    bool fp64;
+};
+
+// Look up an instantiation; returns false if (fp64, N, C) was not compiled.
+bool find_collide_variant(bool fp64, int N, int C, CollideVariant* out);
+bool find_collide_variant_f32(int N, int C, CollideVariant* out);
+bool find_collide_variant_f64(int N, int C, CollideVariant* out);
+
+// Default cluster size for (precision, N).
+int default_cluster_size(bool fp64, int N);
+
+}  // namespace fks

@@ -1,0 +1,218 @@
+"""Thin ctypes binding of libfks.so (include/fks.h).
+
+Argument marshalling only: tensors are passed as device pointers with the
+caller's current CUDA stream; every step of the computation runs in the
+library's kernels.  There is no fallback: if the library or a GPU is
+missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+FKS_FP64 = 0
+FKS_FP32 = 1
+HARD_SPHERE = 0
+MAXWELL = 1
+PERIODIC = 0
+SPECULAR = 1
+
+_STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration", 3: "out of device memory",
+           4: "CUDA error", 5: "numerical health check failed", 6: "timeout"}
+
+
+class FKSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"fks status {status} ({_STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("x0", ctypes.c_double * 3), ("x1", ctypes.c_double * 3), ("bc", ctypes.c_int * 3)]
+
+
+class _VBox(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("L", ctypes.c_double)]
+
+
+class _Kernel(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("C", ctypes.c_double), ("knudsen", ctypes.c_double)]
+
+
+class _Dirs(ctypes.Structure):
+    _fields_ = [("A1", ctypes.c_int), ("A2", ctypes.c_int), ("rule", ctypes.c_int)]
+
+
+_lib = None
+
+# every symbol include/fks.h declares
+EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments", "fks_check",
+           "fks_get_offsets", "fks_set_offsets", "fks_ncells", "fks_nv", "fks_cluster_size",
+           "fks_set_cluster_size", "fks_launch_count", "fks_kernel_transform", "fks_destroy",
+           "fks_last_error", "fks_status_string"]
+
+
+def lib(build: bool = True):
+    """Load libfks.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: run paper_1701_01608_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    L.fks_init.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_VBox), ctypes.POINTER(_Kernel),
+                           ctypes.POINTER(_Dirs), I, ctypes.POINTER(P)]
+    for name in ("fks_collide",):
+        getattr(L, name).argtypes = [P, P, P, P]
+    L.fks_transport.argtypes = [P, P, P, D, P]
+    L.fks_step.argtypes = [P, P, P, D, P]
+    L.fks_moments.argtypes = [P, P, P, P]
+    L.fks_check.argtypes = [P, P, ctypes.POINTER(I)]
+    L.fks_get_offsets.argtypes = [P, P]
+    L.fks_set_offsets.argtypes = [P, P]
+    L.fks_ncells.argtypes = [P]
+    L.fks_ncells.restype = ctypes.c_long
+    L.fks_nv.argtypes = [P]
+    L.fks_cluster_size.argtypes = [P]
+    L.fks_set_cluster_size.argtypes = [P, I]
+    L.fks_launch_count.argtypes = [P]
+    L.fks_launch_count.restype = ctypes.c_long
+    L.fks_kernel_transform.argtypes = [I, D, D, D, ctypes.POINTER(D), ctypes.POINTER(D)]
+    L.fks_destroy.argtypes = [P]
+    L.fks_destroy.restype = None
+    L.fks_last_error.argtypes = [P]
+    L.fks_last_error.restype = ctypes.c_char_p
+    L.fks_status_string.argtypes = [I]
+    L.fks_status_string.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def kernel_transform(ktype: int, C: float, L: float, s: float) -> tuple[float, float]:
+    """phi_R(s), psi_R(s) as the library's table kernel evaluates them (host)."""
+    phi = ctypes.c_double()
+    psi = ctypes.c_double()
+    st = lib().fks_kernel_transform(ktype, C, L, s, ctypes.byref(phi), ctypes.byref(psi))
+    if st != 0:
+        raise FKSError(st, "fks_kernel_transform")
+    return phi.value, psi.value
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dptr(t, dtype) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor, got {t.dtype}")
+    return int(t.data_ptr())
+
+
+@dataclass
+class Config:
+    ncell: tuple = (1, 1, 1)
+    x0: tuple = (0.0, 0.0, 0.0)
+    x1: tuple = (1.0, 1.0, 1.0)
+    bc: tuple = (0, 0, 0)
+    n: int = 16
+    L: float = 8.0
+    kernel: int = HARD_SPHERE
+    C: float = 0.25
+    kn: float = 1.0
+    A1: int = 4
+    A2: int = 4
+    rule: int = 0
+    precision: int = FKS_FP32
+
+
+class Context:
+    """One fks_ctx: spectral tables, offsets and flags on the current device."""
+
+    def __init__(self, cfg: Config):
+        import torch
+        self.cfg = cfg
+        self._L = lib()
+        g = _Grid(cfg.ncell[0], cfg.ncell[1], cfg.ncell[2], (ctypes.c_double * 3)(*cfg.x0),
+                  (ctypes.c_double * 3)(*cfg.x1), (ctypes.c_int * 3)(*cfg.bc))
+        vb = _VBox(cfg.n, cfg.L)
+        k = _Kernel(cfg.kernel, cfg.C, cfg.kn)
+        d = _Dirs(cfg.A1, cfg.A2, cfg.rule)
+        h = ctypes.c_void_p()
+        st = self._L.fks_init(ctypes.byref(g), ctypes.byref(vb), ctypes.byref(k), ctypes.byref(d),
+                              cfg.precision, ctypes.byref(h))
+        if st != 0:
+            raise FKSError(st, "fks_init")
+        self._h = h
+        self.dtype = torch.float64 if cfg.precision == FKS_FP64 else torch.float32
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.fks_destroy(h)
+            self._h = None
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            raise FKSError(st, f"{what}: {self._L.fks_last_error(self._h).decode()}")
+
+    @property
+    def ncells(self) -> int:
+        return self._L.fks_ncells(self._h)
+
+    @property
+    def cluster_size(self) -> int:
+        return self._L.fks_cluster_size(self._h)
+
+    def set_cluster_size(self, C: int):
+        self._check(self._L.fks_set_cluster_size(self._h, C), "fks_set_cluster_size")
+
+    @property
+    def launches(self) -> int:
+        return self._L.fks_launch_count(self._h)
+
+    def collide(self, f, Q, stream=None):
+        self._check(self._L.fks_collide(self._h, _dptr(f, self.dtype), _dptr(Q, self.dtype),
+                                        _stream_ptr(stream)), "fks_collide")
+
+    def transport(self, f, f_out, dt: float, stream=None):
+        self._check(self._L.fks_transport(self._h, _dptr(f, self.dtype), _dptr(f_out, self.dtype), float(dt),
+                                          _stream_ptr(stream)), "fks_transport")
+
+    def step(self, f, f_out, dt: float, stream=None):
+        self._check(self._L.fks_step(self._h, _dptr(f, self.dtype), _dptr(f_out, self.dtype), float(dt),
+                                     _stream_ptr(stream)), "fks_step")
+
+    def moments(self, f, U, stream=None):
+        import torch
+        self._check(self._L.fks_moments(self._h, _dptr(f, self.dtype), _dptr(U, torch.float64),
+                                        _stream_ptr(stream)), "fks_moments")
+
+    def check(self, stream=None) -> int:
+        bits = ctypes.c_int()
+        st = self._L.fks_check(self._h, _stream_ptr(stream), ctypes.byref(bits))
+        self._check(st, "fks_check")
+        return bits.value
+
+    def offsets(self) -> np.ndarray:
+        s = np.empty((3, self.cfg.n))
+        self._check(self._L.fks_get_offsets(self._h, s.ctypes.data_as(ctypes.c_void_p)), "fks_get_offsets")
+        return s
+
+    def set_offsets(self, s):
+        s = np.ascontiguousarray(s, dtype=np.float64).reshape(3, self.cfg.n)
+        self._check(self._L.fks_set_offsets(self._h, s.ctypes.data_as(ctypes.c_void_p)), "fks_set_offsets")

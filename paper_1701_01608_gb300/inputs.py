@@ -142,3 +142,14 @@ def config_uneven_batch(nprob: int = 96, seed: int = 3):
         f = 0.5 * (maxwellian(n, L, u=u1, T=T1) + maxwellian(n, L, u=u2, T=T2))
         probs.append(dict(n=n, L=L, kn=kn, kernel=kernel, f0=f[None]))
     return probs
+
+
+def shock_tube_states(n: int = 32, L: float = 10.0, nx: int = 32):
+    """The two Maxwellian profiles of the shock tube (left rho=1 T=1, right
+    rho=0.125 T=0.8) and, per x index, which one the cells hold (0 left,
+    1 right).  Lets a caller assemble the 32^3 x 32^3 state on the device
+    without a host copy of the whole array."""
+    left = maxwellian(n, L, 1.0, T=1.0)
+    right = maxwellian(n, L, 0.125, T=0.8)
+    xc = (np.arange(nx) + 0.5) / nx
+    return np.stack([left, right]), (xc >= 0.5).astype(np.int64)
