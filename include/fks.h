@@ -140,6 +140,37 @@ long fks_launch_count(const fks_ctx *ctx);
  * kernel runs on the device.  Needs no GPU. */
 fks_status fks_kernel_transform(int ktype, double C, double L, double s, double *phi, double *psi);
 
+/* fks_transport_noalloc -- the transport of fks_transport for callers that
+ * cannot allocate device memory.  It is an addition of this library; the
+ * paper has no counterpart.
+ *
+ * Some callers must not call cudaMalloc: applications whose device memory
+ * is owned entirely by their own pool allocator, plugins that may not grow
+ * the device footprint of the host program, and loops where the implicit
+ * device synchronisation of cudaMalloc would stall an asynchronous pipeline.
+ * fks_init allocates (tables, offsets, flags), so such callers cannot use a
+ * context; this entry point needs none and allocates nothing.
+ *
+ * It advances the particle offsets s (a DEVICE array of 3*n doubles owned by
+ * the caller, read and updated in place; start from zeros) by dt and writes
+ * f_out[j][k] = f[j - delta_k][k'] exactly as fks_transport does (same
+ * kernels, bit-identical results).  f, f_out: device arrays of
+ * nx*ny*nz*n^3 elements (double for FKS_FP64, float for FKS_FP32), distinct.
+ *
+ * Scratch: the per-call table of cell shifts and a flag word live in one
+ * file-scope __device__ array of 256 bytes, which every GPU that loads this
+ * library holds until the process exits.  Limit: n <= 32 (larger n returns
+ * FKS_ERR_UNSUPPORTED before any work); n must be even.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.
+ * Every call shares the array and overwrites it (the flag word is cleared at
+ * the start of each call), so calls that overlap on the GPU -- on different
+ * streams, or from different host threads -- race: serialise them.
+ * Returns FKS_ERR_INVALID_ARG for bad arguments, FKS_ERR_CUDA if a CUDA call
+ * fails.  It calls no cudaMalloc, cudaFree or allocating routine. */
+fks_status fks_transport_noalloc(const fks_grid *grid, const fks_vbox *vbox, int precision, double *s,
+                                 double dt, const void *f, void *f_out, void *stream);
+
 void fks_destroy(fks_ctx *ctx);
 const char *fks_last_error(const fks_ctx *ctx);
 const char *fks_status_string(fks_status s);

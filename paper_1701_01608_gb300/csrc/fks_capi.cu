@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -701,3 +702,79 @@ fks_status fks_kernel_transform(int ktype, double C, double L, double s, double*
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ no-allocation transport
+//
+// fks_transport_noalloc: the transport of fks_transport for callers that
+// cannot allocate device memory.  Its only scratch (the per-call table of
+// cell shifts and a flag word) lives in the file-scope array below, which
+// every GPU that loads this library holds until the process exits.
+namespace {
+
+constexpr int kNoAllocMaxN = 32;            // largest velocity grid n it accepts
+constexpr int kNoAllocFlagOffset = 128;     // byte offset of the flag word
+static __device__ __align__(256) unsigned char g_noalloc_scratch[256];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the host-side name is only a stand-in, not a device address).
+fks_status noalloc_scratch(void** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return FKS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return FKS_ERR_CUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return FKS_OK;
+}
+
+}  // namespace
+
+extern "C" fks_status fks_transport_noalloc(const fks_grid* grid, const fks_vbox* vbox, int precision, double* s,
+                                            double dt, const void* f, void* f_out, void* stream) {
+    if (!grid || !vbox || !s || !f || !f_out || f == f_out) return FKS_ERR_INVALID_ARG;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return FKS_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) {
+        if (!(grid->x1[a] > grid->x0[a])) return FKS_ERR_INVALID_ARG;
+        if (grid->bc[a] != FKS_BC_PERIODIC && grid->bc[a] != FKS_BC_SPECULAR) return FKS_ERR_INVALID_ARG;
+    }
+    if (!(vbox->L > 0.0) || !std::isfinite(vbox->L) || !std::isfinite(dt)) return FKS_ERR_INVALID_ARG;
+    if (vbox->n < 2 || vbox->n % 2 != 0) return FKS_ERR_INVALID_ARG;
+    if (vbox->n > kNoAllocMaxN) return FKS_ERR_UNSUPPORTED;   // beyond the static scratch
+    if (precision != FKS_FP64 && precision != FKS_FP32) return FKS_ERR_UNSUPPORTED;
+    const int n = vbox->n;
+    const int nca[3] = {grid->nx, grid->ny, grid->nz};
+    double dx[3];
+    for (int a = 0; a < 3; ++a) {
+        dx[a] = (grid->x1[a] - grid->x0[a]) / nca[a];
+        if (std::fabs(vbox->L * dt) > 100.0 * dx[a]) return FKS_ERR_INVALID_ARG;
+    }
+    void* base = nullptr;
+    fks_status st = noalloc_scratch(&base);
+    if (st != FKS_OK) return st;
+    signed char* d_delta = static_cast<signed char*>(base);
+    int* d_flags = reinterpret_cast<int*>(static_cast<unsigned char*>(base) + kNoAllocFlagOffset);
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (cudaMemsetAsync(d_flags, 0, sizeof(int), cs) != cudaSuccess) return FKS_ERR_CUDA;
+    offsets_kernel<<<dim3(1, 3), n / 2, 0, cs>>>(n, vbox->L, make_double3(dx[0], dx[1], dx[2]), dt, s, d_delta, d_flags);
+    const long total = (long)grid->nx * grid->ny * grid->nz * n * n * n;
+    const int bs = 256;
+    long blocks = (total + bs - 1) / bs;
+    if (blocks > 152L * 64) blocks = 152L * 64;
+    if (blocks < 1) blocks = 1;
+    if (precision == FKS_FP64)
+        transport_kernel<double><<<(unsigned)blocks, bs, 0, cs>>>(n, grid->nx, grid->ny, grid->nz, grid->bc[0],
+                                                                grid->bc[1], grid->bc[2], d_delta, (const double*)f,
+                                                                (double*)f_out, total);
+    else
+        transport_kernel<float><<<(unsigned)blocks, bs, 0, cs>>>(n, grid->nx, grid->ny, grid->nz, grid->bc[0],
+                                                               grid->bc[1], grid->bc[2], d_delta, (const float*)f,
+                                                               (float*)f_out, total);
+    return cudaGetLastError() == cudaSuccess ? FKS_OK : FKS_ERR_CUDA;
+}

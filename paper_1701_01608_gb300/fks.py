@@ -55,7 +55,7 @@ _lib = None
 EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments", "fks_check",
            "fks_get_offsets", "fks_set_offsets", "fks_ncells", "fks_nv", "fks_cluster_size",
            "fks_set_cluster_size", "fks_launch_count", "fks_kernel_transform", "fks_destroy",
-           "fks_last_error", "fks_status_string"]
+           "fks_last_error", "fks_status_string", "fks_transport_noalloc"]
 
 
 def lib(build: bool = True):
@@ -88,6 +88,7 @@ def lib(build: bool = True):
     L.fks_launch_count.argtypes = [P]
     L.fks_launch_count.restype = ctypes.c_long
     L.fks_kernel_transform.argtypes = [I, D, D, D, ctypes.POINTER(D), ctypes.POINTER(D)]
+    L.fks_transport_noalloc.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_VBox), I, P, D, P, P, P]
     L.fks_destroy.argtypes = [P]
     L.fks_destroy.restype = None
     L.fks_last_error.argtypes = [P]
