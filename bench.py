@@ -22,6 +22,7 @@ sys.path.insert(0, ROOT)
 METRIC = "phase-space pts/s per step (N_v=32^3), learned+BF16 vs FP64 spectral @1e-3"
 NX, NV, LBOX, KN, A1, A2 = 32, 32, 10.0, 0.01, 4, 8
 M = A1 * A2
+GRID = (NX, NX, NX)
 NCELLS = NX ** 3
 PTS = NCELLS * NV ** 3
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
@@ -148,7 +149,7 @@ def run_reference(args):
     O.build()
     tab = O.tables(NV, LBOX, 0, 0.25, A1, A2, 0)
     states, which = I.shock_tube_states(NV, LBOX, NX)
-    sample = int(os.environ.get("FKS_REF_SAMPLE", "8"))
+    sample = int(os.environ.get("FKS_REF_SAMPLE", "256"))
     rng = np.random.Generator(np.random.PCG64(777))
     times = []
     for it in range(args.warmup + args.steps):
@@ -176,9 +177,9 @@ def run_reference(args):
 
 def build_state(torch, dtype, dev):
     from paper_1701_01608_gb300 import inputs as I
-    states, which = I.shock_tube_states(NV, LBOX, NX)
+    states, which = I.shock_tube_states(NV, LBOX, GRID[0])
     st = torch.from_numpy(states).to(device=dev, dtype=dtype)
-    idx = torch.from_numpy(np.repeat(which, NX * NX)).to(dev)
+    idx = torch.from_numpy(np.repeat(which, GRID[1] * GRID[2])).to(dev)
     return st.index_select(0, idx).contiguous()
 
 
@@ -216,14 +217,21 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=int(os.environ.get("FKS_CPU_SAMPLE", "16")))
+    ap.add_argument("--cpu-sample", type=int, default=int(os.environ.get("FKS_CPU_SAMPLE", "1024")))
+    ap.add_argument("--grid", default=None, help="nx,ny,nz spatial cells (default 32,32,32); smaller grids "
+                    "are for profiling runs, not bench lines")
     args = ap.parse_args()
+    global GRID, NCELLS, PTS
+    if args.grid:
+        GRID = tuple(int(v) for v in args.grid.split(","))
+        NCELLS = GRID[0] * GRID[1] * GRID[2]
+        PTS = NCELLS * NV ** 3
     if args.impl == "reference":
         return run_reference(args)
 
     ws, rank, local = dist_setup()
     cpu = None
-    if rank == 0 and ws == 1:
+    if rank == 0 and ws == 1 and args.cpu_sample > 0:
         # the oracle runs before any CUDA call (OpenMP, no fork after CUDA init)
         cpu = cpu_baseline(args.cpu_sample)
     import torch
@@ -235,7 +243,7 @@ def main():
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
     dt = dt_rule()
-    cfg = fks.Config(ncell=(NX, NX, NX), bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
+    cfg = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
                      A1=A1, A2=A2, precision=fks.FKS_FP32)
     ctx = fks.Context(cfg)
     f0 = build_state(torch, torch.float32, dev)
@@ -283,7 +291,7 @@ def main():
 
     fp64 = None
     if not args.no_fp64 and ws == 1:
-        cfg64 = fks.Config(ncell=(NX, NX, NX), bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
+        cfg64 = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
                            A1=A1, A2=A2, precision=fks.FKS_FP64)
         ctx64 = fks.Context(cfg64)
         f64 = build_state(torch, torch.float64, dev)
@@ -298,7 +306,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "hs_shocktube_32x32x32c_32v", "cells": NCELLS, "n_v": NV ** 3, "M": M,
+        "config": {"workload": "hs_shocktube_%dx%dx%dc_32v" % GRID, "cells": NCELLS, "n_v": NV ** 3, "M": M,
                    "kernel": "hard spheres", "knudsen": KN, "bc": "specular x, periodic y z",
                    "dt": dt, "path": "fks_step: offsets + fused transport/collision/projection/Euler kernel",
                    "cluster_size": ctx.cluster_size, "l2": "inputs 4.3 GB > L2 (no flush needed)",

@@ -131,16 +131,22 @@ collide_kernel(CollideArgs args) {
     double* mu = redw + (NT / 32) * 5;                                 // [8] correction coefficients
     signed char* dsm = reinterpret_cast<signed char*>(mu + 8);        // [3][N] shifts
 
-    // shared-window addresses of W and Fh (mapped to a peer rank when stored)
-    const uint32_t W_u32 = smem_addr(W);
-    const uint32_t F_u32 = smem_addr(Fh);
-    // store v at element `idx` of buffer `base` (W_u32 or F_u32) in CTA `dst`
-    auto put = [&](uint32_t base, cpx<T>* local, int dst, long idx, cpx<T> v) {
-        if constexpr (C == 1) {
-            local[idx] = v;
-        } else {
-            st_cluster(map_rank(base + (uint32_t)(idx * (long)sizeof(cpx<T>)), dst), v);
-        }
+    // shared::cluster addresses of W and Fh in every CTA of the cluster: the
+    // window of a CTA is contiguous, so element addresses are base + offset
+    uint32_t Wrank[C], Frank[C];
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+        Wrank[r] = map_rank(smem_addr(W), r);
+        Frank[r] = map_rank(smem_addr(Fh), r);
+    }
+    // store v at element `idx` of W (or Fh) in CTA `dst`
+    auto putW = [&](int dst, long idx, cpx<T> v) {
+        if constexpr (C == 1) W[idx] = v;
+        else st_cluster(Wrank[dst] + (uint32_t)(idx * (long)sizeof(cpx<T>)), v);
+    };
+    auto putF = [&](int dst, long idx, cpx<T> v) {
+        if constexpr (C == 1) Fh[idx] = v;
+        else st_cluster(Frank[dst] + (uint32_t)(idx * (long)sizeof(cpx<T>)), v);
     };
 
     const T* __restrict__ fin = static_cast<const T*>(args.f);
@@ -217,7 +223,7 @@ collide_kernel(CollideArgs args) {
             fft<N, -1>(a);
             const int x = rank * NS + xl;
 #pragma unroll
-            for (int ky = 0; ky < N; ++ky) put(F_u32, Fh, ky / NS, ((long)x * NS + ky % NS) * HF + kz, a[ky]);
+            for (int ky = 0; ky < N; ++ky) putF(ky / NS, ((long)x * NS + ky % NS) * HF + kz, a[ky]);
         }
         cluster_sync_all();
         // F4: x-FFT of (kyl, kz') pencils in place
@@ -266,7 +272,7 @@ collide_kernel(CollideArgs args) {
                 const int ky = rank * NS + t_a;
 #pragma unroll
                 for (int x = 0; x < N; ++x)
-                    put(W_u32, W, x / NS, (((long)t_tab * NS + x % NS) * N + ky) * HP + t_pp, a[x]);
+                    putW(x / NS, (((long)t_tab * NS + x % NS) * N + ky) * HP + t_pp, a[x]);
             }
             cluster_sync_all();
             // ---- y-pass in place

@@ -13,16 +13,22 @@
 #pragma once
 #include <utility>
 
+#if defined(__CUDACC__)
+#define FKS_HD __host__ __device__ __forceinline__
+#else
+#define FKS_HD inline
+#endif
+
 namespace fks {
 
 template <typename T> struct cpx { T x, y; };
 
-template <typename T> __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
-template <typename T> __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
-template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+template <typename T> FKS_HD cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T> FKS_HD cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T> FKS_HD cpx<T> cmul(cpx<T> a, cpx<T> b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
-template <typename T> __device__ __forceinline__ cpx<T> cscale(cpx<T> a, T s) { return {a.x * s, a.y * s}; }
+template <typename T> FKS_HD cpx<T> cscale(cpx<T> a, T s) { return {a.x * s, a.y * s}; }
 
 // ---------------------------------------------------------------- constexpr trig
 namespace detail {
@@ -66,119 +72,150 @@ constexpr SC sincos_frac(long k, long n) {
 
 // W = exp(SIGN * 2 pi i K / LEN) as a compile-time constant
 template <typename T, int SIGN, long K, long LEN>
-__device__ __forceinline__ cpx<T> twiddle() {
+FKS_HD cpx<T> twiddle() {
     constexpr detail::SC sc = detail::sincos_frac(K, LEN);
     return {T(sc.c), T(SIGN * sc.s)};
 }
 
 template <typename T, int SIGN, long K, long LEN>
-__device__ __forceinline__ cpx<T> mul_tw(cpx<T> a) {
+FKS_HD cpx<T> mul_tw(cpx<T> a) {
     if constexpr (K % LEN == 0) return a;
     else if constexpr ((4 * K) % LEN == 0) {
         constexpr long q = ((4 * K) / LEN) % 4;   // multiple of a quarter turn
         if constexpr (q == 2) return {-a.x, -a.y};
         else if constexpr ((q == 1) == (SIGN > 0)) return {-a.y, a.x};   // * i
         else return {a.y, -a.x};                                           // * -i
+    } else if constexpr ((8 * K) % LEN == 0) {
+        // odd multiple of an eighth turn: (+-1 +- i)/sqrt 2
+        constexpr detail::SC sc = detail::sincos_frac(K, LEN);
+        const T h = T(0.707106781186547524400844362104849039);
+        const T cr = sc.c > 0 ? h : -h;
+        const T ci = (SIGN * sc.s) > 0 ? h : -h;
+        return {cr * a.x - ci * a.y, cr * a.y + ci * a.x};
     } else {
         return cmul(a, twiddle<T, SIGN, K, LEN>());
     }
 }
 
 // ---------------------------------------------------------------- FFT kernels
+//
+// Mixed-radix decimation in time: N = R * P with R in {3, 4} at the top and
+// the sub-transforms of size P recursive; sizes 2, 3, 4 and 8 are direct
+// butterflies.  32 = 4 x 8, 16 = 4 x 4, 24 = 3 x 8, 12 = 3 x 4.
 namespace detail {
 
 template <int N> constexpr bool is_pow2() { return N > 0 && (N & (N - 1)) == 0; }
 
-constexpr int bitrev(int i, int n) {
-    int r = 0;
-    for (int b = 1; b < n; b <<= 1) { r = (r << 1) | (i & 1); i >>= 1; }
-    return r;
+template <typename T, int SIGN>
+FKS_HD void dft2(cpx<T>& a0, cpx<T>& a1) {
+    const cpx<T> s = cadd(a0, a1), d = csub(a0, a1);
+    a0 = s;
+    a1 = d;
 }
 
-// one radix-2 DIT butterfly column k (compile-time) for stage LEN
-template <typename T, int SIGN, int N, int LEN, int K>
-__device__ __forceinline__ void r2_column(cpx<T> (&a)[N]) {
-#pragma unroll
-    for (int i = 0; i < N; i += LEN) {
-        cpx<T> u = a[i + K];
-        cpx<T> t = mul_tw<T, SIGN, K, LEN>(a[i + K + LEN / 2]);
-        a[i + K] = cadd(u, t);
-        a[i + K + LEN / 2] = csub(u, t);
-    }
+// a * (SIGN i)
+template <typename T, int SIGN>
+FKS_HD cpx<T> mul_si(cpx<T> a) {
+    if constexpr (SIGN > 0) return {-a.y, a.x};
+    else return {a.y, -a.x};
 }
 
-template <typename T, int SIGN, int N, int LEN, int... K>
-__device__ __forceinline__ void r2_stage(cpx<T> (&a)[N], std::integer_sequence<int, K...>) {
-    (r2_column<T, SIGN, N, LEN, K>(a), ...);
+template <typename T, int SIGN>
+FKS_HD void dft4(cpx<T>& a0, cpx<T>& a1, cpx<T>& a2, cpx<T>& a3) {
+    const cpx<T> s02 = cadd(a0, a2), d02 = csub(a0, a2);
+    const cpx<T> s13 = cadd(a1, a3), d13 = mul_si<T, SIGN>(csub(a1, a3));
+    a0 = cadd(s02, s13);
+    a2 = csub(s02, s13);
+    a1 = cadd(d02, d13);
+    a3 = csub(d02, d13);
 }
 
-template <typename T, int SIGN, int N, int LEN>
-__device__ __forceinline__ void r2_stages(cpx<T> (&a)[N]) {
-    r2_stage<T, SIGN, N, LEN>(a, std::make_integer_sequence<int, LEN / 2>{});
-    if constexpr (LEN < N) r2_stages<T, SIGN, N, LEN * 2>(a);
-}
-
-template <typename T, int SIGN, int N>
-__device__ __forceinline__ void fft_pow2(cpx<T> (&a)[N]) {
-    if constexpr (N == 1) return;
-    else {
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            const int j = bitrev(i, N);
-            if (i < j) { cpx<T> t = a[i]; a[i] = a[j]; a[j] = t; }
-        }
-        r2_stages<T, SIGN, N, 2>(a);
-    }
-}
-
-// radix-3 combine for output column k of an N = 3P transform
-template <typename T, int SIGN, int N, int P, int K>
-__device__ __forceinline__ void r3_column(cpx<T> (&a)[N], const cpx<T> (&b0)[P], const cpx<T> (&b1)[P],
-                                          const cpx<T> (&b2)[P]) {
-    cpx<T> t0 = b0[K];
-    cpx<T> t1 = mul_tw<T, SIGN, K, N>(b1[K]);
-    cpx<T> t2 = mul_tw<T, SIGN, 2 * K, N>(b2[K]);
-    // X[k + qP] = t0 + w3^q t1 + w3^{2q} t2, w3 = exp(SIGN 2 pi i / 3)
+template <typename T, int SIGN>
+FKS_HD void dft3(cpx<T>& a0, cpx<T>& a1, cpx<T>& a2) {
     const T c = T(-0.5);
     const T s = T(SIGN) * T(0.866025403784438646763723170752936183);   // sin(2 pi / 3)
-    cpx<T> sum = cadd(t1, t2);
-    cpx<T> dif = csub(t1, t2);
-    cpx<T> m = {t0.x + c * sum.x, t0.y + c * sum.y};
-    cpx<T> r = {-s * dif.y, s * dif.x};   // i * s * (t1 - t2)
-    a[K] = cadd(t0, sum);
-    a[K + P] = cadd(m, r);
-    a[K + 2 * P] = csub(m, r);
+    const cpx<T> sum = cadd(a1, a2), dif = csub(a1, a2);
+    const cpx<T> m = {a0.x + c * sum.x, a0.y + c * sum.y};
+    const cpx<T> r = {-s * dif.y, s * dif.x};
+    a0 = cadd(a0, sum);
+    a1 = cadd(m, r);
+    a2 = csub(m, r);
 }
 
-template <typename T, int SIGN, int N, int P, int... K>
-__device__ __forceinline__ void r3_all(cpx<T> (&a)[N], const cpx<T> (&b0)[P], const cpx<T> (&b1)[P],
-                                       const cpx<T> (&b2)[P], std::integer_sequence<int, K...>) {
-    (r3_column<T, SIGN, N, P, K>(a, b0, b1, b2), ...);
+template <typename T, int SIGN>
+FKS_HD void dft8(cpx<T> (&a)[8]) {
+    cpx<T> e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    cpx<T> o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+    dft4<T, SIGN>(e0, e1, e2, e3);
+    dft4<T, SIGN>(o0, o1, o2, o3);
+    o1 = mul_tw<T, SIGN, 1, 8>(o1);
+    o2 = mul_tw<T, SIGN, 2, 8>(o2);
+    o3 = mul_tw<T, SIGN, 3, 8>(o3);
+    a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
+    a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
+    a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
+    a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
+}
+
+template <int N> constexpr int top_radix() {
+    if constexpr (N % 3 == 0) return 3;
+    else return 4;
+}
+
+template <typename T, int SIGN, int N, int R, int P, int K>
+FKS_HD void combine_column(cpx<T> (&a)[N], const cpx<T> (&sub)[R][P]) {
+    cpx<T> t[R];
+    t[0] = sub[0][K];
+    t[1] = mul_tw<T, SIGN, K, N>(sub[1][K]);
+    t[2] = mul_tw<T, SIGN, 2 * K, N>(sub[2][K]);
+    if constexpr (R == 3) {
+        dft3<T, SIGN>(t[0], t[1], t[2]);
+    } else {
+        t[3] = mul_tw<T, SIGN, 3 * K, N>(sub[3][K]);
+        dft4<T, SIGN>(t[0], t[1], t[2], t[3]);
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) a[K + P * q] = t[q];
+}
+
+template <typename T, int SIGN, int N, int R, int P, int... K>
+FKS_HD void combine_all(cpx<T> (&a)[N], const cpx<T> (&sub)[R][P], std::integer_sequence<int, K...>) {
+    (combine_column<T, SIGN, N, R, P, K>(a, sub), ...);
 }
 
 }  // namespace detail
 
 template <int N, int SIGN, typename T>
-__device__ __forceinline__ void fft(cpx<T> (&a)[N]) {
-    if constexpr (detail::is_pow2<N>()) {
-        detail::fft_pow2<T, SIGN, N>(a);
+FKS_HD void fft(cpx<T> (&a)[N]) {
+    if constexpr (N == 1) {
+        return;
+    } else if constexpr (N == 2) {
+        detail::dft2<T, SIGN>(a[0], a[1]);
+    } else if constexpr (N == 3) {
+        detail::dft3<T, SIGN>(a[0], a[1], a[2]);
+    } else if constexpr (N == 4) {
+        detail::dft4<T, SIGN>(a[0], a[1], a[2], a[3]);
+    } else if constexpr (N == 8) {
+        detail::dft8<T, SIGN>(a);
     } else {
-        static_assert(N % 3 == 0 && detail::is_pow2<N / 3>(), "FFT size must be 2^a or 3*2^a");
-        constexpr int P = N / 3;
-        cpx<T> b0[P], b1[P], b2[P];
+        constexpr int R = detail::top_radix<N>();
+        constexpr int P = N / R;
+        static_assert(P * R == N, "FFT size must be 2^a or 3*2^a");
+        cpx<T> sub[R][P];
 #pragma unroll
-        for (int m = 0; m < P; ++m) { b0[m] = a[3 * m]; b1[m] = a[3 * m + 1]; b2[m] = a[3 * m + 2]; }
-        fft<P, SIGN>(b0);
-        fft<P, SIGN>(b1);
-        fft<P, SIGN>(b2);
-        detail::r3_all<T, SIGN, N, P>(a, b0, b1, b2, std::make_integer_sequence<int, P>{});
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int m = 0; m < P; ++m) sub[r][m] = a[R * m + r];
+#pragma unroll
+        for (int r = 0; r < R; ++r) fft<P, SIGN>(sub[r]);
+        detail::combine_all<T, SIGN, N, R, P>(a, sub, std::make_integer_sequence<int, P>{});
     }
 }
 
 // ---------------------------------------------------------------- C2R
 namespace detail {
 template <typename T, int N, int K>
-__device__ __forceinline__ void c2r_pre(const cpx<T> (&h)[N / 2], cpx<T> (&z)[N / 2]) {
+FKS_HD void c2r_pre(const cpx<T> (&h)[N / 2], cpx<T> (&z)[N / 2]) {
     // E_k = X_k + conj(X_{N/2-k}),  O_k = (X_k - conj(X_{N/2-k})) e^{+2 pi i k / N},  Z_k = E_k + i O_k
     if constexpr (K == 0) {
         T x0 = h[0].x, xn = h[0].y;
@@ -192,7 +229,7 @@ __device__ __forceinline__ void c2r_pre(const cpx<T> (&h)[N / 2], cpx<T> (&z)[N 
     }
 }
 template <typename T, int N, int... K>
-__device__ __forceinline__ void c2r_pre_all(const cpx<T> (&h)[N / 2], cpx<T> (&z)[N / 2],
+FKS_HD void c2r_pre_all(const cpx<T> (&h)[N / 2], cpx<T> (&z)[N / 2],
                                             std::integer_sequence<int, K...>) {
     (c2r_pre<T, N, K>(h, z), ...);
 }
@@ -200,7 +237,7 @@ __device__ __forceinline__ void c2r_pre_all(const cpx<T> (&h)[N / 2], cpx<T> (&z
 
 // h: N/2 packed Hermitian coefficients (see header); x: N real outputs.
 template <int N, typename T>
-__device__ __forceinline__ void c2r(const cpx<T> (&h)[N / 2], T (&x)[N]) {
+FKS_HD void c2r(const cpx<T> (&h)[N / 2], T (&x)[N]) {
     cpx<T> z[N / 2];
     detail::c2r_pre_all<T, N>(h, z, std::make_integer_sequence<int, N / 2>{});
     fft<N / 2, +1>(z);
