@@ -75,6 +75,41 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, cpx<double> v) {
     asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};\n" ::"r"(addr), "d"(v.x), "d"(v.y) : "memory");
 }
 
+// mbarrier and bulk-copy (TMA) helpers for the per-direction table slab
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: a bulk copy of valid memory always completes; if it has not
+// after ~2^26 polls the kernel records FKS timeout (bit 3) and goes on.
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, unsigned parity, int* flags) {
+    for (long it = 0; it < (1L << 26); ++it)
+        if (mbar_try_wait(bar, parity)) return;
+    atomicOr(flags, 8);
+}
+
 // fold a source cell coordinate: periodic wrap or specular reflection
 __device__ __forceinline__ int fold_cell(int u, int len, int specular, int& flip) {
     if (!specular) {
@@ -103,8 +138,11 @@ struct CollideCfg {
     static constexpr long FH_ELEMS = (long)N * NS * HF;
     static constexpr long W_ELEMS = 2L * NS * N * HP;
     static constexpr long COL_ELEMS = (long)NS * N * N;
-    static constexpr size_t SMEM_BYTES = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS) + sizeof(T) * 2 * COL_ELEMS +
-                                         sizeof(double) * (8 + (NT / 32) * 5 + 8) + 3 * N + 16;
+    static constexpr long TAB_ELEMS = 2L * N * NS * HF;               // one direction's slab (T)
+    static constexpr unsigned TAB_BYTES = (unsigned)(sizeof(T) * TAB_ELEMS);
+    static constexpr size_t SMEM_BYTES = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS) + sizeof(T) * (2 * COL_ELEMS + TAB_ELEMS) +
+                                         sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N + N) + 8 + 3 * N + 16;
+    static_assert(TAB_BYTES % 16 == 0, "bulk copies move whole 16-byte units");
     static_assert(N % C == 0, "cluster size must divide N");
 };
 
@@ -124,12 +162,17 @@ collide_kernel(CollideArgs args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* Fh = reinterpret_cast<cpx<T>*>(smem_raw);                 // [N kx][NS kyl][HF]
     cpx<T>* W = Fh + Cfg::FH_ELEMS;                                    // [2][NS xl][N ky][HP]
-    T* Gs = reinterpret_cast<T*>(W + Cfg::W_ELEMS);                   // [NS xl][N y][N z] gain
-    T* Fs = Gs + Cfg::COL_ELEMS;                                       // [NS xl][N y][N z] f*
+    T* Tb = reinterpret_cast<T*>(W + Cfg::W_ELEMS);                   // [2][N kx][NS kyl][HF] table slab
+    T* Gs = Tb + Cfg::TAB_ELEMS;                                       // [N z][NTASK] gain
+    T* Fs = Gs + Cfg::COL_ELEMS;                                       // [N z][NTASK] f*
     double* red = reinterpret_cast<double*>(Fs + Cfg::COL_ELEMS);     // [8] own partials
     double* redw = red + 8;                                            // [NT/32][5]
     double* mu = redw + (NT / 32) * 5;                                 // [8] correction coefficients
-    signed char* dsm = reinterpret_cast<signed char*>(mu + 8);        // [3][N] shifts
+    double* vzt = mu + 8;                                              // [N] v_z
+    double* vz2t = vzt + N;                                            // [N] v_z^2 / 2
+    double* czt = vz2t + N;                                            // [N] projection correction along z
+    uint64_t* tbar = reinterpret_cast<uint64_t*>(czt + N);            // table-slab mbarrier
+    signed char* dsm = reinterpret_cast<signed char*>(tbar + 1);      // [3][N] shifts
 
     // shared::cluster addresses of W and Fh in every CTA of the cluster: the
     // window of a CTA is contiguous, so element addresses are base + offset
@@ -154,20 +197,36 @@ collide_kernel(CollideArgs args) {
     const T* __restrict__ tab = static_cast<const T*>(args.tables);
     const bool transport = args.delta != nullptr;
     for (int i = tid; i < 3 * N; i += NT) dsm[i] = transport ? args.delta[i] : 0;
-    // every CTA of the cluster is running before any distributed-shared access
-    cluster_sync_all();
-
     const double dv = 2.0 * args.L / N;
     // velocity of grid index i: (i + 1/2 - N/2) dv
     auto vel = [dv](int i) { return ((double)i + 0.5 - 0.5 * N) * dv; };
+    for (int i = tid; i < N; i += NT) {
+        vzt[i] = vel(i);
+        vz2t[i] = 0.5 * vel(i) * vel(i);
+    }
+    if (tid == 0) {
+        mbar_init(tbar, 1);
+        fence_mbar_init();
+    }
+    // every CTA of the cluster is running before any distributed-shared access
+    cluster_sync_all();
+    unsigned tphase = 0;
+    // table slab of direction p (p = M: loss) for this CTA, fetched by one thread
+    auto fetch_tables = [&](int p) {
+        if (tid == 0) {
+            mbar_expect_tx(tbar, Cfg::TAB_BYTES);
+            bulk_g2s(Tb, tab + ((long)p * C + rank) * Cfg::TAB_ELEMS, Cfg::TAB_BYTES, tbar);
+        }
+    };
+    if (cluster_id < args.ncells) fetch_tables(0);
     const int ncx = args.nc[0], ncy = args.nc[1], ncz = args.nc[2];
 
     // z-pass ownership: column (xl, y), x = rank*NS + xl (threads >= NTASK idle)
     const bool has_col = tid < NTASK;
     const int zl_x = has_col ? tid / N : 0, zl_y = tid % N;
     const int zx = rank * NS + zl_x;
-    T* Gcol = Gs + ((long)zl_x * N + zl_y) * N;
-    T* Fcol = Fs + ((long)zl_x * N + zl_y) * N;
+    T* Gcol = Gs + tid;   // element z at Gcol[z * NTASK]
+    T* Fcol = Fs + tid;
 
     // x/y task coordinates
     const int t_tab = tid / (NS * H);
@@ -187,7 +246,7 @@ collide_kernel(CollideArgs args) {
             if (!transport) {
                 const T* src = fin + cell * N3 + ((long)zx * N + zl_y) * N;
 #pragma unroll 4
-                for (int z = 0; z < N; ++z) Fcol[z] = src[z];
+                for (int z = 0; z < N; ++z) Fcol[(long)z * NTASK] = src[z];
             } else {
                 int fx, fy;
                 const int sx = fold_cell(cx - dsm[zx], ncx, args.bc[0], fx);
@@ -200,18 +259,18 @@ collide_kernel(CollideArgs args) {
                     int fz;
                     const int sz = fold_cell(cz - dsm[2 * N + z], ncz, args.bc[2], fz);
                     const int qz = fz ? N - 1 - z : z;
-                    Fcol[z] = base_xy[(long)sz * N3 + qz];
+                    Fcol[(long)z * NTASK] = base_xy[(long)sz * N3 + qz];
                 }
             }
             cpx<T> a[N];
 #pragma unroll
-            for (int z = 0; z < N; ++z) a[z] = {Fcol[z], T(0)};
+            for (int z = 0; z < N; ++z) a[z] = {Fcol[(long)z * NTASK], T(0)};
             fft<N, -1>(a);
             cpx<T>* S = W + ((long)zl_x * N + zl_y) * HP;
 #pragma unroll
             for (int k = 0; k < HF; ++k) S[k] = a[k];
 #pragma unroll
-            for (int z = 0; z < N; ++z) Gcol[z] = T(0);
+            for (int z = 0; z < N; ++z) Gcol[(long)z * NTASK] = T(0);
         }
         __syncthreads();
         // F2 + F3: y-FFT of (xl, kz') pencils, scatter to the ky owner as Fh[x][kyl][kz']
@@ -245,15 +304,17 @@ collide_kernel(CollideArgs args) {
             // ---- x-pass: table product, pack kz'=0 with kz'=N/2, inverse FFT along kx
             const bool active = has_col && (!loss || t_tab == 0);
             cpx<T> a[N];
+            mbar_wait_bounded(tbar, tphase, args.flags);   // table slab of direction p has landed
+            tphase ^= 1u;
             if (active) {
-                const T* tb = tab + ((((long)p * C + rank) * 2 + t_tab) * N) * NS * HF + (long)t_a * HF;
+                const T* tb = Tb + (long)t_tab * N * NS * HF + (long)t_a * HF;
                 const cpx<T>* fb = Fh + (long)t_a * HF;
                 if (t_pp == 0) {
 #pragma unroll
                     for (int kx = 0; kx < N; ++kx) {
                         const long o = (long)kx * NS * HF;
                         const cpx<T> fv = fb[o], fn = fb[o + H];
-                        const T tv = __ldg(tb + o), tn = __ldg(tb + o + H);
+                        const T tv = tb[o], tn = tb[o + H];
                         a[kx] = {tv * fv.x - tn * fn.y, tv * fv.y + tn * fn.x};   // tv fv + i tn fn
                     }
                 } else {
@@ -261,7 +322,7 @@ collide_kernel(CollideArgs args) {
                     for (int kx = 0; kx < N; ++kx) {
                         const long o = (long)kx * NS * HF + t_pp;
                         const cpx<T> fv = fb[o];
-                        const T tv = __ldg(tb + o);
+                        const T tv = tb[o];
                         a[kx] = {tv * fv.x, tv * fv.y};
                     }
                 }
@@ -275,6 +336,9 @@ collide_kernel(CollideArgs args) {
                     putW(x / NS, (((long)t_tab * NS + x % NS) * N + ky) * HP + t_pp, a[x]);
             }
             cluster_sync_all();
+            // every thread of this CTA is past its x-pass: the slab buffer is free
+            if (!loss) fetch_tables(p + 1);
+            else if (cell + nclusters < args.ncells) fetch_tables(0);
             // ---- y-pass in place
             if (active) {
                 cpx<T>* base = W + ((long)t_tab * NS + t_a) * N * HP + t_pp;
@@ -303,25 +367,38 @@ collide_kernel(CollideArgs args) {
                     T bv[N];
                     c2r<N>(h, bv);
 #pragma unroll
-                    for (int z = 0; z < N; ++z) Gcol[z] += av[z] * bv[z];
+                    for (int z = 0; z < N; ++z) Gcol[(long)z * NTASK] += av[z] * bv[z];
                 }
                 cluster_arrive();   // this CTA has finished reading W
             } else {
-                // loss: Q = (G - f* l) / Kn in FP64, projection moments
+                // loss: r = G - f* l in FP64 (the FP32 product is exact in FP64),
+                // Q = r / Kn; the five moments of Q from three FP64 sums per column
                 double s5[5] = {0, 0, 0, 0, 0};
                 const double vx = vel(zx), vy = vel(zl_y);
-                const double v2xy = vx * vx + vy * vy;
+                const double v2xy = 0.5 * (vx * vx + vy * vy);
+                // the column's W slots (tables 0 and 1, 2*HP elements of cpx<T>) are
+                // free after the C2R above: stash r there as N doubles
+                double* rst0 = reinterpret_cast<double*>(W + ((long)zl_x * N + zl_y) * HP);
+                double* rst1 = reinterpret_cast<double*>(W + ((long)(NS + zl_x) * N + zl_y) * HP);
+                constexpr int RS0 = (int)(HP * sizeof(cpx<T>) / sizeof(double));
+                static_assert(2 * RS0 >= N, "stash fits in the column's two W slots");
                 if (has_col) {
+                    double s0 = 0.0, sz = 0.0, szz = 0.0;
 #pragma unroll
                     for (int z = 0; z < N; ++z) {
-                        const double q = ((double)Gcol[z] - (double)Fcol[z] * (double)av[z]) * args.inv_kn;
-                        const double vz = vel(z);
-                        s5[0] += q;
-                        s5[1] += q * vx;
-                        s5[2] += q * vy;
-                        s5[3] += q * vz;
-                        s5[4] += q * 0.5 * (v2xy + vz * vz);
+                        const double r = fma(-(double)Fcol[(long)z * NTASK], (double)av[z], (double)Gcol[(long)z * NTASK]);
+                        if (z < RS0) rst0[z] = r;
+                        else rst1[z - RS0] = r;
+                        s0 += r;
+                        sz = fma(r, vzt[z], sz);
+                        szz = fma(r, vz2t[z], szz);
                     }
+                    const double k = args.inv_kn;
+                    s5[0] = s0 * k;
+                    s5[1] = vx * s0 * k;
+                    s5[2] = vy * s0 * k;
+                    s5[3] = sz * k;
+                    s5[4] = (v2xy * s0 + szz) * k;
                 }
                 // block reduction of the five moments (fixed order: deterministic)
 #pragma unroll
@@ -356,11 +433,14 @@ collide_kernel(CollideArgs args) {
                         for (int j = 0; j < 5; ++j) acc += args.P[i * 5 + j] * tot[j];
                         mu[i] = acc;
                     }
+                    // correction phi(v) . mu = mu0 + mu1 vx + mu2 vy + [mu3 vz + mu4 vz^2/2] + mu4 (vx^2+vy^2)/2
+                    for (int z = 0; z < N; ++z) czt[z] = mu[3] * vzt[z] + mu[4] * vz2t[z];
                 }
-                cluster_sync_all();   // every CTA has read the partials; mu is visible
+                cluster_sync_all();   // every CTA has read the partials; mu and czt are visible
                 if (has_col) {
-                    const double m0 = mu[0], m1 = mu[1], m2 = mu[2], m3 = mu[3], m4 = mu[4];
-                    const double cxy = m0 + m1 * vx + m2 * vy + m4 * 0.5 * v2xy;
+                    const double cxy = mu[0] + mu[1] * vx + mu[2] * vy + mu[4] * v2xy;
+                    const double kn = args.inv_kn, dt = args.dt;
+                    const bool stepm = args.mode == 1;
                     T* dst = fout + cell * N3 + ((long)zx * N + zl_y) * N;
                     bool bad = false, neg = false;
                     constexpr int V = 16 / sizeof(T);
@@ -371,12 +451,11 @@ collide_kernel(CollideArgs args) {
 #pragma unroll
                         for (int j = 0; j < V; ++j) {
                             const int z = z0 + j;
-                            const double vz = vel(z);
-                            const double q = ((double)Gcol[z] - (double)Fcol[z] * (double)av[z]) * args.inv_kn -
-                                             (cxy + m3 * vz + m4 * 0.5 * vz * vz);
-                            const double o = args.mode == 1 ? (double)Fcol[z] + args.dt * q : q;
+                            const double r = z < RS0 ? rst0[z] : rst1[z - RS0];
+                            const double q = fma(r, kn, -(cxy + czt[z]));
+                            const double o = stepm ? fma(dt, q, (double)Fcol[(long)z * NTASK]) : q;
                             bad |= !isfinite(o);
-                            neg |= (args.mode == 1) && (o < 0.0);
+                            neg |= stepm && (o < 0.0);
                             res[j] = (T)o;
                         }
                         if constexpr (sizeof(T) == 4)
