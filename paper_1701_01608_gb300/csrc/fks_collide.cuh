@@ -51,6 +51,11 @@ struct CollideArgs {
 __device__ __forceinline__ void cluster_arrive() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
 }
+// arrive without release: only orders this CTA's earlier reads (whose values
+// are already consumed) before peers overwrite the buffer they read
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
 __device__ __forceinline__ void cluster_wait() {
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
@@ -140,6 +145,7 @@ struct CollideCfg {
     static constexpr long COL_ELEMS = (long)NS * N * N;
     static constexpr long TAB_ELEMS = 2L * N * NS * HF;               // one direction's slab (T)
     static constexpr unsigned TAB_BYTES = (unsigned)(sizeof(T) * TAB_ELEMS);
+    static constexpr bool G_REG = sizeof(T) == 4;   // FP32: gain accumulator in registers
     static constexpr size_t SMEM_BYTES = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS) + sizeof(T) * (2 * COL_ELEMS + TAB_ELEMS) +
                                          sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N + N) + 8 + 3 * N + 16;
     static_assert(TAB_BYTES % 16 == 0, "bulk copies move whole 16-byte units");
@@ -170,8 +176,8 @@ collide_kernel(CollideArgs args) {
     double* mu = redw + (NT / 32) * 5;                                 // [8] correction coefficients
     double* vzt = mu + 8;                                              // [N] v_z
     double* vz2t = vzt + N;                                            // [N] v_z^2 / 2
-    double* czt = vz2t + N;                                            // [N] projection correction along z
-    uint64_t* tbar = reinterpret_cast<uint64_t*>(czt + N);            // table-slab mbarrier
+    T* czt = reinterpret_cast<T*>(vz2t + N);                          // [N] projection correction along z
+    uint64_t* tbar = reinterpret_cast<uint64_t*>(vz2t + 2 * N);       // table-slab mbarrier
     signed char* dsm = reinterpret_cast<signed char*>(tbar + 1);      // [3][N] shifts
 
     // shared::cluster addresses of W and Fh in every CTA of the cluster: the
@@ -228,11 +234,24 @@ collide_kernel(CollideArgs args) {
     T* Gcol = Gs + tid;   // element z at Gcol[z * NTASK]
     T* Fcol = Fs + tid;
 
-    // x/y task coordinates
+    // y-pass task (tab, xl, plane): plane fastest
     const int t_tab = tid / (NS * H);
     const int t_rem = tid % (NS * H);
-    const int t_a = t_rem / H;     // kyl (x-pass) or xl (y-pass)
+    const int t_a = t_rem / H;     // xl
     const int t_pp = t_rem % H;
+    // x-pass task (tab, kyl, plane): the 2*NS tasks of the packed plane 0 come
+    // first, so that their longer code path diverges inside the first warp only
+    int x_tab, x_kyl, x_pp;
+    if (tid < 2 * NS) {
+        x_pp = 0;
+        x_tab = tid / NS;
+        x_kyl = tid % NS;
+    } else {
+        const int u = tid - 2 * NS;
+        x_pp = 1 + u % (H - 1);
+        x_kyl = (u / (H - 1)) % NS;
+        x_tab = u / ((H - 1) * NS);
+    }
 
     for (long cell = cluster_id; cell < args.ncells; cell += nclusters) {
         const int cx = (int)(cell / ((long)ncy * ncz));
@@ -269,8 +288,15 @@ collide_kernel(CollideArgs args) {
             cpx<T>* S = W + ((long)zl_x * N + zl_y) * HP;
 #pragma unroll
             for (int k = 0; k < HF; ++k) S[k] = a[k];
+            if constexpr (!Cfg::G_REG) {
 #pragma unroll
-            for (int z = 0; z < N; ++z) Gcol[(long)z * NTASK] = T(0);
+                for (int z = 0; z < N; ++z) Gcol[(long)z * NTASK] = T(0);
+            }
+        }
+        T Greg[Cfg::G_REG ? N : 1];
+        if constexpr (Cfg::G_REG) {
+#pragma unroll
+            for (int z = 0; z < N; ++z) Greg[z] = T(0);
         }
         __syncthreads();
         // F2 + F3: y-FFT of (xl, kz') pencils, scatter to the ky owner as Fh[x][kyl][kz']
@@ -298,18 +324,19 @@ collide_kernel(CollideArgs args) {
         __syncthreads();
 
         // ---------------- gain and loss ---------------------------------
-        cluster_arrive();   // matches the wait before the first x-pass scatter
+        cluster_arrive_relaxed();   // matches the wait before the first x-pass scatter
         for (int p = 0; p <= args.M; ++p) {
             const bool loss = (p == args.M);
             // ---- x-pass: table product, pack kz'=0 with kz'=N/2, inverse FFT along kx
-            const bool active = has_col && (!loss || t_tab == 0);
+            const bool active = has_col && (!loss || x_tab == 0);
+            const bool active_y = has_col && (!loss || t_tab == 0);
             cpx<T> a[N];
             mbar_wait_bounded(tbar, tphase, args.flags);   // table slab of direction p has landed
             tphase ^= 1u;
             if (active) {
-                const T* tb = Tb + (long)t_tab * N * NS * HF + (long)t_a * HF;
-                const cpx<T>* fb = Fh + (long)t_a * HF;
-                if (t_pp == 0) {
+                const T* tb = Tb + (long)x_tab * N * NS * HF + (long)x_kyl * HF;
+                const cpx<T>* fb = Fh + (long)x_kyl * HF;
+                if (x_pp == 0) {
 #pragma unroll
                     for (int kx = 0; kx < N; ++kx) {
                         const long o = (long)kx * NS * HF;
@@ -320,7 +347,7 @@ collide_kernel(CollideArgs args) {
                 } else {
 #pragma unroll
                     for (int kx = 0; kx < N; ++kx) {
-                        const long o = (long)kx * NS * HF + t_pp;
+                        const long o = (long)kx * NS * HF + x_pp;
                         const cpx<T> fv = fb[o];
                         const T tv = tb[o];
                         a[kx] = {tv * fv.x, tv * fv.y};
@@ -330,17 +357,17 @@ collide_kernel(CollideArgs args) {
             }
             cluster_wait();   // every CTA has finished reading its W (previous z-pass)
             if (active) {
-                const int ky = rank * NS + t_a;
+                const int ky = rank * NS + x_kyl;
 #pragma unroll
                 for (int x = 0; x < N; ++x)
-                    putW(x / NS, (((long)t_tab * NS + x % NS) * N + ky) * HP + t_pp, a[x]);
+                    putW(x / NS, (((long)x_tab * NS + x % NS) * N + ky) * HP + x_pp, a[x]);
             }
             cluster_sync_all();
             // every thread of this CTA is past its x-pass: the slab buffer is free
             if (!loss) fetch_tables(p + 1);
             else if (cell + nclusters < args.ncells) fetch_tables(0);
             // ---- y-pass in place
-            if (active) {
+            if (active_y) {
                 cpx<T>* base = W + ((long)t_tab * NS + t_a) * N * HP + t_pp;
 #pragma unroll
                 for (int y = 0; y < N; ++y) a[y] = base[(long)y * HP];
@@ -367,28 +394,29 @@ collide_kernel(CollideArgs args) {
                     T bv[N];
                     c2r<N>(h, bv);
 #pragma unroll
-                    for (int z = 0; z < N; ++z) Gcol[(long)z * NTASK] += av[z] * bv[z];
+                    for (int z = 0; z < N; ++z) {
+                        if constexpr (Cfg::G_REG) Greg[z] = fma(av[z], bv[z], Greg[z]);
+                        else Gcol[(long)z * NTASK] += av[z] * bv[z];
+                    }
                 }
-                cluster_arrive();   // this CTA has finished reading W
+                cluster_arrive_relaxed();   // this CTA has finished reading W
             } else {
-                // loss: r = G - f* l in FP64 (the FP32 product is exact in FP64),
-                // Q = r / Kn; the five moments of Q from three FP64 sums per column
+                // loss: r = G - f* l by one fused multiply-add (the product is exact,
+                // one rounding of the difference: FP32 relative to r itself), Q = r / Kn;
+                // the five moments of Q from three FP64 sums per column
                 double s5[5] = {0, 0, 0, 0, 0};
                 const double vx = vel(zx), vy = vel(zl_y);
                 const double v2xy = 0.5 * (vx * vx + vy * vy);
-                // the column's W slots (tables 0 and 1, 2*HP elements of cpx<T>) are
-                // free after the C2R above: stash r there as N doubles
-                double* rst0 = reinterpret_cast<double*>(W + ((long)zl_x * N + zl_y) * HP);
-                double* rst1 = reinterpret_cast<double*>(W + ((long)(NS + zl_x) * N + zl_y) * HP);
-                constexpr int RS0 = (int)(HP * sizeof(cpx<T>) / sizeof(double));
-                static_assert(2 * RS0 >= N, "stash fits in the column's two W slots");
+                auto gval = [&](int z) -> T {
+                    if constexpr (Cfg::G_REG) return Greg[z];
+                    else return Gcol[(long)z * NTASK];
+                };
+                auto rval = [&](int z) -> T { return fma(-Fcol[(long)z * NTASK], av[z], gval(z)); };
                 if (has_col) {
                     double s0 = 0.0, sz = 0.0, szz = 0.0;
 #pragma unroll
                     for (int z = 0; z < N; ++z) {
-                        const double r = fma(-(double)Fcol[(long)z * NTASK], (double)av[z], (double)Gcol[(long)z * NTASK]);
-                        if (z < RS0) rst0[z] = r;
-                        else rst1[z - RS0] = r;
+                        const double r = (double)rval(z);
                         s0 += r;
                         sz = fma(r, vzt[z], sz);
                         szz = fma(r, vz2t[z], szz);
@@ -434,12 +462,13 @@ collide_kernel(CollideArgs args) {
                         mu[i] = acc;
                     }
                     // correction phi(v) . mu = mu0 + mu1 vx + mu2 vy + [mu3 vz + mu4 vz^2/2] + mu4 (vx^2+vy^2)/2
-                    for (int z = 0; z < N; ++z) czt[z] = mu[3] * vzt[z] + mu[4] * vz2t[z];
+                    for (int z = 0; z < N; ++z) czt[z] = (T)(mu[3] * vzt[z] + mu[4] * vz2t[z]);
                 }
                 cluster_sync_all();   // every CTA has read the partials; mu and czt are visible
                 if (has_col) {
-                    const double cxy = mu[0] + mu[1] * vx + mu[2] * vy + mu[4] * v2xy;
-                    const double kn = args.inv_kn, dt = args.dt;
+                    // corrected Q = r / Kn - phi(v).mu, then out = Q or f* + dt Q
+                    const T cxy = (T)(mu[0] + mu[1] * vx + mu[2] * vy + mu[4] * v2xy);
+                    const T kn = (T)args.inv_kn, dt = (T)args.dt;
                     const bool stepm = args.mode == 1;
                     T* dst = fout + cell * N3 + ((long)zx * N + zl_y) * N;
                     bool bad = false, neg = false;
@@ -451,12 +480,11 @@ collide_kernel(CollideArgs args) {
 #pragma unroll
                         for (int j = 0; j < V; ++j) {
                             const int z = z0 + j;
-                            const double r = z < RS0 ? rst0[z] : rst1[z - RS0];
-                            const double q = fma(r, kn, -(cxy + czt[z]));
-                            const double o = stepm ? fma(dt, q, (double)Fcol[(long)z * NTASK]) : q;
+                            const T q = fma(rval(z), kn, -(cxy + czt[z]));
+                            const T o = stepm ? fma(dt, q, Fcol[(long)z * NTASK]) : q;
                             bad |= !isfinite(o);
-                            neg |= stepm && (o < 0.0);
-                            res[j] = (T)o;
+                            neg |= stepm && (o < T(0));
+                            res[j] = o;
                         }
                         if constexpr (sizeof(T) == 4)
                             *reinterpret_cast<float4*>(dst + z0) = make_float4(res[0], res[1], res[2], res[3]);
