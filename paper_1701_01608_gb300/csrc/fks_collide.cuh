@@ -21,6 +21,15 @@
 // Inverse-pass packing: the kz' = 0 and kz' = N/2 planes of a real field are
 // each 2-D Hermitian, so they travel together as one complex plane
 // (plane 0 = P_0 + i P_{N/2}); every pass then has exactly N/2 planes.
+//
+// Plane layouts: planes 1..N/2-1 are stored with stride N/2-1 (15 at N = 32),
+// the pair (0, N/2) in a separate array, so that a half-warp of x-pass tasks
+// that straddles two ky rows hits distinct banks.
+//
+// Exchange between the x and y passes: each CTA writes its x-pass output for
+// itself into W[own block] and for every peer into a local staging block; one
+// thread then moves the staged blocks with bulk copies (TMA, shared::cta ->
+// shared::cluster) that complete on the receiving CTA's mbarrier.
 #pragma once
 #include <cooperative_groups.h>
 #include <cstdint>
@@ -34,7 +43,7 @@ namespace fks {
 struct CollideArgs {
     const void* f;          // input distribution, ncells * N^3 (element type T)
     void* out;              // Q or f^{n+1}
-    const void* tables;     // [M+1][C][2][N kx][NS kyl][H+1 kz'] of T
+    const void* tables;     // [M+1][C] slabs: [2][N kx][NS kyl][H-1] planes 1..H-1, then [2][N][NS][2] planes 0, H
     const signed char* delta;  // [3][N] cell shifts for this step (transport) or nullptr
     int* flags;             // health bits (atomicOr)
     long ncells;
@@ -136,28 +145,42 @@ struct CollideCfg {
     static constexpr int NS = N / C;          // slab width (ky for f^, x for W)
     static constexpr int H = N / 2;           // packed planes per inverse transform
     static constexpr int HF = H + 1;          // kz' planes of f^
-    static constexpr int HP = H + 1;          // padded plane stride of W
+    static constexpr int HM = H - 1;          // planes 1..H-1 (main arrays)
     static constexpr int NTASK = N * N / C;   // pencils / columns per pass per CTA
     static constexpr int NT = (NTASK + 31) / 32 * 32;   // threads per CTA (whole warps)
-    // shared memory: Fh, W (cpx<T>); G, f* (T, one column of N per task)
+    static constexpr bool G_REG = sizeof(T) == 4;       // FP32: gain accumulator in registers
+    // f^ slab: main [N kx][NS kyl][HM] + pair [N kx][NS kyl][2]   (cpx<T>)
+    static constexpr long FM_ELEMS = (long)N * NS * HM;
     static constexpr long FH_ELEMS = (long)N * NS * HF;
-    static constexpr long W_ELEMS = 2L * NS * N * HP;
-    static constexpr long COL_ELEMS = (long)NS * N * N;
-    static constexpr long TAB_ELEMS = 2L * N * NS * HF;               // one direction's slab (T)
+    // W: C source blocks, each main [2 tab][NS xl][NS kyl][HM] + packed [2][NS][NS]   (cpx<T>)
+    static constexpr long BLK_MAIN = 2L * NS * NS * HM;
+    static constexpr long BLK = 2L * NS * NS * H;
+    static constexpr long W_ELEMS = (long)C * BLK;
+    static constexpr long S_ELEMS = (long)(C - 1) * BLK;  // staging for the peers' blocks
+    static constexpr unsigned BLK_BYTES = (unsigned)(sizeof(cpx<T>) * BLK);
+    // forward-transform staging [NS xl][N y][HF] reuses W
+    static constexpr long STG_ELEMS = (long)NS * N * HF;
+    // table slab of one direction: main [2][N][NS][HM] + pair [2][N][NS][2]   (T)
+    static constexpr long TAB_ELEMS = 2L * N * NS * HF;
+    static constexpr long TAB_MAIN = 2L * N * NS * HM;
     static constexpr unsigned TAB_BYTES = (unsigned)(sizeof(T) * TAB_ELEMS);
-    static constexpr bool G_REG = sizeof(T) == 4;   // FP32: gain accumulator in registers
-    static constexpr size_t SMEM_BYTES = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS) + sizeof(T) * (2 * COL_ELEMS + TAB_ELEMS) +
-                                         sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N + N) + 8 + 3 * N + 16;
-    static_assert(TAB_BYTES % 16 == 0, "bulk copies move whole 16-byte units");
+    static constexpr long G_ELEMS = G_REG ? 0 : (long)NTASK * N;    // FP64 gain [N z][NTASK]
+    static constexpr size_t SMEM_BYTES = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS + S_ELEMS) +
+                                         sizeof(T) * (TAB_ELEMS + G_ELEMS) +
+                                         sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N) + sizeof(T) * N +
+                                         sizeof(long) * N + 2 * sizeof(uint64_t) + 3 * N + 64;
     static_assert(N % C == 0, "cluster size must divide N");
+    static_assert(TAB_BYTES % 16 == 0 && BLK_BYTES % 16 == 0, "bulk copies move whole 16-byte units");
+    static_assert(STG_ELEMS <= W_ELEMS, "forward staging fits in W");
 };
 
 template <typename T, int N, int C>
 __global__ void __launch_bounds__(CollideCfg<T, N, C>::NT, 1)
 collide_kernel(CollideArgs args) {
     using Cfg = CollideCfg<T, N, C>;
-    constexpr int NS = Cfg::NS, H = Cfg::H, HF = Cfg::HF, HP = Cfg::HP, NT = Cfg::NT, NTASK = Cfg::NTASK;
+    constexpr int NS = Cfg::NS, H = Cfg::H, HF = Cfg::HF, HM = Cfg::HM, NT = Cfg::NT, NTASK = Cfg::NTASK;
     constexpr long N3 = (long)N * N * N;
+    constexpr long BLK = Cfg::BLK, BLK_MAIN = Cfg::BLK_MAIN;
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -165,37 +188,40 @@ collide_kernel(CollideArgs args) {
     const long cluster_id = blockIdx.x / C;
     const long nclusters = gridDim.x / C;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T>* Fh = reinterpret_cast<cpx<T>*>(smem_raw);                 // [N kx][NS kyl][HF]
-    cpx<T>* W = Fh + Cfg::FH_ELEMS;                                    // [2][NS xl][N ky][HP]
-    T* Tb = reinterpret_cast<T*>(W + Cfg::W_ELEMS);                   // [2][N kx][NS kyl][HF] table slab
-    T* Gs = Tb + Cfg::TAB_ELEMS;                                       // [N z][NTASK] gain
-    T* Fs = Gs + Cfg::COL_ELEMS;                                       // [N z][NTASK] f*
-    double* red = reinterpret_cast<double*>(Fs + Cfg::COL_ELEMS);     // [8] own partials
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cpx<T>* Fm = reinterpret_cast<cpx<T>*>(smem_raw);                 // f^ planes 1..H-1
+    cpx<T>* Fp = Fm + Cfg::FM_ELEMS;                                   // f^ planes 0, H
+    cpx<T>* W = Fm + Cfg::FH_ELEMS;                                    // [C src][block]
+    cpx<T>* S = W + Cfg::W_ELEMS;                                      // [C-1][block] staging
+    T* Tb = reinterpret_cast<T*>(S + Cfg::S_ELEMS);                   // table slab
+    T* Gs = Tb + Cfg::TAB_ELEMS;                                       // FP64 gain [N z][NTASK]
+    double* red = reinterpret_cast<double*>(Gs + Cfg::G_ELEMS);       // [8] own partials
     double* redw = red + 8;                                            // [NT/32][5]
     double* mu = redw + (NT / 32) * 5;                                 // [8] correction coefficients
     double* vzt = mu + 8;                                              // [N] v_z
     double* vz2t = vzt + N;                                            // [N] v_z^2 / 2
     T* czt = reinterpret_cast<T*>(vz2t + N);                          // [N] projection correction along z
-    uint64_t* tbar = reinterpret_cast<uint64_t*>(vz2t + 2 * N);       // table-slab mbarrier
-    signed char* dsm = reinterpret_cast<signed char*>(tbar + 1);      // [3][N] shifts
+    long* zoff = reinterpret_cast<long*>(czt + N + (N & 1));          // [N] gather offsets along z
+    uint64_t* tbar = reinterpret_cast<uint64_t*>(zoff + N);           // table-slab mbarrier
+    uint64_t* xbar = tbar + 1;                                         // exchange mbarrier
+    signed char* dsm = reinterpret_cast<signed char*>(xbar + 1);      // [3][N] shifts
 
-    // shared::cluster addresses of W and Fh in every CTA of the cluster: the
-    // window of a CTA is contiguous, so element addresses are base + offset
-    uint32_t Wrank[C], Frank[C];
+    // shared::cluster addresses of Fm/Fp (forward exchange) and W in every CTA
+    uint32_t Frank[C], Wrank[C];
 #pragma unroll
     for (int r = 0; r < C; ++r) {
+        Frank[r] = map_rank(smem_addr(Fm), r);
         Wrank[r] = map_rank(smem_addr(W), r);
-        Frank[r] = map_rank(smem_addr(Fh), r);
     }
-    // store v at element `idx` of W (or Fh) in CTA `dst`
-    auto putW = [&](int dst, long idx, cpx<T> v) {
-        if constexpr (C == 1) W[idx] = v;
-        else st_cluster(Wrank[dst] + (uint32_t)(idx * (long)sizeof(cpx<T>)), v);
-    };
+    // store v at element idx of the f^ slab (main/pair arrays are one buffer) of CTA dst
     auto putF = [&](int dst, long idx, cpx<T> v) {
-        if constexpr (C == 1) Fh[idx] = v;
+        if constexpr (C == 1) Fm[idx] = v;
         else st_cluster(Frank[dst] + (uint32_t)(idx * (long)sizeof(cpx<T>)), v);
+    };
+    // element offset of f^ plane kz (0..H) for (kx, kyl)
+    auto fidx = [](int kx, int kyl, int kz) -> long {
+        if (kz == 0 || kz == H) return Cfg::FM_ELEMS + ((long)kx * NS + kyl) * 2 + (kz == H ? 1 : 0);
+        return ((long)kx * NS + kyl) * HM + (kz - 1);
     };
 
     const T* __restrict__ fin = static_cast<const T*>(args.f);
@@ -212,11 +238,12 @@ collide_kernel(CollideArgs args) {
     }
     if (tid == 0) {
         mbar_init(tbar, 1);
+        mbar_init(xbar, 1);
         fence_mbar_init();
     }
     // every CTA of the cluster is running before any distributed-shared access
     cluster_sync_all();
-    unsigned tphase = 0;
+    unsigned tphase = 0, xphase = 0;
     // table slab of direction p (p = M: loss) for this CTA, fetched by one thread
     auto fetch_tables = [&](int p) {
         if (tid == 0) {
@@ -231,13 +258,13 @@ collide_kernel(CollideArgs args) {
     const bool has_col = tid < NTASK;
     const int zl_x = has_col ? tid / N : 0, zl_y = tid % N;
     const int zx = rank * NS + zl_x;
-    T* Gcol = Gs + tid;   // element z at Gcol[z * NTASK]
-    T* Fcol = Fs + tid;
+    const int z_src = zl_y / NS, z_kyl = zl_y % NS;   // where column y sits in W
+    T* Gcol = Gs + tid;   // FP64: element z at Gcol[z * NTASK]
 
-    // y-pass task (tab, xl, plane): plane fastest
+    // y-pass task (tab, xl, plane), plane fastest
     const int t_tab = tid / (NS * H);
     const int t_rem = tid % (NS * H);
-    const int t_a = t_rem / H;     // xl
+    const int t_xl = t_rem / H;
     const int t_pp = t_rem % H;
     // x-pass task (tab, kyl, plane): the 2*NS tasks of the packed plane 0 come
     // first, so that their longer code path diverges inside the first warp only
@@ -248,46 +275,57 @@ collide_kernel(CollideArgs args) {
         x_kyl = tid % NS;
     } else {
         const int u = tid - 2 * NS;
-        x_pp = 1 + u % (H - 1);
-        x_kyl = (u / (H - 1)) % NS;
-        x_tab = u / ((H - 1) * NS);
+        x_pp = 1 + u % HM;
+        x_kyl = (u / HM) % NS;
+        x_tab = u / (HM * NS);
     }
+    // offset of (tab, xl, kyl, plane) inside a W block
+    auto widx = [](int tb, int xl, int kyl, int pp) -> long {
+        if (pp == 0) return BLK_MAIN + ((long)tb * NS + xl) * NS + kyl;
+        return (((long)tb * NS + xl) * NS + kyl) * HM + (pp - 1);
+    };
+    // y-pass lane addressing: element (src, kyl) at ybase + src*BLK + kyl*ystride
+    const long ybase = widx(t_tab, t_xl, 0, t_pp);
+    const long ystride = t_pp == 0 ? 1 : HM;
 
     for (long cell = cluster_id; cell < args.ncells; cell += nclusters) {
         const int cx = (int)(cell / ((long)ncy * ncz));
         const int cy = (int)((cell / ncz) % ncy);
         const int cz = (int)(cell % ncz);
+        // gather offsets along z for this cell (relative to the (x, y) source row)
+        if (tid < N) {
+            if (!transport) {
+                zoff[tid] = cell * N3 + tid;
+            } else {
+                int fz;
+                const int sz = fold_cell(cz - dsm[2 * N + tid], ncz, args.bc[2], fz);
+                zoff[tid] = (long)sz * N3 + (fz ? N - 1 - tid : tid);
+            }
+        }
+        __syncthreads();
+        // base of the f* column (x, y, :) of the transported cell
+        const T* colbase;
+        if (!transport) {
+            colbase = fin + ((long)zx * N + zl_y) * N;
+        } else {
+            int fx, fy;
+            const int sx = fold_cell(cx - dsm[zx], ncx, args.bc[0], fx);
+            const int sy = fold_cell(cy - dsm[N + zl_y], ncy, args.bc[1], fy);
+            const int qx = fx ? N - 1 - zx : zx;
+            const int qy = fy ? N - 1 - zl_y : zl_y;
+            colbase = fin + ((long)sx * ncy + sy) * ncz * N3 + ((long)qx * N + qy) * N;
+        }
 
         // ---------------- forward transform -----------------------------
-        // F1: gather the f* column (x, y, :) of the transported cell into
-        // shared memory, z-R2C; staging S = W[0] as [xl][y][HP]
+        // F1: z-R2C of this CTA's columns; staging = W as [xl][y][HF]
         if (has_col) {
-            if (!transport) {
-                const T* src = fin + cell * N3 + ((long)zx * N + zl_y) * N;
-#pragma unroll 4
-                for (int z = 0; z < N; ++z) Fcol[(long)z * NTASK] = src[z];
-            } else {
-                int fx, fy;
-                const int sx = fold_cell(cx - dsm[zx], ncx, args.bc[0], fx);
-                const int sy = fold_cell(cy - dsm[N + zl_y], ncy, args.bc[1], fy);
-                const int qx = fx ? N - 1 - zx : zx;
-                const int qy = fy ? N - 1 - zl_y : zl_y;
-                const T* base_xy = fin + ((long)sx * ncy + sy) * ncz * N3 + ((long)qx * N + qy) * N;
-#pragma unroll 4
-                for (int z = 0; z < N; ++z) {
-                    int fz;
-                    const int sz = fold_cell(cz - dsm[2 * N + z], ncz, args.bc[2], fz);
-                    const int qz = fz ? N - 1 - z : z;
-                    Fcol[(long)z * NTASK] = base_xy[(long)sz * N3 + qz];
-                }
-            }
             cpx<T> a[N];
 #pragma unroll
-            for (int z = 0; z < N; ++z) a[z] = {Fcol[(long)z * NTASK], T(0)};
+            for (int z = 0; z < N; ++z) a[z] = {colbase[zoff[z]], T(0)};
             fft<N, -1>(a);
-            cpx<T>* S = W + ((long)zl_x * N + zl_y) * HP;
+            cpx<T>* stg = W + ((long)zl_x * N + zl_y) * HF;
 #pragma unroll
-            for (int k = 0; k < HF; ++k) S[k] = a[k];
+            for (int k = 0; k < HF; ++k) stg[k] = a[k];
             if constexpr (!Cfg::G_REG) {
 #pragma unroll
                 for (int z = 0; z < N; ++z) Gcol[(long)z * NTASK] = T(0);
@@ -299,32 +337,33 @@ collide_kernel(CollideArgs args) {
             for (int z = 0; z < N; ++z) Greg[z] = T(0);
         }
         __syncthreads();
-        // F2 + F3: y-FFT of (xl, kz') pencils, scatter to the ky owner as Fh[x][kyl][kz']
+        // F2 + F3: y-FFT of (xl, kz') pencils, scatter to the ky owner (pre-x-FFT, x in place of kx)
         if (tid < NS * HF) {
             const int xl = tid / HF, kz = tid % HF;
             cpx<T> a[N];
 #pragma unroll
-            for (int y = 0; y < N; ++y) a[y] = W[((long)xl * N + y) * HP + kz];
+            for (int y = 0; y < N; ++y) a[y] = W[((long)xl * N + y) * HF + kz];
             fft<N, -1>(a);
             const int x = rank * NS + xl;
 #pragma unroll
-            for (int ky = 0; ky < N; ++ky) putF(ky / NS, ((long)x * NS + ky % NS) * HF + kz, a[ky]);
+            for (int ky = 0; ky < N; ++ky) putF(ky / NS, fidx(x, ky % NS, kz), a[ky]);
         }
         cluster_sync_all();
         // F4: x-FFT of (kyl, kz') pencils in place
         if (tid < NS * HF) {
             const int kyl = tid / HF, kz = tid % HF;
+            const long b0 = fidx(0, kyl, kz), st = fidx(1, kyl, kz) - b0;
             cpx<T> a[N];
 #pragma unroll
-            for (int x = 0; x < N; ++x) a[x] = Fh[((long)x * NS + kyl) * HF + kz];
+            for (int x = 0; x < N; ++x) a[x] = Fm[b0 + x * st];
             fft<N, -1>(a);
 #pragma unroll
-            for (int kx = 0; kx < N; ++kx) Fh[((long)kx * NS + kyl) * HF + kz] = a[kx];
+            for (int kx = 0; kx < N; ++kx) Fm[b0 + kx * st] = a[kx];
         }
         __syncthreads();
 
         // ---------------- gain and loss ---------------------------------
-        cluster_arrive_relaxed();   // matches the wait before the first x-pass scatter
+        cluster_arrive();   // matches the wait before the first x-pass exchange (W staging reads done)
         for (int p = 0; p <= args.M; ++p) {
             const bool loss = (p == args.M);
             // ---- x-pass: table product, pack kz'=0 with kz'=N/2, inverse FFT along kx
@@ -334,20 +373,22 @@ collide_kernel(CollideArgs args) {
             mbar_wait_bounded(tbar, tphase, args.flags);   // table slab of direction p has landed
             tphase ^= 1u;
             if (active) {
-                const T* tb = Tb + (long)x_tab * N * NS * HF + (long)x_kyl * HF;
-                const cpx<T>* fb = Fh + (long)x_kyl * HF;
                 if (x_pp == 0) {
+                    const cpx<T>* fb = Fp + (long)x_kyl * 2;
+                    const T* tb = Tb + Cfg::TAB_MAIN + (long)x_tab * N * NS * 2 + (long)x_kyl * 2;
 #pragma unroll
                     for (int kx = 0; kx < N; ++kx) {
-                        const long o = (long)kx * NS * HF;
-                        const cpx<T> fv = fb[o], fn = fb[o + H];
-                        const T tv = tb[o], tn = tb[o + H];
+                        const long o = (long)kx * NS * 2;
+                        const cpx<T> fv = fb[o], fn = fb[o + 1];
+                        const T tv = tb[o], tn = tb[o + 1];
                         a[kx] = {tv * fv.x - tn * fn.y, tv * fv.y + tn * fn.x};   // tv fv + i tn fn
                     }
                 } else {
+                    const cpx<T>* fb = Fm + (long)x_kyl * HM + (x_pp - 1);
+                    const T* tb = Tb + (long)x_tab * N * NS * HM + (long)x_kyl * HM + (x_pp - 1);
 #pragma unroll
                     for (int kx = 0; kx < N; ++kx) {
-                        const long o = (long)kx * NS * HF + x_pp;
+                        const long o = (long)kx * NS * HM;
                         const cpx<T> fv = fb[o];
                         const T tv = tb[o];
                         a[kx] = {tv * fv.x, tv * fv.y};
@@ -357,40 +398,69 @@ collide_kernel(CollideArgs args) {
             }
             cluster_wait();   // every CTA has finished reading its W (previous z-pass)
             if (active) {
-                const int ky = rank * NS + x_kyl;
+                // own block directly into W[rank], peers' blocks into staging
 #pragma unroll
-                for (int x = 0; x < N; ++x)
-                    putW(x / NS, (((long)x_tab * NS + x % NS) * N + ky) * HP + x_pp, a[x]);
+                for (int x = 0; x < N; ++x) {
+                    const int dst = x / NS;
+                    const long o = widx(x_tab, x % NS, x_kyl, x_pp);
+                    if (dst == rank) W[(long)rank * BLK + o] = a[x];
+                    else S[(long)(dst < rank ? dst : dst - 1) * BLK + o] = a[x];
+                }
             }
-            cluster_sync_all();
-            // every thread of this CTA is past its x-pass: the slab buffer is free
-            if (!loss) fetch_tables(p + 1);
-            else if (cell + nclusters < args.ncells) fetch_tables(0);
+            if constexpr (C > 1) {
+                if (tid == 0) mbar_expect_tx(xbar, (C - 1) * Cfg::BLK_BYTES);
+            }
+            __syncthreads();   // this CTA's x-pass is complete: staging written, slab free
+            if (tid == 0) {
+                if constexpr (C > 1) {
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+#pragma unroll
+                    for (int dst = 0; dst < C; ++dst) {
+                        if (dst == rank) continue;
+                        const cpx<T>* src = S + (long)(dst < rank ? dst : dst - 1) * BLK;
+                        const uint32_t d = Wrank[dst] + (uint32_t)((long)rank * BLK * (long)sizeof(cpx<T>));
+                        const uint32_t bar = map_rank(smem_addr(xbar), dst);
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
+                            "r"(smem_addr(src)), "r"(Cfg::BLK_BYTES), "r"(bar)
+                            : "memory");
+                    }
+                }
+                if (!loss) fetch_tables(p + 1);
+                else if (cell + nclusters < args.ncells) fetch_tables(0);
+            }
+            if constexpr (C > 1) {
+                mbar_wait_bounded(xbar, xphase, args.flags);   // every peer's block has landed
+                xphase ^= 1u;
+            }
             // ---- y-pass in place
             if (active_y) {
-                cpx<T>* base = W + ((long)t_tab * NS + t_a) * N * HP + t_pp;
 #pragma unroll
-                for (int y = 0; y < N; ++y) a[y] = base[(long)y * HP];
+                for (int y = 0; y < N; ++y) a[y] = W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * ystride];
                 fft<N, +1>(a);
 #pragma unroll
-                for (int y = 0; y < N; ++y) base[(long)y * HP] = a[y];
+                for (int y = 0; y < N; ++y) W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * ystride] = a[y];
             }
             __syncthreads();
             // ---- z-pass: C2R along z, products
             T av[N];
             if (has_col) {
-                const cpx<T>* c0 = W + ((long)zl_x * N + zl_y) * HP;          // table 0
+                const cpx<T>* wb = W + (long)z_src * BLK;
                 cpx<T> h[H];
+                h[0] = wb[widx(0, zl_x, z_kyl, 0)];
+                const cpx<T>* m0 = wb + widx(0, zl_x, z_kyl, 1);
 #pragma unroll
-                for (int k = 0; k < H; ++k) h[k] = c0[k];
+                for (int k = 1; k < H; ++k) h[k] = m0[k - 1];
                 c2r<N>(h, av);
             }
             if (!loss) {
                 if (has_col) {
-                    const cpx<T>* c1 = W + ((long)(NS + zl_x) * N + zl_y) * HP;   // table 1
+                    const cpx<T>* wb = W + (long)z_src * BLK;
                     cpx<T> h[H];
+                    h[0] = wb[widx(1, zl_x, z_kyl, 0)];
+                    const cpx<T>* m1 = wb + widx(1, zl_x, z_kyl, 1);
 #pragma unroll
-                    for (int k = 0; k < H; ++k) h[k] = c1[k];
+                    for (int k = 1; k < H; ++k) h[k] = m1[k - 1];
                     T bv[N];
                     c2r<N>(h, bv);
 #pragma unroll
@@ -399,19 +469,25 @@ collide_kernel(CollideArgs args) {
                         else Gcol[(long)z * NTASK] += av[z] * bv[z];
                     }
                 }
-                cluster_arrive_relaxed();   // this CTA has finished reading W
+                cluster_arrive();   // this CTA has finished with W (its accesses ordered before peers' copies)
             } else {
                 // loss: r = G - f* l by one fused multiply-add (the product is exact,
-                // one rounding of the difference: FP32 relative to r itself), Q = r / Kn;
+                // one rounding of the difference: relative to r itself), Q = r / Kn;
                 // the five moments of Q from three FP64 sums per column
                 double s5[5] = {0, 0, 0, 0, 0};
                 const double vx = vel(zx), vy = vel(zl_y);
                 const double v2xy = 0.5 * (vx * vx + vy * vy);
-                auto gval = [&](int z) -> T {
-                    if constexpr (Cfg::G_REG) return Greg[z];
-                    else return Gcol[(long)z * NTASK];
+                T col[N];
+                if (has_col) {
+#pragma unroll
+                    for (int z = 0; z < N; ++z) col[z] = colbase[zoff[z]];
+                }
+                auto rval = [&](int z) -> T {
+                    T g;
+                    if constexpr (Cfg::G_REG) g = Greg[z];
+                    else g = Gcol[(long)z * NTASK];
+                    return fma(-col[z], av[z], g);
                 };
-                auto rval = [&](int z) -> T { return fma(-Fcol[(long)z * NTASK], av[z], gval(z)); };
                 if (has_col) {
                     double s0 = 0.0, sz = 0.0, szz = 0.0;
 #pragma unroll
@@ -461,7 +537,7 @@ collide_kernel(CollideArgs args) {
                         for (int j = 0; j < 5; ++j) acc += args.P[i * 5 + j] * tot[j];
                         mu[i] = acc;
                     }
-                    // correction phi(v) . mu = mu0 + mu1 vx + mu2 vy + [mu3 vz + mu4 vz^2/2] + mu4 (vx^2+vy^2)/2
+                    // correction phi(v).mu = mu0 + mu1 vx + mu2 vy + mu4 (vx^2+vy^2)/2 + [mu3 vz + mu4 vz^2/2]
                     for (int z = 0; z < N; ++z) czt[z] = (T)(mu[3] * vzt[z] + mu[4] * vz2t[z]);
                 }
                 cluster_sync_all();   // every CTA has read the partials; mu and czt are visible
@@ -481,7 +557,7 @@ collide_kernel(CollideArgs args) {
                         for (int j = 0; j < V; ++j) {
                             const int z = z0 + j;
                             const T q = fma(rval(z), kn, -(cxy + czt[z]));
-                            const T o = stepm ? fma(dt, q, Fcol[(long)z * NTASK]) : q;
+                            const T o = stepm ? fma(dt, q, col[z]) : q;
                             bad |= !isfinite(o);
                             neg |= stepm && (o < T(0));
                             res[j] = o;
@@ -496,7 +572,7 @@ collide_kernel(CollideArgs args) {
                 }
             }
         }
-        // the loss pass ended with a full cluster sync: W, Fh and red are free
+        // the loss pass ended with a full cluster sync: W, Fh, S and red are free
     }
 }
 
