@@ -140,6 +140,32 @@ __device__ __forceinline__ int fold_cell(int u, int len, int specular, int& flip
     return r;
 }
 
+// Padding (in cpx elements) between the W source blocks: the z-pass lanes of a
+// shared-memory phase read column y = src*NS + kyl at
+// src*(BLK+pad) + kyl*(H-1) (+ k); pick the pad (a multiple of 16 bytes) that
+// minimises the worst bank multiplicity of one phase.
+template <int ESZ>   // bytes per complex element (8 or 16)
+constexpr int best_block_pad(int N, int NS, int HM, long BLK) {
+    const int lanes = ESZ == 8 ? 16 : 8;          // lanes per shared-memory phase
+    const int words = ESZ / 4;
+    const int step = ESZ == 8 ? 2 : 1;            // pads keep 16-byte alignment
+    int best_pad = 0, best_m = 1 << 30;
+    for (int pad = 0; pad < 32; pad += step) {
+        int worst = 0;
+        for (int ph = 0; ph + lanes <= N; ph += lanes) {
+            int cnt[32] = {};
+            for (int l = 0; l < lanes; ++l) {
+                const int y = ph + l;
+                const long e = (long)(y / NS) * (BLK + pad) + (long)(y % NS) * HM;
+                for (int w = 0; w < words; ++w) ++cnt[(int)((e * words + w) % 32)];
+            }
+            for (int b = 0; b < 32; ++b) worst = cnt[b] > worst ? cnt[b] : worst;
+        }
+        if (worst < best_m) { best_m = worst; best_pad = pad; }
+    }
+    return best_pad;
+}
+
 template <typename T, int N, int C>
 struct CollideCfg {
     static constexpr int NS = N / C;          // slab width (ky for f^, x for W)
@@ -155,8 +181,9 @@ struct CollideCfg {
     // W: C source blocks, each main [2 tab][NS xl][NS kyl][HM] + packed [2][NS][NS]   (cpx<T>)
     static constexpr long BLK_MAIN = 2L * NS * NS * HM;
     static constexpr long BLK = 2L * NS * NS * H;
-    static constexpr long W_ELEMS = (long)C * BLK;
-    static constexpr long S_ELEMS = (long)(C - 1) * BLK;  // staging for the peers' blocks
+    static constexpr long BLK_STRIDE = BLK + best_block_pad<(int)sizeof(cpx<T>)>(N, NS, HM, BLK);
+    static constexpr long W_ELEMS = (long)C * BLK_STRIDE;
+    static constexpr long S_ELEMS_RAW = (long)(C - 1) * BLK;  // staging for the peers' blocks
     static constexpr unsigned BLK_BYTES = (unsigned)(sizeof(cpx<T>) * BLK);
     // forward-transform staging [NS xl][N y][HF] reuses W
     static constexpr long STG_ELEMS = (long)NS * N * HF;
@@ -165,6 +192,7 @@ struct CollideCfg {
     static constexpr long TAB_MAIN = 2L * N * NS * HM;
     static constexpr unsigned TAB_BYTES = (unsigned)(sizeof(T) * TAB_ELEMS);
     static constexpr long G_ELEMS = G_REG ? 0 : (long)NTASK * N;    // FP64 gain [N z][NTASK]
+    static constexpr long S_ELEMS = (long)(C - 1) * (BLK + best_block_pad<(int)sizeof(cpx<T>)>(N, NS, HM, BLK));
     static constexpr size_t SMEM_BYTES = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS + S_ELEMS) +
                                          sizeof(T) * (TAB_ELEMS + G_ELEMS) +
                                          sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N) + sizeof(T) * N +
@@ -180,7 +208,7 @@ collide_kernel(CollideArgs args) {
     using Cfg = CollideCfg<T, N, C>;
     constexpr int NS = Cfg::NS, H = Cfg::H, HF = Cfg::HF, HM = Cfg::HM, NT = Cfg::NT, NTASK = Cfg::NTASK;
     constexpr long N3 = (long)N * N * N;
-    constexpr long BLK = Cfg::BLK, BLK_MAIN = Cfg::BLK_MAIN;
+    constexpr long BLK = Cfg::BLK_STRIDE, BLK_MAIN = Cfg::BLK_MAIN;   // block stride in W (padded)
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
