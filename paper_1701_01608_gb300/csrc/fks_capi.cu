@@ -118,37 +118,23 @@ __global__ void tables_kernel(TableParams tp, double* A, double* B) {
 }
 
 // Pack into the collision kernel's layout: for every direction p (slot M =
-// loss) and cluster rank r one contiguous slab of 2 N NS (H+1) values:
-//   [tab][kx][kyl][H-1]  for kz = 1..H-1   (kz - 1 fastest)
-//   [tab][kx][kyl][2]    for kz = 0 and kz = H
+// loss) and cluster rank r one contiguous slab [tab][kx][kyl][kz = 0..n/2];
 // table 0 = alpha N^-3, table 1 = w_p alphap N^-3; slot M: betaL N^-3
 // (betaL = sum_p w_p alpha_p alphap_p) and zeros.
 template <typename T>
 __global__ void pack_tables_kernel(int n, int M, int C, int HF, const double* A, const double* B,
                                    const double* w, T* out) {
     const int NS = n / C;
-    const int H = HF - 1, HM = H - 1;
     const double s3 = 1.0 / ((double)n * n * n);
-    const long slab = 2L * n * NS * HF;
-    const long main_sz = 2L * n * NS * HM;
-    const long total = (long)(M + 1) * C * slab;
+    const long per = (long)n * NS * HF;
+    const long total = (long)(M + 1) * C * 2 * per;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-        const long e = i % slab;
-        const int r = (int)((i / slab) % C);
-        const int p = (int)(i / (slab * C));
-        int tab, kx, kyl, kz;
-        if (e < main_sz) {
-            kz = 1 + (int)(e % HM);
-            kyl = (int)((e / HM) % NS);
-            kx = (int)((e / ((long)HM * NS)) % n);
-            tab = (int)(e / ((long)HM * NS * n));
-        } else {
-            const long f = e - main_sz;
-            kz = (f % 2) ? H : 0;
-            kyl = (int)((f / 2) % NS);
-            kx = (int)((f / (2L * NS)) % n);
-            tab = (int)(f / (2L * NS * n));
-        }
+        const int kz = (int)(i % HF);
+        const int kyl = (int)((i / HF) % NS);
+        const int kx = (int)((i / ((long)HF * NS)) % n);
+        const int tab = (int)((i / per) % 2);
+        const int r = (int)((i / (per * 2)) % C);
+        const int p = (int)(i / (per * 2 * C));
         const int ky = r * NS + kyl;
         const long src = ((long)kx * n + ky) * HF + kz;
         const long plane = (long)n * n * HF;

@@ -22,9 +22,10 @@
 // each 2-D Hermitian, so they travel together as one complex plane
 // (plane 0 = P_0 + i P_{N/2}); every pass then has exactly N/2 planes.
 //
-// Plane layouts: planes 1..N/2-1 are stored with stride N/2-1 (15 at N = 32),
-// the pair (0, N/2) in a separate array, so that a half-warp of x-pass tasks
-// that straddles two ky rows hits distinct banks.
+// Plane layouts: f^, the table slab and the exchange buffer W store the planes
+// of one (kx or x, ky) row contiguously with an odd stride (N/2+1), and the
+// x-pass tasks are assigned to lanes so that the lanes of one shared-memory
+// phase hit distinct banks (see xpass_task_map).
 //
 // Exchange between the x and y passes: each CTA writes its x-pass output for
 // itself into W[own block] and for every peer into a local staging block; one
@@ -170,45 +171,82 @@ template <typename T, int N, int C>
 struct CollideCfg {
     static constexpr int NS = N / C;          // slab width (ky for f^, x for W)
     static constexpr int H = N / 2;           // packed planes per inverse transform
-    static constexpr int HF = H + 1;          // kz' planes of f^
-    static constexpr int HM = H - 1;          // planes 1..H-1 (main arrays)
+    static constexpr int HF = H + 1;          // kz' planes of f^ (odd row stride)
+    static constexpr int HP = H + 1;          // row stride of W (odd)
     static constexpr int NTASK = N * N / C;   // pencils / columns per pass per CTA
     static constexpr int NT = (NTASK + 31) / 32 * 32;   // threads per CTA (whole warps)
     static constexpr bool G_REG = sizeof(T) == 4;       // FP32: gain accumulator in registers
-    // f^ slab: main [N kx][NS kyl][HM] + pair [N kx][NS kyl][2]   (cpx<T>)
-    static constexpr long FM_ELEMS = (long)N * NS * HM;
-    static constexpr long FH_ELEMS = (long)N * NS * HF;
-    // W: C source blocks, each main [2 tab][NS xl][NS kyl][HM] + packed [2][NS][NS]   (cpx<T>)
-    static constexpr long BLK_MAIN = 2L * NS * NS * HM;
-    static constexpr long BLK = 2L * NS * NS * H;
-    static constexpr long BLK_STRIDE = BLK + best_block_pad<(int)sizeof(cpx<T>)>(N, NS, HM, BLK);
+    static constexpr long FH_ELEMS = (long)N * NS * HF;  // f^ slab [N kx][NS kyl][HF]
+    // W: C source blocks, each [2 tab][NS xl][NS kyl][HP]   (cpx<T>)
+    static constexpr long BLK = 2L * NS * NS * HP;
+    static constexpr long BLK_STRIDE = BLK + best_block_pad<(int)sizeof(cpx<T>)>(N, NS, HP, BLK);
     static constexpr long W_ELEMS = (long)C * BLK_STRIDE;
-    static constexpr long S_ELEMS_RAW = (long)(C - 1) * BLK;  // staging for the peers' blocks
+    static constexpr long S_ELEMS = (long)(C - 1) * BLK_STRIDE;   // staging for the peers' blocks
     static constexpr unsigned BLK_BYTES = (unsigned)(sizeof(cpx<T>) * BLK);
     // forward-transform staging [NS xl][N y][HF] reuses W
     static constexpr long STG_ELEMS = (long)NS * N * HF;
-    // table slab of one direction: main [2][N][NS][HM] + pair [2][N][NS][2]   (T)
+    // table slab of one direction: [2 tab][N kx][NS kyl][HF]   (T)
     static constexpr long TAB_ELEMS = 2L * N * NS * HF;
-    static constexpr long TAB_MAIN = 2L * N * NS * HM;
     static constexpr unsigned TAB_BYTES = (unsigned)(sizeof(T) * TAB_ELEMS);
     static constexpr long G_ELEMS = G_REG ? 0 : (long)NTASK * N;    // FP64 gain [N z][NTASK]
-    static constexpr long S_ELEMS = (long)(C - 1) * (BLK + best_block_pad<(int)sizeof(cpx<T>)>(N, NS, HM, BLK));
+    static constexpr size_t SMEM_BASE = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS + S_ELEMS) + sizeof(T) * G_ELEMS +
+                                        sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N) + sizeof(T) * N +
+                                        sizeof(long) * N + 2 * sizeof(uint64_t) + 3 * N + 4 * NT + 64;
+    // the table slab is staged in shared memory (bulk-copy prefetch) when it fits
+    static constexpr bool TAB_SMEM = SMEM_BASE + sizeof(T) * TAB_ELEMS <= 227u * 1024u;
+    static constexpr long TB_ELEMS = TAB_SMEM ? TAB_ELEMS : 0;
     static constexpr size_t SMEM_BYTES = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS + S_ELEMS) +
-                                         sizeof(T) * (TAB_ELEMS + G_ELEMS) +
+                                         sizeof(T) * (TB_ELEMS + G_ELEMS) +
                                          sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N) + sizeof(T) * N +
-                                         sizeof(long) * N + 2 * sizeof(uint64_t) + 3 * N + 64;
+                                         sizeof(long) * N + 2 * sizeof(uint64_t) + 3 * N + 4 * NT + 64;
     static_assert(N % C == 0, "cluster size must divide N");
     static_assert(TAB_BYTES % 16 == 0 && BLK_BYTES % 16 == 0, "bulk copies move whole 16-byte units");
     static_assert(STG_ELEMS <= W_ELEMS, "forward staging fits in W");
 };
 
+// Lane assignment of the x-pass tasks (tab, kyl, plane).  Tasks of the packed
+// plane 0 take the first 2*NS lanes (their longer code path diverges in the
+// first warp only).  The others are placed group by group (a group = the
+// lanes of one shared-memory phase, 16 for 8-byte and 8 for 16-byte elements)
+// so that (kyl + plane) differs modulo the group size inside a group: the
+// row stride of f^, W and the tables is odd, so their addresses then fall on
+// distinct banks.  Written by one thread into map[NT] as tab<<16|kyl<<8|plane.
+template <int N, int C, int ESZ>
+__device__ void xpass_task_map(unsigned* map, unsigned char* used) {
+    constexpr int NS = N / C, H = N / 2, NTASK = N * N / C;
+    constexpr int G = ESZ == 8 ? 16 : 8;
+    constexpr int NTK = 2 * NS * (H - 1);           // non-packed tasks
+    for (int i = 0; i < NTK; ++i) used[i] = 0;
+    for (int t = 0; t < 2 * NS; ++t) map[t] = ((unsigned)(t / NS) << 16) | ((unsigned)(t % NS) << 8);
+    int slot = 2 * NS;
+    while (slot < NTASK) {
+        const int gend = (slot / G + 1) * G < NTASK ? (slot / G + 1) * G : NTASK;
+        bool taken[G] = {};
+        // residues already used by packed tasks sharing this group
+        for (int s = (slot / G) * G; s < slot; ++s) taken[(((map[s] >> 8) & 255u) + (map[s] & 255u)) % G] = true;
+        for (int pass = 0; pass < 2 && slot < gend; ++pass) {
+            for (int i = 0; i < NTK && slot < gend; ++i) {
+                if (used[i]) continue;
+                const int tab = i / (NS * (H - 1));
+                const int kyl = (i / (H - 1)) % NS;
+                const int pp = 1 + i % (H - 1);
+                const int res = (kyl + pp) % G;
+                if (pass == 0 && taken[res]) continue;   // second pass: fill what is left
+                taken[res] = true;
+                used[i] = 1;
+                map[slot++] = ((unsigned)tab << 16) | ((unsigned)kyl << 8) | (unsigned)pp;
+            }
+        }
+    }
+}
+
 template <typename T, int N, int C>
 __global__ void __launch_bounds__(CollideCfg<T, N, C>::NT, 1)
 collide_kernel(CollideArgs args) {
     using Cfg = CollideCfg<T, N, C>;
-    constexpr int NS = Cfg::NS, H = Cfg::H, HF = Cfg::HF, HM = Cfg::HM, NT = Cfg::NT, NTASK = Cfg::NTASK;
+    constexpr int NS = Cfg::NS, H = Cfg::H, HF = Cfg::HF, HP = Cfg::HP, NT = Cfg::NT, NTASK = Cfg::NTASK;
     constexpr long N3 = (long)N * N * N;
-    constexpr long BLK = Cfg::BLK_STRIDE, BLK_MAIN = Cfg::BLK_MAIN;   // block stride in W (padded)
+    constexpr long BLK = Cfg::BLK_STRIDE;   // block stride in W (padded)
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -217,12 +255,11 @@ collide_kernel(CollideArgs args) {
     const long nclusters = gridDim.x / C;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    cpx<T>* Fm = reinterpret_cast<cpx<T>*>(smem_raw);                 // f^ planes 1..H-1
-    cpx<T>* Fp = Fm + Cfg::FM_ELEMS;                                   // f^ planes 0, H
-    cpx<T>* W = Fm + Cfg::FH_ELEMS;                                    // [C src][block]
+    cpx<T>* Fh = reinterpret_cast<cpx<T>*>(smem_raw);                 // f^ slab [N kx][NS kyl][HF]
+    cpx<T>* W = Fh + Cfg::FH_ELEMS;                                    // [C src][block]
     cpx<T>* S = W + Cfg::W_ELEMS;                                      // [C-1][block] staging
     T* Tb = reinterpret_cast<T*>(S + Cfg::S_ELEMS);                   // table slab
-    T* Gs = Tb + Cfg::TAB_ELEMS;                                       // FP64 gain [N z][NTASK]
+    T* Gs = Tb + Cfg::TB_ELEMS;                                        // FP64 gain [N z][NTASK]
     double* red = reinterpret_cast<double*>(Gs + Cfg::G_ELEMS);       // [8] own partials
     double* redw = red + 8;                                            // [NT/32][5]
     double* mu = redw + (NT / 32) * 5;                                 // [8] correction coefficients
@@ -232,24 +269,20 @@ collide_kernel(CollideArgs args) {
     long* zoff = reinterpret_cast<long*>(czt + N + (N & 1));          // [N] gather offsets along z
     uint64_t* tbar = reinterpret_cast<uint64_t*>(zoff + N);           // table-slab mbarrier
     uint64_t* xbar = tbar + 1;                                         // exchange mbarrier
-    signed char* dsm = reinterpret_cast<signed char*>(xbar + 1);      // [3][N] shifts
+    unsigned* xmap = reinterpret_cast<unsigned*>(xbar + 1);           // [NT] x-pass task map
+    signed char* dsm = reinterpret_cast<signed char*>(xmap + NT);     // [3][N] shifts
 
-    // shared::cluster addresses of Fm/Fp (forward exchange) and W in every CTA
+    // shared::cluster addresses of Fh (forward exchange) and W in every CTA
     uint32_t Frank[C], Wrank[C];
 #pragma unroll
     for (int r = 0; r < C; ++r) {
-        Frank[r] = map_rank(smem_addr(Fm), r);
+        Frank[r] = map_rank(smem_addr(Fh), r);
         Wrank[r] = map_rank(smem_addr(W), r);
     }
-    // store v at element idx of the f^ slab (main/pair arrays are one buffer) of CTA dst
+    // store v at element idx of the f^ slab of CTA dst
     auto putF = [&](int dst, long idx, cpx<T> v) {
-        if constexpr (C == 1) Fm[idx] = v;
+        if constexpr (C == 1) Fh[idx] = v;
         else st_cluster(Frank[dst] + (uint32_t)(idx * (long)sizeof(cpx<T>)), v);
-    };
-    // element offset of f^ plane kz (0..H) for (kx, kyl)
-    auto fidx = [](int kx, int kyl, int kz) -> long {
-        if (kz == 0 || kz == H) return Cfg::FM_ELEMS + ((long)kx * NS + kyl) * 2 + (kz == H ? 1 : 0);
-        return ((long)kx * NS + kyl) * HM + (kz - 1);
     };
 
     const T* __restrict__ fin = static_cast<const T*>(args.f);
@@ -268,13 +301,15 @@ collide_kernel(CollideArgs args) {
         mbar_init(tbar, 1);
         mbar_init(xbar, 1);
         fence_mbar_init();
+        // scratch for the task-map construction: the (not yet used) W buffer
+        xpass_task_map<N, C, (int)sizeof(cpx<T>)>(xmap, reinterpret_cast<unsigned char*>(W));
     }
     // every CTA of the cluster is running before any distributed-shared access
     cluster_sync_all();
     unsigned tphase = 0, xphase = 0;
     // table slab of direction p (p = M: loss) for this CTA, fetched by one thread
     auto fetch_tables = [&](int p) {
-        if (tid == 0) {
+        if (Cfg::TAB_SMEM && tid == 0) {
             mbar_expect_tx(tbar, Cfg::TAB_BYTES);
             bulk_g2s(Tb, tab + ((long)p * C + rank) * Cfg::TAB_ELEMS, Cfg::TAB_BYTES, tbar);
         }
@@ -294,27 +329,15 @@ collide_kernel(CollideArgs args) {
     const int t_rem = tid % (NS * H);
     const int t_xl = t_rem / H;
     const int t_pp = t_rem % H;
-    // x-pass task (tab, kyl, plane): the 2*NS tasks of the packed plane 0 come
-    // first, so that their longer code path diverges inside the first warp only
-    int x_tab, x_kyl, x_pp;
-    if (tid < 2 * NS) {
-        x_pp = 0;
-        x_tab = tid / NS;
-        x_kyl = tid % NS;
-    } else {
-        const int u = tid - 2 * NS;
-        x_pp = 1 + u % HM;
-        x_kyl = (u / HM) % NS;
-        x_tab = u / (HM * NS);
-    }
+    // x-pass task (tab, kyl, plane) from the lane map (built before the first cluster barrier)
+    const unsigned xm = tid < NTASK ? xmap[tid] : 0u;
+    const int x_tab = tid < NTASK ? (int)(xm >> 16) : 2;
+    const int x_kyl = (int)((xm >> 8) & 255u);
+    const int x_pp = (int)(xm & 255u);
     // offset of (tab, xl, kyl, plane) inside a W block
-    auto widx = [](int tb, int xl, int kyl, int pp) -> long {
-        if (pp == 0) return BLK_MAIN + ((long)tb * NS + xl) * NS + kyl;
-        return (((long)tb * NS + xl) * NS + kyl) * HM + (pp - 1);
-    };
-    // y-pass lane addressing: element (src, kyl) at ybase + src*BLK + kyl*ystride
+    auto widx = [](int tb, int xl, int kyl, int pp) -> long { return (((long)tb * NS + xl) * NS + kyl) * HP + pp; };
+    // y-pass lane addressing: element (src, kyl) at ybase + src*BLK + kyl*HP
     const long ybase = widx(t_tab, t_xl, 0, t_pp);
-    const long ystride = t_pp == 0 ? 1 : HM;
 
     for (long cell = cluster_id; cell < args.ncells; cell += nclusters) {
         const int cx = (int)(cell / ((long)ncy * ncz));
@@ -374,19 +397,18 @@ collide_kernel(CollideArgs args) {
             fft<N, -1>(a);
             const int x = rank * NS + xl;
 #pragma unroll
-            for (int ky = 0; ky < N; ++ky) putF(ky / NS, fidx(x, ky % NS, kz), a[ky]);
+            for (int ky = 0; ky < N; ++ky) putF(ky / NS, ((long)x * NS + ky % NS) * HF + kz, a[ky]);
         }
         cluster_sync_all();
         // F4: x-FFT of (kyl, kz') pencils in place
         if (tid < NS * HF) {
             const int kyl = tid / HF, kz = tid % HF;
-            const long b0 = fidx(0, kyl, kz), st = fidx(1, kyl, kz) - b0;
             cpx<T> a[N];
 #pragma unroll
-            for (int x = 0; x < N; ++x) a[x] = Fm[b0 + x * st];
+            for (int x = 0; x < N; ++x) a[x] = Fh[((long)x * NS + kyl) * HF + kz];
             fft<N, -1>(a);
 #pragma unroll
-            for (int kx = 0; kx < N; ++kx) Fm[b0 + kx * st] = a[kx];
+            for (int kx = 0; kx < N; ++kx) Fh[((long)kx * NS + kyl) * HF + kz] = a[kx];
         }
         __syncthreads();
 
@@ -398,25 +420,26 @@ collide_kernel(CollideArgs args) {
             const bool active = has_col && (!loss || x_tab == 0);
             const bool active_y = has_col && (!loss || t_tab == 0);
             cpx<T> a[N];
-            mbar_wait_bounded(tbar, tphase, args.flags);   // table slab of direction p has landed
-            tphase ^= 1u;
+            if constexpr (Cfg::TAB_SMEM) {
+                mbar_wait_bounded(tbar, tphase, args.flags);   // table slab of direction p has landed
+                tphase ^= 1u;
+            }
             if (active) {
+                const cpx<T>* fb = Fh + (long)x_kyl * HF;
+                const T* tslab = Cfg::TAB_SMEM ? Tb : tab + ((long)p * C + rank) * Cfg::TAB_ELEMS;
+                const T* tb = tslab + (long)x_tab * N * NS * HF + (long)x_kyl * HF;
                 if (x_pp == 0) {
-                    const cpx<T>* fb = Fp + (long)x_kyl * 2;
-                    const T* tb = Tb + Cfg::TAB_MAIN + (long)x_tab * N * NS * 2 + (long)x_kyl * 2;
 #pragma unroll
                     for (int kx = 0; kx < N; ++kx) {
-                        const long o = (long)kx * NS * 2;
-                        const cpx<T> fv = fb[o], fn = fb[o + 1];
-                        const T tv = tb[o], tn = tb[o + 1];
+                        const long o = (long)kx * NS * HF;
+                        const cpx<T> fv = fb[o], fn = fb[o + H];
+                        const T tv = tb[o], tn = tb[o + H];
                         a[kx] = {tv * fv.x - tn * fn.y, tv * fv.y + tn * fn.x};   // tv fv + i tn fn
                     }
                 } else {
-                    const cpx<T>* fb = Fm + (long)x_kyl * HM + (x_pp - 1);
-                    const T* tb = Tb + (long)x_tab * N * NS * HM + (long)x_kyl * HM + (x_pp - 1);
 #pragma unroll
                     for (int kx = 0; kx < N; ++kx) {
-                        const long o = (long)kx * NS * HM;
+                        const long o = (long)kx * NS * HF + x_pp;
                         const cpx<T> fv = fb[o];
                         const T tv = tb[o];
                         a[kx] = {tv * fv.x, tv * fv.y};
@@ -464,31 +487,27 @@ collide_kernel(CollideArgs args) {
             // ---- y-pass in place
             if (active_y) {
 #pragma unroll
-                for (int y = 0; y < N; ++y) a[y] = W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * ystride];
+                for (int y = 0; y < N; ++y) a[y] = W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP];
                 fft<N, +1>(a);
 #pragma unroll
-                for (int y = 0; y < N; ++y) W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * ystride] = a[y];
+                for (int y = 0; y < N; ++y) W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP] = a[y];
             }
             __syncthreads();
             // ---- z-pass: C2R along z, products
             T av[N];
             if (has_col) {
-                const cpx<T>* wb = W + (long)z_src * BLK;
+                const cpx<T>* c0 = W + (long)z_src * BLK + widx(0, zl_x, z_kyl, 0);
                 cpx<T> h[H];
-                h[0] = wb[widx(0, zl_x, z_kyl, 0)];
-                const cpx<T>* m0 = wb + widx(0, zl_x, z_kyl, 1);
 #pragma unroll
-                for (int k = 1; k < H; ++k) h[k] = m0[k - 1];
+                for (int k = 0; k < H; ++k) h[k] = c0[k];
                 c2r<N>(h, av);
             }
             if (!loss) {
                 if (has_col) {
-                    const cpx<T>* wb = W + (long)z_src * BLK;
+                    const cpx<T>* c1 = W + (long)z_src * BLK + widx(1, zl_x, z_kyl, 0);
                     cpx<T> h[H];
-                    h[0] = wb[widx(1, zl_x, z_kyl, 0)];
-                    const cpx<T>* m1 = wb + widx(1, zl_x, z_kyl, 1);
 #pragma unroll
-                    for (int k = 1; k < H; ++k) h[k] = m1[k - 1];
+                    for (int k = 0; k < H; ++k) h[k] = c1[k];
                     T bv[N];
                     c2r<N>(h, bv);
 #pragma unroll
