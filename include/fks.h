@@ -113,7 +113,9 @@ fks_status fks_moments(fks_ctx *ctx, const void *f, double *U, void *stream);
 
 /* Synchronises `stream`, reads and clears the health bits of the kernels
  * launched so far: bit 0 = non-finite value written, bit 1 = negative f
- * after a step.  Returns FKS_ERR_NUMERIC if bit 0 was set, and stores the
+ * after a step, bit 2 = cell shift out of range, bit 3 = a bulk copy into
+ * shared memory did not complete within its bounded wait.  Returns
+ * FKS_ERR_NUMERIC for bits 0 and 2, FKS_ERR_TIMEOUT for bit 3, and stores the
  * bits in *bits if bits != NULL. */
 fks_status fks_check(fks_ctx *ctx, void *stream, int *bits);
 
@@ -139,6 +141,44 @@ long fks_launch_count(const fks_ctx *ctx);
  * (R = 2L/(3+sqrt 2)) evaluated on the host by the same code the table
  * kernel runs on the device.  Needs no GPU. */
 fks_status fks_kernel_transform(int ktype, double C, double L, double s, double *phi, double *psi);
+
+/* ---------------------------------------------------------------- batches
+ * Independent space-homogeneous problems (one cell each, no transport) of
+ * uneven size: problem i has n[i]^3 velocities on [-L[i], L[i]]^3, kernel
+ * ktype[i] with constant C[i], Knudsen number knudsen[i]; all share the
+ * direction set.  Problems of one n form a class run by one persistent
+ * launch over per-problem descriptors (the spectral operator of Appendix A,
+ * the FP64 projection and, for steps, the Euler update of Eq. disc_relax);
+ * the classes run concurrently.  Arrays of problem pointers are HOST arrays
+ * of nprob DEVICE pointers (n[i]^3 elements each, distinct, 16-byte
+ * aligned).  Descriptors are cached per pointer set (the first call with a
+ * new set uploads them synchronously). */
+typedef struct fks_batch fks_batch;
+
+fks_status fks_batch_init(int nprob, const int *n, const double *L, const int *ktype, const double *C,
+                          const double *knudsen, const fks_dirs *dirs, int precision, fks_batch **out);
+
+/* Q[i] = projected Q(f[i]) / Kn_i for every problem. */
+fks_status fks_batch_collide(fks_batch *b, const void *const *f, void *const *Q, void *stream);
+
+/* f_out[i] = f[i] + dt[i] Q(f[i]) for every problem (dt: host array). */
+fks_status fks_batch_step(fks_batch *b, const void *const *f, void *const *f_out, const double *dt, void *stream);
+
+/* nsteps steps alternating fa -> fb -> fa ...: captured once per (fa, fb,
+ * dt, nsteps) into a CUDA graph and replayed on `stream`.  The result is in
+ * fb if nsteps is odd, else in fa. */
+fks_status fks_batch_run(fks_batch *b, void *const *fa, void *const *fb, const double *dt, int nsteps, void *stream);
+
+/* As fks_check, for the batch kernels. */
+fks_status fks_batch_check(fks_batch *b, void *stream, int *bits);
+
+/* Cluster size used for the class of velocity grid n (-1 if none); the
+ * setter rebuilds that class's tables (used by the autotuner). */
+int fks_batch_cluster_size(const fks_batch *b, int n);
+fks_status fks_batch_set_cluster_size(fks_batch *b, int n, int C);
+long fks_batch_launch_count(const fks_batch *b);
+void fks_batch_destroy(fks_batch *b);
+const char *fks_batch_last_error(const fks_batch *b);
 
 /* fks_transport_noalloc -- the transport of fks_transport for callers that
  * cannot allocate device memory.  It is an addition of this library; the

@@ -41,6 +41,18 @@ namespace cg = cooperative_groups;
 
 namespace fks {
 
+// One independent space-homogeneous problem of a batch (one cell, no transport).
+struct BatchItem {
+    const void* f;          // n^3 input values
+    void* out;              // n^3 output values
+    const void* tables;     // this problem's table slabs (kernel type, L)
+    const double* P;        // 25 projection coefficients for (n, L)
+    double inv_kn;
+    double dt;
+    double L;
+    double pad_;
+};
+
 struct CollideArgs {
     const void* f;          // input distribution, ncells * N^3 (element type T)
     void* out;              // Q or f^{n+1}
@@ -56,6 +68,7 @@ struct CollideArgs {
     double dt;              // Euler step (step mode)
     int mode;               // 0 collide (out = Q), 1 step (out = f* + dt Q)
     double P[25];           // dv^6 (C C^T)^-1 over the rows phi = (1, v, |v|^2/2)
+    const BatchItem* items; // batch mode: ncells items, each a homogeneous problem
 };
 
 __device__ __forceinline__ void cluster_arrive() {
@@ -240,7 +253,7 @@ __device__ void xpass_task_map(unsigned* map, unsigned char* used) {
     }
 }
 
-template <typename T, int N, int C>
+template <typename T, int N, int C, bool BATCH = false>
 __global__ void __launch_bounds__(CollideCfg<T, N, C>::NT, 1)
 collide_kernel(CollideArgs args) {
     using Cfg = CollideCfg<T, N, C>;
@@ -285,14 +298,16 @@ collide_kernel(CollideArgs args) {
         else st_cluster(Frank[dst] + (uint32_t)(idx * (long)sizeof(cpx<T>)), v);
     };
 
-    const T* __restrict__ fin = static_cast<const T*>(args.f);
-    T* __restrict__ fout = static_cast<T*>(args.out);
-    const T* __restrict__ tab = static_cast<const T*>(args.tables);
-    const bool transport = args.delta != nullptr;
+    // per-item data: the cells of one problem, or (batch) one problem per item
+    auto item_tables = [&](long it) -> const T* {
+        if constexpr (BATCH) return static_cast<const T*>(args.items[it].tables);
+        else return static_cast<const T*>(args.tables);
+    };
+    const bool transport = !BATCH && args.delta != nullptr;
     for (int i = tid; i < 3 * N; i += NT) dsm[i] = transport ? args.delta[i] : 0;
-    const double dv = 2.0 * args.L / N;
+    double dv = 2.0 * args.L / N;
     // velocity of grid index i: (i + 1/2 - N/2) dv
-    auto vel = [dv](int i) { return ((double)i + 0.5 - 0.5 * N) * dv; };
+    auto vel = [&dv](int i) { return ((double)i + 0.5 - 0.5 * N) * dv; };
     for (int i = tid; i < N; i += NT) {
         vzt[i] = vel(i);
         vz2t[i] = 0.5 * vel(i) * vel(i);
@@ -308,13 +323,13 @@ collide_kernel(CollideArgs args) {
     cluster_sync_all();
     unsigned tphase = 0, xphase = 0;
     // table slab of direction p (p = M: loss) for this CTA, fetched by one thread
-    auto fetch_tables = [&](int p) {
+    auto fetch_tables = [&](const T* tab, int p) {
         if (Cfg::TAB_SMEM && tid == 0) {
             mbar_expect_tx(tbar, Cfg::TAB_BYTES);
             bulk_g2s(Tb, tab + ((long)p * C + rank) * Cfg::TAB_ELEMS, Cfg::TAB_BYTES, tbar);
         }
     };
-    if (cluster_id < args.ncells) fetch_tables(0);
+    if (cluster_id < args.ncells) fetch_tables(item_tables(cluster_id), 0);
     const int ncx = args.nc[0], ncy = args.nc[1], ncz = args.nc[2];
 
     // z-pass ownership: column (xl, y), x = rank*NS + xl (threads >= NTASK idle)
@@ -339,7 +354,35 @@ collide_kernel(CollideArgs args) {
     // y-pass lane addressing: element (src, kyl) at ybase + src*BLK + kyl*HP
     const long ybase = widx(t_tab, t_xl, 0, t_pp);
 
-    for (long cell = cluster_id; cell < args.ncells; cell += nclusters) {
+    for (long item = cluster_id; item < args.ncells; item += nclusters) {
+        // batch: item = one homogeneous problem (cell 0 of its own arrays)
+        const long cell = BATCH ? 0 : item;
+        const T* __restrict__ fin;
+        T* __restrict__ fout;
+        const T* __restrict__ tab = item_tables(item);
+        const double* Pm;
+        double inv_kn, dt_step;
+        if constexpr (BATCH) {
+            const BatchItem& bi = args.items[item];
+            fin = static_cast<const T*>(bi.f);
+            fout = static_cast<T*>(bi.out);
+            Pm = bi.P;
+            inv_kn = bi.inv_kn;
+            dt_step = bi.dt;
+            // velocity tables of this problem's box (read after the barrier below;
+            // the previous item's last reads precede its final cluster barrier)
+            dv = 2.0 * bi.L / N;
+            if (tid < N) {
+                vzt[tid] = vel(tid);
+                vz2t[tid] = 0.5 * vel(tid) * vel(tid);
+            }
+        } else {
+            fin = static_cast<const T*>(args.f);
+            fout = static_cast<T*>(args.out);
+            Pm = args.P;
+            inv_kn = args.inv_kn;
+            dt_step = args.dt;
+        }
         const int cx = (int)(cell / ((long)ncy * ncz));
         const int cy = (int)((cell / ncz) % ncy);
         const int cz = (int)(cell % ncz);
@@ -477,8 +520,8 @@ collide_kernel(CollideArgs args) {
                             : "memory");
                     }
                 }
-                if (!loss) fetch_tables(p + 1);
-                else if (cell + nclusters < args.ncells) fetch_tables(0);
+                if (!loss) fetch_tables(tab, p + 1);
+                else if (item + nclusters < args.ncells) fetch_tables(item_tables(item + nclusters), 0);
             }
             if constexpr (C > 1) {
                 mbar_wait_bounded(xbar, xphase, args.flags);   // every peer's block has landed
@@ -544,7 +587,7 @@ collide_kernel(CollideArgs args) {
                         sz = fma(r, vzt[z], sz);
                         szz = fma(r, vz2t[z], szz);
                     }
-                    const double k = args.inv_kn;
+                    const double k = inv_kn;
                     s5[0] = s0 * k;
                     s5[1] = vx * s0 * k;
                     s5[2] = vy * s0 * k;
@@ -581,7 +624,7 @@ collide_kernel(CollideArgs args) {
                     }
                     for (int i = 0; i < 5; ++i) {
                         double acc = 0.0;
-                        for (int j = 0; j < 5; ++j) acc += args.P[i * 5 + j] * tot[j];
+                        for (int j = 0; j < 5; ++j) acc += Pm[i * 5 + j] * tot[j];
                         mu[i] = acc;
                     }
                     // correction phi(v).mu = mu0 + mu1 vx + mu2 vy + mu4 (vx^2+vy^2)/2 + [mu3 vz + mu4 vz^2/2]
@@ -591,7 +634,7 @@ collide_kernel(CollideArgs args) {
                 if (has_col) {
                     // corrected Q = r / Kn - phi(v).mu, then out = Q or f* + dt Q
                     const T cxy = (T)(mu[0] + mu[1] * vx + mu[2] * vy + mu[4] * v2xy);
-                    const T kn = (T)args.inv_kn, dt = (T)args.dt;
+                    const T kn = (T)inv_kn, dt = (T)dt_step;
                     const bool stepm = args.mode == 1;
                     T* dst = fout + cell * N3 + ((long)zx * N + zl_y) * N;
                     bool bad = false, neg = false;

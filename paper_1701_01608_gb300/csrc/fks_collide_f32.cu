@@ -6,7 +6,8 @@ namespace fks {
 template <int N, int C>
 static bool variant(CollideVariant* out) {
     using Cfg = CollideCfg<float, N, C>;
-    out->func = reinterpret_cast<const void*>(&collide_kernel<float, N, C>);
+    out->func = reinterpret_cast<const void*>(&collide_kernel<float, N, C, false>);
+    out->func_batch = reinterpret_cast<const void*>(&collide_kernel<float, N, C, true>);
     out->N = N;
     out->C = C;
     out->NT = Cfg::NT;

@@ -10,7 +10,8 @@ namespace fks {
 
 // One instantiation of collide_kernel<T, N, C>.
 struct CollideVariant {
-    const void* func;     // host stub of the kernel
+    const void* func;     // host stub of the kernel (cells of one problem)
+    const void* func_batch;   // host stub of the batch kernel (one homogeneous problem per item)
     int N, C, NT;
     size_t smem;
     bool fp64;

@@ -55,7 +55,10 @@ _lib = None
 EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments", "fks_check",
            "fks_get_offsets", "fks_set_offsets", "fks_ncells", "fks_nv", "fks_cluster_size",
            "fks_set_cluster_size", "fks_launch_count", "fks_kernel_transform", "fks_destroy",
-           "fks_last_error", "fks_status_string", "fks_transport_noalloc"]
+           "fks_last_error", "fks_status_string", "fks_transport_noalloc",
+           "fks_batch_init", "fks_batch_collide", "fks_batch_step", "fks_batch_run", "fks_batch_check",
+           "fks_batch_cluster_size", "fks_batch_set_cluster_size", "fks_batch_launch_count",
+           "fks_batch_destroy", "fks_batch_last_error"]
 
 
 def lib(build: bool = True):
@@ -89,6 +92,22 @@ def lib(build: bool = True):
     L.fks_launch_count.restype = ctypes.c_long
     L.fks_kernel_transform.argtypes = [I, D, D, D, ctypes.POINTER(D), ctypes.POINTER(D)]
     L.fks_transport_noalloc.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_VBox), I, P, D, P, P, P]
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    PD = ctypes.POINTER(ctypes.c_double)
+    PI = ctypes.POINTER(ctypes.c_int)
+    L.fks_batch_init.argtypes = [I, PI, PD, PI, PD, PD, ctypes.POINTER(_Dirs), I, PP]
+    L.fks_batch_collide.argtypes = [P, PP, PP, P]
+    L.fks_batch_step.argtypes = [P, PP, PP, PD, P]
+    L.fks_batch_run.argtypes = [P, PP, PP, PD, I, P]
+    L.fks_batch_check.argtypes = [P, P, PI]
+    L.fks_batch_cluster_size.argtypes = [P, I]
+    L.fks_batch_set_cluster_size.argtypes = [P, I, I]
+    L.fks_batch_launch_count.argtypes = [P]
+    L.fks_batch_launch_count.restype = ctypes.c_long
+    L.fks_batch_destroy.argtypes = [P]
+    L.fks_batch_destroy.restype = None
+    L.fks_batch_last_error.argtypes = [P]
+    L.fks_batch_last_error.restype = ctypes.c_char_p
     L.fks_destroy.argtypes = [P]
     L.fks_destroy.restype = None
     L.fks_last_error.argtypes = [P]
@@ -217,3 +236,80 @@ class Context:
     def set_offsets(self, s):
         s = np.ascontiguousarray(s, dtype=np.float64).reshape(3, self.cfg.n)
         self._check(self._L.fks_set_offsets(self._h, s.ctypes.data_as(ctypes.c_void_p)), "fks_set_offsets")
+
+
+class Batch:
+    """fks_batch: independent homogeneous problems of uneven size.
+
+    problems: list of dicts with keys n, L, kernel, C (default 0.25), kn."""
+
+    def __init__(self, problems, A1=4, A2=8, rule=0, precision=FKS_FP32):
+        import torch
+        self._L = lib()
+        k = len(problems)
+        self.problems = problems
+        self.n = [int(p["n"]) for p in problems]
+        arr = lambda t, xs: (t * k)(*xs)
+        d = _Dirs(A1, A2, rule)
+        h = ctypes.c_void_p()
+        st = self._L.fks_batch_init(k, arr(ctypes.c_int, self.n), arr(ctypes.c_double, [p["L"] for p in problems]),
+                                    arr(ctypes.c_int, [int(p.get("kernel", 0)) for p in problems]),
+                                    arr(ctypes.c_double, [float(p.get("C", 0.25)) for p in problems]),
+                                    arr(ctypes.c_double, [float(p["kn"]) for p in problems]), ctypes.byref(d),
+                                    precision, ctypes.byref(h))
+        if st != 0:
+            raise FKSError(st, "fks_batch_init")
+        self._h = h
+        self.dtype = torch.float64 if precision == FKS_FP64 else torch.float32
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.fks_batch_destroy(h)
+            self._h = None
+
+    def _check(self, st, what):
+        if st != 0:
+            raise FKSError(st, f"{what}: {self._L.fks_batch_last_error(self._h).decode()}")
+
+    def _ptrs(self, ts):
+        if len(ts) != len(self.n):
+            raise ValueError("one tensor per problem")
+        for t, n in zip(ts, self.n):
+            _dptr(t, self.dtype)
+            if t.numel() != n ** 3:
+                raise ValueError("problem tensor must hold n^3 values")
+        return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+    def _dts(self, dt):
+        if isinstance(dt, (int, float)):
+            dt = [float(dt)] * len(self.n)
+        return (ctypes.c_double * len(self.n))(*dt)
+
+    def collide(self, fs, Qs, stream=None):
+        self._check(self._L.fks_batch_collide(self._h, self._ptrs(fs), self._ptrs(Qs), _stream_ptr(stream)),
+                    "fks_batch_collide")
+
+    def step(self, fs, outs, dt, stream=None):
+        self._check(self._L.fks_batch_step(self._h, self._ptrs(fs), self._ptrs(outs), self._dts(dt),
+                                           _stream_ptr(stream)), "fks_batch_step")
+
+    def run(self, fa, fb, dt, nsteps: int, stream=None):
+        """nsteps ping-pong steps through one CUDA graph; result in fb if nsteps is odd else fa."""
+        self._check(self._L.fks_batch_run(self._h, self._ptrs(fa), self._ptrs(fb), self._dts(dt), int(nsteps),
+                                          _stream_ptr(stream)), "fks_batch_run")
+
+    def check(self, stream=None) -> int:
+        bits = ctypes.c_int()
+        self._check(self._L.fks_batch_check(self._h, _stream_ptr(stream), ctypes.byref(bits)), "fks_batch_check")
+        return bits.value
+
+    def cluster_size(self, n: int) -> int:
+        return self._L.fks_batch_cluster_size(self._h, n)
+
+    def set_cluster_size(self, n: int, C: int):
+        self._check(self._L.fks_batch_set_cluster_size(self._h, n, C), "fks_batch_set_cluster_size")
+
+    @property
+    def launches(self) -> int:
+        return self._L.fks_batch_launch_count(self._h)
