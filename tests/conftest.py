@@ -18,3 +18,17 @@ def oracle():
     import oracle as O
     O.build()
     return O
+
+
+# FP32 parity bound.  Q = G - L is a difference of two terms of size ||L||;
+# FP32 rounds both, so the attainable error is a fraction of the loss scale,
+# not of Q: relative L2 <= 1e-5 wherever ||L|| / ||Q|| <= 40 (cells away from
+# equilibrium), and ||dQ|| <= 2.5e-7 ||L|| / Kn in general.
+FP32_REL = 1e-5
+FP32_LOSS = 2.5e-7
+
+
+def fp32_within(Q_gpu, Q_ref, loss_ref_over_kn):
+    import numpy as np
+    err = float(np.linalg.norm(np.asarray(Q_gpu) - np.asarray(Q_ref)))
+    return err <= max(FP32_REL * float(np.linalg.norm(Q_ref)), FP32_LOSS * float(np.linalg.norm(loss_ref_over_kn)))
