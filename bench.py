@@ -28,6 +28,17 @@ PTS = NCELLS * NV ** 3
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0   # fallback figure for a GB300
+
+
+HBM_PEAK_GBS = _hbm_peak()
+
+
 def flops_per_cell(n=NV, m=M):
     """Algorithmic flops of the operator per cell: (2M+2) real 3-D transforms
     at 2.5 N_v log2 N_v each, plus (4M+20) N_v pointwise."""
@@ -217,6 +228,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-bgk", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=int(os.environ.get("FKS_CPU_SAMPLE", "1024")))
     ap.add_argument("--grid", default=None, help="nx,ny,nz spatial cells (default 32,32,32); smaller grids "
                     "are for profiling runs, not bench lines")
@@ -289,6 +301,23 @@ def main():
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
         del host_in, host_out, fa, fb
 
+    # BGK relaxation step on the same workload: HBM bound (8 B per point)
+    bgk = None
+    if not args.no_bgk:
+        cfgb = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=fks.BGK, kn=KN, precision=fks.FKS_FP32)
+        ctxb = fks.Context(cfgb)
+        tb, perb, _, _, _ = time_steps(torch, ctxb, f0, args.steps, args.warmup, dt, ws)
+        tb = max_over_ranks(tb, ws)
+        bms = float(np.mean(perb))
+        gbs = 8.0 * PTS / (bms / 1e3) / 1e9
+        bgk = {"value": ws * PTS * args.steps / (tb / 1e3), "unit": "pts/s", "ms_per_step": tb / args.steps,
+               "roofline": {"bound": "hbm", "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                            "frac": gbs / HBM_PEAK_GBS, "traffic": None,
+                            "algorithmic_bytes_per_launch": 8.0 * PTS,
+                            "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+               "note": "BGK relaxation (Sec. 2) with the fused transport gather, FP32"}
+        del ctxb
+
     fp64 = None
     if not args.no_fp64 and ws == 1:
         cfg64 = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
@@ -321,6 +350,7 @@ def main():
         "gpu_launches": launches,
         "health_bits": bits,
         "fp64_spectral": fp64,
+        "bgk_step": bgk,
     }
     print(json.dumps(out), flush=True)
 

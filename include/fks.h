@@ -46,7 +46,7 @@ typedef enum {
 
 enum { FKS_BC_PERIODIC = 0, FKS_BC_SPECULAR = 1 };
 enum { FKS_FP64 = 0, FKS_FP32 = 1 };
-enum { FKS_HARD_SPHERE = 0, FKS_MAXWELL = 1 };
+enum { FKS_HARD_SPHERE = 0, FKS_MAXWELL = 1, FKS_BGK = 2 };
 
 /* Spatial grid: nx*ny*nz cells on the box [x0, x1]; bc[a] applies to both
  * walls of axis a.  nx = ny = nz = 1 is the space-homogeneous problem. */
@@ -67,7 +67,11 @@ typedef struct {
  *   FKS_MAXWELL:     B~(|x|,|y|) = 4C (|x||y|)^-1/2, a separable kernel whose
  *                    collision kernel B = C (sin(theta)/2)^-1/2 does not
  *                    depend on |g| (Maxwell type).
- * The operator returned is Q / knudsen. */
+ * The operator returned is Q / knudsen.
+ *   FKS_BGK:         the BGK relaxation nu (M[f] - f) of Sec. 2 with the
+ *                    cell's Maxwellian M[f] and nu = rho / knudsen (C unused),
+ *                    followed by the same conservation projection; not
+ *                    available in batches. */
 typedef struct {
     int type;
     double C;

@@ -14,6 +14,7 @@ Functions and the passage each follows:
                             over half-sphere directions, fast spectral operator)
   galerkin               -- Appendix A, Eq. CF1 (O(N_v^2) sum), brute force
   project                -- conservation correction (collision invariants, Sec. 2)
+  bgk                    -- BGK relaxation nu (M[f] - f) (Sec. 2, BGK approximation)
   step                   -- Eq. disc_relax: transport, then f = f* + dt Q(f*)
 
 Pins: every function is checked against values fixed outside this module by
@@ -80,6 +81,7 @@ def _L():
             lib.or_moments.argtypes = [I, D, Lg, P, P]
             lib.or_offsets.argtypes = [I, D, D, D, P, P]
             lib.or_transport.argtypes = [P, P, I, P, P, P]
+            lib.or_bgk.argtypes = [I, D, D, I, Lg, P, P]
             _lib = lib
     return _lib
 
@@ -204,6 +206,15 @@ def galerkin(f, tab: Tables, kn: float = 1.0) -> np.ndarray:
     return Q
 
 
+def bgk(f, n: int, L: float, kn: float = 1.0, project: bool = True) -> np.ndarray:
+    """BGK operator nu (M[f] - f), nu = rho / Kn, projected (Sec. 2, BGK approximation)."""
+    f = _f64(f)
+    nc = f.size // n ** 3
+    Q = np.empty_like(f)
+    _L().or_bgk(n, L, 1.0 / kn, 1 if project else 0, nc, _p(f), _p(Q))
+    return Q
+
+
 def project(Q, n: int, L: float) -> np.ndarray:
     Q = _f64(Q).copy()
     cells = Q.reshape(-1, n, n, n)
@@ -263,5 +274,8 @@ class Solver:
 
     def step(self, f, dt):
         fs = self.transport(f, dt)
-        Q = collide(fs, self.tab, self.kn, project=True)
+        if self.tab is None:   # BGK relaxation
+            Q = bgk(fs, self.n, self.L, self.kn, project=True)
+        else:
+            Q = collide(fs, self.tab, self.kn, project=True)
         return fs + dt * Q

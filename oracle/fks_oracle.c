@@ -608,3 +608,37 @@ void or_transport(const int *nc, const int *bc, int n, const int *delta,
                         }
             }
 }
+
+/* ------------------------------------------------------------------ */
+/* BGK relaxation operator (Sec. 2, BGK approximation; Sec. 2.3)         */
+/* ------------------------------------------------------------------ */
+
+/* Q = nu (M[f] - f) for every cell, with M[f] the Maxwellian of the cell's
+ * moments rho, u, T (3/2 rho T = E - rho |u|^2 / 2) evaluated at the grid
+ * points, collision frequency nu = rho / Kn (the paper leaves nu(x, t) free),
+ * followed by the conservation projection if project != 0 (the discrete
+ * Maxwellian does not carry the discrete moments of f exactly). */
+void or_bgk(int n, double L, double inv_kn, int project, long ncells, const double *f, double *Q)
+{
+    double v[64];
+    or_vgrid(n, L, v);
+    long n3 = (long)n * n * n;
+    for (long c = 0; c < ncells; ++c) {
+        double U[5];
+        or_moments(n, L, 1, f + c * n3, U);
+        double rho = U[0];
+        double u[3] = {U[1] / rho, U[2] / rho, U[3] / rho};
+        double T = (U[4] - 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2])) / (1.5 * rho);
+        double nu = rho * inv_kn;
+        double pre = rho * pow(2.0 * OR_PI * T, -1.5);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                for (int k = 0; k < n; ++k) {
+                    double dx = v[i] - u[0], dy = v[j] - u[1], dz = v[k] - u[2];
+                    double M = pre * exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * T));
+                    long id = c * n3 + ((long)i * n + j) * n + k;
+                    Q[id] = nu * (M - f[id]);
+                }
+        if (project) or_project(n, L, Q + c * n3);
+    }
+}

@@ -277,6 +277,7 @@ static void gl_rule(int m, double a, double b, double* x, double* w) {
 using namespace fks;
 
 struct fks_ctx {
+    bool bgk = false;           // BGK relaxation instead of the spectral operator
     fks_grid grid;
     fks_vbox vbox;
     fks_kernel kern;
@@ -495,7 +496,8 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
     }
     if (!(vbox->L > 0.0) || !std::isfinite(vbox->L)) return FKS_ERR_INVALID_ARG;
     if (vbox->n != 8 && vbox->n != 16 && vbox->n != 24 && vbox->n != 32) return FKS_ERR_UNSUPPORTED;
-    if (kernel->type != FKS_HARD_SPHERE && kernel->type != FKS_MAXWELL) return FKS_ERR_INVALID_ARG;
+    if (kernel->type != FKS_HARD_SPHERE && kernel->type != FKS_MAXWELL && kernel->type != FKS_BGK)
+        return FKS_ERR_INVALID_ARG;
     if (!(kernel->C > 0.0) || !(kernel->knudsen > 0.0)) return FKS_ERR_INVALID_ARG;
     if (dirs->A1 < 1 || dirs->A2 < 1 || dirs->A1 * dirs->A2 > 4096 || (dirs->rule != 0 && dirs->rule != 1))
         return FKS_ERR_INVALID_ARG;
@@ -514,8 +516,14 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
     const int nca[3] = {grid->nx, grid->ny, grid->nz};
     for (int a = 0; a < 3; ++a) c->dx[a] = (grid->x1[a] - grid->x0[a]) / nca[a];
     cudaGetDevice(&c->device);
-    fks_status st = configure_variant(c, default_cluster_size(c->fp64, c->n));
-    if (st == FKS_OK) st = build_tables(c);
+    c->bgk = kernel->type == FKS_BGK;
+    fks_status st = FKS_OK;
+    if (!c->bgk) {
+        st = configure_variant(c, default_cluster_size(c->fp64, c->n));
+        if (st == FKS_OK) st = build_tables(c);
+    } else {
+        c->C = 1;
+    }
     if (st == FKS_OK) {
         if (cudaMalloc(&c->d_s, sizeof(double) * 3 * c->n) != cudaSuccess ||
             cudaMalloc(&c->d_delta, 3 * c->n) != cudaSuccess || cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess)
@@ -551,6 +559,7 @@ long fks_launch_count(const fks_ctx* c) { return c ? c->launches : -1; }
 
 fks_status fks_set_cluster_size(fks_ctx* c, int C) {
     if (!c) return FKS_ERR_INVALID_ARG;
+    if (c->bgk) return fail(c, FKS_ERR_UNSUPPORTED, "the BGK kernel has no cluster size");
     if (C == c->C) return FKS_OK;
     // tables are laid out per cluster rank: rebuild them for the new size
     CollideVariant v;
@@ -565,8 +574,32 @@ fks_status fks_set_cluster_size(fks_ctx* c, int C) {
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+static fks_status launch_bgk_ctx(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
+                                 cudaStream_t s) {
+    BgkArgs a;
+    a.f = f;
+    a.out = out;
+    a.delta = delta;
+    a.flags = c->d_flags;
+    a.ncells = c->ncells;
+    a.nc[0] = c->grid.nx;
+    a.nc[1] = c->grid.ny;
+    a.nc[2] = c->grid.nz;
+    for (int i = 0; i < 3; ++i) a.bc[i] = c->grid.bc[i];
+    a.L = c->vbox.L;
+    a.inv_kn = 1.0 / c->kern.knudsen;
+    a.dt = dt;
+    a.mode = mode;
+    std::memcpy(a.P, c->P, sizeof(a.P));
+    cudaError_t e = launch_bgk(c->fp64, c->n, a, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "BGK kernel launch");
+    c->launches += 1;
+    return FKS_OK;
+}
+
 static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
                                  cudaStream_t s) {
+    if (c->bgk) return launch_bgk_ctx(c, f, out, delta, dt, mode, s);
     CollideArgs a;
     a.f = f;
     a.out = out;
@@ -917,6 +950,7 @@ fks_status fks_batch_init(int nprob, const int* n, const double* L, const int* k
         return FKS_ERR_INVALID_ARG;
     for (int i = 0; i < nprob; ++i) {
         if (n[i] != 8 && n[i] != 16 && n[i] != 24 && n[i] != 32) return FKS_ERR_UNSUPPORTED;
+        if (ktype[i] == FKS_BGK) return FKS_ERR_UNSUPPORTED;
         if (!(L[i] > 0.0) || !std::isfinite(L[i]) || (ktype[i] != 0 && ktype[i] != 1) || !(C[i] > 0.0) ||
             !(knudsen[i] > 0.0))
             return FKS_ERR_INVALID_ARG;

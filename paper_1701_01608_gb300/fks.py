@@ -19,6 +19,7 @@ FKS_FP64 = 0
 FKS_FP32 = 1
 HARD_SPHERE = 0
 MAXWELL = 1
+BGK = 2
 PERIODIC = 0
 SPECULAR = 1
 
