@@ -6,22 +6,29 @@
 //   Q   = nu (M - f*), nu = rho / Kn, then the conservation projection
 //   out = Q  or  f* + dt Q
 // One CTA per cell (persistent over cells).  HBM bound: f is read from DRAM
-// once, the two later passes over the cell hit L2, and out is written once.
+// once, the second pass over the cell hits L2, and out is written once.
 #include <cuda_runtime.h>
 
 #include "fks_internal.h"
 
 namespace fks {
 
-template <typename T, int N, int BS>
-__global__ void __launch_bounds__(BS) bgk_kernel(BgkArgs a) {
+// One CTA of BS = 8N threads per cell: thread t owns velocity index z = t % N
+// and the rows (x, y) = t / N + 8 j, so its z-part of the gather offset and of
+// the velocity is fixed.  Two passes over the cell: moments, then output.  The
+// projection sums of Q = nu (M - f) need no pass: M is a product of one-axis
+// factors, so sum phi M follows from one-axis sums, and sum phi f is pass 1.
+template <typename T, int N>
+__global__ void __launch_bounds__(8 * N) bgk_kernel(BgkArgs a) {
+    constexpr int BS = 8 * N;
     constexpr int N3 = N * N * N;
-    constexpr int PER = (N3 + BS - 1) / BS;
-    using Acc = T;   // per-thread partial sums (FP64 in FP64 mode); block sums in FP64
-    __shared__ double red[BS / 32][5];
+    constexpr int ROWS = N * N / 8;   // rows per thread
+    __shared__ double red[(BS + 31) / 32][5];
     __shared__ double cell5[8];
-    __shared__ long src_x[N], src_y[N], src_z[N];   // element offsets of the source row pieces
-    __shared__ T ex[N], ey[N], ez[N];               // separable Maxwellian factors
+    __shared__ double mu[8];
+    __shared__ long src_x[N], src_y[N], src_z[N];   // element offsets of the source pieces
+    __shared__ T gx[N], gy[N], gz[N];               // one-axis Maxwellian factors (gx carries rho (2 pi T)^-3/2)
+    __shared__ T vgT[N];
     __shared__ double vg[N];
     __shared__ signed char dsm[3 * N];
 
@@ -30,9 +37,13 @@ __global__ void __launch_bounds__(BS) bgk_kernel(BgkArgs a) {
     T* __restrict__ fout = static_cast<T*>(a.out);
     const bool transport = a.delta != nullptr;
     const double dv = 2.0 * a.L / N;
-    for (int i = tid; i < N; i += BS) vg[i] = ((double)i + 0.5 - 0.5 * N) * dv;
+    for (int i = tid; i < N; i += BS) {
+        vg[i] = ((double)i + 0.5 - 0.5 * N) * dv;
+        vgT[i] = (T)vg[i];
+    }
     for (int i = tid; i < 3 * N; i += BS) dsm[i] = transport ? a.delta[i] : 0;
     const int ncx = a.nc[0], ncy = a.nc[1], ncz = a.nc[2];
+    const int z = tid % N, r0 = tid / N;
 
     auto block_sum5 = [&](double (&s)[5]) {
 #pragma unroll
@@ -44,7 +55,7 @@ __global__ void __launch_bounds__(BS) bgk_kernel(BgkArgs a) {
         __syncthreads();
         if (tid < 5) {
             double acc = 0.0;
-            for (int w = 0; w < BS / 32; ++w) acc += red[w][tid];
+            for (int w = 0; w < (BS + 31) / 32; ++w) acc += red[w][tid];
             cell5[tid] = acc;
         }
         __syncthreads();
@@ -54,8 +65,7 @@ __global__ void __launch_bounds__(BS) bgk_kernel(BgkArgs a) {
         const int cx = (int)(cell / ((long)ncy * ncz));
         const int cy = (int)((cell / ncz) % ncy);
         const int cz = (int)(cell % ncz);
-        __syncthreads();   // previous cell's readers of the row tables are done
-        // source offsets along each axis: cell part * N^3 + velocity part
+        __syncthreads();   // the previous cell's readers of the shared tables are done
         for (int i = tid; i < 3 * N; i += BS) {
             const int ax = i / N, k = i % N;
             const int c0 = ax == 0 ? cx : (ax == 1 ? cy : cz);
@@ -68,89 +78,83 @@ __global__ void __launch_bounds__(BS) bgk_kernel(BgkArgs a) {
             else src_z[k] = (long)sc * N3 + q;
         }
         __syncthreads();
-        auto load = [&](int e) -> T {
-            const int x = e / (N * N), y = (e / N) % N, z = e % N;
-            return fin[src_x[x] + src_y[y] + src_z[z]];
-        };
-        // pass 1: moments
+        const T* fz = fin + src_z[z];
+        const T vz = vgT[z];
+        // pass 1: moments (per-thread partials in T, block sums in FP64)
         {
-            Acc s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+            T s0 = 0, s1 = 0, s2 = 0, s4 = 0;
 #pragma unroll 4
-            for (int j = 0; j < PER; ++j) {
-                const int e = tid + j * BS;
-                if (e >= N3) break;
-                const T fv = load(e);
-                const int x = e / (N * N), y = (e / N) % N, z = e % N;
-                const T vx = (T)vg[x], vy = (T)vg[y], vz = (T)vg[z];
+            for (int j = 0; j < ROWS; ++j) {
+                const int r = r0 + 8 * j, x = r / N, y = r % N;
+                const T fv = fz[src_x[x] + src_y[y]];
+                const T vx = vgT[x], vy = vgT[y];
                 s0 += fv;
                 s1 += fv * vx;
                 s2 += fv * vy;
-                s3 += fv * vz;
-                s4 += fv * (T)0.5 * (vx * vx + vy * vy + vz * vz);
+                s4 += fv * (vx * vx + vy * vy);
             }
-            double s[5] = {(double)s0, (double)s1, (double)s2, (double)s3, (double)s4};
+            double s[5] = {(double)s0, (double)s1, (double)s2, (double)vz * (double)s0,
+                           0.5 * ((double)s4 + (double)vz * (double)vz * (double)s0)};
             block_sum5(s);
         }
-        const double dv3 = dv * dv * dv;
-        const double rho = cell5[0] * dv3;
-        const double ux = cell5[1] * dv3 / rho, uy = cell5[2] * dv3 / rho, uz = cell5[3] * dv3 / rho;
-        const double Tt = (cell5[4] * dv3 - 0.5 * rho * (ux * ux + uy * uy + uz * uz)) / (1.5 * rho);
-        const double nu = rho * a.inv_kn;
-        __syncthreads();
-        for (int i = tid; i < 3 * N; i += BS) {
-            const int ax = i / N, k = i % N;
-            const double u = ax == 0 ? ux : (ax == 1 ? uy : uz);
-            const double d = vg[k] - u;
-            const double g = exp(-d * d / (2.0 * Tt));
-            (ax == 0 ? ex : (ax == 1 ? ey : ez))[k] = (T)(ax == 0 ? rho * pow(2.0 * 3.14159265358979323846 * Tt, -1.5) * g : g);
+        if (tid < N) {
+            // cell moments, Maxwellian factors, projection coefficients
+            const double dv3 = dv * dv * dv;
+            const double rho = cell5[0] * dv3;
+            const double ux = cell5[1] * dv3 / rho, uy = cell5[2] * dv3 / rho, uz = cell5[3] * dv3 / rho;
+            const double Tt = (cell5[4] * dv3 - 0.5 * rho * (ux * ux + uy * uy + uz * uz)) / (1.5 * rho);
+            const double A = rho * pow(2.0 * 3.14159265358979323846 * Tt, -1.5);
+            const double dx = vg[tid] - ux, dy = vg[tid] - uy, dz = vg[tid] - uz;
+            gx[tid] = (T)(A * exp(-dx * dx / (2.0 * Tt)));
+            gy[tid] = (T)exp(-dy * dy / (2.0 * Tt));
+            gz[tid] = (T)exp(-dz * dz / (2.0 * Tt));
         }
         __syncthreads();
-        const T tnu = (T)nu;
-        auto qval = [&](int e, T fv) -> T {
-            const int x = e / (N * N), y = (e / N) % N, z = e % N;
-            return tnu * (ex[x] * ey[y] * ez[z] - fv);
-        };
-        // pass 2: projection sums of Q
-        {
-            Acc s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
-#pragma unroll 4
-            for (int j = 0; j < PER; ++j) {
-                const int e = tid + j * BS;
-                if (e >= N3) break;
-                const T q = qval(e, load(e));
-                const int x = e / (N * N), y = (e / N) % N, z = e % N;
-                const T vx = (T)vg[x], vy = (T)vg[y], vz = (T)vg[z];
-                s0 += q;
-                s1 += q * vx;
-                s2 += q * vy;
-                s3 += q * vz;
-                s4 += q * (T)0.5 * (vx * vx + vy * vy + vz * vz);
+        if (tid == 0) {
+            const double dv3 = dv * dv * dv;
+            const double nu = cell5[0] * dv3 * a.inv_kn;
+            double X[3], Y[3], Z[3];   // sums of g, v g, v^2 g per axis (of the stored values)
+            for (int k = 0; k < 3; ++k) X[k] = Y[k] = Z[k] = 0.0;
+            for (int i = 0; i < N; ++i) {
+                const double v = vg[i];
+                const double g[3] = {(double)gx[i], (double)gy[i], (double)gz[i]};
+                X[0] += g[0]; X[1] += v * g[0]; X[2] += v * v * g[0];
+                Y[0] += g[1]; Y[1] += v * g[1]; Y[2] += v * v * g[1];
+                Z[0] += g[2]; Z[1] += v * g[2]; Z[2] += v * v * g[2];
             }
-            double s[5] = {(double)s0, (double)s1, (double)s2, (double)s3, (double)s4};
-            block_sum5(s);
+            const double sM[5] = {X[0] * Y[0] * Z[0], X[1] * Y[0] * Z[0], X[0] * Y[1] * Z[0], X[0] * Y[0] * Z[1],
+                                  0.5 * (X[2] * Y[0] * Z[0] + X[0] * Y[2] * Z[0] + X[0] * Y[0] * Z[2])};
+            double sQ[5];
+            for (int i = 0; i < 5; ++i) sQ[i] = nu * (sM[i] - cell5[i]);
+            for (int i = 0; i < 5; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j < 5; ++j) acc += a.P[i * 5 + j] * sQ[j];
+                mu[i] = acc;
+            }
+            mu[5] = nu;
         }
-        double mu[5];
-        for (int i = 0; i < 5; ++i) {
-            double acc = 0.0;
-            for (int j = 0; j < 5; ++j) acc += a.P[i * 5 + j] * cell5[j];
-            mu[i] = acc;
-        }
-        // pass 3: corrected Q, output
-        const T m0 = (T)mu[0], m1 = (T)mu[1], m2 = (T)mu[2], m3 = (T)mu[3], m4 = (T)mu[4];
+        __syncthreads();
+        // pass 2: corrected Q = nu (M - f) - phi.mu, output
+        const T tnu = (T)mu[5];
+        const T m0 = (T)mu[0], m1 = (T)mu[1], m2 = (T)mu[2], m4 = (T)mu[4];
+        const T cz_ = (T)(mu[3] * (double)vz + 0.5 * mu[4] * (double)vz * (double)vz);
+        const T gzz = gz[z];
         const T tdt = (T)a.dt;
+        const bool stepm = a.mode == 1;
+        T* oz = fout + cell * N3 + z;
         bool bad = false, neg = false;
 #pragma unroll 4
-        for (int j = 0; j < PER; ++j) {
-            const int e = tid + j * BS;
-            if (e >= N3) break;
-            const T fv = load(e);
-            const int x = e / (N * N), y = (e / N) % N, z = e % N;
-            const T vx = (T)vg[x], vy = (T)vg[y], vz = (T)vg[z];
-            const T q = qval(e, fv) - (m0 + m1 * vx + m2 * vy + m3 * vz + m4 * (T)0.5 * (vx * vx + vy * vy + vz * vz));
-            const T o = a.mode == 1 ? fv + tdt * q : q;
+        for (int j = 0; j < ROWS; ++j) {
+            const int r = r0 + 8 * j, x = r / N, y = r % N;
+            const T fv = fz[src_x[x] + src_y[y]];
+            const T vx = vgT[x], vy = vgT[y];
+            const T M = gx[x] * gy[y] * gzz;
+            const T corr = m0 + m1 * vx + m2 * vy + (T)0.5 * m4 * (vx * vx + vy * vy) + cz_;
+            const T q = tnu * (M - fv) - corr;
+            const T o = stepm ? fv + tdt * q : q;
             bad |= !isfinite(o);
-            neg |= a.mode == 1 && o < T(0);
-            fout[cell * N3 + e] = o;
+            neg |= stepm && o < T(0);
+            oz[(long)r * N] = o;
         }
         if (bad) atomicOr(a.flags, 1);
         if (neg) atomicOr(a.flags, 2);
@@ -159,9 +163,8 @@ __global__ void __launch_bounds__(BS) bgk_kernel(BgkArgs a) {
 
 template <typename T, int N>
 static cudaError_t launch_n(const BgkArgs& a, cudaStream_t s) {
-    constexpr int BS = 256;
-    long grid = a.ncells < 152L * 8 ? a.ncells : 152L * 8;
-    bgk_kernel<T, N, BS><<<(unsigned)grid, BS, 0, s>>>(a);
+    long grid = a.ncells < 152L * 16 ? a.ncells : 152L * 16;
+    bgk_kernel<T, N><<<(unsigned)grid, 8 * N, 0, s>>>(a);
     return cudaGetLastError();
 }
 
