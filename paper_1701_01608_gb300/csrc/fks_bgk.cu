@@ -19,7 +19,7 @@ namespace fks {
 // projection sums of Q = nu (M - f) need no pass: M is a product of one-axis
 // factors, so sum phi M follows from one-axis sums, and sum phi f is pass 1.
 template <typename T, int N>
-__global__ void __launch_bounds__(8 * N) bgk_kernel(BgkArgs a) {
+__global__ void __launch_bounds__(8 * N, 1024 / (8 * N)) bgk_kernel(BgkArgs a) {
     constexpr int BS = 8 * N;
     constexpr int N3 = N * N * N;
     constexpr int ROWS = N * N / 8;   // rows per thread
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(8 * N) bgk_kernel(BgkArgs a) {
         // pass 1: moments (per-thread partials in T, block sums in FP64)
         {
             T s0 = 0, s1 = 0, s2 = 0, s4 = 0;
-#pragma unroll 4
+#pragma unroll 8
             for (int j = 0; j < ROWS; ++j) {
                 const int r = r0 + 8 * j, x = r / N, y = r % N;
                 const T fv = fz[src_x[x] + src_y[y]];
@@ -110,28 +110,32 @@ __global__ void __launch_bounds__(8 * N) bgk_kernel(BgkArgs a) {
             gz[tid] = (T)exp(-dz * dz / (2.0 * Tt));
         }
         __syncthreads();
-        if (tid == 0) {
+        if (tid < 32) {
+            // one-axis sums of g, v g, v^2 g (of the stored factors) by warp 0, then the
+            // Maxwellian's moment sums, sum phi Q = nu (sum phi M - sum phi f) and mu = P sum phi Q
+            double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            for (int i = tid; i < N; i += 32) {
+                const double v = vg[i];
+                const double g0 = (double)gx[i], g1 = (double)gy[i], g2 = (double)gz[i];
+                acc[0] += g0; acc[1] += v * g0; acc[2] += v * v * g0;
+                acc[3] += g1; acc[4] += v * g1; acc[5] += v * v * g1;
+                acc[6] += g2; acc[7] += v * g2; acc[8] += v * v * g2;
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+            const double *X = acc, *Y = acc + 3, *Z = acc + 6;
             const double dv3 = dv * dv * dv;
             const double nu = cell5[0] * dv3 * a.inv_kn;
-            double X[3], Y[3], Z[3];   // sums of g, v g, v^2 g per axis (of the stored values)
-            for (int k = 0; k < 3; ++k) X[k] = Y[k] = Z[k] = 0.0;
-            for (int i = 0; i < N; ++i) {
-                const double v = vg[i];
-                const double g[3] = {(double)gx[i], (double)gy[i], (double)gz[i]};
-                X[0] += g[0]; X[1] += v * g[0]; X[2] += v * v * g[0];
-                Y[0] += g[1]; Y[1] += v * g[1]; Y[2] += v * v * g[1];
-                Z[0] += g[2]; Z[1] += v * g[2]; Z[2] += v * v * g[2];
-            }
             const double sM[5] = {X[0] * Y[0] * Z[0], X[1] * Y[0] * Z[0], X[0] * Y[1] * Z[0], X[0] * Y[0] * Z[1],
                                   0.5 * (X[2] * Y[0] * Z[0] + X[0] * Y[2] * Z[0] + X[0] * Y[0] * Z[2])};
-            double sQ[5];
-            for (int i = 0; i < 5; ++i) sQ[i] = nu * (sM[i] - cell5[i]);
-            for (int i = 0; i < 5; ++i) {
-                double acc = 0.0;
-                for (int j = 0; j < 5; ++j) acc += a.P[i * 5 + j] * sQ[j];
-                mu[i] = acc;
+            if (tid < 5) {
+                double m = 0.0;
+                for (int j = 0; j < 5; ++j) m += a.P[tid * 5 + j] * nu * (sM[j] - cell5[j]);
+                mu[tid] = m;
             }
-            mu[5] = nu;
+            if (tid == 5) mu[5] = nu;
         }
         __syncthreads();
         // pass 2: corrected Q = nu (M - f) - phi.mu, output
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(8 * N) bgk_kernel(BgkArgs a) {
         const bool stepm = a.mode == 1;
         T* oz = fout + cell * N3 + z;
         bool bad = false, neg = false;
-#pragma unroll 4
+#pragma unroll 8
         for (int j = 0; j < ROWS; ++j) {
             const int r = r0 + 8 * j, x = r / N, y = r % N;
             const T fv = fz[src_x[x] + src_y[y]];
