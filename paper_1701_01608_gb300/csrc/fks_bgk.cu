@@ -13,17 +13,35 @@
 
 namespace fks {
 
-// One CTA of BS = 8N threads per cell: thread t owns velocity index z = t % N
-// and the rows (x, y) = t / N + 8 j, so its z-part of the gather offset and of
-// the velocity is fixed.  Two passes over the cell: moments, then output.  The
-// projection sums of Q = nu (M - f) need no pass: M is a product of one-axis
-// factors, so sum phi M follows from one-axis sums, and sum phi f is pass 1.
+// One CTA of BS = 2N^2/V... threads per cell, organised as rows of N/V lanes:
+// lane group t owns velocity indices z0 .. z0+V-1 (V = 16 bytes / sizeof T)
+// and the rows (x, y) = t / (N/V) + RPI j.  Where the thread's V source
+// elements are contiguous (the usual case) they move as one 16-byte access.
+// Two passes over the cell: moments, then output; the projection sums of
+// Q = nu (M - f) need no pass (M is a product of one-axis factors).  The
+// second read and the output use evict-first hints, so that they do not push
+// out of L2 the cells still waiting for their second pass.
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+    using type = float4;
+};
+template <>
+struct Vec<double> {
+    using type = double2;
+};
+
 template <typename T, int N>
-__global__ void __launch_bounds__(8 * N, 1024 / (8 * N)) bgk_kernel(BgkArgs a) {
-    constexpr int BS = 8 * N;
+__global__ void __launch_bounds__(256, 4) bgk_kernel(BgkArgs a) {
+    constexpr int BS = 256;
+    constexpr int V = 16 / (int)sizeof(T);          // elements per 16-byte access
+    constexpr int LPR = N / V;                       // lanes per row
+    constexpr int RPI = BS / LPR;                    // rows per iteration
+    constexpr int ROWS = (N * N + RPI - 1) / RPI;    // iterations
     constexpr int N3 = N * N * N;
-    constexpr int ROWS = N * N / 8;   // rows per thread
-    __shared__ double red[(BS + 31) / 32][5];
+    using VT = typename Vec<T>::type;
+    __shared__ double red[BS / 32][5];
     __shared__ double cell5[8];
     __shared__ double mu[8];
     __shared__ long src_x[N], src_y[N], src_z[N];   // element offsets of the source pieces
@@ -43,7 +61,8 @@ __global__ void __launch_bounds__(8 * N, 1024 / (8 * N)) bgk_kernel(BgkArgs a) {
     }
     for (int i = tid; i < 3 * N; i += BS) dsm[i] = transport ? a.delta[i] : 0;
     const int ncx = a.nc[0], ncy = a.nc[1], ncz = a.nc[2];
-    const int z = tid % N, r0 = tid / N;
+    const bool lane_ok = tid < LPR * RPI;
+    const int z0 = (tid % LPR) * V, r0 = tid / LPR;
 
     auto block_sum5 = [&](double (&s)[5]) {
 #pragma unroll
@@ -55,7 +74,7 @@ __global__ void __launch_bounds__(8 * N, 1024 / (8 * N)) bgk_kernel(BgkArgs a) {
         __syncthreads();
         if (tid < 5) {
             double acc = 0.0;
-            for (int w = 0; w < (BS + 31) / 32; ++w) acc += red[w][tid];
+            for (int w = 0; w < BS / 32; ++w) acc += red[w][tid];
             cell5[tid] = acc;
         }
         __syncthreads();
@@ -78,45 +97,80 @@ __global__ void __launch_bounds__(8 * N, 1024 / (8 * N)) bgk_kernel(BgkArgs a) {
             else src_z[k] = (long)sc * N3 + q;
         }
         __syncthreads();
-        const T* fz = fin + src_z[z];
-        const T vz = vgT[z];
+        // this thread's V source offsets along z, and whether they are one aligned run
+        long zo[V];
+        bool vec = true;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            zo[k] = src_z[z0 + k];
+            vec &= zo[k] == zo[0] + k;
+        }
+        vec &= (zo[0] % V) == 0;
+        T vz[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) vz[k] = vgT[z0 + k];
+        auto row_base = [&](int r) -> long { return src_x[r / N] + src_y[r % N]; };
+        auto load_run = [&](long rb, T (&v)[V], bool last) {
+            if (vec) {
+                const VT* pv = reinterpret_cast<const VT*>(fin + rb + zo[0]);
+                const VT w = last ? __ldcs(pv) : *pv;
+                const T* pw = reinterpret_cast<const T*>(&w);
+#pragma unroll
+                for (int k = 0; k < V; ++k) v[k] = pw[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) v[k] = last ? __ldcs(fin + rb + zo[k]) : fin[rb + zo[k]];
+            }
+        };
         // pass 1: moments (per-thread partials in T, block sums in FP64)
         {
-            T s0 = 0, s1 = 0, s2 = 0, s4 = 0;
-#pragma unroll 8
-            for (int j = 0; j < ROWS; ++j) {
-                const int r = r0 + 8 * j, x = r / N, y = r % N;
-                const T fv = fz[src_x[x] + src_y[y]];
-                const T vx = vgT[x], vy = vgT[y];
-                s0 += fv;
-                s1 += fv * vx;
-                s2 += fv * vy;
-                s4 += fv * (vx * vx + vy * vy);
+            T s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+            if (lane_ok) {
+#pragma unroll 4
+                for (int j = 0; j < ROWS; ++j) {
+                    const int r = r0 + RPI * j;
+                    if (r >= N * N) break;
+                    T v[V];
+                    load_run(row_base(r), v, false);
+                    const T vx = vgT[r / N], vy = vgT[r % N];
+                    T sr = 0, sz = 0, szz = 0;
+#pragma unroll
+                    for (int k = 0; k < V; ++k) {
+                        sr += v[k];
+                        sz += v[k] * vz[k];
+                        szz += v[k] * vz[k] * vz[k];
+                    }
+                    s0 += sr;
+                    s1 += sr * vx;
+                    s2 += sr * vy;
+                    s3 += sz;
+                    s4 += sr * (vx * vx + vy * vy) + szz;
+                }
             }
-            double s[5] = {(double)s0, (double)s1, (double)s2, (double)vz * (double)s0,
-                           0.5 * ((double)s4 + (double)vz * (double)vz * (double)s0)};
+            double s[5] = {(double)s0, (double)s1, (double)s2, (double)s3, 0.5 * (double)s4};
             block_sum5(s);
         }
         if (tid < N) {
-            // cell moments, Maxwellian factors, projection coefficients
+            // cell moments and the Maxwellian's one-axis factors (in T)
             const double dv3 = dv * dv * dv;
             const double rho = cell5[0] * dv3;
             const double ux = cell5[1] * dv3 / rho, uy = cell5[2] * dv3 / rho, uz = cell5[3] * dv3 / rho;
             const double Tt = (cell5[4] * dv3 - 0.5 * rho * (ux * ux + uy * uy + uz * uz)) / (1.5 * rho);
-            const double A = rho * pow(2.0 * 3.14159265358979323846 * Tt, -1.5);
-            const double dx = vg[tid] - ux, dy = vg[tid] - uy, dz = vg[tid] - uz;
-            gx[tid] = (T)(A * exp(-dx * dx / (2.0 * Tt)));
-            gy[tid] = (T)exp(-dy * dy / (2.0 * Tt));
-            gz[tid] = (T)exp(-dz * dz / (2.0 * Tt));
+            const T A = (T)(rho / (2.0 * 3.14159265358979323846 * Tt * sqrt(2.0 * 3.14159265358979323846 * Tt)));
+            const T i2T = (T)(0.5 / Tt);
+            const T dx = vgT[tid] - (T)ux, dy = vgT[tid] - (T)uy, dz = vgT[tid] - (T)uz;
+            gx[tid] = A * exp(-dx * dx * i2T);
+            gy[tid] = exp(-dy * dy * i2T);
+            gz[tid] = exp(-dz * dz * i2T);
         }
         __syncthreads();
         if (tid < 32) {
             // one-axis sums of g, v g, v^2 g (of the stored factors) by warp 0, then the
             // Maxwellian's moment sums, sum phi Q = nu (sum phi M - sum phi f) and mu = P sum phi Q
-            double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            T acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int i = tid; i < N; i += 32) {
-                const double v = vg[i];
-                const double g0 = (double)gx[i], g1 = (double)gy[i], g2 = (double)gz[i];
+                const T v = vgT[i];
+                const T g0 = gx[i], g1 = gy[i], g2 = gz[i];
                 acc[0] += g0; acc[1] += v * g0; acc[2] += v * v * g0;
                 acc[3] += g1; acc[4] += v * g1; acc[5] += v * v * g1;
                 acc[6] += g2; acc[7] += v * g2; acc[8] += v * v * g2;
@@ -125,50 +179,74 @@ __global__ void __launch_bounds__(8 * N, 1024 / (8 * N)) bgk_kernel(BgkArgs a) {
             for (int k = 0; k < 9; ++k)
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
-            const double *X = acc, *Y = acc + 3, *Z = acc + 6;
-            const double dv3 = dv * dv * dv;
-            const double nu = cell5[0] * dv3 * a.inv_kn;
-            const double sM[5] = {X[0] * Y[0] * Z[0], X[1] * Y[0] * Z[0], X[0] * Y[1] * Z[0], X[0] * Y[0] * Z[1],
-                                  0.5 * (X[2] * Y[0] * Z[0] + X[0] * Y[2] * Z[0] + X[0] * Y[0] * Z[2])};
-            if (tid < 5) {
-                double m = 0.0;
-                for (int j = 0; j < 5; ++j) m += a.P[tid * 5 + j] * nu * (sM[j] - cell5[j]);
-                mu[tid] = m;
+            if (tid < 6) {
+                double X[3], Y[3], Z[3];
+                for (int k = 0; k < 3; ++k) {
+                    X[k] = (double)acc[k];
+                    Y[k] = (double)acc[3 + k];
+                    Z[k] = (double)acc[6 + k];
+                }
+                const double dv3 = dv * dv * dv;
+                const double nu = cell5[0] * dv3 * a.inv_kn;
+                const double sM[5] = {X[0] * Y[0] * Z[0], X[1] * Y[0] * Z[0], X[0] * Y[1] * Z[0], X[0] * Y[0] * Z[1],
+                                      0.5 * (X[2] * Y[0] * Z[0] + X[0] * Y[2] * Z[0] + X[0] * Y[0] * Z[2])};
+                if (tid < 5) {
+                    double m = 0.0;
+                    for (int j = 0; j < 5; ++j) m += a.P[tid * 5 + j] * nu * (sM[j] - cell5[j]);
+                    mu[tid] = m;
+                } else {
+                    mu[5] = nu;
+                }
             }
-            if (tid == 5) mu[5] = nu;
         }
         __syncthreads();
         // pass 2: corrected Q = nu (M - f) - phi.mu, output
-        const T tnu = (T)mu[5];
-        const T m0 = (T)mu[0], m1 = (T)mu[1], m2 = (T)mu[2], m4 = (T)mu[4];
-        const T cz_ = (T)(mu[3] * (double)vz + 0.5 * mu[4] * (double)vz * (double)vz);
-        const T gzz = gz[z];
-        const T tdt = (T)a.dt;
-        const bool stepm = a.mode == 1;
-        T* oz = fout + cell * N3 + z;
-        bool bad = false, neg = false;
-#pragma unroll 8
-        for (int j = 0; j < ROWS; ++j) {
-            const int r = r0 + 8 * j, x = r / N, y = r % N;
-            const T fv = fz[src_x[x] + src_y[y]];
-            const T vx = vgT[x], vy = vgT[y];
-            const T M = gx[x] * gy[y] * gzz;
-            const T corr = m0 + m1 * vx + m2 * vy + (T)0.5 * m4 * (vx * vx + vy * vy) + cz_;
-            const T q = tnu * (M - fv) - corr;
-            const T o = stepm ? fv + tdt * q : q;
-            bad |= !isfinite(o);
-            neg |= stepm && o < T(0);
-            oz[(long)r * N] = o;
+        if (lane_ok) {
+            const T tnu = (T)mu[5];
+            const T m0 = (T)mu[0], m1 = (T)mu[1], m2 = (T)mu[2], m3 = (T)mu[3], m4 = (T)mu[4];
+            T gzz[V], czz[V];
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                gzz[k] = gz[z0 + k];
+                czz[k] = m3 * vz[k] + (T)0.5 * m4 * vz[k] * vz[k];
+            }
+            const T tdt = (T)a.dt;
+            const bool stepm = a.mode == 1;
+            T* oc = fout + cell * N3 + z0;
+            bool bad = false, neg = false;
+#pragma unroll 4
+            for (int j = 0; j < ROWS; ++j) {
+                const int r = r0 + RPI * j;
+                if (r >= N * N) break;
+                T v[V];
+                load_run(row_base(r), v, true);
+                const T vx = vgT[r / N], vy = vgT[r % N];
+                const T gxy = gx[r / N] * gy[r % N];
+                const T cxy = m0 + m1 * vx + m2 * vy + (T)0.5 * m4 * (vx * vx + vy * vy);
+                T o[V];
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const T q = tnu * (gxy * gzz[k] - v[k]) - (cxy + czz[k]);
+                    o[k] = stepm ? v[k] + tdt * q : q;
+                    bad |= !isfinite(o[k]);
+                    neg |= stepm && o[k] < T(0);
+                }
+                VT w;
+                T* pw = reinterpret_cast<T*>(&w);
+#pragma unroll
+                for (int k = 0; k < V; ++k) pw[k] = o[k];
+                __stcs(reinterpret_cast<VT*>(oc + (long)r * N), w);
+            }
+            if (bad) atomicOr(a.flags, 1);
+            if (neg) atomicOr(a.flags, 2);
         }
-        if (bad) atomicOr(a.flags, 1);
-        if (neg) atomicOr(a.flags, 2);
     }
 }
 
 template <typename T, int N>
 static cudaError_t launch_n(const BgkArgs& a, cudaStream_t s) {
-    long grid = a.ncells < 152L * 16 ? a.ncells : 152L * 16;
-    bgk_kernel<T, N><<<(unsigned)grid, 8 * N, 0, s>>>(a);
+    long grid = a.ncells < 152L * 8 ? a.ncells : 152L * 8;
+    bgk_kernel<T, N><<<(unsigned)grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
