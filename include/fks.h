@@ -184,6 +184,51 @@ long fks_batch_launch_count(const fks_batch *b);
 void fks_batch_destroy(fks_batch *b);
 const char *fks_batch_last_error(const fks_batch *b);
 
+/* ---------------------------------------------------------------- learned surrogate
+ * A convolutional surrogate of the collision operator for cells near
+ * equilibrium (an extension, not in the paper): six 3x3x3 convolutions over
+ * the n^3 velocity grid, channels 2 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU
+ * between layers, zero padding, BF16 weights and FP32 accumulation.  Inputs
+ * per cell: f / rho and M[f] / rho; output y ~ Q Kn / (rho^2 out_scale).  The
+ * parameters are one flat FP32 master vector: per layer W[co][ci][27] (tap
+ * (dx+1)*9 + (dy+1)*3 + (dz+1)) then bias[co].  n must be a multiple of 8.
+ * The network owns its activations for batches of up to max_batch cells. */
+typedef struct fks_net fks_net;
+
+fks_status fks_net_init(int n, int max_batch, unsigned long long seed, fks_net **out);
+long fks_net_num_params(const fks_net *net);
+/* host copies of the FP32 master parameters (count = fks_net_num_params) */
+fks_status fks_net_set_params(fks_net *net, const float *host, long count);
+fks_status fks_net_get_params(fks_net *net, float *host, long count);
+/* y[b][n^3] = net(x[b][2][n^3]) for b < batch (device arrays) */
+fks_status fks_net_forward(fks_net *net, int batch, const float *x, float *y, void *stream);
+/* grad (device, num_params floats) = d(sum gy * y)/d params, through the BF16
+ * weights (the rounding is treated as the identity) */
+fks_status fks_net_gradient(fks_net *net, int batch, const float *x, const float *gy, float *grad, void *stream);
+/* one Adam step on the mean squared error against target; *loss (device
+ * float) is incremented by the batch's loss */
+fks_status fks_net_train_step(fks_net *net, int batch, const float *x, const float *target, float lr, float *loss,
+                              void *stream);
+long fks_net_launch_count(const fks_net *net);
+const char *fks_net_last_error(const fks_net *net);
+void fks_net_destroy(fks_net *net);
+
+/* Network inputs of ncells FP32 cells: x[c] = (f/rho, M[f]/rho), rho[c]
+ * (FP64) and dist[c] = ||f/rho - M/rho|| / ||M/rho|| (device arrays). */
+fks_status fks_surrogate_inputs(int n, double L, long ncells, const float *f, float *x, double *rho, float *dist,
+                                void *stream);
+
+/* Q for every cell of an FP32 spectral context by the surrogate: Q = rho^2 y
+ * out_scale / Kn, projected onto the conservation constraints; indicator =
+ * ind_scale (dist + relative moment defect of the raw output); cells whose
+ * indicator exceeds `threshold` (or is not finite) are recomputed with the
+ * spectral operator.  Synchronises `stream` once (to read the routed count,
+ * stored in *nrouted). */
+fks_status fks_surrogate_collide(fks_ctx *ctx, fks_net *net, const void *f, void *Q, double out_scale,
+                                 double ind_scale, double threshold, long *nrouted, void *stream);
+/* host copy of the last indicators (count = number of cells) */
+fks_status fks_surrogate_indicator(const fks_ctx *ctx, float *host, long count);
+
 /* fks_transport_noalloc -- the transport of fks_transport for callers that
  * cannot allocate device memory.  It is an addition of this library; the
  * paper has no counterpart.

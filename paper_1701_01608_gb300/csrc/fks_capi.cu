@@ -276,28 +276,6 @@ static void gl_rule(int m, double a, double b, double* x, double* w) {
 
 using namespace fks;
 
-struct fks_ctx {
-    bool bgk = false;           // BGK relaxation instead of the spectral operator
-    fks_grid grid;
-    fks_vbox vbox;
-    fks_kernel kern;
-    fks_dirs dirs;
-    bool fp64;
-    int n, M, C;
-    long ncells;
-    double dx[3];
-    void* tables = nullptr;     // collision-kernel layout, element T
-    double* d_s = nullptr;      // [3][n] offsets
-    signed char* d_delta = nullptr;
-    int* d_flags = nullptr;
-    double P[25];
-    CollideVariant var;
-    int max_clusters = 0;
-    long launches = 0;
-    std::string err;
-    int device = 0;
-};
-
 static fks_status fail(fks_ctx* c, fks_status s, const std::string& msg) {
     if (c) c->err = msg;
     return s;
@@ -538,6 +516,11 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
         return st;
     }
     projection_matrix(c->n, c->vbox.L, c->P);
+    if (cudaMalloc(&c->d_P, sizeof(c->P)) != cudaSuccess ||
+        cudaMemcpy(c->d_P, c->P, sizeof(c->P), cudaMemcpyHostToDevice) != cudaSuccess) {
+        fks_destroy(c);
+        return FKS_ERR_OOM;
+    }
     *out = c;
     return FKS_OK;
 }
@@ -548,6 +531,12 @@ void fks_destroy(fks_ctx* c) {
     cudaFree(c->d_s);
     cudaFree(c->d_delta);
     cudaFree(c->d_flags);
+    cudaFree(c->d_P);
+    cudaFree(c->s_rho);
+    cudaFree(c->s_dist);
+    cudaFree(c->s_ind);
+    cudaFree(c->s_items);
+    cudaFree(c->s_count);
     delete c;
 }
 

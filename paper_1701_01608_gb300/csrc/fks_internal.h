@@ -3,7 +3,9 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <string>
 
+#include "../../include/fks.h"
 #include "fks_collide.cuh"
 
 namespace fks {
@@ -40,3 +42,40 @@ cudaError_t launch_bgk(bool fp64, int n, const BgkArgs& a, cudaStream_t s);
 int default_cluster_size(bool fp64, int N);
 
 }  // namespace fks
+
+// Context state (fks_capi.cu); visible to the other translation units.
+struct fks_ctx {
+    bool bgk = false;           // BGK relaxation instead of the spectral operator
+    fks_grid grid;
+    fks_vbox vbox;
+    fks_kernel kern;
+    fks_dirs dirs;
+    bool fp64;
+    int n, M, C;
+    long ncells;
+    double dx[3];
+    void* tables = nullptr;     // collision-kernel layout, element T
+    double* d_s = nullptr;      // [3][n] offsets
+    signed char* d_delta = nullptr;
+    int* d_flags = nullptr;
+    double P[25];
+    fks::CollideVariant var;
+    int max_clusters = 0;
+    long launches = 0;
+    std::string err;
+    int device = 0;
+    double* d_P = nullptr;      // device copy of P (batch-mode descriptors)
+    // surrogate routing workspace (allocated on first use)
+    double* s_rho = nullptr;
+    float* s_dist = nullptr;
+    float* s_ind = nullptr;
+    fks::BatchItem* s_items = nullptr;
+    int* s_count = nullptr;
+};
+
+
+// Surrogate network internals (fks_net.cu) used by the routing path.
+const float* fks_net_forward_internal(fks_net* m, int batch, const float* x, cudaStream_t s, fks_status* st);
+float* fks_net_input_buffer(fks_net* m);
+int fks_net_grid(const fks_net* m);
+int fks_net_max_batch(const fks_net* m);

@@ -59,7 +59,10 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_last_error", "fks_status_string", "fks_transport_noalloc",
            "fks_batch_init", "fks_batch_collide", "fks_batch_step", "fks_batch_run", "fks_batch_check",
            "fks_batch_cluster_size", "fks_batch_set_cluster_size", "fks_batch_launch_count",
-           "fks_batch_destroy", "fks_batch_last_error"]
+           "fks_batch_destroy", "fks_batch_last_error",
+           "fks_net_init", "fks_net_num_params", "fks_net_set_params", "fks_net_get_params", "fks_net_forward",
+           "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
+           "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator"]
 
 
 def lib(build: bool = True):
@@ -109,6 +112,23 @@ def lib(build: bool = True):
     L.fks_batch_destroy.restype = None
     L.fks_batch_last_error.argtypes = [P]
     L.fks_batch_last_error.restype = ctypes.c_char_p
+    L.fks_net_init.argtypes = [I, I, ctypes.c_ulonglong, PP]
+    L.fks_net_num_params.argtypes = [P]
+    L.fks_net_num_params.restype = ctypes.c_long
+    L.fks_net_set_params.argtypes = [P, P, ctypes.c_long]
+    L.fks_net_get_params.argtypes = [P, P, ctypes.c_long]
+    L.fks_net_forward.argtypes = [P, I, P, P, P]
+    L.fks_net_gradient.argtypes = [P, I, P, P, P, P]
+    L.fks_net_train_step.argtypes = [P, I, P, P, ctypes.c_float, P, P]
+    L.fks_net_launch_count.argtypes = [P]
+    L.fks_net_launch_count.restype = ctypes.c_long
+    L.fks_net_last_error.argtypes = [P]
+    L.fks_net_last_error.restype = ctypes.c_char_p
+    L.fks_net_destroy.argtypes = [P]
+    L.fks_net_destroy.restype = None
+    L.fks_surrogate_inputs.argtypes = [I, D, ctypes.c_long, P, P, P, P, P]
+    L.fks_surrogate_collide.argtypes = [P, P, P, P, D, D, D, ctypes.POINTER(ctypes.c_long), P]
+    L.fks_surrogate_indicator.argtypes = [P, P, ctypes.c_long]
     L.fks_destroy.argtypes = [P]
     L.fks_destroy.restype = None
     L.fks_last_error.argtypes = [P]
@@ -229,6 +249,22 @@ class Context:
         self._check(st, "fks_check")
         return bits.value
 
+    def surrogate_collide(self, net: "Net", f, Q, out_scale: float, ind_scale: float, threshold: float,
+                          stream=None) -> int:
+        """Q by the learned surrogate, cells over the indicator threshold by the spectral operator;
+        returns the number of routed cells."""
+        nr = ctypes.c_long()
+        self._check(self._L.fks_surrogate_collide(self._h, net._h, _dptr(f, self.dtype), _dptr(Q, self.dtype),
+                                                  float(out_scale), float(ind_scale), float(threshold),
+                                                  ctypes.byref(nr), _stream_ptr(stream)), "fks_surrogate_collide")
+        return nr.value
+
+    def indicator(self) -> np.ndarray:
+        out = np.empty(self.ncells, dtype=np.float32)
+        self._check(self._L.fks_surrogate_indicator(self._h, out.ctypes.data_as(ctypes.c_void_p), self.ncells),
+                    "fks_surrogate_indicator")
+        return out
+
     def offsets(self) -> np.ndarray:
         s = np.empty((3, self.cfg.n))
         self._check(self._L.fks_get_offsets(self._h, s.ctypes.data_as(ctypes.c_void_p)), "fks_get_offsets")
@@ -314,3 +350,69 @@ class Batch:
     @property
     def launches(self) -> int:
         return self._L.fks_batch_launch_count(self._h)
+
+
+class Net:
+    """fks_net: the convolutional collision surrogate (BF16 weights, FP32 accumulation)."""
+
+    def __init__(self, n: int, max_batch: int, seed: int = 0):
+        self._L = lib()
+        h = ctypes.c_void_p()
+        st = self._L.fks_net_init(n, max_batch, seed, ctypes.byref(h))
+        if st != 0:
+            raise FKSError(st, "fks_net_init")
+        self._h = h
+        self.n = n
+        self.max_batch = max_batch
+        self.num_params = int(self._L.fks_net_num_params(h))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.fks_net_destroy(h)
+            self._h = None
+
+    def _check(self, st, what):
+        if st != 0:
+            raise FKSError(st, f"{what}: {self._L.fks_net_last_error(self._h).decode()}")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        self._check(self._L.fks_net_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p), self.num_params),
+                    "fks_net_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self._L.fks_net_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p), p.size),
+                    "fks_net_set_params")
+
+    def forward(self, x, y, stream=None):
+        import torch
+        self._check(self._L.fks_net_forward(self._h, x.shape[0], _dptr(x, torch.float32), _dptr(y, torch.float32),
+                                            _stream_ptr(stream)), "fks_net_forward")
+
+    def gradient(self, x, gy, grad, stream=None):
+        import torch
+        self._check(self._L.fks_net_gradient(self._h, x.shape[0], _dptr(x, torch.float32),
+                                             _dptr(gy, torch.float32), _dptr(grad, torch.float32),
+                                             _stream_ptr(stream)), "fks_net_gradient")
+
+    def train_step(self, x, target, lr: float, loss, stream=None):
+        import torch
+        self._check(self._L.fks_net_train_step(self._h, x.shape[0], _dptr(x, torch.float32),
+                                               _dptr(target, torch.float32), float(lr), _dptr(loss, torch.float32),
+                                               _stream_ptr(stream)), "fks_net_train_step")
+
+    @property
+    def launches(self) -> int:
+        return self._L.fks_net_launch_count(self._h)
+
+
+def surrogate_inputs(n: int, L: float, f, x, rho, dist, stream=None):
+    """x = (f/rho, M[f]/rho), rho (FP64), dist = ||f/rho - M/rho|| / ||M/rho|| for every cell of f."""
+    import torch
+    st = lib().fks_surrogate_inputs(n, float(L), f.shape[0], _dptr(f, torch.float32), _dptr(x, torch.float32),
+                                    _dptr(rho, torch.float64), _dptr(dist, torch.float32), _stream_ptr(stream))
+    if st != 0:
+        raise FKSError(st, "fks_surrogate_inputs")

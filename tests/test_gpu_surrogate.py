@@ -1,0 +1,129 @@
+"""Learned surrogate on the GPU: network forward and gradients against the
+FP64 oracle network (same BF16-rounded weights), training sanity, network
+inputs, and the routed surrogate collision (all-routed equals the spectral
+operator bit for bit; none-routed equals the oracle network + projection)."""
+import numpy as np
+import pytest
+
+from oracle import net as onet
+from paper_1701_01608_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fks():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_01608_gb300 import fks
+    fks.lib()
+    return fks
+
+
+def oracle_params(p32):
+    """FP32 master -> the values the GPU computes with: BF16 weights, FP32 biases."""
+    p = p32.astype(np.float64).copy()
+    off = 0
+    for co, ci in onet.layer_shapes():
+        p[off:off + co * ci * 27] = onet.bf16_round(p32[off:off + co * ci * 27])
+        off += co * ci * 27 + co
+    return p
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_forward_matches_oracle(fks, n):
+    net = fks.Net(n, 2, seed=3)
+    rng = np.random.default_rng(n)
+    x = rng.random((2, 2, n, n, n)).astype(np.float32)
+    y = torch.empty((2, 1, n, n, n), device="cuda")
+    net.forward(torch.from_numpy(x).cuda(), y)
+    yo, _ = onet.forward(oracle_params(net.get_params()), x.astype(np.float64))
+    assert rel(y.cpu().numpy(), yo) < 2e-5
+
+
+def test_gradient_matches_oracle(fks):
+    n = 16
+    net = fks.Net(n, 2, seed=5)
+    rng = np.random.default_rng(1)
+    x = rng.random((2, 2, n, n, n)).astype(np.float32)
+    gy = rng.standard_normal((2, 1, n, n, n)).astype(np.float32)
+    grad = torch.empty(net.num_params, device="cuda")
+    net.gradient(torch.from_numpy(x).cuda(), torch.from_numpy(gy).cuda(), grad)
+    po = oracle_params(net.get_params())
+    _, acts = onet.forward(po, x.astype(np.float64))
+    go = onet.backward(po, acts, gy.astype(np.float64))
+    g = grad.cpu().numpy()
+    off = 0
+    for co, ci in onet.layer_shapes():
+        for size in (co * ci * 27, co):
+            assert rel(g[off:off + size], go[off:off + size]) < 1e-4, (co, ci, size)
+            off += size
+
+
+def test_training_reduces_loss(fks):
+    n = 8
+    net = fks.Net(n, 4, seed=7)
+    rng = np.random.default_rng(2)
+    x = torch.from_numpy(rng.random((4, 2, n, n, n)).astype(np.float32)).cuda()
+    t = torch.from_numpy(0.1 * rng.standard_normal((4, 1, n, n, n)).astype(np.float32)).cuda()
+    losses = []
+    for _ in range(30):
+        loss = torch.zeros(1, device="cuda")
+        net.train_step(x, t, 1e-3, loss)
+        losses.append(loss.item())
+    assert losses[-1] < 0.5 * losses[0]
+
+
+def test_network_inputs(fks, oracle):
+    n, L = 16, 8.0
+    f = I.two_stream((3, 1, 1), n, L, seed=4, noise=0.05).astype(np.float32)
+    fd = torch.from_numpy(f).cuda()
+    x = torch.empty((3, 2, n, n, n), device="cuda")
+    rho = torch.empty(3, dtype=torch.float64, device="cuda")
+    dist = torch.empty(3, device="cuda")
+    fks.surrogate_inputs(n, L, fd, x, rho, dist)
+    U = oracle.moments(f.astype(np.float64), n, L)
+    for c in range(3):
+        r = U[c, 0]
+        u = U[c, 1:4] / r
+        T = (U[c, 4] - 0.5 * r * u @ u) / (1.5 * r)
+        M = I.maxwellian(n, L, 1.0, u, T)
+        g = f[c] / r
+        assert abs(rho[c].item() - r) < 1e-12 * r
+        np.testing.assert_allclose(x[c, 0].cpu().numpy(), g, rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(x[c, 1].cpu().numpy(), M, rtol=1e-5, atol=1e-9 * M.max())
+        assert abs(dist[c].item() - np.linalg.norm(g - M) / np.linalg.norm(M)) < 1e-5
+
+
+def test_routed_surrogate_collide(fks, oracle):
+    n, L, kn = 16, 8.0, 0.3
+    ctx = fks.Context(fks.Config(ncell=(5, 1, 1), n=n, L=L, kn=kn, A1=4, A2=4, precision=fks.FKS_FP32))
+    net = fks.Net(n, 2, seed=11)   # batches of 2 over 5 cells: a ragged last batch
+    f = I.two_stream((5, 1, 1), n, L, seed=6, noise=0.05).astype(np.float32)
+    fd = torch.from_numpy(f).cuda()
+    Qs = torch.empty_like(fd)
+    ctx.collide(fd, Qs)
+    Q = torch.empty_like(fd)
+    assert ctx.surrogate_collide(net, fd, Q, 1.0, 1.0, -1.0) == 5          # every cell routed
+    assert torch.equal(Q, Qs)
+    assert ctx.surrogate_collide(net, fd, Q, 2.5, 1.0, 1e30) == 0          # none routed
+    ind = ctx.indicator()
+    assert np.all(np.isfinite(ind)) and np.all(ind > 0)
+    # oracle: network on the same inputs, rho^2 y scale / Kn, projection
+    po = oracle_params(net.get_params())
+    U = oracle.moments(f.astype(np.float64), n, L)
+    xs = []
+    for c in range(5):
+        r = U[c, 0]
+        u = U[c, 1:4] / r
+        T = (U[c, 4] - 0.5 * r * u @ u) / (1.5 * r)
+        xs.append(np.stack([f[c] / r, I.maxwellian(n, L, 1.0, u, T)]))
+    yo, _ = onet.forward(po, np.stack(xs))
+    Qo = np.stack([(U[c, 0] ** 2) * yo[c, 0] * 2.5 / kn for c in range(5)])
+    Qo = oracle.project(Qo, n, L)
+    assert rel(Q.cpu().numpy(), Qo) < 1e-4
