@@ -69,14 +69,16 @@ def test_training_reduces_loss(fks):
     n = 8
     net = fks.Net(n, 4, seed=7)
     rng = np.random.default_rng(2)
-    x = torch.from_numpy(rng.random((4, 2, n, n, n)).astype(np.float32)).cuda()
-    t = torch.from_numpy(0.1 * rng.standard_normal((4, 1, n, n, n)).astype(np.float32)).cuda()
+    xh = rng.random((4, 2, n, n, n)).astype(np.float32)
+    x = torch.from_numpy(xh).cuda()
+    # a target the network can represent: a relaxation-like difference of its inputs
+    t = torch.from_numpy(0.5 * (xh[:, 1:2] - xh[:, 0:1])).cuda()
     losses = []
-    for _ in range(30):
+    for _ in range(60):
         loss = torch.zeros(1, device="cuda")
-        net.train_step(x, t, 1e-3, loss)
+        net.train_step(x, t, 3e-3, loss)
         losses.append(loss.item())
-    assert losses[-1] < 0.5 * losses[0]
+    assert losses[-1] < 0.25 * losses[0]
 
 
 def test_network_inputs(fks, oracle):
