@@ -129,3 +129,33 @@ def test_routed_surrogate_collide(fks, oracle):
     Qo = np.stack([(U[c, 0] ** 2) * yo[c, 0] * 2.5 / kn for c in range(5)])
     Qo = oracle.project(Qo, n, L)
     assert rel(Q.cpu().numpy(), Qo) < 1e-4
+
+
+def test_train_calibrate_route(fks):
+    """Train a small surrogate on spectral (f, Q) pairs, calibrate its indicator
+    on held-out cells, and check the routing contract: with a threshold, every
+    cell is either exact (routed to the spectral operator) or has a calibrated
+    indicator below the threshold."""
+    from paper_1701_01608_gb300 import surrogate as S
+    n, L = 16, 8.0
+    f = torch.cat([S.two_stream_cells(torch, 48, n=n, L=L, seed=3)])
+    Q = S.labels(torch, f, n=n, L=L, kn=1.0)
+    sur = S.train(torch, f, Q, epochs=6, batch=8, lr=2e-3, n=n, L=L, holdout=0.25)
+    assert sur.train_loss[-1] < sur.train_loss[0]
+    assert sur.calib["covered"] >= 0.9
+    ctx = fks.Context(fks.Config(ncell=(f.shape[0], 1, 1), n=n, L=L, kn=1.0, A1=4, A2=8, precision=fks.FKS_FP32))
+    out = torch.empty_like(f)
+    thr = float(np.median(sur.ind_scale * ctx_indicators(fks, ctx, sur, f)))
+    routed = ctx.surrogate_collide(sur.net, f, out, sur.out_scale, sur.ind_scale, thr)
+    ind = ctx.indicator()
+    assert 0 < routed < f.shape[0]
+    Qh, oh = Q.cpu().numpy(), out.cpu().numpy()
+    for c in range(f.shape[0]):
+        if not ind[c] <= thr:
+            assert np.array_equal(oh[c], Qh[c])      # routed: the spectral result itself
+
+
+def ctx_indicators(fks, ctx, sur, f):
+    tmp = torch.empty_like(f)
+    ctx.surrogate_collide(sur.net, f, tmp, sur.out_scale, 1.0, 1e30)
+    return ctx.indicator()
