@@ -150,6 +150,62 @@ def cpu_baseline(sample_cells: int = 16, fp32_input=None) -> dict:
             "seconds": el}
 
 
+def learned_path(torch, fks, dev, args, sample=512, threshold=1e-3):
+    """Learned surrogate collision (BF16 conv net, calibrated indicator, cells over the
+    threshold routed to the FP32 spectral operator) against the FP32 spectral collision
+    and the FP64 spectral operator, on a sample of non-equilibrium cells of the
+    workload's velocity grid (shock-tube cells after a few steps, two-stream cells)."""
+    from paper_1701_01608_gb300 import surrogate as S
+    t0 = time.perf_counter()
+    ftr = torch.cat([S.shock_tube_cells(torch, NV, LBOX, nx=32, ny=2, nz=2, steps=(0, 4, 8, 16), seed=0),
+                     S.two_stream_cells(torch, 128, NV, LBOX, seed=1)])
+    Qtr = S.labels(torch, ftr, NV, LBOX, kn=1.0)
+    sur = S.train(torch, ftr, Qtr, epochs=8, batch=8, lr=2e-3, n=NV, L=LBOX, holdout=0.2)
+    train_s = time.perf_counter() - t0
+    del ftr, Qtr
+    f = torch.cat([S.shock_tube_cells(torch, NV, LBOX, nx=32, ny=4, nz=2, steps=(6,), seed=5)[:sample - 64],
+                   S.two_stream_cells(torch, 64, NV, LBOX, seed=9)]).contiguous()
+    nc = f.shape[0]
+    c32 = fks.Context(fks.Config(ncell=(nc, 1, 1), n=NV, L=LBOX, kn=KN, A1=A1, A2=A2, precision=fks.FKS_FP32))
+    c64 = fks.Context(fks.Config(ncell=(nc, 1, 1), n=NV, L=LBOX, kn=KN, A1=A1, A2=A2, precision=fks.FKS_FP64))
+    Q64 = torch.empty(f.shape, dtype=torch.float64, device=dev)
+    c64.collide(f.double(), Q64)
+    Qs = torch.empty_like(f)
+    Ql = torch.empty_like(f)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        return s.elapsed_time(e) / reps
+
+    t_spec = timed(lambda: c32.collide(f, Qs))
+    routed = [0]
+    t_learn = timed(lambda: routed.__setitem__(0, c32.surrogate_collide(sur.net, f, Ql, sur.out_scale,
+                                                                        sur.ind_scale, threshold)))
+
+    def err(Q):
+        d = (Q.double() - Q64).flatten(1).norm(dim=1) / Q64.flatten(1).norm(dim=1)
+        return float(d.max().item()), float(d.median().item())
+
+    el, ml = err(Ql)
+    es, ms = err(Qs)
+    pts = nc * NV ** 3
+    return {"value": pts / (t_learn / 1e3), "unit": "pts/s", "ms": t_learn, "cells": nc,
+            "routed_fraction": routed[0] / nc, "threshold": threshold,
+            "err_vs_fp64": {"max": el, "median": ml},
+            "spectral_fp32_collide": {"value": pts / (t_spec / 1e3), "ms": t_spec, "err_vs_fp64": {"max": es, "median": ms}},
+            "speedup_vs_spectral_fp32": t_spec / t_learn,
+            "train_seconds": train_s, "train_loss_last": sur.train_loss[-1], "calibration": sur.calib,
+            "note": "collision operator only (the part the surrogate replaces), same sample for both paths; "
+                    "net: 6 x conv3d 3^3, 32 ch, BF16 weights, FP32 accumulation on CUDA cores"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -229,6 +285,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bgk", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=int(os.environ.get("FKS_CPU_SAMPLE", "1024")))
     ap.add_argument("--grid", default=None, help="nx,ny,nz spatial cells (default 32,32,32); smaller grids "
                     "are for profiling runs, not bench lines")
@@ -318,6 +375,10 @@ def main():
                "note": "BGK relaxation (Sec. 2) with the fused transport gather, FP32"}
         del ctxb
 
+    learned = None
+    if not args.no_learned and ws == 1:
+        learned = learned_path(torch, fks, dev, args)
+
     fp64 = None
     if not args.no_fp64 and ws == 1:
         cfg64 = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
@@ -351,6 +412,7 @@ def main():
         "health_bits": bits,
         "fp64_spectral": fp64,
         "bgk_step": bgk,
+        "learned": learned,
     }
     print(json.dumps(out), flush=True)
 
