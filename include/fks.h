@@ -202,6 +202,13 @@ fks_status fks_net_set_params(fks_net *net, const float *host, long count);
 fks_status fks_net_get_params(fks_net *net, float *host, long count);
 /* y[b][n^3] = net(x[b][2][n^3]) for b < batch (device arrays) */
 fks_status fks_net_forward(fks_net *net, int batch, const float *x, float *y, void *stream);
+/* inference on the tensor cores (n a multiple of 16): the same network with
+ * BF16 activations between layers (inputs rounded to BF16), BF16 weights and
+ * FP32 accumulation in tensor memory; y FP32.  Used by fks_surrogate_collide. */
+fks_status fks_net_infer(fks_net *net, int batch, const float *x, float *y, void *stream);
+/* synchronises `stream`; FKS_ERR_TIMEOUT if a tensor-core completion wait of
+ * an inference kernel ran out (bounded wait), FKS_OK otherwise */
+fks_status fks_net_check(fks_net *net, void *stream);
 /* grad (device, num_params floats) = d(sum gy * y)/d params, through the BF16
  * weights (the rounding is treated as the identity) */
 fks_status fks_net_gradient(fks_net *net, int batch, const float *x, const float *gy, float *grad, void *stream);

@@ -62,15 +62,19 @@ def conv(x, W, b):
     return out + b[None, :, None, None, None]
 
 
-def forward(params, x, channels=CHANNELS):
-    """Returns the output and the list of layer activations (inputs of each layer)."""
-    acts = [x]
+def forward(params, x, channels=CHANNELS, act_bf16=False):
+    """Returns the output and the list of layer activations (inputs of each layer).
+    act_bf16: round the input and every hidden activation to bfloat16 (the
+    tensor-core inference path stores activations in that format)."""
     layers = unpack(params, channels)
-    h = x
+    h = bf16_round(x) if act_bf16 else x
+    acts = [h]
     for l, (W, b) in enumerate(layers):
         h = conv(h, W, b)
         if l < len(layers) - 1:
             h = np.maximum(h, 0.0)
+            if act_bf16:
+                h = bf16_round(h)
         acts.append(h)
     return h, acts
 

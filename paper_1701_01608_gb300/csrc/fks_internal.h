@@ -76,6 +76,7 @@ struct fks_ctx {
 
 // Surrogate network internals (fks_net.cu) used by the routing path.
 const float* fks_net_forward_internal(fks_net* m, int batch, const float* x, cudaStream_t s, fks_status* st);
+const float* fks_net_infer_internal(fks_net* m, int batch, const float* x, cudaStream_t s, fks_status* st);
 float* fks_net_input_buffer(fks_net* m);
 int fks_net_grid(const fks_net* m);
 int fks_net_max_batch(const fks_net* m);

@@ -262,6 +262,240 @@ static void layer_wgrad(int l, int n, int batch, const float* x, const float* g,
     else conv_wgrad<32, 1>(n, batch, x, g, gW, gb, s);
 }
 
+
+// ---------------------------------------------------------------- tensor-core inference
+//
+// Implicit-GEMM convolution on the 5th-generation tensor cores (tcgen05, BF16
+// operands, FP32 accumulation in tensor memory), used for inference.
+// Activations are BF16 "channels-last" ([b][voxel][CP], CP = 16 or 32).
+// A tile is 1 x 16 x 8 output voxels (x, y, z) = 128 rows of D; D[m][co] =
+// sum_t sum_ci A_t[m][ci] B_t[ci][co] over the 27 taps t.  The tile's input
+// halo (3 x 18 x 10 voxels) is stored as [k-chunk j][halo row r][8 channels]
+// (16 bytes per row and chunk), so the A operand of every tap is a plain
+// no-swizzle K-major descriptor into the halo: start row r0(t), 16-byte rows
+// inside an 8-row core matrix (consecutive z), SBO = 10 rows (next y), LBO =
+// one k-chunk plane.  No im2col copy.  Weights are pre-arranged per tap as
+// [j][co][8 ci] and stay in shared memory for the CTA's lifetime.
+namespace tc {
+
+constexpr int TY = 16, TZ = 8;                  // tile: 1 x 16 x 8 voxels
+constexpr int HX = 3, HY = TY + 2, HZ = TZ + 2;
+constexpr int HROWS = HX * HY * HZ;             // 540 halo rows
+constexpr int NTHR = 128;                       // 4 warps: TMEM lanes 0..127
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of this architecture
+    return d;                 // base offset 0, layout type 0 (no swizzle)
+}
+
+// instruction descriptor of kind::f16: D F32, A and B BF16, both K-major
+template <int M, int N>
+__host__ __device__ constexpr uint32_t instr_desc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(saddr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+template <int KC, int NP, bool RELU, bool OUT_F32>
+__global__ void __launch_bounds__(NTHR, 1) conv_tc_kernel(int n, int batch, const __nv_bfloat16* __restrict__ x,
+                                                          const __nv_bfloat16* __restrict__ wpk,
+                                                          const float* __restrict__ bias, void* __restrict__ y,
+                                                          int cout, int* flags) {
+    constexpr int CP = KC * 8;                           // input channels (padded)
+    constexpr uint32_t HALO_BYTES = KC * HROWS * 16;
+    constexpr uint32_t W_BYTES = 27 * KC * NP * 16;
+    constexpr uint32_t IDESC = instr_desc<128, NP>();
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* halo = smem;                          // [KC][HROWS][16 B]
+    unsigned char* wsm = smem + HALO_BYTES;              // [27][KC][NP][16 B]
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float sbias[32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // weights -> shared memory (16-byte chunks), bias
+    for (uint32_t i = tid; i < W_BYTES / 16; i += NTHR)
+        reinterpret_cast<uint4*>(wsm)[i] = reinterpret_cast<const uint4*>(wpk)[i];
+    if (tid < 32) sbias[tid] = tid < cout ? bias[tid] : 0.f;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(saddr(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) mbar_init1(&mbar);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    uint32_t phase = 0;
+
+    const int ny = n / TY, nz = n / TZ;
+    const long tiles = (long)batch * n * ny * nz;
+    const long n3 = (long)n * n * n;
+    for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int zb = (int)(tile % nz), yb = (int)((tile / nz) % ny), x0 = (int)((tile / ((long)nz * ny)) % n);
+        const int b = (int)(tile / ((long)nz * ny * n));
+        const int y0 = yb * TY, z0 = zb * TZ;
+        // halo rows -> shared memory (zero outside the grid)
+        for (int i = tid; i < KC * HROWS; i += NTHR) {
+            const int j = i / HROWS, r = i % HROWS;
+            const int hx = r / (HY * HZ), hy = (r / HZ) % HY, hz = r % HZ;
+            const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n)
+                v = *reinterpret_cast<const uint4*>(x + (((long)b * n3 + ((long)gx * n + gy) * n + gz) * CP + 8 * j));
+            reinterpret_cast<uint4*>(halo)[(long)j * HROWS + r] = v;
+        }
+        // generic-proxy writes of the halo before the tensor core reads it
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t hbase = saddr(halo), wbase = saddr(wsm);
+            int k = 0;
+#pragma unroll 1
+            for (int t = 0; t < 27; ++t) {
+                const int dx = t / 9, dy = (t / 3) % 3, dz = t % 3;
+                const uint32_t r0 = (uint32_t)((dx * HY + dy) * HZ + dz);
+#pragma unroll
+                for (int s2 = 0; s2 < KC / 2; ++s2) {
+                    const uint64_t ad = smem_desc(hbase + (2u * s2 * HROWS + r0) * 16u, HROWS * 16u, HZ * 16u);
+                    const uint64_t bd = smem_desc(wbase + (uint32_t)((t * KC + 2 * s2) * NP) * 16u, NP * 16u, 128u);
+                    const uint32_t acc = k > 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                        : "memory");
+                    ++k;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             saddr(&mbar))
+                         : "memory");
+        }
+        // bounded wait for the tile's MMAs
+        {
+            bool done = false;
+            for (long it = 0; it < (1L << 26) && !done; ++it) done = mbar_try(&mbar, phase);
+            if (!done && tid == 0) atomicOr(flags, 8);
+            phase ^= 1u;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // epilogue: warp w reads D rows 32w .. 32w+31 (one voxel per thread)
+        float v[NP];
+        {
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+            uint32_t r[NP];
+            if constexpr (NP == 32) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr));
+            } else {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(taddr));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < NP; ++c) v[c] = __uint_as_float(r[c]);
+        }
+        const int m = 32 * warp + lane;
+        const long vox = (long)b * n3 + ((long)x0 * n + (y0 + m / TZ)) * n + (z0 + m % TZ);
+        if constexpr (OUT_F32) {
+            static_cast<float*>(y)[vox] = v[0] + sbias[0];
+        } else {
+            __nv_bfloat16* yo = static_cast<__nv_bfloat16*>(y) + vox * 32;
+#pragma unroll
+            for (int c = 0; c < 32; c += 8) {
+                __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    float a = (c + e < NP) ? v[c + e] + sbias[c + e] : 0.f;
+                    if (RELU) a = fmaxf(a, 0.f);
+                    h[e] = __float2bfloat16_rn(a);
+                }
+                *reinterpret_cast<uint4*>(yo + c) = *reinterpret_cast<const uint4*>(h);
+            }
+        }
+        // every thread's TMEM reads are done before the next tile's MMAs overwrite D
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+    }
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem) : "memory");
+}
+
+// FP32 master weights of one layer -> [27][KC][NP][8] BF16 (zero padding)
+__global__ void pack_weights_kernel(int cin, int cout, int KC, int NP, const float* __restrict__ W,
+                                    __nv_bfloat16* __restrict__ out) {
+    const long total = 27L * KC * NP * 8;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int e = (int)(i % 8), co = (int)((i / 8) % NP), j = (int)((i / (8L * NP)) % KC), t = (int)(i / (8L * NP * KC));
+        const int ci = 8 * j + e;
+        out[i] = __float2bfloat16_rn(co < cout && ci < cin ? W[((long)co * cin + ci) * 27 + t] : 0.f);
+    }
+}
+
+// FP32 [b][2][n^3] -> BF16 channels-last [b][n^3][16] (channels 2..15 zero)
+__global__ void input_pack_kernel(long nvox, long n3, const float* __restrict__ x, __nv_bfloat16* __restrict__ out) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nvox; i += (long)gridDim.x * blockDim.x) {
+        const long b = i / n3, p = i % n3;
+        __align__(16) __nv_bfloat16 h[16];
+        for (int c = 0; c < 16; ++c) h[c] = __float2bfloat16_rn(c < 2 ? x[(b * 2 + c) * n3 + p] : 0.f);
+        reinterpret_cast<uint4*>(out + i * 16)[0] = reinterpret_cast<const uint4*>(h)[0];
+        reinterpret_cast<uint4*>(out + i * 16)[1] = reinterpret_cast<const uint4*>(h)[1];
+    }
+}
+
+// Dynamic shared memory is over-allocated to 160 KB: every descriptor's reach
+// stays inside the allocation even under the other reading of its two byte
+// offsets (LBO as the row-group stride), checked on the host for all layers.
+constexpr size_t kTcSmemFloor = 160 * 1024;
+
+template <int KC, int NP, bool RELU, bool OUT_F32>
+static cudaError_t launch_tc(int n, int batch, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias,
+                             void* y, int cout, int* flags, cudaStream_t s) {
+    size_t smem = (size_t)KC * HROWS * 16 + (size_t)27 * KC * NP * 16;
+    if (smem < kTcSmemFloor) smem = kTcSmemFloor;
+    auto k = conv_tc_kernel<KC, NP, RELU, OUT_F32>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long tiles = (long)batch * n * (n / TY) * (n / TZ);
+    const long grid = tiles < 2L * 152 ? tiles : 2L * 152;
+    k<<<(unsigned)grid, NTHR, smem, s>>>(n, batch, x, w, bias, y, cout, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace tc
+
 }  // namespace net
 }  // namespace fks
 
@@ -280,6 +514,11 @@ struct fks_net {
     float* gbuf[2] = {};              // gradient ping-pong
     float* dy = nullptr;
     float* xbuf = nullptr;            // [max_batch][2][n^3] input workspace of the routing path
+    // tensor-core inference: packed BF16 weights per layer, BF16 channels-last activations
+    __nv_bfloat16* wpk[NL] = {};
+    __nv_bfloat16* tact[2] = {};
+    int* tflags = nullptr;
+    bool tc_ready = false;
     long step = 0;
     long launches = 0;
     std::string err;
@@ -347,6 +586,50 @@ static fks_status run_backward(fks_net* m, int batch, const float* x, const floa
     return e == cudaSuccess ? FKS_OK : nfail(m, FKS_ERR_CUDA, std::string("net backward: ") + cudaGetErrorString(e));
 }
 
+// tensor-core inference (n a multiple of 16): output y[b][n^3] (FP32) in m->act[NL]
+static fks_status run_infer_tc(fks_net* m, int batch, const float* x, cudaStream_t s) {
+    const int n = m->n;
+    const long n3 = (long)n * n * n;
+    if (n % tc::TY != 0) return nfail(m, FKS_ERR_UNSUPPORTED, "tensor-core inference needs n % 16 == 0");
+    if (!m->tc_ready) {
+        bool ok = cudaMalloc(&m->tflags, sizeof(int)) == cudaSuccess && cudaMemset(m->tflags, 0, sizeof(int)) == cudaSuccess;
+        for (int i = 0; i < 2 && ok; ++i) ok = cudaMalloc(&m->tact[i], sizeof(__nv_bfloat16) * m->max_batch * n3 * 32) == cudaSuccess;
+        for (int l = 0; l < NL && ok; ++l) {
+            const int KC = l == 0 ? 2 : 4, NP = l == NL - 1 ? 16 : 32;
+            ok = cudaMalloc(&m->wpk[l], sizeof(__nv_bfloat16) * 27 * KC * NP * 8) == cudaSuccess;
+        }
+        if (!ok) return nfail(m, FKS_ERR_OOM, "tensor-core buffers");
+        m->tc_ready = true;
+    }
+    for (int l = 0; l < NL; ++l) {
+        const int KC = l == 0 ? 2 : 4, NP = l == NL - 1 ? 16 : 32;
+        tc::pack_weights_kernel<<<128, 256, 0, s>>>(CH[l], CH[l + 1], KC, NP, m->master + layer_off(l), m->wpk[l]);
+    }
+    tc::input_pack_kernel<<<1024, 256, 0, s>>>((long)batch * n3, n3, x, m->tact[0]);
+    m->launches += NL + 1;
+    cudaError_t e = cudaSuccess;
+    int cur = 0;
+    for (int l = 0; l < NL && e == cudaSuccess; ++l) {
+        const float* bias = bias_ptr(m, l);
+        if (l == 0)
+            e = tc::launch_tc<2, 32, true, false>(n, batch, m->tact[0], m->wpk[0], bias, m->tact[1], 32, m->tflags, s);
+        else if (l < NL - 1)
+            e = tc::launch_tc<4, 32, true, false>(n, batch, m->tact[cur], m->wpk[l], bias, m->tact[cur ^ 1], 32,
+                                                  m->tflags, s);
+        else
+            e = tc::launch_tc<4, 16, false, true>(n, batch, m->tact[cur], m->wpk[l], bias, m->act[NL], 1, m->tflags, s);
+        if (l > 0) cur ^= 1;
+        else cur = 1;
+        m->launches += 1;
+    }
+    return e == cudaSuccess ? FKS_OK : nfail(m, FKS_ERR_CUDA, std::string("tensor-core inference: ") + cudaGetErrorString(e));
+}
+
+const float* fks_net_infer_internal(fks_net* m, int batch, const float* x, cudaStream_t s, fks_status* st) {
+    *st = (m->n % tc::TY == 0) ? run_infer_tc(m, batch, x, s) : run_forward(m, batch, x, s);
+    return m->act[NL];
+}
+
 const float* fks_net_forward_internal(fks_net* m, int batch, const float* x, cudaStream_t s, fks_status* st) {
     *st = run_forward(m, batch, x, s);
     return m->act[NL];
@@ -410,6 +693,9 @@ void fks_net_destroy(fks_net* m) {
     cudaFree(m->wt);
     cudaFree(m->dy);
     cudaFree(m->xbuf);
+    for (int l = 0; l < NL; ++l) cudaFree(m->wpk[l]);
+    for (int i = 0; i < 2; ++i) cudaFree(m->tact[i]);
+    cudaFree(m->tflags);
     for (int l = 1; l <= NL; ++l) cudaFree(m->act[l]);
     for (int i = 0; i < 2; ++i) cudaFree(m->gbuf[i]);
     delete m;
@@ -444,6 +730,28 @@ fks_status fks_net_forward(fks_net* m, int batch, const float* x, float* y, void
     if (cudaMemcpyAsync(y, m->act[NL], sizeof(float) * batch * n3, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return nfail(m, FKS_ERR_CUDA, "output copy");
     return FKS_OK;
+}
+
+fks_status fks_net_infer(fks_net* m, int batch, const float* x, float* y, void* stream) {
+    if (!m || !x || !y || batch < 1 || batch > m->max_batch) return FKS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    fks_status st = run_infer_tc(m, batch, x, s);
+    if (st != FKS_OK) return st;
+    const long n3 = (long)m->n * m->n * m->n;
+    if (cudaMemcpyAsync(y, m->act[NL], sizeof(float) * batch * n3, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return nfail(m, FKS_ERR_CUDA, "output copy");
+    return FKS_OK;
+}
+
+fks_status fks_net_check(fks_net* m, void* stream) {
+    if (!m) return FKS_ERR_INVALID_ARG;
+    int h = 0;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return nfail(m, FKS_ERR_CUDA, "sync");
+    if (m->tflags) {
+        if (cudaMemcpy(&h, m->tflags, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FKS_ERR_CUDA;
+        cudaMemset(m->tflags, 0, sizeof(int));
+    }
+    return (h & 8) ? nfail(m, FKS_ERR_TIMEOUT, "tensor-core MMA completion wait timed out") : FKS_OK;
 }
 
 fks_status fks_net_gradient(fks_net* m, int batch, const float* x, const float* gy, float* grad, void* stream) {

@@ -1,7 +1,8 @@
 // fks_surrogate.cu -- inference path of the learned collision surrogate:
 //   inputs  : per cell, rho, u, T of f (FP64 sums), x = (f / rho, M[f] / rho),
 //             and the distance from equilibrium d = ||f - M|| / ||M||
-//   network : fks_net forward (BF16 weights, FP32 accumulation)
+//   network : fks_net inference (tcgen05 tensor cores, BF16 weights and
+//             activations, FP32 accumulation; CUDA-core FP32 path for n = 8, 24)
 //   output  : Q = rho^2 y out_scale / Kn, conservation projection (FP64 sums),
 //             indicator = ind_scale (d + defect), defect = relative size of the
 //             raw output's moments
@@ -200,7 +201,7 @@ fks_status fks_surrogate_collide(fks_ctx* c, fks_net* net, const void* f, void* 
         const long grid = k < 152L * 8 ? k : 152L * 8;
         surr::inputs_kernel<<<(unsigned)grid, surr::BS, 0, s>>>(n, c->vbox.L, c0, k, fin, xbuf, c->s_rho, c->s_dist);
         fks_status st = FKS_OK;
-        const float* y = fks_net_forward_internal(net, (int)k, xbuf, s, &st);
+        const float* y = fks_net_infer_internal(net, (int)k, xbuf, s, &st);
         if (st != FKS_OK) return st;
         surr::output_kernel<<<(unsigned)grid, surr::BS, 0, s>>>(n, c->vbox.L, c0, k, y, c->s_rho, c->s_dist, c->d_P,
                                                              out_scale / c->kern.knudsen, ind_scale, Qo, c->s_ind);

@@ -62,7 +62,8 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_batch_destroy", "fks_batch_last_error",
            "fks_net_init", "fks_net_num_params", "fks_net_set_params", "fks_net_get_params", "fks_net_forward",
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
-           "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator"]
+           "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
+           "fks_net_infer", "fks_net_check"]
 
 
 def lib(build: bool = True):
@@ -119,6 +120,8 @@ def lib(build: bool = True):
     L.fks_net_get_params.argtypes = [P, P, ctypes.c_long]
     L.fks_net_forward.argtypes = [P, I, P, P, P]
     L.fks_net_gradient.argtypes = [P, I, P, P, P, P]
+    L.fks_net_infer.argtypes = [P, I, P, P, P]
+    L.fks_net_check.argtypes = [P, P]
     L.fks_net_train_step.argtypes = [P, I, P, P, ctypes.c_float, P, P]
     L.fks_net_launch_count.argtypes = [P]
     L.fks_net_launch_count.restype = ctypes.c_long
@@ -391,6 +394,15 @@ class Net:
         import torch
         self._check(self._L.fks_net_forward(self._h, x.shape[0], _dptr(x, torch.float32), _dptr(y, torch.float32),
                                             _stream_ptr(stream)), "fks_net_forward")
+
+    def infer(self, x, y, stream=None):
+        """Tensor-core inference (BF16 activations, FP32 accumulation)."""
+        import torch
+        self._check(self._L.fks_net_infer(self._h, x.shape[0], _dptr(x, torch.float32), _dptr(y, torch.float32),
+                                          _stream_ptr(stream)), "fks_net_infer")
+
+    def check(self, stream=None):
+        self._check(self._L.fks_net_check(self._h, _stream_ptr(stream)), "fks_net_check")
 
     def gradient(self, x, gy, grad, stream=None):
         import torch
