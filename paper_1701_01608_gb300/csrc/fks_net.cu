@@ -475,16 +475,12 @@ __global__ void input_pack_kernel(long nvox, long n3, const float* __restrict__ 
     }
 }
 
-// Dynamic shared memory is over-allocated to 160 KB: every descriptor's reach
-// stays inside the allocation even under the other reading of its two byte
-// offsets (LBO as the row-group stride), checked on the host for all layers.
-constexpr size_t kTcSmemFloor = 160 * 1024;
-
 template <int KC, int NP, bool RELU, bool OUT_F32>
 static cudaError_t launch_tc(int n, int batch, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias,
                              void* y, int cout, int* flags, cudaStream_t s) {
-    size_t smem = (size_t)KC * HROWS * 16 + (size_t)27 * KC * NP * 16;
-    if (smem < kTcSmemFloor) smem = kTcSmemFloor;
+    // exact size: the last byte any descriptor reaches is the last byte of
+    // the halo (A) or of the weight block (B) for every tap
+    const size_t smem = (size_t)KC * HROWS * 16 + (size_t)27 * KC * NP * 16;
     auto k = conv_tc_kernel<KC, NP, RELU, OUT_F32>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
