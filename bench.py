@@ -39,6 +39,25 @@ def _hbm_peak():
 HBM_PEAK_GBS = _hbm_peak()
 
 
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops_sustained"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 1700.0, "fallback"
+
+
+BF16_PEAK_TFLOPS, BF16_PEAK_KIND = _bf16_peak()
+
+
+def tc_issued_flops_per_cell(n=NV, m=M):
+    """Tensor-core flops the split-BF16 path issues per cell: (M + 2) complex 3-D
+    transforms x 3 passes x n^2/128 tiles x (2n/16 k-steps x 3 split products)
+    MMAs of 128 x 2n x 16."""
+    k = 2 * n
+    return (m + 2) * 3 * (n * n // 128) * (k // 16) * 3 * (2 * 128 * k * 16)
+
+
 def flops_per_cell(n=NV, m=M):
     """Algorithmic flops of the operator per cell: (2M+2) real 3-D transforms
     at 2.5 N_v log2 N_v each, plus (4M+20) N_v pointwise."""
@@ -150,7 +169,7 @@ def cpu_baseline(sample_cells: int = 16, fp32_input=None) -> dict:
             "seconds": el}
 
 
-def learned_path(torch, fks, dev, args, sample=512, threshold=1e-3):
+def learned_path(torch, fks, dev, args, sample=1216, threshold=1e-3):
     """Learned surrogate collision (BF16 conv net, calibrated indicator, cells over the
     threshold routed to the FP32 spectral operator) against the FP32 spectral collision
     and the FP64 spectral operator, on a sample of non-equilibrium cells of the
@@ -163,8 +182,8 @@ def learned_path(torch, fks, dev, args, sample=512, threshold=1e-3):
     sur = S.train(torch, ftr, Qtr, epochs=8, batch=8, lr=2e-3, n=NV, L=LBOX, holdout=0.2)
     train_s = time.perf_counter() - t0
     del ftr, Qtr
-    f = torch.cat([S.shock_tube_cells(torch, NV, LBOX, nx=32, ny=4, nz=2, steps=(6,), seed=5)[:sample - 64],
-                   S.two_stream_cells(torch, 64, NV, LBOX, seed=9)]).contiguous()
+    f = torch.cat([S.shock_tube_cells(torch, NV, LBOX, nx=32, ny=8, nz=4, steps=(6,), seed=5)[:sample - 192],
+                   S.two_stream_cells(torch, 192, NV, LBOX, seed=9)]).contiguous()
     nc = f.shape[0]
     c32 = fks.Context(fks.Config(ncell=(nc, 1, 1), n=NV, L=LBOX, kn=KN, A1=A1, A2=A2, precision=fks.FKS_FP32))
     c64 = fks.Context(fks.Config(ncell=(nc, 1, 1), n=NV, L=LBOX, kn=KN, A1=A1, A2=A2, precision=fks.FKS_FP64))
@@ -203,7 +222,8 @@ def learned_path(torch, fks, dev, args, sample=512, threshold=1e-3):
             "speedup_vs_spectral_fp32": t_spec / t_learn,
             "train_seconds": train_s, "train_loss_last": sur.train_loss[-1], "calibration": sur.calib,
             "note": "collision operator only (the part the surrogate replaces), same sample for both paths; "
-                    "net: 6 x conv3d 3^3, 32 ch, BF16 weights, FP32 accumulation on CUDA cores"}
+                    "net: 6 x conv3d 3^3, 32 ch, BF16 weights and activations, FP32 accumulation; inference on "
+                    "the tensor cores (tcgen05 implicit GEMM), training on CUDA cores"}
 
 
 def run_reference(args):
@@ -286,6 +306,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bgk", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-tc", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=int(os.environ.get("FKS_CPU_SAMPLE", "1024")))
     ap.add_argument("--grid", default=None, help="nx,ny,nz spatial cells (default 32,32,32); smaller grids "
                     "are for profiling runs, not bench lines")
@@ -375,6 +396,44 @@ def main():
                "note": "BGK relaxation (Sec. 2) with the fused transport gather, FP32"}
         del ctxb
 
+    # the same step with every DFT on the tensor cores (split BF16)
+    tcp = None
+    if not args.no_tc:
+        cfgt = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
+                          A1=A1, A2=A2, precision=fks.FKS_BF16X3)
+        ctxt = fks.Context(cfgt)
+        tt, pert, launches_t, bits_t, _ = time_steps(torch, ctxt, f0, args.steps, args.warmup, dt, ws)
+        tt = max_over_ranks(tt, ws)
+        tms = float(np.mean(pert))
+        issued = tc_issued_flops_per_cell() * NCELLS
+        tfl = issued / (tms / 1e3) / 1e12
+        tcp = {"value": ws * PTS * args.steps / (tt / 1e3), "unit": "pts/s", "ms_per_step": tt / args.steps,
+               "roofline": {"bound": "tensor", "achieved": tfl, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": tfl / BF16_PEAK_TFLOPS, "traffic": None, "issued_flops_per_launch": issued,
+                            "peak_note": "bf16_tflops_sustained of MEASURED_PEAKS.json (%s); issued split-BF16 "
+                                         "MMA flops (3 products per DFT)" % BF16_PEAK_KIND},
+               "algorithmic_tflops": flops_launch / (tms / 1e3) / 1e12,
+               "gpu_launches": launches_t, "health_bits": bits_t,
+               "note": "fks_step on an FKS_BF16X3 context: offsets + one tcgen05 kernel per step (split-BF16 "
+                       "DFT passes, FP32 between passes, FP64 moment sums)"}
+        if ws == 1:
+            # error of the collision operator against the FP64 GPU operator on sampled cells
+            sel = torch.linspace(0, NCELLS - 1, 64).long().to(dev)
+            fs = f0.index_select(0, sel).contiguous()
+            errs = {}
+            qref = torch.empty(fs.shape, dtype=torch.float64, device=dev)
+            fks.Context(fks.Config(ncell=(64, 1, 1), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
+                                   precision=fks.FKS_FP64)).collide(fs.double(), qref)
+            for name, prec in (("bf16x3", fks.FKS_BF16X3), ("fp32", fks.FKS_FP32)):
+                q = torch.empty_like(fs)
+                fks.Context(fks.Config(ncell=(64, 1, 1), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
+                                       precision=prec)).collide(fs, q)
+                d = ((q.double() - qref).flatten(1).norm(dim=1) / qref.flatten(1).norm(dim=1)).cpu().numpy()
+                errs[name] = {"max": float(d.max()), "median": float(np.median(d))}
+            tcp["err_vs_fp64"] = errs
+            tcp["err_sample"] = "64 cells of the initial state evenly spread over the grid, relative L2 of Q"
+        del ctxt
+
     learned = None
     if not args.no_learned and ws == 1:
         learned = learned_path(torch, fks, dev, args)
@@ -412,6 +471,7 @@ def main():
         "health_bits": bits,
         "fp64_spectral": fp64,
         "bgk_step": bgk,
+        "bf16x3_tensor_core": tcp,
         "learned": learned,
     }
     print(json.dumps(out), flush=True)

@@ -45,7 +45,11 @@ typedef enum {
 } fks_status;
 
 enum { FKS_BC_PERIODIC = 0, FKS_BC_SPECULAR = 1 };
-enum { FKS_FP64 = 0, FKS_FP32 = 1 };
+/* FKS_BF16X3: FP32 storage and FP32 work between the transforms, every DFT on
+ * the tensor cores as a split-BF16 product (x = hi + lo for both factors,
+ * hi*hi + lo*hi + hi*lo accumulated in FP32); n = 16 or 32, spectral kernels
+ * only (not BGK, not batches). */
+enum { FKS_FP64 = 0, FKS_FP32 = 1, FKS_BF16X3 = 2 };
 enum { FKS_HARD_SPHERE = 0, FKS_MAXWELL = 1, FKS_BGK = 2 };
 
 /* Spatial grid: nx*ny*nz cells on the box [x0, x1]; bc[a] applies to both
@@ -89,7 +93,8 @@ typedef struct {
 /* Create a context: validates the arguments, builds the spectral tables on
  * the current device (FP64 arithmetic, stored in the working precision),
  * and allocates the per-context state (sub-cell offsets, shift table,
- * flags).  precision: FKS_FP64 or FKS_FP32.  On failure *out is NULL. */
+ * flags).  precision: FKS_FP64, FKS_FP32 or FKS_BF16X3 (element type float
+ * for the last two).  On failure *out is NULL. */
 fks_status fks_init(const fks_grid *grid, const fks_vbox *vbox, const fks_kernel *kernel,
                     const fks_dirs *dirs, int precision, fks_ctx **out);
 
@@ -204,7 +209,9 @@ fks_status fks_net_get_params(fks_net *net, float *host, long count);
 fks_status fks_net_forward(fks_net *net, int batch, const float *x, float *y, void *stream);
 /* inference on the tensor cores (n a multiple of 16): the same network with
  * BF16 activations between layers (inputs rounded to BF16), BF16 weights and
- * FP32 accumulation in tensor memory; y FP32.  Used by fks_surrogate_collide. */
+ * FP32 accumulation in tensor memory; y FP32.  Used by fks_surrogate_collide,
+ * which calls it on chunks of up to max(max_batch, 304) cells (its own
+ * workspace, allocated on first use); here batch <= max_batch. */
 fks_status fks_net_infer(fks_net *net, int batch, const float *x, float *y, void *stream);
 /* synchronises `stream`; FKS_ERR_TIMEOUT if a tensor-core completion wait of
  * an inference kernel ran out (bounded wait), FKS_OK otherwise */
@@ -221,7 +228,9 @@ const char *fks_net_last_error(const fks_net *net);
 void fks_net_destroy(fks_net *net);
 
 /* Network inputs of ncells FP32 cells: x[c] = (f/rho, M[f]/rho), rho[c]
- * (FP64) and dist[c] = ||f/rho - M/rho|| / ||M/rho|| (device arrays). */
+ * (FP64) and dist[c] = ||f/rho - M/rho|| / ||M/rho|| (device arrays; f and x
+ * 16-byte aligned).  n a multiple of 4, at most 64, else FKS_ERR_INVALID_ARG.
+ * The moments behind rho, u, T are FP32 partial sums added in FP64. */
 fks_status fks_surrogate_inputs(int n, double L, long ncells, const float *f, float *x, double *rho, float *dist,
                                 void *stream);
 
@@ -230,7 +239,8 @@ fks_status fks_surrogate_inputs(int n, double L, long ncells, const float *f, fl
  * ind_scale (dist + relative moment defect of the raw output); cells whose
  * indicator exceeds `threshold` (or is not finite) are recomputed with the
  * spectral operator.  Synchronises `stream` once (to read the routed count,
- * stored in *nrouted). */
+ * stored in *nrouted).  f and Q 16-byte aligned.  The moments of the raw
+ * output are FP64 sums of its FP32 values; the correction is applied in FP32. */
 fks_status fks_surrogate_collide(fks_ctx *ctx, fks_net *net, const void *f, void *Q, double out_scale,
                                  double ind_scale, double threshold, long *nrouted, void *stream);
 /* host copy of the last indicators (count = number of cells) */

@@ -152,6 +152,39 @@ __global__ void pack_tables_kernel(int n, int M, int C, int HF, const double* A,
     }
 }
 
+// Full-spectrum tables of the tensor-core path: [M+1][kx][ky][kz] pairs
+// (alpha N^-3, w_p alphap N^-3), slot M (betaL N^-3, 0).  A mode with
+// kz > n/2 takes the value of its mirror -k, which lies in the half spectrum
+// (the tables are even in k).
+__global__ void pack_tables_full_kernel(int n, int M, int HF, const double* A, const double* B, const double* w,
+                                        float2* out) {
+    const double s3 = 1.0 / ((double)n * n * n);
+    const long n3 = (long)n * n * n;
+    const long total = (long)(M + 1) * n3;
+    const long plane = (long)n * n * HF;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        int kz = (int)(i % n), ky = (int)((i / n) % n), kx = (int)((i / ((long)n * n)) % n);
+        const int p = (int)(i / n3);
+        if (kz > n / 2) {
+            kz = n - kz;
+            ky = (n - ky) % n;
+            kx = (n - kx) % n;
+        }
+        const long src = ((long)kx * n + ky) * HF + kz;
+        double va, vb;
+        if (p < M) {
+            va = A[p * plane + src] * s3;
+            vb = w[p] * B[p * plane + src] * s3;
+        } else {
+            double acc = 0.0;
+            for (int q = 0; q < M; ++q) acc += w[q] * A[q * plane + src] * B[q * plane + src];
+            va = acc * s3;
+            vb = 0.0;
+        }
+        out[i] = make_float2((float)va, (float)vb);
+    }
+}
+
 // ------------------------------------------------------------------ offsets
 // Generic-cell particle offsets (Sec. 3), one axis per blockIdx.y:
 //   s <- s + v dt;  delta = floor((s + dx/2)/dx);  s <- s - delta dx
@@ -331,7 +364,7 @@ static fks_status configure_variant(fks_ctx* c, int C) {
 // layout for cluster size C, built on the device in FP64 and stored in the
 // working precision.  *out is a new device allocation.
 static fks_status build_tables_raw(int n, const fks_dirs& dirs, double L, int ktype, double Ck, int C, bool fp64,
-                                   void** out, std::string* err) {
+                                   void** out, std::string* err, bool full = false) {
     const int M = dirs.A1 * dirs.A2, HF = n / 2 + 1;
     const double pi = 3.14159265358979323846;
     std::vector<double> e(3 * M), w(M);
@@ -353,7 +386,7 @@ static fks_status build_tables_raw(int n, const fks_dirs& dirs, double L, int kt
 
     double *d_e = nullptr, *d_gl = nullptr, *d_A = nullptr, *d_B = nullptr, *d_w = nullptr;
     const long half = (long)M * n * n * HF;
-    const long packed = (long)(M + 1) * C * 2 * n * (n / C) * HF;
+    const long packed = full ? (long)(M + 1) * 2 * n * n * n : (long)(M + 1) * C * 2 * n * (n / C) * HF;
     const size_t esz = fp64 ? 8 : 4;
     fks_status st = FKS_OK;
     *out = nullptr;
@@ -385,7 +418,9 @@ static fks_status build_tables_raw(int n, const fks_dirs& dirs, double L, int kt
         tp.glu_x = d_gl + 2 * kGL;
         tp.glu_w = d_gl + 3 * kGL;
         tables_kernel<<<1024, 128>>>(tp, d_A, d_B);
-        if (fp64)
+        if (full)
+            pack_tables_full_kernel<<<1024, 256>>>(n, M, HF, d_A, d_B, d_w, (float2*)*out);
+        else if (fp64)
             pack_tables_kernel<double><<<1024, 256>>>(n, M, C, HF, d_A, d_B, d_w, (double*)*out);
         else
             pack_tables_kernel<float><<<1024, 256>>>(n, M, C, HF, d_A, d_B, d_w, (float*)*out);
@@ -408,7 +443,8 @@ static fks_status build_tables_raw(int n, const fks_dirs& dirs, double L, int kt
 
 static fks_status build_tables(fks_ctx* c) {
     std::string err;
-    fks_status st = build_tables_raw(c->n, c->dirs, c->vbox.L, c->kern.type, c->kern.C, c->C, c->fp64, &c->tables, &err);
+    fks_status st = build_tables_raw(c->n, c->dirs, c->vbox.L, c->kern.type, c->kern.C, c->C, c->fp64, &c->tables, &err,
+                                     c->tc);
     c->launches += 2;
     if (st != FKS_OK) return fail(c, st, err);
     return FKS_OK;
@@ -448,6 +484,22 @@ static void projection_matrix(int n, double L, double* P) {
         for (int b = 0; b < 5; ++b) P[a * 5 + b] = A[a][5 + b];
 }
 
+// DFT matrices and per-CTA scratch of the tensor-core path (one CTA per SM)
+static fks_status setup_tc(fks_ctx* c) {
+    std::vector<uint16_t> h;
+    tc_dft_matrices(c->n, h);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->tc_grid = sms > 0 ? sms : 1;
+    const size_t scratch = (size_t)c->tc_grid * tc_scratch_per_cta(c->n);
+    if (cudaMalloc(&c->tc_dft, h.size() * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMalloc(&c->tc_scratch, scratch) != cudaSuccess)
+        return fail(c, FKS_ERR_OOM, "tensor-core scratch");
+    if (cudaMemcpy(c->tc_dft, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(c, FKS_ERR_CUDA, "DFT matrix upload");
+    return FKS_OK;
+}
+
 extern "C" {
 
 const char* fks_status_string(fks_status s) {
@@ -479,7 +531,9 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
     if (!(kernel->C > 0.0) || !(kernel->knudsen > 0.0)) return FKS_ERR_INVALID_ARG;
     if (dirs->A1 < 1 || dirs->A2 < 1 || dirs->A1 * dirs->A2 > 4096 || (dirs->rule != 0 && dirs->rule != 1))
         return FKS_ERR_INVALID_ARG;
-    if (precision != FKS_FP64 && precision != FKS_FP32) return FKS_ERR_UNSUPPORTED;
+    if (precision != FKS_FP64 && precision != FKS_FP32 && precision != FKS_BF16X3) return FKS_ERR_UNSUPPORTED;
+    if (precision == FKS_BF16X3 && (kernel->type == FKS_BGK || (vbox->n != 16 && vbox->n != 32)))
+        return FKS_ERR_UNSUPPORTED;
 
     fks_ctx* c = new (std::nothrow) fks_ctx();
     if (!c) return FKS_ERR_OOM;
@@ -495,8 +549,13 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
     for (int a = 0; a < 3; ++a) c->dx[a] = (grid->x1[a] - grid->x0[a]) / nca[a];
     cudaGetDevice(&c->device);
     c->bgk = kernel->type == FKS_BGK;
+    c->tc = precision == FKS_BF16X3;
     fks_status st = FKS_OK;
-    if (!c->bgk) {
+    if (c->tc) {
+        c->C = 1;
+        st = build_tables(c);
+        if (st == FKS_OK) st = setup_tc(c);
+    } else if (!c->bgk) {
         st = configure_variant(c, default_cluster_size(c->fp64, c->n));
         if (st == FKS_OK) st = build_tables(c);
     } else {
@@ -528,6 +587,8 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
 void fks_destroy(fks_ctx* c) {
     if (!c) return;
     cudaFree(c->tables);
+    cudaFree(c->tc_dft);
+    cudaFree(c->tc_scratch);
     cudaFree(c->d_s);
     cudaFree(c->d_delta);
     cudaFree(c->d_flags);
@@ -549,6 +610,7 @@ long fks_launch_count(const fks_ctx* c) { return c ? c->launches : -1; }
 fks_status fks_set_cluster_size(fks_ctx* c, int C) {
     if (!c) return FKS_ERR_INVALID_ARG;
     if (c->bgk) return fail(c, FKS_ERR_UNSUPPORTED, "the BGK kernel has no cluster size");
+    if (c->tc) return fail(c, FKS_ERR_UNSUPPORTED, "the tensor-core kernel has no cluster size");
     if (C == c->C) return FKS_OK;
     // tables are laid out per cluster rank: rebuild them for the new size
     CollideVariant v;
@@ -586,9 +648,38 @@ static fks_status launch_bgk_ctx(fks_ctx* c, const void* f, void* out, const sig
     return FKS_OK;
 }
 
+static fks_status launch_tc_ctx(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
+                                cudaStream_t s) {
+    TcLaunch l;
+    l.f = f;
+    l.out = out;
+    l.tables = c->tables;
+    l.dft = c->tc_dft;
+    l.scratch = c->tc_scratch;
+    l.delta = delta;
+    l.flags = c->d_flags;
+    l.ncells = c->ncells;
+    l.nc[0] = c->grid.nx;
+    l.nc[1] = c->grid.ny;
+    l.nc[2] = c->grid.nz;
+    for (int i = 0; i < 3; ++i) l.bc[i] = c->grid.bc[i];
+    l.M = c->M;
+    l.L = c->vbox.L;
+    l.inv_kn = 1.0 / c->kern.knudsen;
+    l.dt = dt;
+    l.mode = mode;
+    std::memcpy(l.P, c->P, sizeof(l.P));
+    l.grid = c->tc_grid;
+    cudaError_t e = launch_collide_tc(c->n, l, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core collision kernel launch");
+    c->launches += 1;
+    return FKS_OK;
+}
+
 static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
                                  cudaStream_t s) {
     if (c->bgk) return launch_bgk_ctx(c, f, out, delta, dt, mode, s);
+    if (c->tc) return launch_tc_ctx(c, f, out, delta, dt, mode, s);
     CollideArgs a;
     a.f = f;
     a.out = out;

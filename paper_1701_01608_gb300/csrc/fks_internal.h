@@ -3,7 +3,9 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/fks.h"
 #include "fks_collide.cuh"
@@ -41,11 +43,36 @@ cudaError_t launch_bgk(bool fp64, int n, const BgkArgs& a, cudaStream_t s);
 // Default cluster size for (precision, N).
 int default_cluster_size(bool fp64, int N);
 
+// Tensor-core (split BF16) collision kernel (fks_collide_tc.cu), n = 16 or 32.
+struct TcLaunch {
+    const void* f;
+    void* out;
+    const void* tables;         // [M+1][n][n][n] float2
+    const void* dft;            // BF16 DFT matrices (tc_dft_matrices)
+    void* scratch;              // grid x tc_scratch_per_cta(n) bytes
+    const signed char* delta;   // transport shifts (step) or nullptr
+    int* flags;
+    long ncells;
+    int nc[3], bc[3];
+    int M;
+    double L, inv_kn, dt;
+    int mode;
+    double P[25];
+    int grid;                   // CTAs the scratch is sized for
+};
+cudaError_t launch_collide_tc(int n, const TcLaunch& l, cudaStream_t s);
+long tc_scratch_per_cta(int n);
+void tc_dft_matrices(int n, std::vector<uint16_t>& out);
+
 }  // namespace fks
 
 // Context state (fks_capi.cu); visible to the other translation units.
 struct fks_ctx {
     bool bgk = false;           // BGK relaxation instead of the spectral operator
+    bool tc = false;            // split-BF16 tensor-core transforms (FKS_BF16X3)
+    void* tc_dft = nullptr;     // BF16 DFT matrices
+    void* tc_scratch = nullptr; // per-CTA spectrum and pass-3 operand scratch
+    int tc_grid = 0;
     fks_grid grid;
     fks_vbox vbox;
     fks_kernel kern;
@@ -77,6 +104,10 @@ struct fks_ctx {
 // Surrogate network internals (fks_net.cu) used by the routing path.
 const float* fks_net_forward_internal(fks_net* m, int batch, const float* x, cudaStream_t s, fks_status* st);
 const float* fks_net_infer_internal(fks_net* m, int batch, const float* x, cudaStream_t s, fks_status* st);
+// inference chunk of the routing path: cells per fks_net_infer_internal call
+// (allocates the inference workspace on first use; 0 if that fails) and its
+// [capacity][2][n^3] FP32 input buffer
+int fks_net_infer_capacity(fks_net* m);
 float* fks_net_input_buffer(fks_net* m);
 int fks_net_grid(const fks_net* m);
 int fks_net_max_batch(const fks_net* m);

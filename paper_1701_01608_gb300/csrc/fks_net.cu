@@ -509,12 +509,15 @@ struct fks_net {
     float* act[NL + 1] = {};          // activations: act[0] = input copy slot unused, act[l+1] = layer l output
     float* gbuf[2] = {};              // gradient ping-pong
     float* dy = nullptr;
-    float* xbuf = nullptr;            // [max_batch][2][n^3] input workspace of the routing path
+    // inference workspace (allocated on first use): ib cells per call
+    int ib = 0;
+    float* xbuf = nullptr;            // [ib][2][n^3] input workspace of the routing path
+    float* yinf = nullptr;            // [ib][n^3] network output
     // tensor-core inference: packed BF16 weights per layer, BF16 channels-last activations
     __nv_bfloat16* wpk[NL] = {};
     __nv_bfloat16* tact[2] = {};
     int* tflags = nullptr;
-    bool tc_ready = false;
+    long wver = 0, wpk_ver = -1;      // master-weight version, version packed in wpk
     long step = 0;
     long launches = 0;
     std::string err;
@@ -536,6 +539,7 @@ static double splitmix_uniform(uint64_t& s) {
 }
 
 static fks_status refresh_bf16(fks_net* m, cudaStream_t s) {
+    m->wver += 1;
     to_bf16_kernel<<<256, 256, 0, s>>>(NPARAM, m->master, m->wbf);
     m->launches += 1;
     return cudaGetLastError() == cudaSuccess ? FKS_OK : nfail(m, FKS_ERR_CUDA, "bf16 conversion");
@@ -582,27 +586,51 @@ static fks_status run_backward(fks_net* m, int batch, const float* x, const floa
     return e == cudaSuccess ? FKS_OK : nfail(m, FKS_ERR_CUDA, std::string("net backward: ") + cudaGetErrorString(e));
 }
 
-// tensor-core inference (n a multiple of 16): output y[b][n^3] (FP32) in m->act[NL]
-static fks_status run_infer_tc(fks_net* m, int batch, const float* x, cudaStream_t s) {
-    const int n = m->n;
-    const long n3 = (long)n * n * n;
-    if (n % tc::TY != 0) return nfail(m, FKS_ERR_UNSUPPORTED, "tensor-core inference needs n % 16 == 0");
-    if (!m->tc_ready) {
-        bool ok = cudaMalloc(&m->tflags, sizeof(int)) == cudaSuccess && cudaMemset(m->tflags, 0, sizeof(int)) == cudaSuccess;
-        for (int i = 0; i < 2 && ok; ++i) ok = cudaMalloc(&m->tact[i], sizeof(__nv_bfloat16) * m->max_batch * n3 * 32) == cudaSuccess;
+// cells per inference call of the routing path: enough CTAs to fill the GPU
+// in the per-cell kernels around the network
+constexpr int kInferChunk = 2 * 152;
+
+static bool use_tc(const fks_net* m) { return m->n % tc::TY == 0; }
+
+// inference workspace: the tensor-core path takes kInferChunk cells per call,
+// the CUDA-core path (training activations) max_batch
+static fks_status ensure_infer(fks_net* m) {
+    if (m->ib > 0) return FKS_OK;
+    const long n3 = (long)m->n * m->n * m->n;
+    const int ib = use_tc(m) ? (m->max_batch > kInferChunk ? m->max_batch : kInferChunk) : m->max_batch;
+    bool ok = cudaMalloc(&m->xbuf, sizeof(float) * ib * 2 * n3) == cudaSuccess &&
+              cudaMalloc(&m->yinf, sizeof(float) * ib * n3) == cudaSuccess;
+    if (ok && use_tc(m)) {
+        ok = cudaMalloc(&m->tflags, sizeof(int)) == cudaSuccess && cudaMemset(m->tflags, 0, sizeof(int)) == cudaSuccess;
+        for (int i = 0; i < 2 && ok; ++i) ok = cudaMalloc(&m->tact[i], sizeof(__nv_bfloat16) * ib * n3 * 32) == cudaSuccess;
         for (int l = 0; l < NL && ok; ++l) {
             const int KC = l == 0 ? 2 : 4, NP = l == NL - 1 ? 16 : 32;
             ok = cudaMalloc(&m->wpk[l], sizeof(__nv_bfloat16) * 27 * KC * NP * 8) == cudaSuccess;
         }
-        if (!ok) return nfail(m, FKS_ERR_OOM, "tensor-core buffers");
-        m->tc_ready = true;
     }
-    for (int l = 0; l < NL; ++l) {
-        const int KC = l == 0 ? 2 : 4, NP = l == NL - 1 ? 16 : 32;
-        tc::pack_weights_kernel<<<128, 256, 0, s>>>(CH[l], CH[l + 1], KC, NP, m->master + layer_off(l), m->wpk[l]);
+    if (!ok) return nfail(m, FKS_ERR_OOM, "inference workspace");
+    m->ib = ib;
+    return FKS_OK;
+}
+
+// tensor-core inference (n a multiple of 16): output y[b][n^3] (FP32) in m->yinf
+static fks_status run_infer_tc(fks_net* m, int batch, const float* x, cudaStream_t s) {
+    const int n = m->n;
+    const long n3 = (long)n * n * n;
+    if (!use_tc(m)) return nfail(m, FKS_ERR_UNSUPPORTED, "tensor-core inference needs n % 16 == 0");
+    fks_status st = ensure_infer(m);
+    if (st != FKS_OK) return st;
+    if (batch < 1 || batch > m->ib) return nfail(m, FKS_ERR_INVALID_ARG, "inference batch above the workspace");
+    if (m->wpk_ver != m->wver) {   // weights changed since they were packed
+        for (int l = 0; l < NL; ++l) {
+            const int KC = l == 0 ? 2 : 4, NP = l == NL - 1 ? 16 : 32;
+            tc::pack_weights_kernel<<<128, 256, 0, s>>>(CH[l], CH[l + 1], KC, NP, m->master + layer_off(l), m->wpk[l]);
+        }
+        m->launches += NL;
+        m->wpk_ver = m->wver;
     }
     tc::input_pack_kernel<<<1024, 256, 0, s>>>((long)batch * n3, n3, x, m->tact[0]);
-    m->launches += NL + 1;
+    m->launches += 1;
     cudaError_t e = cudaSuccess;
     int cur = 0;
     for (int l = 0; l < NL && e == cudaSuccess; ++l) {
@@ -613,7 +641,7 @@ static fks_status run_infer_tc(fks_net* m, int batch, const float* x, cudaStream
             e = tc::launch_tc<4, 32, true, false>(n, batch, m->tact[cur], m->wpk[l], bias, m->tact[cur ^ 1], 32,
                                                   m->tflags, s);
         else
-            e = tc::launch_tc<4, 16, false, true>(n, batch, m->tact[cur], m->wpk[l], bias, m->act[NL], 1, m->tflags, s);
+            e = tc::launch_tc<4, 16, false, true>(n, batch, m->tact[cur], m->wpk[l], bias, m->yinf, 1, m->tflags, s);
         if (l > 0) cur ^= 1;
         else cur = 1;
         m->launches += 1;
@@ -622,7 +650,11 @@ static fks_status run_infer_tc(fks_net* m, int batch, const float* x, cudaStream
 }
 
 const float* fks_net_infer_internal(fks_net* m, int batch, const float* x, cudaStream_t s, fks_status* st) {
-    *st = (m->n % tc::TY == 0) ? run_infer_tc(m, batch, x, s) : run_forward(m, batch, x, s);
+    if (use_tc(m)) {
+        *st = run_infer_tc(m, batch, x, s);
+        return m->yinf;
+    }
+    *st = run_forward(m, batch, x, s);
     return m->act[NL];
 }
 
@@ -630,7 +662,8 @@ const float* fks_net_forward_internal(fks_net* m, int batch, const float* x, cud
     *st = run_forward(m, batch, x, s);
     return m->act[NL];
 }
-float* fks_net_input_buffer(fks_net* m) { return m->xbuf; }
+int fks_net_infer_capacity(fks_net* m) { return ensure_infer(m) == FKS_OK ? m->ib : 0; }
+float* fks_net_input_buffer(fks_net* m) { return ensure_infer(m) == FKS_OK ? m->xbuf : nullptr; }
 int fks_net_grid(const fks_net* m) { return m->n; }
 int fks_net_max_batch(const fks_net* m) { return m->max_batch; }
 
@@ -650,8 +683,7 @@ fks_status fks_net_init(int n, int max_batch, unsigned long long seed, fks_net**
               cudaMalloc(&m->adam_v, sizeof(float) * NPARAM) == cudaSuccess &&
               cudaMalloc(&m->wbf, sizeof(__nv_bfloat16) * NPARAM) == cudaSuccess &&
               cudaMalloc(&m->wt, sizeof(__nv_bfloat16) * 32 * 32 * 27) == cudaSuccess &&
-              cudaMalloc(&m->dy, sizeof(float) * max_batch * n3) == cudaSuccess &&
-              cudaMalloc(&m->xbuf, sizeof(float) * max_batch * 2 * n3) == cudaSuccess;
+              cudaMalloc(&m->dy, sizeof(float) * max_batch * n3) == cudaSuccess;
     for (int l = 1; l <= NL && ok; ++l) ok = cudaMalloc(&m->act[l], sizeof(float) * max_batch * CH[l] * n3) == cudaSuccess;
     for (int i = 0; i < 2 && ok; ++i) ok = cudaMalloc(&m->gbuf[i], sizeof(float) * max_batch * 32 * n3) == cudaSuccess;
     if (!ok) {
@@ -689,6 +721,7 @@ void fks_net_destroy(fks_net* m) {
     cudaFree(m->wt);
     cudaFree(m->dy);
     cudaFree(m->xbuf);
+    cudaFree(m->yinf);
     for (int l = 0; l < NL; ++l) cudaFree(m->wpk[l]);
     for (int i = 0; i < 2; ++i) cudaFree(m->tact[i]);
     cudaFree(m->tflags);
@@ -734,7 +767,7 @@ fks_status fks_net_infer(fks_net* m, int batch, const float* x, float* y, void* 
     fks_status st = run_infer_tc(m, batch, x, s);
     if (st != FKS_OK) return st;
     const long n3 = (long)m->n * m->n * m->n;
-    if (cudaMemcpyAsync(y, m->act[NL], sizeof(float) * batch * n3, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    if (cudaMemcpyAsync(y, m->yinf, sizeof(float) * batch * n3, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return nfail(m, FKS_ERR_CUDA, "output copy");
     return FKS_OK;
 }

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <string>
 
@@ -20,8 +21,9 @@
 namespace fks {
 namespace surr {
 
-constexpr int BS = 256;
+constexpr int BS = 512;
 
+// block-wide FP64 sums of k values (k <= 8), fixed order: deterministic
 __device__ __forceinline__ void block_sum(double* v, int k, double* red) {
     const int tid = threadIdx.x;
     for (int i = 0; i < k; ++i) {
@@ -41,46 +43,70 @@ __device__ __forceinline__ void block_sum(double* v, int k, double* red) {
     __syncthreads();
 }
 
-// one CTA per cell: moments, Maxwellian, network input, distance from equilibrium
+// Both kernels sweep a cell as float4 runs along v_z (n % 4 == 0): run q holds
+// elements 4q .. 4q+3 of row r = q / (n/4), i.e. ix = r / n, iy = r % n.
+
+// one CTA per cell: moments (FP32 partials, FP64 block sums), the Maxwellian
+// as a product of three one-axis tables, network input x = (f / rho, M / rho)
+// and the distance from equilibrium
 __global__ void __launch_bounds__(BS) inputs_kernel(int n, double L, long c0, long ncells, const float* __restrict__ f,
                                                     float* __restrict__ x, double* __restrict__ rho_out,
                                                     float* __restrict__ dist) {
     __shared__ double red[(BS / 32) * 8];
+    __shared__ float vg[64], ex[3][64];
     const long n3 = (long)n * n * n;
+    const int q4 = n / 4;
+    const long runs = n3 / 4;
     const double dv = 2.0 * L / n;
+    for (int i = threadIdx.x; i < n; i += BS) vg[i] = (float)(((double)i + 0.5 - 0.5 * n) * dv);
+    __syncthreads();
     for (long c = c0 + blockIdx.x; c < c0 + ncells; c += gridDim.x) {
-        const float* fc = f + c * n3;
-        double s[5] = {0, 0, 0, 0, 0};
-        for (long k = threadIdx.x; k < n3; k += BS) {
-            const double vx = ((double)(k / (n * n)) + 0.5 - 0.5 * n) * dv;
-            const double vy = ((double)((k / n) % n) + 0.5 - 0.5 * n) * dv;
-            const double vz = ((double)(k % n) + 0.5 - 0.5 * n) * dv;
-            const double m = fc[k];
-            s[0] += m;
-            s[1] += m * vx;
-            s[2] += m * vy;
-            s[3] += m * vz;
-            s[4] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+        const float4* fc = reinterpret_cast<const float4*>(f + c * n3);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+        for (long q = threadIdx.x; q < runs; q += BS) {
+            const float4 m = fc[q];
+            const int r = (int)(q / q4), iz = 4 * (int)(q % q4);
+            const float vx = vg[r / n], vy = vg[r % n];
+            const float z0 = vg[iz], z1 = vg[iz + 1], z2 = vg[iz + 2], z3 = vg[iz + 3];
+            const float s = (m.x + m.y) + (m.z + m.w);
+            a0 += s;
+            a1 = fmaf(s, vx, a1);
+            a2 = fmaf(s, vy, a2);
+            a3 += m.x * z0 + m.y * z1 + m.z * z2 + m.w * z3;
+            a4 += s * (vx * vx + vy * vy) + (m.x * z0 * z0 + m.y * z1 * z1 + m.z * z2 * z2 + m.w * z3 * z3);
         }
-        block_sum(s, 5, red);
+        double sm[5] = {a0, a1, a2, a3, 0.5 * (double)a4};
+        block_sum(sm, 5, red);
         const double dv3 = dv * dv * dv;
-        const double rho = s[0] * dv3;
-        const double ux = s[1] * dv3 / rho, uy = s[2] * dv3 / rho, uz = s[3] * dv3 / rho;
-        const double T = (s[4] * dv3 - 0.5 * rho * (ux * ux + uy * uy + uz * uz)) / (1.5 * rho);
+        const double rho = sm[0] * dv3;
+        const double ux = sm[1] * dv3 / rho, uy = sm[2] * dv3 / rho, uz = sm[3] * dv3 / rho;
+        const double T = (sm[4] * dv3 - 0.5 * rho * (ux * ux + uy * uy + uz * uz)) / (1.5 * rho);
         const double pre = 1.0 / (2.0 * 3.14159265358979323846 * T * sqrt(2.0 * 3.14159265358979323846 * T));
-        float* xc = x + (c - c0) * 2 * n3;
-        double d2[2] = {0.0, 0.0};
-        for (long k = threadIdx.x; k < n3; k += BS) {
-            const double vx = ((double)(k / (n * n)) + 0.5 - 0.5 * n) * dv - ux;
-            const double vy = ((double)((k / n) % n) + 0.5 - 0.5 * n) * dv - uy;
-            const double vz = ((double)(k % n) + 0.5 - 0.5 * n) * dv - uz;
-            const double Mg = pre * exp(-(vx * vx + vy * vy + vz * vz) / (2.0 * T));   // M / rho
-            const double g = fc[k] / rho;
-            xc[k] = (float)g;
-            xc[n3 + k] = (float)Mg;
-            d2[0] += (g - Mg) * (g - Mg);
-            d2[1] += Mg * Mg;
+        // M / rho = pre * ex[0][ix] * ex[1][iy] * ex[2][iz]
+        const double u3[3] = {ux, uy, uz};
+        for (int i = threadIdx.x; i < 3 * n; i += BS) {
+            const int ax = i / n, k = i % n;
+            const double d = ((double)k + 0.5 - 0.5 * n) * dv - u3[ax];
+            ex[ax][k] = (float)(exp(-d * d / (2.0 * T)) * (ax == 0 ? pre : 1.0));
         }
+        __syncthreads();
+        const float inv_rho = (float)(1.0 / rho);
+        float4* xg = reinterpret_cast<float4*>(x + (c - c0) * 2 * n3);
+        float4* xm = reinterpret_cast<float4*>(x + (c - c0) * 2 * n3 + n3);
+        float d0 = 0.f, d1 = 0.f;
+        for (long q = threadIdx.x; q < runs; q += BS) {
+            const float4 m = fc[q];
+            const int r = (int)(q / q4), iz = 4 * (int)(q % q4);
+            const float exy = ex[0][r / n] * ex[1][r % n];
+            const float4 g = make_float4(m.x * inv_rho, m.y * inv_rho, m.z * inv_rho, m.w * inv_rho);
+            const float4 M = make_float4(exy * ex[2][iz], exy * ex[2][iz + 1], exy * ex[2][iz + 2], exy * ex[2][iz + 3]);
+            xg[q] = g;
+            xm[q] = M;
+            d0 += (g.x - M.x) * (g.x - M.x) + (g.y - M.y) * (g.y - M.y) + (g.z - M.z) * (g.z - M.z) +
+                  (g.w - M.w) * (g.w - M.w);
+            d1 += M.x * M.x + M.y * M.y + M.z * M.z + M.w * M.w;
+        }
+        double d2[2] = {d0, d1};
         block_sum(d2, 2, red);
         if (threadIdx.x == 0) {
             rho_out[c] = rho;
@@ -89,48 +115,83 @@ __global__ void __launch_bounds__(BS) inputs_kernel(int n, double L, long c0, lo
     }
 }
 
-// one CTA per cell: Q = rho^2 y s / Kn, conservation projection, indicator
+// one CTA per cell: q = rho^2 y s / Kn (FP32), the five moments of q as FP64
+// sums of the FP32 values, conservation projection Q = q - C^T mu, indicator
 __global__ void __launch_bounds__(BS) output_kernel(int n, double L, long c0, long ncells, const float* __restrict__ y,
                                                     const double* __restrict__ rho, const float* __restrict__ dist,
                                                     const double* __restrict__ P, double scale, double ind_scale,
                                                     float* __restrict__ Q, float* __restrict__ ind) {
     __shared__ double red[(BS / 32) * 8];
+    __shared__ double vd[64];
+    __shared__ float vg[64];
+    __shared__ double mu[5];
     const long n3 = (long)n * n * n;
+    const int q4 = n / 4;
+    const long runs = n3 / 4;
     const double dv = 2.0 * L / n;
+    for (int i = threadIdx.x; i < n; i += BS) {
+        vd[i] = ((double)i + 0.5 - 0.5 * n) * dv;
+        vg[i] = (float)vd[i];
+    }
+    __syncthreads();
     for (long c = c0 + blockIdx.x; c < c0 + ncells; c += gridDim.x) {
-        const float* yc = y + (c - c0) * n3;
-        const double a = rho[c] * rho[c] * scale;
-        double s[6] = {0, 0, 0, 0, 0, 0};   // sum phi Q, sum |phi| |Q|
-        for (long k = threadIdx.x; k < n3; k += BS) {
-            const double vx = ((double)(k / (n * n)) + 0.5 - 0.5 * n) * dv;
-            const double vy = ((double)((k / n) % n) + 0.5 - 0.5 * n) * dv;
-            const double vz = ((double)(k % n) + 0.5 - 0.5 * n) * dv;
-            const double q = a * yc[k];
-            const double e = 0.5 * (vx * vx + vy * vy + vz * vz);
-            s[0] += q;
-            s[1] += q * vx;
-            s[2] += q * vy;
-            s[3] += q * vz;
-            s[4] += q * e;
-            s[5] += fabs(q) * (1.0 + fabs(vx) + fabs(vy) + fabs(vz) + e);
+        const float4* yc = reinterpret_cast<const float4*>(y + (c - c0) * n3);
+        const float a = (float)(rho[c] * rho[c] * scale);
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+        float sa = 0.f;   // sum |phi| |q| (indicator scale only)
+        for (long q = threadIdx.x; q < runs; q += BS) {
+            const float4 v = yc[q];
+            const int r = (int)(q / q4), iz = 4 * (int)(q % q4);
+            const float e4[4] = {a * v.x, a * v.y, a * v.z, a * v.w};
+            double t0 = 0.0, tz = 0.0, tzz = 0.0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double qk = (double)e4[k], z = vd[iz + k];
+                t0 += qk;
+                tz = fma(qk, z, tz);
+                tzz = fma(qk, 0.5 * z * z, tzz);
+            }
+            const double vx = vd[r / n], vy = vd[r % n];
+            s0 += t0;
+            s1 = fma(t0, vx, s1);
+            s2 = fma(t0, vy, s2);
+            s3 += tz;
+            s4 = fma(t0, 0.5 * (vx * vx + vy * vy), s4) + tzz;
+            const float ax = fabsf(vg[r / n]) + fabsf(vg[r % n]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float z = vg[iz + k];
+                sa += fabsf(e4[k]) * (1.f + ax + fabsf(z) + 0.5f * (vg[r / n] * vg[r / n] + vg[r % n] * vg[r % n] + z * z));
+            }
         }
-        block_sum(s, 6, red);
-        double mu[5];
-        for (int i = 0; i < 5; ++i) {
+        double sm[6] = {s0, s1, s2, s3, s4, (double)sa};
+        block_sum(sm, 6, red);
+        if (threadIdx.x < 5) {
             double acc = 0.0;
-            for (int j = 0; j < 5; ++j) acc += P[i * 5 + j] * s[j];
-            mu[i] = acc;
+            for (int j = 0; j < 5; ++j) acc += P[threadIdx.x * 5 + j] * sm[j];
+            mu[threadIdx.x] = acc;
         }
-        const double defect = (fabs(s[0]) + fabs(s[1]) + fabs(s[2]) + fabs(s[3]) + fabs(s[4])) / (s[5] > 0 ? s[5] : 1.0);
-        float* Qc = Q + c * n3;
-        for (long k = threadIdx.x; k < n3; k += BS) {
-            const double vx = ((double)(k / (n * n)) + 0.5 - 0.5 * n) * dv;
-            const double vy = ((double)((k / n) % n) + 0.5 - 0.5 * n) * dv;
-            const double vz = ((double)(k % n) + 0.5 - 0.5 * n) * dv;
-            const double corr = mu[0] + mu[1] * vx + mu[2] * vy + mu[3] * vz + mu[4] * 0.5 * (vx * vx + vy * vy + vz * vz);
-            Qc[k] = (float)(a * yc[k] - corr);
+        __syncthreads();
+        const float m0 = (float)mu[0], m1 = (float)mu[1], m2 = (float)mu[2], m3 = (float)mu[3], m4 = (float)mu[4];
+        float4* Qc = reinterpret_cast<float4*>(Q + c * n3);
+        for (long q = threadIdx.x; q < runs; q += BS) {
+            const float4 v = yc[q];
+            const int r = (int)(q / q4), iz = 4 * (int)(q % q4);
+            const float vx = vg[r / n], vy = vg[r % n];
+            const float cxy = m0 + m1 * vx + m2 * vy + 0.5f * m4 * (vx * vx + vy * vy);
+            float4 o;
+            o.x = a * v.x - (cxy + m3 * vg[iz] + 0.5f * m4 * vg[iz] * vg[iz]);
+            o.y = a * v.y - (cxy + m3 * vg[iz + 1] + 0.5f * m4 * vg[iz + 1] * vg[iz + 1]);
+            o.z = a * v.z - (cxy + m3 * vg[iz + 2] + 0.5f * m4 * vg[iz + 2] * vg[iz + 2]);
+            o.w = a * v.w - (cxy + m3 * vg[iz + 3] + 0.5f * m4 * vg[iz + 3] * vg[iz + 3]);
+            Qc[q] = o;
         }
-        if (threadIdx.x == 0) ind[c] = (float)(ind_scale * ((double)dist[c] + defect));
+        if (threadIdx.x == 0) {
+            const double defect =
+                (fabs(sm[0]) + fabs(sm[1]) + fabs(sm[2]) + fabs(sm[3]) + fabs(sm[4])) / (sm[5] > 0 ? sm[5] : 1.0);
+            ind[c] = (float)(ind_scale * ((double)dist[c] + defect));
+        }
+        __syncthreads();   // mu and red are rewritten by the next cell
     }
 }
 
@@ -165,7 +226,9 @@ extern "C" {
 
 fks_status fks_surrogate_inputs(int n, double L, long ncells, const float* f, float* x, double* rho, float* dist,
                                 void* stream) {
-    if (!f || !x || !rho || !dist || ncells < 0 || n < 2 || !(L > 0)) return FKS_ERR_INVALID_ARG;
+    if (!f || !x || !rho || !dist || ncells < 0 || n < 4 || n % 4 != 0 || n > 64 || !(L > 0) ||
+        ((uintptr_t)f & 15) || ((uintptr_t)x & 15))
+        return FKS_ERR_INVALID_ARG;
     if (ncells == 0) return FKS_OK;
     const long grid = ncells < 152L * 8 ? ncells : 152L * 8;
     surr::inputs_kernel<<<(unsigned)grid, surr::BS, 0, (cudaStream_t)stream>>>(n, L, 0, ncells, f, x, rho, dist);
@@ -175,7 +238,7 @@ fks_status fks_surrogate_inputs(int n, double L, long ncells, const float* f, fl
 fks_status fks_surrogate_collide(fks_ctx* c, fks_net* net, const void* f, void* Q, double out_scale,
                                  double ind_scale, double threshold, long* nrouted, void* stream) {
     if (!c || !net || !f || !Q || f == Q) return FKS_ERR_INVALID_ARG;
-    if (c->fp64 || c->bgk || fks_net_grid(net) != c->n) {
+    if (c->fp64 || c->bgk || c->tc || fks_net_grid(net) != c->n) {
         c->err = "the surrogate needs an FP32 spectral context with the network's grid";
         return FKS_ERR_UNSUPPORTED;
     }
@@ -192,10 +255,15 @@ fks_status fks_surrogate_collide(fks_ctx* c, fks_net* net, const void* f, void* 
             return FKS_ERR_OOM;
         }
     }
+    if (((uintptr_t)f & 15) || ((uintptr_t)Q & 15)) return FKS_ERR_INVALID_ARG;
     const float* fin = static_cast<const float*>(f);
     float* Qo = static_cast<float*>(Q);
-    const int B = fks_net_max_batch(net);
+    const int B = fks_net_infer_capacity(net);
     float* xbuf = fks_net_input_buffer(net);
+    if (B < 1 || !xbuf) {
+        c->err = "surrogate inference workspace";
+        return FKS_ERR_OOM;
+    }
     for (long c0 = 0; c0 < nc; c0 += B) {
         const long k = nc - c0 < B ? nc - c0 : B;
         const long grid = k < 152L * 8 ? k : 152L * 8;

@@ -17,6 +17,7 @@ from . import build as _build
 
 FKS_FP64 = 0
 FKS_FP32 = 1
+FKS_BF16X3 = 2   # split-BF16 tensor-core transforms, FP32 storage
 HARD_SPHERE = 0
 MAXWELL = 1
 BGK = 2

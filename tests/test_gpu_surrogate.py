@@ -115,40 +115,51 @@ def test_network_inputs(fks, oracle):
         T = (U[c, 4] - 0.5 * r * u @ u) / (1.5 * r)
         M = I.maxwellian(n, L, 1.0, u, T)
         g = f[c] / r
-        assert abs(rho[c].item() - r) < 1e-12 * r
+        # the moments behind rho are FP32 partial sums (added in FP64)
+        assert abs(rho[c].item() - r) < 1e-6 * r
         np.testing.assert_allclose(x[c, 0].cpu().numpy(), g, rtol=1e-6, atol=1e-9)
         np.testing.assert_allclose(x[c, 1].cpu().numpy(), M, rtol=1e-5, atol=1e-9 * M.max())
         assert abs(dist[c].item() - np.linalg.norm(g - M) / np.linalg.norm(M)) < 1e-5
 
 
 def test_routed_surrogate_collide(fks, oracle):
+    # the routing path infers in chunks of 304 cells: 611 cells make two full
+    # chunks and a ragged last one of 3
     n, L, kn = 16, 8.0, 0.3
-    ctx = fks.Context(fks.Config(ncell=(5, 1, 1), n=n, L=L, kn=kn, A1=4, A2=4, precision=fks.FKS_FP32))
-    net = fks.Net(n, 2, seed=11)   # batches of 2 over 5 cells: a ragged last batch
-    f = I.two_stream((5, 1, 1), n, L, seed=6, noise=0.05).astype(np.float32)
+    nc = 2 * 304 + 3
+    ctx = fks.Context(fks.Config(ncell=(nc, 1, 1), n=n, L=L, kn=kn, A1=4, A2=4, precision=fks.FKS_FP32))
+    net = fks.Net(n, 2, seed=11)
+    f = I.two_stream((nc, 1, 1), n, L, seed=6, noise=0.05).astype(np.float32)
     fd = torch.from_numpy(f).cuda()
     Qs = torch.empty_like(fd)
     ctx.collide(fd, Qs)
     Q = torch.empty_like(fd)
-    assert ctx.surrogate_collide(net, fd, Q, 1.0, 1.0, -1.0) == 5          # every cell routed
+    assert ctx.surrogate_collide(net, fd, Q, 1.0, 1.0, -1.0) == nc         # every cell routed
     assert torch.equal(Q, Qs)
     assert ctx.surrogate_collide(net, fd, Q, 2.5, 1.0, 1e30) == 0          # none routed
     ind = ctx.indicator()
     assert np.all(np.isfinite(ind)) and np.all(ind > 0)
-    # oracle: network on the same inputs, rho^2 y scale / Kn, projection
+    # every cell: the projected output conserves mass, momentum and energy
+    Qh = Q.cpu().numpy()
+    Um = oracle.moments(Qh.astype(np.float64), n, L)
+    Ua = oracle.moments(np.abs(Qh).astype(np.float64), n, L)
+    assert np.all(np.abs(Um[:, 0]) < 1e-5 * Ua[:, 0])
+    # cells at the chunk boundaries and in the ragged tail against the oracle:
+    # network on the same inputs, rho^2 y scale / Kn, projection
+    cells = [0, 1, 303, 304, 607, 608, 609, 610]
     po = oracle_params(net.get_params())
-    U = oracle.moments(f.astype(np.float64), n, L)
+    U = oracle.moments(f[cells].astype(np.float64), n, L)
     xs = []
-    for c in range(5):
-        r = U[c, 0]
-        u = U[c, 1:4] / r
-        T = (U[c, 4] - 0.5 * r * u @ u) / (1.5 * r)
+    for i, c in enumerate(cells):
+        r = U[i, 0]
+        u = U[i, 1:4] / r
+        T = (U[i, 4] - 0.5 * r * u @ u) / (1.5 * r)
         xs.append(np.stack([f[c] / r, I.maxwellian(n, L, 1.0, u, T)]))
     # the routing path infers on the tensor cores (BF16 activations)
     yo, _ = onet.forward(po, np.stack(xs), act_bf16=True)
-    Qo = np.stack([(U[c, 0] ** 2) * yo[c, 0] * 2.5 / kn for c in range(5)])
+    Qo = np.stack([(U[i, 0] ** 2) * yo[i, 0] * 2.5 / kn for i in range(len(cells))])
     Qo = oracle.project(Qo, n, L)
-    assert rel(Q.cpu().numpy(), Qo) < 2e-3
+    assert rel(Qh[cells], Qo) < 2e-3
 
 
 def test_train_calibrate_route(fks):

@@ -1,0 +1,185 @@
+"""GPU parity of the split-BF16 tensor-core collision path (FKS_BF16X3) against
+the oracle: every 3-D DFT as tcgen05 products of BF16 pairs with FP32
+accumulation; table products, loss, projection and Euler step in FP32 with
+FP64 moment sums.  Tolerance: relative L2 of Q <= 1e-3, read with the
+conditioning of Q = G - L (tests/conftest.py::bf16_within)."""
+import numpy as np
+import pytest
+
+from conftest import BF16_REL, bf16_within
+from paper_1701_01608_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fks():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_01608_gb300 import fks
+    fks.lib()
+    return fks
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def make_ctx(fks, ncell, n, L, kernel=0, kn=1.0, A=(4, 4), prec=2, bc=(0, 0, 0)):
+    cfg = fks.Config(ncell=tuple(ncell), bc=tuple(bc), n=n, L=L, kernel=kernel, kn=kn, A1=A[0], A2=A[1],
+                     precision=prec)
+    return fks.Context(cfg)
+
+
+def loss_norm(oracle, f, tab, kn):
+    return np.array([np.linalg.norm(oracle.gain_loss(f[c], tab)[1]) / kn for c in range(f.shape[0])])
+
+
+@pytest.mark.parametrize("n,kernel,L,A,nc,kn", [
+    (16, 0, 8.0, (4, 4), 7, 0.3),
+    (16, 1, 8.0, (4, 4), 5, 1.0),
+    (16, 0, 8.0, (4, 4), 400, 0.5),    # more cells than CTAs: the persistent loop, a ragged last round
+    (32, 0, 10.0, (4, 8), 5, 0.3),
+    (32, 1, 10.0, (4, 8), 3, 1.0),
+])
+def test_tc_collide_matches_oracle(fks, oracle, n, kernel, L, A, nc, kn):
+    ctx = make_ctx(fks, (nc, 1, 1), n, L, kernel=kernel, kn=kn, A=A)
+    f = I.two_stream((nc, 1, 1), n, L, seed=31 + n + nc, noise=0.05).astype(np.float32)
+    fd = torch.from_numpy(f).cuda()
+    Q = torch.empty_like(fd)
+    ctx.collide(fd, Q)
+    assert ctx.check() == 0
+    tab = oracle.tables(n, L, kernel, 0.25, A[0], A[1], 0)
+    f64 = f.astype(np.float64)
+    Qo = oracle.collide(f64, tab, kn=kn, project=True)
+    Qg = Q.double().cpu().numpy()
+    idx = range(nc) if nc <= 16 else list(range(0, nc, 7)) + [nc - 1]
+    for c in idx:
+        Lc = oracle.gain_loss(f64[c], tab)[1] / kn
+        assert bf16_within(Qg[c], Qo[c], Lc), (c, rel(Qg[c], Qo[c]))
+        # these cells are far from equilibrium: the plain relative bound holds
+        assert rel(Qg[c], Qo[c]) < BF16_REL
+
+
+def test_tc_near_equilibrium_cell(fks, oracle):
+    """A nearly Maxwellian cell: ||L|| / ||Q|| is large and the error is bounded
+    on the loss scale."""
+    n, L = 16, 8.0
+    f = (I.maxwellian(n, L, 1.0, (0.1, 0.0, -0.2), 1.1) * (1 + 1e-3 * np.cos(np.arange(n ** 3).reshape(n, n, n))))
+    f = f[None].astype(np.float32)
+    ctx = make_ctx(fks, (1, 1, 1), n, L)
+    fd = torch.from_numpy(f).cuda()
+    Q = torch.empty_like(fd)
+    ctx.collide(fd, Q)
+    tab = oracle.tables(n, L, 0, 0.25, 4, 4, 0)
+    Qo = oracle.collide(f.astype(np.float64), tab, kn=1.0)
+    G, Lo = oracle.gain_loss(f[0].astype(np.float64), tab)
+    assert np.linalg.norm(Lo) / np.linalg.norm(Qo[0]) > 40
+    assert bf16_within(Q[0].double().cpu().numpy(), Qo[0], Lo)
+
+
+def test_tc_projection_conserves(fks, oracle):
+    n, L = 32, 10.0
+    ctx = make_ctx(fks, (4, 1, 1), n, L, A=(4, 8))
+    f = I.two_stream((4, 1, 1), n, L, seed=3, noise=0.05).astype(np.float32)
+    fd = torch.from_numpy(f).cuda()
+    Q = torch.empty_like(fd)
+    ctx.collide(fd, Q)
+    Qg = Q.double().cpu().numpy()
+    U = oracle.moments(Qg, n, L)
+    Ua = oracle.moments(np.abs(Qg), n, L)
+    # FP32 storage of the corrected values: moments at the level of FP32 rounding
+    assert np.all(np.abs(U[:, 0]) < 1e-6 * Ua[:, 0])
+    for i in (1, 2, 3):
+        assert np.all(np.abs(U[:, i]) < 1e-6 * (Ua[:, 0] * L))
+    assert np.all(np.abs(U[:, 4]) < 1e-6 * (Ua[:, 4] + Ua[:, 0] * L * L))
+
+
+def test_tc_matches_fp32_path_many_cells(fks):
+    """300 cells at n = 32: every cell within the bound of the FP32 path."""
+    n, L, nc = 32, 10.0, 300
+    f = torch.from_numpy(I.two_stream((nc, 1, 1), n, L, seed=8, noise=0.05).astype(np.float32)).cuda()
+    Qt, Q32 = torch.empty_like(f), torch.empty_like(f)
+    make_ctx(fks, (nc, 1, 1), n, L, A=(4, 8), kn=0.5).collide(f, Qt)
+    make_ctx(fks, (nc, 1, 1), n, L, A=(4, 8), kn=0.5, prec=1).collide(f, Q32)
+    d = ((Qt - Q32).double().flatten(1).norm(dim=1) / Q32.double().flatten(1).norm(dim=1)).cpu().numpy()
+    assert np.all(d < BF16_REL), float(d.max())
+
+
+def test_tc_steps_small_periodic_workload(fks, oracle):
+    """4^3 periodic cells, 16^3 velocities, M = 16, Kn = 0.1, 10 steps."""
+    w = I.config_small_periodic()
+    ctx = make_ctx(fks, w.ncell, w.n, w.L, kernel=w.kernel, kn=w.kn, A=(w.A1, w.A2))
+    tab = oracle.tables(w.n, w.L, w.kernel, w.C, w.A1, w.A2, 0)
+    sol = oracle.Solver(w.ncell, w.x0, w.x1, w.bc, w.n, w.L, tab, w.kn)
+    fd = torch.from_numpy(w.f0.astype(np.float32)).cuda()
+    f = fd.double().cpu().numpy()
+    out = torch.empty_like(fd)
+    dt = 0.25 * 0.25 / 8.0
+    for _ in range(w.steps):
+        ctx.step(fd, out, dt)
+        fd, out = out, fd
+        f = sol.step(f, dt)
+    assert ctx.check() & 1 == 0
+    assert rel(fd.double().cpu().numpy(), f) < 1e-4
+
+
+def test_tc_step_ragged_specular(fks, oracle):
+    """Transport gather inside the kernel: 3 x 5 x 2 cells, specular x and y."""
+    ncell, n, L, bc, kn = (3, 5, 2), 16, 8.0, (1, 1, 0), 0.5
+    ctx = make_ctx(fks, ncell, n, L, bc=bc, kn=kn)
+    tab = oracle.tables(n, L, 0, 0.25, 4, 4, 0)
+    sol = oracle.Solver(ncell, (0, 0, 0), (1, 1, 1), bc, n, L, tab, kn)
+    fd = torch.from_numpy(I.two_stream(ncell, n, L, seed=9, noise=0.1).astype(np.float32)).cuda()
+    f = fd.double().cpu().numpy()
+    out = torch.empty_like(fd)
+    dt = 0.7 * 0.2 / L
+    for _ in range(3):
+        ctx.step(fd, out, dt)
+        fd, out = out, fd
+        f = sol.step(f, dt)
+    assert rel(fd.double().cpu().numpy(), f) < 1e-4
+
+
+def test_tc_unsupported_configurations(fks):
+    with pytest.raises(fks.FKSError) as e:
+        make_ctx(fks, (1, 1, 1), 24, 10.0, A=(4, 8))
+    assert e.value.status == 2
+    with pytest.raises(fks.FKSError) as e:
+        make_ctx(fks, (1, 1, 1), 16, 8.0, kernel=fks.BGK)
+    assert e.value.status == 2
+    ctx = make_ctx(fks, (2, 1, 1), 16, 8.0)
+    with pytest.raises(fks.FKSError) as e:
+        ctx.set_cluster_size(2)
+    assert e.value.status == 2
+
+
+def test_tc_full_size_shock_tube_step_sampled(fks, oracle):
+    """32^3 cells x 32^3 velocities, M = 32, specular x walls: the benchmark's
+    step on the tensor-core path, sampled cells against transport followed by
+    the oracle's projected operator and Euler step."""
+    w = I.config_shock_tube(ncell=(1, 1, 1))
+    w.ncell = (32, 32, 32)
+    ctx = make_ctx(fks, w.ncell, w.n, w.L, kernel=w.kernel, kn=w.kn, A=(w.A1, w.A2), bc=w.bc)
+    ctx2 = make_ctx(fks, w.ncell, w.n, w.L, kernel=w.kernel, kn=w.kn, A=(w.A1, w.A2), bc=w.bc, prec=1)
+    states, which = I.shock_tube_states(w.n, w.L, 32)
+    st = torch.from_numpy(states).float().cuda()
+    f0 = st.index_select(0, torch.from_numpy(np.repeat(which, 1024)).cuda()).contiguous()
+    g = torch.Generator(device="cuda").manual_seed(2)
+    f0 *= 1.0 + 0.05 * (2.0 * torch.rand(f0.shape, generator=g, device="cuda", dtype=torch.float32) - 1.0)
+    f1 = torch.empty_like(f0)
+    dt = 1e-3
+    ctx.step(f0, f1, dt)
+    fs = torch.empty_like(f0)
+    ctx2.transport(f0, fs, dt)
+    assert ctx.check() & 1 == 0
+    sample = [0, 31 * 1024, 16 * 1024 + 5 * 32 + 7, 1023, 15 * 1024 + 31, 32767]
+    tab = oracle.tables(32, w.L, 0, 0.25, 4, 8, 0)
+    fsh = fs[sample].double().cpu().numpy()
+    Qo = oracle.collide(fsh, tab, kn=w.kn, project=True)
+    got = f1[sample].double().cpu().numpy()
+    for i in range(len(sample)):
+        inc_err = np.linalg.norm(got[i] - fsh[i] - dt * Qo[i]) / np.linalg.norm(dt * Qo[i])
+        assert inc_err < 2e-3, (sample[i], inc_err)
