@@ -20,8 +20,8 @@
 // (alpha_p + i w_p alphap_p) F gives a_p + i b_p: 1 + M + 1 complex 3-D
 // transforms per cell.
 //
-// Work split: one CTA of 128 threads per cell (persistent over cells), one
-// thread per TMEM lane.  Passes 1 (along z) and 2 (along y) run for a group of
+// Work split: one CTA of 512 threads per cell (persistent over cells); warp w
+// reads TMEM lanes 32 (w % 4) .. +31 and a quarter (w / 4) of the columns.  Passes 1 (along z) and 2 (along y) run for a group of
 // 8 x-planes at a time entirely on chip: each pass's epilogue reads its
 // accumulators from TMEM and writes the next operand, transposed, into shared
 // memory.  Pass 3 (along x) needs every plane, so the second epilogue writes
@@ -123,14 +123,37 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 
-// generated operand lists of the 32x32b TMEM loads and stores (16 and 32 columns)
+// operand lists of the 32x32b TMEM loads and stores (4, 8 and 16 columns); a
+// wait ties the loaded registers so that no use is scheduled before it
+__device__ __forceinline__ void tld4(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void twait4(uint32_t (&r)[4]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3])::"memory");
+}
+__device__ __forceinline__ void tst4(uint32_t taddr, const uint32_t (&r)[4]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
+                 : "memory");
+}
+__device__ __forceinline__ void tld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void twait8(uint32_t (&r)[8]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])::"memory");
+}
+__device__ __forceinline__ void tst8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
 __device__ __forceinline__ void tld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                  : "r"(taddr));
 }
-// completes this thread's TMEM loads; the registers are tied to the wait so
-// that no use of them can be scheduled before it
 __device__ __forceinline__ void twait16(uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])::"memory");
 }
@@ -138,71 +161,41 @@ __device__ __forceinline__ void tst16(uint32_t taddr, const uint32_t (&r)[16]) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
                  : "memory");
 }
-__device__ __forceinline__ void tld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(taddr));
-}
-// completes this thread's TMEM loads; the registers are tied to the wait so
-// that no use of them can be scheduled before it
-__device__ __forceinline__ void twait32(uint32_t (&r)[32]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
-}
-__device__ __forceinline__ void tst32(uint32_t taddr, const uint32_t (&r)[32]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
-                 : "memory");
-}
 
-
+// X consecutive TMEM columns of this thread's lane <-> registers
 template <int X>
-struct TRow;
-template <>
-struct TRow<16> {
-    static __device__ __forceinline__ void load(uint32_t t, float* v) {
-        uint32_t r[16];
-        tld16(t, r);
-        twait16(r);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-    }
-    static __device__ __forceinline__ void store(uint32_t t, const float* v) {
-        uint32_t r[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) r[i] = __float_as_uint(v[i]);
-        tst16(t, r);
-    }
-};
-template <>
-struct TRow<32> {
-    static __device__ __forceinline__ void load(uint32_t t, float* v) {
-        uint32_t r[32];
-        tld32(t, r);
-        twait32(r);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-    }
-    static __device__ __forceinline__ void store(uint32_t t, const float* v) {
-        uint32_t r[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(v[i]);
-        tst32(t, r);
-    }
-};
-template <>
-struct TRow<64> {
-    static __device__ __forceinline__ void load(uint32_t t, float* v) {
-        uint32_t r[32], s[32];
-        tld32(t, r);
-        tld32(t + 32, s);
-        twait32(r);
-        twait32(s);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            v[i] = __uint_as_float(r[i]);
-            v[32 + i] = __uint_as_float(s[i]);
-        }
-    }
-};
+struct TCols;
+#define FKS_TCOLS(X)                                                                   \
+    template <>                                                                        \
+    struct TCols<X> {                                                                  \
+        /* two X-column groups (re and im of a D slice) with one wait */               \
+        static __device__ __forceinline__ void load2(uint32_t t0, uint32_t t1, float* u, float* v) { \
+            uint32_t r[X], q[X];                                                       \
+            tld##X(t0, r);                                                             \
+            tld##X(t1, q);                                                             \
+            twait##X(r);                                                               \
+            twait##X(q);                                                               \
+            _Pragma("unroll") for (int i = 0; i < X; ++i) {                            \
+                u[i] = __uint_as_float(r[i]);                                          \
+                v[i] = __uint_as_float(q[i]);                                          \
+            }                                                                          \
+        }                                                                              \
+        static __device__ __forceinline__ void load(uint32_t t, float* u) {            \
+            uint32_t r[X];                                                             \
+            tld##X(t, r);                                                              \
+            twait##X(r);                                                               \
+            _Pragma("unroll") for (int i = 0; i < X; ++i) u[i] = __uint_as_float(r[i]); \
+        }                                                                              \
+        static __device__ __forceinline__ void store(uint32_t t, const float* u) {     \
+            uint32_t r[X];                                                             \
+            _Pragma("unroll") for (int i = 0; i < X; ++i) r[i] = __float_as_uint(u[i]); \
+            tst##X(t, r);                                                              \
+        }                                                                              \
+    };
+FKS_TCOLS(4)
+FKS_TCOLS(8)
+FKS_TCOLS(16)
+#undef FKS_TCOLS
 
 // BF16 split of an FP32 value: x = hi + lo + O(2^-18 |x|)
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
@@ -227,12 +220,17 @@ struct Args {
     double P[25];
 };
 
+constexpr int NTH = 512;   // 16 warps: warp w owns TMEM lanes 32 (w % 4) .. +31, column slice w / 4
+
 template <int N>
-__global__ void __launch_bounds__(128, 1) collide_tc_kernel(const __grid_constant__ Args a) {
+__global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constant__ Args a) {
     using C = Cfg<N>;
     constexpr int K = C::K, KCH = C::KCH, TILES = C::TILES, GT = C::GT, GROWS = C::GROWS;
+    constexpr int ZS = N / 4;          // columns of one slice (of re, and of im)
+    constexpr int HZ = N / 2;          // z values per thread in the pass-1 operand build
     constexpr long N3 = C::N3;
     constexpr uint32_t ID = idesc_bf16(128, K);
+    static_assert(2 * GROWS <= NTH, "two threads per pass-1 operand row");
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t bar_mma, bar_ld;
     __shared__ uint32_t tmem_base;
@@ -240,15 +238,16 @@ __global__ void __launch_bounds__(128, 1) collide_tc_kernel(const __grid_constan
     __shared__ int dsm[3 * N];
     __shared__ float vg[N];
     __shared__ double vgd[N];
-    __shared__ double red[4][5];
+    __shared__ double red[NTH / 32][5];
     __shared__ double mu[5];
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, cs = warp >> 2;
     const uint32_t sbase = smem_addr(smem);
-    for (uint32_t i = tid; i < 4 * C::BMAT / 16; i += 128) reinterpret_cast<uint4*>(smem + C::SM_B)[i] = a.dft[i];
+    for (uint32_t i = tid; i < 4 * C::BMAT / 16; i += NTH) reinterpret_cast<uint4*>(smem + C::SM_B)[i] = a.dft[i];
     const bool transport = a.delta != nullptr;
-    for (int i = tid; i < 3 * N; i += 128) dsm[i] = transport ? (int)a.delta[i] : 0;
+    for (int i = tid; i < 3 * N; i += NTH) dsm[i] = transport ? (int)a.delta[i] : 0;
     const double dv = 2.0 * a.L / N;
     if (tid < N) {
         vgd[tid] = ((double)tid + 0.5 - 0.5 * N) * dv;
@@ -270,7 +269,7 @@ __global__ void __launch_bounds__(128, 1) collide_tc_kernel(const __grid_constan
     __syncthreads();
     fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);   // this warp's TMEM lanes
+    const uint32_t tlane = tmem + ((uint32_t)(32 * quad) << 16);   // this warp's TMEM lanes
     uint32_t ph_mma = 0, ph_ld = 0;
     float2* fh = a.fh + (long)blockIdx.x * N3;
     unsigned char* a3 = a.a3 + (long)blockIdx.x * C::A3_CELL;
@@ -338,22 +337,24 @@ __global__ void __launch_bounds__(128, 1) collide_tc_kernel(const __grid_constan
             const bool fwd = t < 0;
             const uint32_t bdir = sbase + C::SM_B + (fwd ? 0u : 2u * C::BMAT);
             for (int g = 0; g < C::GROUPS; ++g) {
-                // ---- pass-1 operand: rows m = xl N + y, line (x, y, :) along z
-                for (int m = tid; m < GROWS; m += 128) {
-                    const int xl = m / N, y = m % N, x = C::GX * g + xl;
-                    float re[N], im[N];
+                // ---- pass-1 operand: rows m = xl N + y, line (x, y, :) along z; two threads per
+                // row, each with HZ consecutive z (whole 16-byte chunks of re and of im)
+                if (tid < 2 * GROWS) {
+                    const int m = tid >> 1, h = tid & 1;
+                    const int xl = m / N, y = m % N, x = C::GX * g + xl, z0 = h * HZ;
+                    float re[HZ], im[HZ];
                     if (fwd) {
                         const float* fr = frow(x, y);
 #pragma unroll
-                        for (int z = 0; z < N; ++z) {
-                            re[z] = fr[zoff[z]];
+                        for (int z = 0; z < HZ; ++z) {
+                            re[z] = fr[zoff[z0 + z]];
                             im[z] = 0.f;
                         }
                     } else {
-                        const float4* F = reinterpret_cast<const float4*>(fh + ((long)x * N + y) * N);
-                        const float4* T4 = reinterpret_cast<const float4*>(a.tab + (((long)t * N + x) * N + y) * N);
+                        const float4* F = reinterpret_cast<const float4*>(fh + ((long)x * N + y) * N + z0);
+                        const float4* T4 = reinterpret_cast<const float4*>(a.tab + (((long)t * N + x) * N + y) * N + z0);
 #pragma unroll
-                        for (int z2 = 0; z2 < N / 2; ++z2) {
+                        for (int z2 = 0; z2 < HZ / 2; ++z2) {
                             const float4 fv = F[z2], tv = __ldg(T4 + z2);
                             re[2 * z2] = fv.x * tv.x - fv.y * tv.y;
                             im[2 * z2] = fv.x * tv.y + fv.y * tv.x;
@@ -362,16 +363,17 @@ __global__ void __launch_bounds__(128, 1) collide_tc_kernel(const __grid_constan
                         }
                     }
 #pragma unroll
-                    for (int c = 0; c < KCH; ++c) {
-                        __align__(16) __nv_bfloat16 h[8], l[8];
+                    for (int c = 0; c < HZ / 8; ++c) {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int k = 8 * c + j;
-                            split_bf16(k < N ? re[k] : im[k - N], h[j], l[j]);
+                        for (int part = 0; part < 2; ++part) {
+                            __align__(16) __nv_bfloat16 hb[8], lb[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) split_bf16(part ? im[8 * c + j] : re[8 * c + j], hb[j], lb[j]);
+                            const int kc = part * (N / 8) + z0 / 8 + c;
+                            unsigned char* dst = smem + C::SM_A1 + kc * C::GPLANE + m * 16;
+                            *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(hb);
+                            *reinterpret_cast<uint4*>(dst + C::GSPLIT) = *reinterpret_cast<const uint4*>(lb);
                         }
-                        unsigned char* dst = smem + C::SM_A1 + c * C::GPLANE + m * 16;
-                        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
-                        *reinterpret_cast<uint4*>(dst + C::GSPLIT) = *reinterpret_cast<const uint4*>(l);
                     }
                 }
                 fence_async_smem();
@@ -386,19 +388,20 @@ __global__ void __launch_bounds__(128, 1) collide_tc_kernel(const __grid_constan
                 // ---- epilogue 1: line (xl, y) -> pass-2 operand rows m2 = z' 8 + xl, k = y (re), N + y (im)
 #pragma unroll 1
                 for (int tt = 0; tt < GT; ++tt) {
-                    const int m = 128 * tt + 32 * warp + lane;
+                    const int m = 128 * tt + 32 * quad + lane;
                     const int xl = m / N, y = m % N;
-                    float d[K];
-                    TRow<K>::load(tlane + C::ACC1 + tt * K, d);
-                    unsigned char* base = smem + C::SM_A2 + (y / 8) * C::GPLANE + xl * 16 + (y % 8) * 2;
+                    float dr[ZS], di[ZS];
+                    const uint32_t tc = tlane + C::ACC1 + tt * K + ZS * cs;
+                    TCols<ZS>::load2(tc, tc + N, dr, di);
+                    unsigned char* base = smem + C::SM_A2 + (y / 8) * C::GPLANE + xl * 16 + (y % 8) * 2 + ZS * cs * 128;
                     unsigned char* bim = base + (N / 8) * C::GPLANE;
 #pragma unroll
-                    for (int z = 0; z < N; ++z) {
+                    for (int z = 0; z < ZS; ++z) {
                         __nv_bfloat16 h, l;
-                        split_bf16(d[z], h, l);
+                        split_bf16(dr[z], h, l);
                         *reinterpret_cast<__nv_bfloat16*>(base + z * 128) = h;
                         *reinterpret_cast<__nv_bfloat16*>(base + z * 128 + C::GSPLIT) = l;
-                        split_bf16(d[N + z], h, l);
+                        split_bf16(di[z], h, l);
                         *reinterpret_cast<__nv_bfloat16*>(bim + z * 128) = h;
                         *reinterpret_cast<__nv_bfloat16*>(bim + z * 128 + C::GSPLIT) = l;
                     }
@@ -417,19 +420,20 @@ __global__ void __launch_bounds__(128, 1) collide_tc_kernel(const __grid_constan
                 // [split][part][tile][128 rows][16 B] in A1 (free: pass 1 has completed)
 #pragma unroll 1
                 for (int tt = 0; tt < GT; ++tt) {
-                    const int m2 = 128 * tt + 32 * warp + lane;
+                    const int m2 = 128 * tt + 32 * quad + lane;
                     const int z = m2 / 8, xl = m2 % 8;
-                    float d[K];
-                    TRow<K>::load(tlane + C::ACC2 + tt * K, d);
+                    float dr[ZS], di[ZS];
+                    const uint32_t tc = tlane + C::ACC2 + tt * K + ZS * cs;
+                    TCols<ZS>::load2(tc, tc + N, dr, di);
 #pragma unroll
-                    for (int yy = 0; yy < N; ++yy) {
-                        const int r = yy * N + z;
+                    for (int j = 0; j < ZS; ++j) {
+                        const int r = (ZS * cs + j) * N + z;
                         unsigned char* b0 = smem + C::SM_A1 + (r / 128) * C::TPLANE + (r % 128) * 16 + xl * 2;
                         __nv_bfloat16 h, l;
-                        split_bf16(d[yy], h, l);   // re: part 0
+                        split_bf16(dr[j], h, l);   // re: part 0
                         *reinterpret_cast<__nv_bfloat16*>(b0) = h;
                         *reinterpret_cast<__nv_bfloat16*>(b0 + 2 * TILES * C::TPLANE) = l;
-                        split_bf16(d[N + yy], h, l);   // im: part 1
+                        split_bf16(di[j], h, l);   // im: part 1
                         *reinterpret_cast<__nv_bfloat16*>(b0 + TILES * C::TPLANE) = h;
                         *reinterpret_cast<__nv_bfloat16*>(b0 + 3 * TILES * C::TPLANE) = l;
                     }
@@ -478,43 +482,45 @@ __global__ void __launch_bounds__(128, 1) collide_tc_kernel(const __grid_constan
                 }
                 wait_bar(&bar_mma, ph_mma);
                 fence_after();
-                // epilogue 3: line (y', z') along x, outputs x'
-                const int r = 128 * T + 32 * warp + lane, yy = r / N, zz = r % N;
-                float d[K];
-                TRow<K>::load(tlane + (uint32_t)(T & 1) * K, d);
-                const uint32_t gaddr = tlane + C::GCOL + (uint32_t)T * N;
+                // epilogue 3: line (y', z') along x, outputs x' of this warp's slice
+                const int r = 128 * T + 32 * quad + lane, yy = r / N, zz = r % N;
+                const int x0 = ZS * cs;
+                float dr[ZS], di[ZS];
+                const uint32_t tc = tlane + (uint32_t)(T & 1) * K + x0;
+                TCols<ZS>::load2(tc, tc + N, dr, di);
+                const uint32_t gaddr = tlane + C::GCOL + (uint32_t)T * N + x0;
                 if (fwd) {
 #pragma unroll
-                    for (int x = 0; x < N; ++x) fh[((long)x * N + yy) * N + zz] = make_float2(d[x], d[N + x]);
+                    for (int j = 0; j < ZS; ++j) fh[((long)(x0 + j) * N + yy) * N + zz] = make_float2(dr[j], di[j]);
                 } else if (t < a.M) {
-                    float gv[N];
+                    float gv[ZS];
                     if (t == 0) {
 #pragma unroll
-                        for (int x = 0; x < N; ++x) gv[x] = d[x] * d[N + x];
+                        for (int j = 0; j < ZS; ++j) gv[j] = dr[j] * di[j];
                     } else {
-                        TRow<N>::load(gaddr, gv);
+                        TCols<ZS>::load(gaddr, gv);
 #pragma unroll
-                        for (int x = 0; x < N; ++x) gv[x] = fmaf(d[x], d[N + x], gv[x]);
+                        for (int j = 0; j < ZS; ++j) gv[j] = fmaf(dr[j], di[j], gv[j]);
                     }
-                    TRow<N>::store(gaddr, gv);
+                    TCols<ZS>::store(gaddr, gv);
                     wait_st();
                 } else {
                     // loss: r = G - f* l (one rounding), q = r / Kn; FP64 moment sums
-                    float gv[N];
-                    TRow<N>::load(gaddr, gv);
+                    float gv[ZS];
+                    TCols<ZS>::load(gaddr, gv);
                     const float kn = (float)a.inv_kn;
                     double sr = 0.0, sx = 0.0, sxx = 0.0;
 #pragma unroll
-                    for (int x = 0; x < N; ++x) {
-                        const float fv = frow(x, yy)[zoff[zz]];
-                        const float q = fmaf(-fv, d[x], gv[x]) * kn;
-                        gv[x] = q;
-                        const double qd = (double)q;
+                    for (int j = 0; j < ZS; ++j) {
+                        const float fv = frow(x0 + j, yy)[zoff[zz]];
+                        const float q = fmaf(-fv, dr[j], gv[j]) * kn;
+                        gv[j] = q;
+                        const double qd = (double)q, vx = vgd[x0 + j];
                         sr += qd;
-                        sx = fma(qd, vgd[x], sx);
-                        sxx = fma(qd, 0.5 * vgd[x] * vgd[x], sxx);
+                        sx = fma(qd, vx, sx);
+                        sxx = fma(qd, 0.5 * vx * vx, sxx);
                     }
-                    TRow<N>::store(gaddr, gv);
+                    TCols<ZS>::store(gaddr, gv);
                     wait_st();
                     const double vy = vgd[yy], vz = vgd[zz];
                     s5[0] += sr;
@@ -526,7 +532,6 @@ __global__ void __launch_bounds__(128, 1) collide_tc_kernel(const __grid_constan
                 fence_before();
                 __syncthreads();
             }
-            if (fwd) __syncthreads();   // fh complete before the direction passes read it
         }
         if (s_abort) break;
 
@@ -540,8 +545,9 @@ __global__ void __launch_bounds__(128, 1) collide_tc_kernel(const __grid_constan
         }
         __syncthreads();
         if (tid < 5) {
-            double tot[5];
-            for (int j = 0; j < 5; ++j) tot[j] = red[0][j] + red[1][j] + red[2][j] + red[3][j];
+            double tot[5] = {0, 0, 0, 0, 0};
+            for (int w = 0; w < NTH / 32; ++w)
+                for (int j = 0; j < 5; ++j) tot[j] += red[w][j];
             double acc = 0.0;
             for (int j = 0; j < 5; ++j) acc += a.P[tid * 5 + j] * tot[j];
             mu[tid] = acc;
@@ -554,16 +560,18 @@ __global__ void __launch_bounds__(128, 1) collide_tc_kernel(const __grid_constan
         bool bad = false, neg = false;
 #pragma unroll 1
         for (int T = 0; T < TILES; ++T) {
-            const int r = 128 * T + 32 * warp + lane, yy = r / N, zz = r % N;
-            float gv[N];
-            TRow<N>::load(tlane + C::GCOL + (uint32_t)T * N, gv);
+            const int r = 128 * T + 32 * quad + lane, yy = r / N, zz = r % N;
+            const int x0 = ZS * cs;
+            float gv[ZS];
+            TCols<ZS>::load(tlane + C::GCOL + (uint32_t)T * N + x0, gv);
             const float vy = vg[yy], vz = vg[zz];
             const float cyz = m0 + m2 * vy + m3 * vz + 0.5f * m4 * (vy * vy + vz * vz);
             float* dst = a.out + cell * N3 + (long)yy * N + zz;
 #pragma unroll
-            for (int x = 0; x < N; ++x) {
+            for (int j = 0; j < ZS; ++j) {
+                const int x = x0 + j;
                 const float vx = vg[x];
-                const float q = gv[x] - (cyz + m1 * vx + 0.5f * m4 * vx * vx);
+                const float q = gv[j] - (cyz + m1 * vx + 0.5f * m4 * vx * vx);
                 const float o = stepm ? fmaf(dt, q, frow(x, yy)[zoff[zz]]) : q;
                 bad |= !isfinite(o);
                 neg |= stepm && (o < 0.f);
@@ -644,7 +652,7 @@ static cudaError_t launch_n(const tcd::Args& a, int grid, cudaStream_t s) {
     const int smem = C::SMEM > 117 * 1024 ? (int)C::SMEM : 117 * 1024;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, 128, smem, s>>>(a);
+    k<<<grid, tcd::NTH, smem, s>>>(a);
     return cudaGetLastError();
 }
 
