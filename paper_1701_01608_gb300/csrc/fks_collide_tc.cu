@@ -63,13 +63,15 @@ struct Cfg {
     static constexpr uint32_t TPLANE = 128 * 16;
     static constexpr uint32_t TSPLIT = KCH * TPLANE;
     static constexpr long A3_CELL = 2L * TILES * TSPLIT;     // pass-3 operands of one cell (bytes)
-    // shared memory: DFT matrices, then group buffers A1 (also the staging of
-    // the second epilogue) and A2; pass 3 double-buffers its tiles over A1|A2
+    // shared memory: the DFT matrices of the current direction (hi, lo), group
+    // buffers A1 and A2, the staging of the second epilogue; pass 3
+    // double-buffers its tiles over A1|A2
     static constexpr uint32_t SM_B = 0;
-    static constexpr uint32_t SM_A1 = SM_B + 4 * BMAT;
+    static constexpr uint32_t SM_A1 = SM_B + 2 * BMAT;
     static constexpr uint32_t SM_A2 = SM_A1 + GBUF;
-    static constexpr uint32_t SMEM = SM_A2 + GBUF;
-    static_assert(4 * TILES * TPLANE <= GBUF, "staging fits in A1");
+    static constexpr uint32_t STAGE = 4 * TILES * TPLANE;
+    static constexpr uint32_t SM_ST = SM_A2 + GBUF;
+    static constexpr uint32_t SMEM = SM_ST + STAGE;
     static_assert(4 * TSPLIT <= 2 * GBUF, "two pass-3 tiles fit in A1|A2");
     // tensor memory columns
     static constexpr int ACC1 = 0;                     // pass-1 accumulators (GT x K)
@@ -221,18 +223,17 @@ struct Args {
 };
 
 constexpr int NTH = 512;   // 16 warps: warp w owns TMEM lanes 32 (w % 4) .. +31, column slice w / 4
+constexpr int BULK = 32;   // the thread (warp 1) that issues and completes the bulk stores
 
 template <int N>
 __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constant__ Args a) {
     using C = Cfg<N>;
     constexpr int K = C::K, KCH = C::KCH, TILES = C::TILES, GT = C::GT, GROWS = C::GROWS;
     constexpr int ZS = N / 4;          // columns of one slice (of re, and of im)
-    constexpr int HZ = N / 2;          // z values per thread in the pass-1 operand build
     constexpr long N3 = C::N3;
     constexpr uint32_t ID = idesc_bf16(128, K);
-    static_assert(2 * GROWS <= NTH, "two threads per pass-1 operand row");
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t bar_mma, bar_ld;
+    __shared__ uint64_t bar1, bar2, bar3[2], bar_ld;   // pass-1, pass-2, pass-3 MMAs; pass-3 loads
     __shared__ uint32_t tmem_base;
     __shared__ long zoff[N];
     __shared__ int dsm[3 * N];
@@ -245,7 +246,6 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, cs = warp >> 2;
     const uint32_t sbase = smem_addr(smem);
-    for (uint32_t i = tid; i < 4 * C::BMAT / 16; i += NTH) reinterpret_cast<uint4*>(smem + C::SM_B)[i] = a.dft[i];
     const bool transport = a.delta != nullptr;
     for (int i = tid; i < 3 * N; i += NTH) dsm[i] = transport ? (int)a.delta[i] : 0;
     const double dv = 2.0 * a.L / N;
@@ -260,7 +260,10 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&bar_mma, 1);
+        mbar_init(&bar1, 1);
+        mbar_init(&bar2, 1);
+        mbar_init(&bar3[0], 1);
+        mbar_init(&bar3[1], 1);
         mbar_init(&bar_ld, 1);
         fence_mbar_init();
         s_abort = 0;
@@ -270,7 +273,8 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
     fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t tlane = tmem + ((uint32_t)(32 * quad) << 16);   // this warp's TMEM lanes
-    uint32_t ph_mma = 0, ph_ld = 0;
+    // mbarrier phases; every barrier has at most one commit or load outstanding
+    uint32_t ph1 = 0, ph2 = 0, ph3a = 0, ph3b = 0, ph_ld = 0;
     float2* fh = a.fh + (long)blockIdx.x * N3;
     unsigned char* a3 = a.a3 + (long)blockIdx.x * C::A3_CELL;
     const int ncx = a.nc[0], ncy = a.nc[1], ncz = a.nc[2];
@@ -290,22 +294,27 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
             s_abort = 1;
         }
     };
-    // MMAs of one pass over ntile 128-row tiles of an operand in shared memory
-    auto issue = [&](uint32_t abase, uint32_t aplane, uint32_t asplit, int ntile, uint32_t bbase, uint32_t dcol) {
+    // MMAs of one pass over ntile 128-row tiles of an operand in shared memory.
+    // The start-address field of a descriptor is the address >> 4 in its low
+    // bits, so a descriptor of base + off is the base descriptor + off / 16
+    // (every address here is below 2^18 bytes: no carry out of the field).
+    auto issue = [&](uint32_t abase, uint32_t aplane, uint32_t asplit, int ntile, uint32_t bbase, uint32_t dcol,
+                     uint64_t* bar) {
+        const uint64_t a0 = sdesc(abase, aplane, 128), b0 = sdesc(bbase, C::BPLANE, 128);
         for (int tt = 0; tt < ntile; ++tt) {
 #pragma unroll
             for (int s = 0; s < C::KSTEPS; ++s) {
-                const uint32_t ao = abase + 2u * s * aplane + (uint32_t)tt * 128u * 16u;
-                const uint64_t ah = sdesc(ao, aplane, 128), al = sdesc(ao + asplit, aplane, 128);
-                const uint64_t bh = sdesc(bbase + 2u * s * C::BPLANE, C::BPLANE, 128);
-                const uint64_t bl = sdesc(bbase + C::BMAT + 2u * s * C::BPLANE, C::BPLANE, 128);
+                const uint64_t ah = a0 + ((2u * s * aplane + (uint32_t)tt * 2048u) >> 4);
+                const uint64_t al = ah + (asplit >> 4);
+                const uint64_t bh = b0 + ((2u * s * C::BPLANE) >> 4);
+                const uint64_t bl = bh + (C::BMAT >> 4);
                 const uint32_t d = tmem + dcol + (uint32_t)tt * K;
                 mma(d, ah, bh, ID, s > 0 ? 1u : 0u);
                 mma(d, al, bh, ID, 1u);
                 mma(d, ah, bl, ID, 1u);
             }
         }
-        commit(&bar_mma);
+        commit(bar);
     };
 
     for (long cell = blockIdx.x; cell < a.ncells; cell += gridDim.x) {
@@ -335,55 +344,80 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
         // transform t: -1 forward (f* -> fh), 0..M-1 gain directions, M loss
         for (int t = -1; t <= a.M; ++t) {
             const bool fwd = t < 0;
-            const uint32_t bdir = sbase + C::SM_B + (fwd ? 0u : 2u * C::BMAT);
-            for (int g = 0; g < C::GROUPS; ++g) {
-                // ---- pass-1 operand: rows m = xl N + y, line (x, y, :) along z; two threads per
-                // row, each with HZ consecutive z (whole 16-byte chunks of re and of im)
-                if (tid < 2 * GROWS) {
-                    const int m = tid >> 1, h = tid & 1;
-                    const int xl = m / N, y = m % N, x = C::GX * g + xl, z0 = h * HZ;
-                    float re[HZ], im[HZ];
-                    if (fwd) {
-                        const float* fr = frow(x, y);
+            const uint32_t bdir = sbase + C::SM_B;
+            if (t <= 0) {
+                // DFT matrices of this direction (the previous transform's MMAs have completed)
+                const uint4* src = a.dft + (fwd ? 0 : 2 * C::BMAT / 16);
+                for (uint32_t i = tid; i < 2 * C::BMAT / 16; i += NTH) reinterpret_cast<uint4*>(smem + C::SM_B)[i] = src[i];
+            }
+
+            // pass-1 operand of group g into A1: rows m = xl N + y, line (x, y, :) along z.
+            // Unit e = (row, z pair): consecutive threads take consecutive pairs of a row,
+            // so the loads of a warp are contiguous; each thread writes its 4-byte piece
+            // (two BF16) of the 16-byte chunks of re and im, hi and lo.
+            auto build = [&](int g) {
+                constexpr int PAIRS = N / 2;
+                constexpr int EPT = GROWS * PAIRS / NTH;   // units per thread (8 at n = 32, 2 at n = 16)
+                static_assert(GROWS * PAIRS % NTH == 0, "whole units per thread");
+                float r0[EPT], i0[EPT], r1[EPT], i1[EPT];
+                if (fwd) {
 #pragma unroll
-                        for (int z = 0; z < HZ; ++z) {
-                            re[z] = fr[zoff[z0 + z]];
-                            im[z] = 0.f;
-                        }
-                    } else {
-                        const float4* F = reinterpret_cast<const float4*>(fh + ((long)x * N + y) * N + z0);
-                        const float4* T4 = reinterpret_cast<const float4*>(a.tab + (((long)t * N + x) * N + y) * N + z0);
+                    for (int u = 0; u < EPT; ++u) {
+                        const int e = tid + u * NTH, m = e / PAIRS, z2 = e % PAIRS;
+                        const float* fr = frow(C::GX * g + m / N, m % N);
+                        r0[u] = fr[zoff[2 * z2]];
+                        r1[u] = fr[zoff[2 * z2 + 1]];
+                        i0[u] = i1[u] = 0.f;
+                    }
+                } else {
+                    // all loads of the thread first: EPT coefficient and EPT table vectors in flight
+                    float4 fv[EPT], tv[EPT];
+                    const float4* F4 = reinterpret_cast<const float4*>(fh + (long)C::GX * g * N * N);
+                    const float4* T4 = reinterpret_cast<const float4*>(a.tab + ((long)t * N + C::GX * g) * N * N);
 #pragma unroll
-                        for (int z2 = 0; z2 < HZ / 2; ++z2) {
-                            const float4 fv = F[z2], tv = __ldg(T4 + z2);
-                            re[2 * z2] = fv.x * tv.x - fv.y * tv.y;
-                            im[2 * z2] = fv.x * tv.y + fv.y * tv.x;
-                            re[2 * z2 + 1] = fv.z * tv.z - fv.w * tv.w;
-                            im[2 * z2 + 1] = fv.z * tv.w + fv.w * tv.z;
-                        }
+                    for (int u = 0; u < EPT; ++u) {
+                        fv[u] = F4[tid + u * NTH];
+                        tv[u] = __ldg(T4 + tid + u * NTH);
                     }
 #pragma unroll
-                    for (int c = 0; c < HZ / 8; ++c) {
-#pragma unroll
-                        for (int part = 0; part < 2; ++part) {
-                            __align__(16) __nv_bfloat16 hb[8], lb[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) split_bf16(part ? im[8 * c + j] : re[8 * c + j], hb[j], lb[j]);
-                            const int kc = part * (N / 8) + z0 / 8 + c;
-                            unsigned char* dst = smem + C::SM_A1 + kc * C::GPLANE + m * 16;
-                            *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(hb);
-                            *reinterpret_cast<uint4*>(dst + C::GSPLIT) = *reinterpret_cast<const uint4*>(lb);
-                        }
+                    for (int u = 0; u < EPT; ++u) {
+                        r0[u] = fv[u].x * tv[u].x - fv[u].y * tv[u].y;
+                        i0[u] = fv[u].x * tv[u].y + fv[u].y * tv[u].x;
+                        r1[u] = fv[u].z * tv[u].z - fv[u].w * tv[u].w;
+                        i1[u] = fv[u].z * tv[u].w + fv[u].w * tv[u].z;
                     }
+                }
+#pragma unroll
+                for (int u = 0; u < EPT; ++u) {
+                    const int e = tid + u * NTH, m = e / PAIRS, z2 = e % PAIRS;
+                    const __nv_bfloat162 hr = __floats2bfloat162_rn(r0[u], r1[u]);
+                    const __nv_bfloat162 hi = __floats2bfloat162_rn(i0[u], i1[u]);
+                    const float2 fr2 = __bfloat1622float2(hr), fi2 = __bfloat1622float2(hi);
+                    const __nv_bfloat162 lr = __floats2bfloat162_rn(r0[u] - fr2.x, r1[u] - fr2.y);
+                    const __nv_bfloat162 li = __floats2bfloat162_rn(i0[u] - fi2.x, i1[u] - fi2.y);
+                    const int c = z2 / 4;   // chunk of z = 2 z2 (8 z per chunk)
+                    unsigned char* dre = smem + C::SM_A1 + c * C::GPLANE + m * 16 + (z2 % 4) * 4;
+                    unsigned char* dim = dre + (N / 8) * C::GPLANE;
+                    *reinterpret_cast<__nv_bfloat162*>(dre) = hr;
+                    *reinterpret_cast<__nv_bfloat162*>(dre + C::GSPLIT) = lr;
+                    *reinterpret_cast<__nv_bfloat162*>(dim) = hi;
+                    *reinterpret_cast<__nv_bfloat162*>(dim + C::GSPLIT) = li;
                 }
                 fence_async_smem();
                 fence_before();
                 __syncthreads();
                 if (tid == 0) {
                     fence_after();
-                    issue(sbase + C::SM_A1, C::GPLANE, C::GSPLIT, GT, bdir, C::ACC1);
+                    issue(sbase + C::SM_A1, C::GPLANE, C::GSPLIT, GT, bdir, C::ACC1, &bar1);
                 }
-                wait_bar(&bar_mma, ph_mma);
+            };
+
+            // Group pipeline: build(g+1) runs beside the pass-2 MMAs of g, and the
+            // second epilogue of g beside the pass-1 MMAs of g+1; the bulk stores of
+            // g's staging drain while group g+1 runs its first epilogue.
+            build(0);
+            for (int g = 0; g < C::GROUPS; ++g) {
+                wait_bar(&bar1, ph1);   // A2 and ACC2 were released when pass 2 of g-1 completed
                 fence_after();
                 // ---- epilogue 1: line (xl, y) -> pass-2 operand rows m2 = z' 8 + xl, k = y (re), N + y (im)
 #pragma unroll 1
@@ -393,7 +427,8 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
                     float dr[ZS], di[ZS];
                     const uint32_t tc = tlane + C::ACC1 + tt * K + ZS * cs;
                     TCols<ZS>::load2(tc, tc + N, dr, di);
-                    unsigned char* base = smem + C::SM_A2 + (y / 8) * C::GPLANE + xl * 16 + (y % 8) * 2 + ZS * cs * 128;
+                    unsigned char* base =
+                        smem + C::SM_A2 + (y / 8) * C::GPLANE + xl * 16 + (y % 8) * 2 + ZS * cs * 128;
                     unsigned char* bim = base + (N / 8) * C::GPLANE;
 #pragma unroll
                     for (int z = 0; z < ZS; ++z) {
@@ -406,18 +441,20 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
                         *reinterpret_cast<__nv_bfloat16*>(bim + z * 128 + C::GSPLIT) = l;
                     }
                 }
+                if (tid == BULK) bulk_wait_read();   // the staging of g-1 has been read out
                 fence_async_smem();
                 fence_before();
                 __syncthreads();
                 if (tid == 0) {
                     fence_after();
-                    issue(sbase + C::SM_A2, C::GPLANE, C::GSPLIT, GT, bdir, C::ACC2);
+                    issue(sbase + C::SM_A2, C::GPLANE, C::GSPLIT, GT, bdir, C::ACC2, &bar2);
                 }
-                wait_bar(&bar_mma, ph_mma);
+                if (g + 1 < C::GROUPS) build(g + 1);   // A1 and ACC1 are free
+                wait_bar(&bar2, ph2);
                 fence_after();
                 // ---- epilogue 2: line (z', xl) along y -> staging of the pass-3 operand:
                 // row r = y' N + z' of tile r / 128, k = x (re) or N + x (im); blocks
-                // [split][part][tile][128 rows][16 B] in A1 (free: pass 1 has completed)
+                // [split][part][tile][128 rows][16 B]
 #pragma unroll 1
                 for (int tt = 0; tt < GT; ++tt) {
                     const int m2 = 128 * tt + 32 * quad + lane;
@@ -428,7 +465,7 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
 #pragma unroll
                     for (int j = 0; j < ZS; ++j) {
                         const int r = (ZS * cs + j) * N + z;
-                        unsigned char* b0 = smem + C::SM_A1 + (r / 128) * C::TPLANE + (r % 128) * 16 + xl * 2;
+                        unsigned char* b0 = smem + C::SM_ST + (r / 128) * C::TPLANE + (r % 128) * 16 + xl * 2;
                         __nv_bfloat16 h, l;
                         split_bf16(dr[j], h, l);   // re: part 0
                         *reinterpret_cast<__nv_bfloat16*>(b0) = h;
@@ -441,26 +478,25 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
                 fence_async_smem();
                 fence_before();
                 __syncthreads();
-                if (tid == 0) {
+                if (tid == BULK) {
                     // block (split, part, tile) -> global k-chunk part * KCH/2 + g of that tile
                     for (int sp = 0; sp < 2; ++sp)
                         for (int part = 0; part < 2; ++part)
                             for (int T = 0; T < TILES; ++T) {
                                 unsigned char* dst =
                                     a3 + ((long)(sp * TILES + T) * KCH + part * (KCH / 2) + g) * C::TPLANE;
-                                const uint32_t src = sbase + C::SM_A1 + ((sp * 2 + part) * TILES + T) * C::TPLANE;
+                                const uint32_t src = sbase + C::SM_ST + ((sp * 2 + part) * TILES + T) * C::TPLANE;
                                 bulk_s2g(dst, src, C::TPLANE);
                             }
                     bulk_commit();
-                    bulk_wait_read();   // A1 may be rewritten
                 }
-                __syncthreads();
             }
             // every pass-3 operand of this transform is in global memory
-            if (tid == 0) bulk_wait_all();
+            if (tid == BULK) bulk_wait_all();
             __syncthreads();
 
-            // ---- pass 3 (along x), one 128-line tile at a time, loads double-buffered
+            // ---- pass 3 (along x): tiles double-buffered in A1|A2 and in TMEM; the MMAs
+            // of tile T+1 run beside the epilogue of tile T
             auto load_tile = [&](int T) {
                 const uint32_t buf = C::SM_A1 + (uint32_t)(T & 1) * 2u * C::TSPLIT;
                 mbar_expect_tx(&bar_ld, 2 * C::TSPLIT);
@@ -468,20 +504,23 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
                     bulk_g2s(smem + buf + sp * C::TSPLIT, a3 + (long)(sp * TILES + T) * KCH * C::TPLANE, C::TSPLIT,
                              &bar_ld);
             };
-            if (tid == 0) load_tile(0);
+            auto mma_tile = [&](int T) {   // thread 0: tile T has landed -> MMAs into accumulator T & 1
+                wait_bar(&bar_ld, ph_ld);
+                fence_after();
+                issue(sbase + C::SM_A1 + (uint32_t)(T & 1) * 2u * C::TSPLIT, C::TPLANE, C::TSPLIT, 1, bdir,
+                      (uint32_t)(T & 1) * K, &bar3[T & 1]);
+            };
+            if (tid == 0) {
+                load_tile(0);
+                mma_tile(0);
+                if (TILES > 1) load_tile(1);
+            }
 #pragma unroll 1
             for (int T = 0; T < TILES; ++T) {
-                if (tid == 0) {
-                    wait_bar(&bar_ld, ph_ld);
-                    fence_after();
-                    issue(sbase + C::SM_A1 + (uint32_t)(T & 1) * 2u * C::TSPLIT, C::TPLANE, C::TSPLIT, 1, bdir,
-                          (uint32_t)(T & 1) * K);
-                    if (T + 1 < TILES) load_tile(T + 1);   // its buffer's MMAs (tile T-1) have completed
-                } else {
-                    ph_ld ^= 1u;   // keep every thread's phase in step with thread 0
-                }
-                wait_bar(&bar_mma, ph_mma);
+                if (tid == 0 && T + 1 < TILES) mma_tile(T + 1);   // accumulator (T+1) & 1 was read by tile T-1
+                wait_bar(&bar3[T & 1], (T & 1) ? ph3b : ph3a);
                 fence_after();
+                if (tid == 0 && T + 2 < TILES) load_tile(T + 2);   // buffer T & 1: the MMAs of tile T are done
                 // epilogue 3: line (y', z') along x, outputs x' of this warp's slice
                 const int r = 128 * T + 32 * quad + lane, yy = r / N, zz = r % N;
                 const int x0 = ZS * cs;
@@ -584,7 +623,7 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
         __syncthreads();   // TMEM gain columns and zoff are reused by the next cell
     }
     // leave no asynchronous work behind
-    if (tid == 0) bulk_wait_all();
+    if (tid == BULK) bulk_wait_all();
     fence_before();
     __syncthreads();
     fence_after();
