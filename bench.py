@@ -50,6 +50,21 @@ def _bf16_peak():
 BF16_PEAK_TFLOPS, BF16_PEAK_KIND = _bf16_peak()
 
 
+# DRAM bytes per cell of one launch (dram__bytes_read.sum + dram__bytes_write.sum of one
+# ncu capture on the 16x16x8 = 2048-cell shock tube, divided by 2048; traffic grows with
+# the cells of a launch).  Valid for the kernels as profiled; None once a kernel changes.
+DRAM_BYTES_PER_CELL = {
+    "collide_f32": (274375424 + 221985792) / 2048,   # collide_kernel<float, 32, 4>
+    "bgk_f32": (315430656 + 209028864) / 2048,       # bgk_kernel<float, 32>
+    "collide_tc": (635289344 + 1520071000) / 2048,   # collide_tc_kernel<32> (scratch written back from L2)
+}
+
+
+def traffic(kernel):
+    b = DRAM_BYTES_PER_CELL.get(kernel)
+    return None if b is None else b * NCELLS
+
+
 def tc_issued_flops_per_cell(n=NV, m=M):
     """Tensor-core flops the split-BF16 path issues per cell: (M + 2) complex 3-D
     transforms x 3 passes x n^2/128 tiles x (2n/16 k-steps x 3 split products)
@@ -349,6 +364,31 @@ def main():
     flops_launch = flops_per_cell() * NCELLS
     achieved = flops_launch / (step_ms / 1e3) / 1e12
 
+    # stage timers (CUDA events, each stage alone; the step fuses transport, collision,
+    # projection and the Euler update into one kernel)
+    stages = None
+    if ws == 1:
+        tmp = torch.empty_like(f0)
+        U = torch.empty((NCELLS, 5), dtype=torch.float64, device=dev)
+
+        def ev_ms(fn, reps=2):
+            fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        stages = {"transport_ms": ev_ms(lambda: ctx.transport(f0, tmp, dt)),
+                  "moments_ms": ev_ms(lambda: ctx.moments(f0, U)),
+                  "collide_ms": ev_ms(lambda: ctx.collide(f0, tmp)),
+                  "step_ms": step_ms,
+                  "note": "FP32; transport = offsets + gather kernel (2 x 4 B per point), moments = FP64 sums"}
+        del tmp, U
+
     e2e = None
     if not args.no_e2e:
         # public API with host buffers: H2D of the step's input, the step, D2H of the result
@@ -390,7 +430,7 @@ def main():
         gbs = 8.0 * PTS / (bms / 1e3) / 1e9
         bgk = {"value": ws * PTS * args.steps / (tb / 1e3), "unit": "pts/s", "ms_per_step": tb / args.steps,
                "roofline": {"bound": "hbm", "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                            "frac": gbs / HBM_PEAK_GBS, "traffic": None,
+                            "frac": gbs / HBM_PEAK_GBS, "traffic": traffic("bgk_f32"),
                             "algorithmic_bytes_per_launch": 8.0 * PTS,
                             "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
                "note": "BGK relaxation (Sec. 2) with the fused transport gather, FP32"}
@@ -409,7 +449,8 @@ def main():
         tfl = issued / (tms / 1e3) / 1e12
         tcp = {"value": ws * PTS * args.steps / (tt / 1e3), "unit": "pts/s", "ms_per_step": tt / args.steps,
                "roofline": {"bound": "tensor", "achieved": tfl, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": tfl / BF16_PEAK_TFLOPS, "traffic": None, "issued_flops_per_launch": issued,
+                            "frac": tfl / BF16_PEAK_TFLOPS, "traffic": traffic("collide_tc"),
+                            "issued_flops_per_launch": issued,
                             "peak_note": "bf16_tflops_sustained of MEASURED_PEAKS.json (%s); issued split-BF16 "
                                          "MMA flops (3 products per DFT)" % BF16_PEAK_KIND},
                "algorithmic_tflops": flops_launch / (tms / 1e3) / 1e12,
@@ -462,7 +503,8 @@ def main():
                    "cluster_size": ctx.cluster_size, "l2": "inputs 4.3 GB > L2 (no flush needed)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic("collide_f32"),
+                     "traffic_note": "dram bytes of one ncu capture on 2048 cells, scaled by the cells of a launch",
                      "algorithmic_flops_per_launch": flops_launch,
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived, not measured)"},
         "cpu_baseline": cpu,
@@ -470,6 +512,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches,
         "health_bits": bits,
+        "stages": stages,
         "fp64_spectral": fp64,
         "bgk_step": bgk,
         "bf16x3_tensor_core": tcp,

@@ -246,6 +246,15 @@ fks_status fks_surrogate_collide(fks_ctx *ctx, fks_net *net, const void *f, void
 /* host copy of the last indicators (count = number of cells) */
 fks_status fks_surrogate_indicator(const fks_ctx *ctx, float *host, long count);
 
+/* Self-test of the failure detection of the kernels' waits (no GPU fault):
+ * one thread waits, with the bounded-wait helper of the collision kernels
+ * (bulk-copy and tensor-core completions), on an mbarrier that nothing
+ * arrives at; after `polls` polls (1 .. 2^26) it records the timeout bit and
+ * returns.  Synchronises `stream`.  Returns FKS_ERR_TIMEOUT (the expected
+ * result), FKS_ERR_INVALID_ARG for polls out of range, FKS_ERR_CUDA or
+ * FKS_ERR_OOM on a CUDA failure.  The device stays usable. */
+fks_status fks_selftest_wait(long polls, void *stream);
+
 /* fks_transport_noalloc -- the transport of fks_transport for callers that
  * cannot allocate device memory.  It is an addition of this library; the
  * paper has no counterpart.

@@ -500,6 +500,16 @@ static fks_status setup_tc(fks_ctx* c) {
     return FKS_OK;
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier that nothing
+// arrives at, with the helper every kernel uses, and records the timeout bit.
+__global__ void selftest_wait_kernel(long polls, int* flags) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_wait_bounded(&bar, 0, flags, polls);
+}
+
 extern "C" {
 
 const char* fks_status_string(fks_status s) {
@@ -805,6 +815,24 @@ fks_status fks_check(fks_ctx* c, void* stream, int* bits) {
     if (h & 4) return fail(c, FKS_ERR_NUMERIC, "cell shift out of range");
     if (h & 8) return fail(c, FKS_ERR_TIMEOUT, "a bulk copy did not complete in time");
     return FKS_OK;
+}
+
+fks_status fks_selftest_wait(long polls, void* stream) {
+    if (polls < 1 || polls > (1L << 26)) return FKS_ERR_INVALID_ARG;
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return FKS_ERR_OOM;
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        selftest_wait_kernel<<<1, 32, 0, s>>>(polls, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return FKS_ERR_CUDA;
+    return (h & 8) ? FKS_ERR_TIMEOUT : FKS_OK;
 }
 
 fks_status fks_get_offsets(fks_ctx* c, double* s) {

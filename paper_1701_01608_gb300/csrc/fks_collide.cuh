@@ -131,11 +131,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 // Bounded wait: a bulk copy of valid memory always completes; if it has not
-// after ~2^26 polls the kernel records FKS timeout (bit 3) and goes on.
-__device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, unsigned parity, int* flags) {
-    for (long it = 0; it < (1L << 26); ++it)
-        if (mbar_try_wait(bar, parity)) return;
+// after `polls` polls (default ~2^26) the kernel records FKS timeout (bit 3)
+// and goes on.  Returns whether the phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* flags, long polls = 1L << 26) {
+    for (long it = 0; it < polls; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
     atomicOr(flags, 8);
+    return false;
 }
 
 // fold a source cell coordinate: periodic wrap or specular reflection

@@ -64,7 +64,7 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_init", "fks_net_num_params", "fks_net_set_params", "fks_net_get_params", "fks_net_forward",
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
            "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
-           "fks_net_infer", "fks_net_check"]
+           "fks_net_infer", "fks_net_check", "fks_selftest_wait"]
 
 
 def lib(build: bool = True):
@@ -133,6 +133,7 @@ def lib(build: bool = True):
     L.fks_surrogate_inputs.argtypes = [I, D, ctypes.c_long, P, P, P, P, P]
     L.fks_surrogate_collide.argtypes = [P, P, P, P, D, D, D, ctypes.POINTER(ctypes.c_long), P]
     L.fks_surrogate_indicator.argtypes = [P, P, ctypes.c_long]
+    L.fks_selftest_wait.argtypes = [ctypes.c_long, P]
     L.fks_destroy.argtypes = [P]
     L.fks_destroy.restype = None
     L.fks_last_error.argtypes = [P]
@@ -429,3 +430,9 @@ def surrogate_inputs(n: int, L: float, f, x, rho, dist, stream=None):
                                     _dptr(rho, torch.float64), _dptr(dist, torch.float32), _stream_ptr(stream))
     if st != 0:
         raise FKSError(st, "fks_surrogate_inputs")
+
+
+def selftest_wait(polls: int = 4096, stream=None) -> int:
+    """Run the bounded-wait self-test (a wait that nothing completes); returns its
+    status: FKS_ERR_TIMEOUT (6) is the expected result."""
+    return lib().fks_selftest_wait(int(polls), _stream_ptr(stream))

@@ -247,3 +247,44 @@ def test_full_size_shock_tube_step_sampled(fks, oracle):
     ctx3.collide(fs[sample].contiguous(), Q)
     for i in range(len(sample)):
         assert rel(Q[i].double().cpu().numpy(), Qo[i]) < 1e-5
+
+
+def test_bounded_wait_times_out_and_device_stays_usable(fks, oracle):
+    """Failure detection without a GPU fault: a wait that nothing completes runs
+    out after its poll limit, the status says so, and the next work is correct."""
+    assert fks.selftest_wait(4096) == 6          # FKS_ERR_TIMEOUT
+    assert fks.selftest_wait(0) == 1             # FKS_ERR_INVALID_ARG
+    ctx = make_ctx(fks, (2, 1, 1), 8, 6.0, prec=0)
+    f = I.two_stream((2, 1, 1), 8, 6.0, seed=5)
+    fd = to_dev(f, ctx)
+    Q = torch.empty_like(fd)
+    ctx.collide(fd, Q)
+    assert ctx.check() == 0
+    Qo = oracle.collide(f, oracle.tables(8, 6.0, 0, 0.25, 4, 4, 0), kn=1.0)
+    assert rel(host64(Q), Qo) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_checkpoint_resume_is_bitwise(fks, prec):
+    """Checkpoint after 3 steps (f and the sub-cell offsets), resume in a new
+    context: 3 more steps reproduce the uninterrupted run bit for bit."""
+    w = I.config_small_periodic()
+    mk = lambda: make_ctx(fks, w.ncell, w.n, w.L, kernel=w.kernel, kn=w.kn, A=(w.A1, w.A2), prec=prec)
+    dt = 0.25 * 0.25 / 8.0
+    a = mk()
+    fa = to_dev(w.f0, a)
+    fb = torch.empty_like(fa)
+    for i in range(6):
+        a.step(fa, fb, dt)
+        fa, fb = fb, fa
+        if i == 2:
+            saved_f = fa.clone().cpu()
+            saved_s = a.offsets()
+    b = mk()
+    b.set_offsets(saved_s)
+    ga = saved_f.cuda()
+    gb = torch.empty_like(ga)
+    for _ in range(3):
+        b.step(ga, gb, dt)
+        ga, gb = gb, ga
+    assert torch.equal(ga, fa)
