@@ -16,6 +16,9 @@ Functions and the passage each follows:
   project                -- conservation correction (collision invariants, Sec. 2)
   bgk                    -- BGK relaxation nu (M[f] - f) (Sec. 2, BGK approximation)
   step                   -- Eq. disc_relax: transport, then f = f* + dt Q(f*)
+  pad, truncate,
+  collide_b, galerkin_b  -- variant B: Eq. CF1 with l + m = k not reduced mod n,
+                            evaluated with 2n transforms (Sec. 5); brute force
 
 Pins: every function is checked against values fixed outside this module by
 tests/test_oracle_*.py (numpy.fft, scipy quadrature / Bessel functions, closed
@@ -82,6 +85,10 @@ def _L():
             lib.or_offsets.argtypes = [I, D, D, D, P, P]
             lib.or_transport.argtypes = [P, P, I, P, P, P]
             lib.or_bgk.argtypes = [I, D, D, I, Lg, P, P]
+            lib.or_pad.argtypes = [I, P, P]
+            lib.or_truncate.argtypes = [I, P, P]
+            lib.or_collide_b.argtypes = [I, D, I, P, P, P, P, D, I, Lg, P, P]
+            lib.or_galerkin_b.argtypes = [I, D, I, D, I, I, I, D, P, P]
             _lib = lib
     return _lib
 
@@ -212,6 +219,43 @@ def bgk(f, n: int, L: float, kn: float = 1.0, project: bool = True) -> np.ndarra
     nc = f.size // n ** 3
     Q = np.empty_like(f)
     _L().or_bgk(n, L, 1.0 / kn, 1 if project else 0, nc, _p(f), _p(Q))
+    return Q
+
+
+def pad(f, n: int) -> np.ndarray:
+    """Trigonometric interpolant of an n^3 cell on the 2n grid (Nyquist split)."""
+    f = _f64(f).reshape(n, n, n)
+    f2 = np.empty((2 * n,) * 3)
+    _L().or_pad(n, _p(f), _p(f2))
+    return f2
+
+
+def truncate(Q2, n: int) -> np.ndarray:
+    """Modes |k| <= n/2 of a (2n)^3 array (+-n/2 folded), on the n grid."""
+    Q2 = _f64(Q2).reshape((2 * n,) * 3)
+    Q = np.empty((n, n, n))
+    _L().or_truncate(n, _p(Q2), _p(Q))
+    return Q
+
+
+def collide_b(f, tab2: Tables, kn: float = 1.0, project: bool = True) -> np.ndarray:
+    """Variant B (de-aliased) Q(f)/Kn for every n^3 cell of f; tab2 = tables(2n, L, ...)."""
+    f = _f64(f)
+    n = tab2.n // 2
+    shp = f.shape
+    assert shp[-3:] == (n, n, n)
+    nc = int(np.prod(shp[:-3])) if len(shp) > 3 else 1
+    Q = np.empty_like(f)
+    _L().or_collide_b(n, tab2.L, tab2.M, _p(tab2.alpha), _p(tab2.alphap), _p(tab2.w), _p(tab2.betaL),
+                      1.0 / kn, 1 if project else 0, nc, _p(f), _p(Q))
+    return Q
+
+
+def galerkin_b(f, n: int, L: float, ktype=HARD_SPHERE, C=0.25, A1=4, A2=4, rule=0, kn: float = 1.0) -> np.ndarray:
+    """Brute-force unprojected variant B (Eq. CF1 without mod n) of one n^3 cell; n <= 8."""
+    f = _f64(f).reshape(n, n, n)
+    Q = np.empty_like(f)
+    _L().or_galerkin_b(n, L, ktype, C, A1, A2, rule, 1.0 / kn, _p(f), _p(Q))
     return Q
 
 

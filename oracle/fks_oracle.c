@@ -642,3 +642,157 @@ void or_bgk(int n, double L, double inv_kn, int project, long ncells, const doub
         if (project) or_project(n, L, Q + c * n3);
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* variant B: the de-aliased operator of Eq. CF1 (l + m = k over the    */
+/* modes l, m in [-n/2, n/2]^3, not reduced mod n), evaluated with      */
+/* transforms of size 2n as in Sec. 5 (2n^3 transforms for n^3 modes).  */
+/* Reading of the inclusive mode range: the coefficient of a Nyquist    */
+/* component is split equally between +n/2 and -n/2; the result keeps   */
+/* the modes |k| <= n/2 and folds +-n/2 back onto the Nyquist index.    */
+/* ------------------------------------------------------------------ */
+
+/* f2 = the trigonometric interpolant of f on the 2n grid of the same box
+ * (points v_0 + j dv/2): FFT_n, Nyquist split, placement on the 2n index
+ * grid, inverse FFT_2n.  f2 at even indices equals f. */
+void or_pad(int n, const double *f, double *f2)
+{
+    int m = 2 * n;
+    long n3 = (long)n * n * n, m3 = (long)m * m * m;
+    cplx *F = (cplx *)malloc(sizeof(cplx) * n3);
+    cplx *G = (cplx *)calloc(m3, sizeof(cplx));
+    for (long k = 0; k < n3; ++k) F[k] = f[k];
+    or_fft3d(F, n, -1);
+    for (long k = 0; k < n3; ++k) {
+        int kk[3] = {(int)(k / ((long)n * n)), (int)((k / n) % n), (int)(k % n)};
+        int fl[3], nf = 0, s0[3];
+        for (int a = 0; a < 3; ++a) {
+            s0[a] = kappa(kk[a], n);
+            if (2 * kk[a] == n) fl[nf++] = a;
+        }
+        cplx val = F[k] / (double)n3 / (double)(1 << nf);
+        for (int c = 0; c < (1 << nf); ++c) {
+            int s[3] = {s0[0], s0[1], s0[2]};
+            for (int b = 0; b < nf; ++b)
+                if (c & (1 << b)) s[fl[b]] = -s[fl[b]];
+            long t = ((long)((s[0] + m) % m) * m + (s[1] + m) % m) * m + (s[2] + m) % m;
+            G[t] += val;
+        }
+    }
+    or_fft3d(G, m, +1);
+    for (long k = 0; k < m3; ++k) f2[k] = creal(G[k]);
+    free(F); free(G);
+}
+
+/* Q = the modes |k| <= n/2 of Q2 (2n grid), +-n/2 folded onto the Nyquist
+ * index, evaluated on the n grid: FFT_2n, selection, inverse FFT_n. */
+void or_truncate(int n, const double *Q2, double *Q)
+{
+    int m = 2 * n;
+    long n3 = (long)n * n * n, m3 = (long)m * m * m;
+    cplx *A = (cplx *)malloc(sizeof(cplx) * m3);
+    cplx *C = (cplx *)calloc(n3, sizeof(cplx));
+    for (long k = 0; k < m3; ++k) A[k] = Q2[k];
+    or_fft3d(A, m, -1);
+    for (long k = 0; k < m3; ++k) {
+        int kk[3] = {(int)(k / ((long)m * m)), (int)((k / m) % m), (int)(k % m)};
+        int s[3], keep = 1;
+        for (int a = 0; a < 3; ++a) {
+            s[a] = kappa(kk[a], m);
+            if (2 * abs(s[a]) > n) keep = 0;
+        }
+        if (!keep) continue;
+        long t = ((long)((s[0] + n) % n) * n + (s[1] + n) % n) * n + (s[2] + n) % n;
+        C[t] += A[k] / (double)m3;
+    }
+    or_fft3d(C, n, +1);
+    for (long k = 0; k < n3; ++k) Q[k] = creal(C[k]);
+    free(A); free(C);
+}
+
+/* Variant B for every cell: f2 = pad(f); gain and loss on the 2n grid with
+ * the tables of the 2n grid (alpha2, alphap2, betaL2 of or_tables(2n, L, ...));
+ * Q = truncate((G2 - L2) inv_kn), then the projection on the n grid. */
+void or_collide_b(int n, double L, int M, const double *alpha2, const double *alphap2, const double *w,
+                  const double *betaL2, double inv_kn, int project, long ncells, const double *f, double *Q)
+{
+    long n3 = (long)n * n * n, m3 = 8 * n3;
+#pragma omp parallel
+    {
+        double *f2 = (double *)malloc(sizeof(double) * m3);
+        double *G2 = (double *)malloc(sizeof(double) * m3);
+        double *L2 = (double *)malloc(sizeof(double) * m3);
+#pragma omp for schedule(dynamic)
+        for (long c = 0; c < ncells; ++c) {
+            or_pad(n, f + c * n3, f2);
+            or_gain_loss(2 * n, M, alpha2, alphap2, w, betaL2, f2, G2, L2);
+            for (long k = 0; k < m3; ++k) G2[k] = (G2[k] - L2[k]) * inv_kn;
+            or_truncate(n, G2, Q + c * n3);
+            if (project) or_project(n, L, Q + c * n3);
+        }
+        free(f2); free(G2); free(L2);
+    }
+}
+
+/* Brute-force Eq. CF1 without reduction mod n (unprojected): coefficients
+ * g_l of f on l in [-n/2, n/2]^3 (Nyquist split), beta(l, m) = sum_p w_p
+ * [alpha_p(l) alphap_p(m) - alpha_p(m) alphap_p(m)] with alpha_p(l) =
+ * phi(xi_l . e_p), alphap_p(l) = psi(|xi_l x e_p|) at the exact frequency
+ * xi_l = (pi/L) l, Qhat_k = sum_{l + m = k} beta(l, m) g_l g_m for |k| <= n/2,
+ * folded onto the n index grid and summed back: Q_j = sum_k Qhat_k e^{i xi_k v_j}.
+ * Cost O((n+1)^6 M): for n <= 8. */
+void or_galerkin_b(int n, double L, int ktype, double C, int A1, int A2, int rule, double inv_kn,
+                   const double *f, double *Q)
+{
+    int M = A1 * A2, ne = n + 1, h = n / 2;
+    long n3 = (long)n * n * n, e3 = (long)ne * ne * ne;
+    double *e = (double *)malloc(sizeof(double) * 3 * M), *w = (double *)malloc(sizeof(double) * M);
+    or_directions(A1, A2, rule, e, w);
+    double R = 2.0 / (3.0 + sqrt(2.0)) * L, hx = OR_PI / L;
+    gl_init();
+    cplx *F = (cplx *)malloc(sizeof(cplx) * n3);
+    for (long k = 0; k < n3; ++k) F[k] = f[k];
+    or_fft3d(F, n, -1);
+    /* extended coefficients and tables, index (l + h) per axis */
+    cplx *g = (cplx *)malloc(sizeof(cplx) * e3);
+    double *a = (double *)malloc(sizeof(double) * M * e3), *b = (double *)malloc(sizeof(double) * M * e3);
+    for (long i = 0; i < e3; ++i) {
+        int l[3] = {(int)(i / ((long)ne * ne)) - h, (int)((i / ne) % ne) - h, (int)(i % ne) - h};
+        int nf = 0;
+        long src = 0;
+        for (int x = 0; x < 3; ++x) {
+            if (abs(l[x]) == h) ++nf;
+            src = src * n + (l[x] + n) % n;
+        }
+        g[i] = F[src] / (double)n3 / (double)(1 << nf);
+        double xi[3] = {hx * l[0], hx * l[1], hx * l[2]};
+        for (int p = 0; p < M; ++p) {
+            double de = xi[0] * e[3 * p] + xi[1] * e[3 * p + 1] + xi[2] * e[3 * p + 2];
+            double q2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2] - de * de;
+            a[(long)p * e3 + i] = or_phi(ktype, C, R, de);
+            b[(long)p * e3 + i] = or_psi(ktype, C, R, sqrt(q2 > 0 ? q2 : 0.0));
+        }
+    }
+    cplx *Qc = (cplx *)calloc(n3, sizeof(cplx));
+#pragma omp parallel for schedule(dynamic)
+    for (long ik = 0; ik < e3; ++ik) {
+        int k[3] = {(int)(ik / ((long)ne * ne)) - h, (int)((ik / ne) % ne) - h, (int)(ik % ne) - h};
+        cplx acc = 0;
+        for (long il = 0; il < e3; ++il) {
+            int l[3] = {(int)(il / ((long)ne * ne)) - h, (int)((il / ne) % ne) - h, (int)(il % ne) - h};
+            int mm[3] = {k[0] - l[0], k[1] - l[1], k[2] - l[2]};
+            if (abs(mm[0]) > h || abs(mm[1]) > h || abs(mm[2]) > h) continue;
+            long im = ((long)(mm[0] + h) * ne + (mm[1] + h)) * ne + (mm[2] + h);
+            double beta = 0.0;
+            for (int p = 0; p < M; ++p)
+                beta += w[p] * (a[(long)p * e3 + il] - a[(long)p * e3 + im]) * b[(long)p * e3 + im];
+            acc += beta * g[il] * g[im];
+        }
+        long t = ((long)((k[0] + n) % n) * n + (k[1] + n) % n) * n + (k[2] + n) % n;
+#pragma omp critical
+        Qc[t] += acc;
+    }
+    or_fft3d(Qc, n, +1);
+    for (long j = 0; j < n3; ++j) Q[j] = creal(Qc[j]) * inv_kn;
+    free(e); free(w); free(F); free(g); free(a); free(b); free(Qc);
+}
