@@ -246,6 +246,18 @@ fks_status fks_surrogate_collide(fks_ctx *ctx, fks_net *net, const void *f, void
 /* host copy of the last indicators (count = number of cells) */
 fks_status fks_surrogate_indicator(const fks_ctx *ctx, float *host, long count);
 
+/* Variant B (de-aliased operator), Appendix A Eq. CF1 with l + m = k over the
+ * modes l, m in [-n/2, n/2]^3, not reduced mod n, evaluated with transforms of
+ * size 2n as in Sec. 5 (2n^3 transforms for n^3 modes).  on != 0: from then on
+ * fks_collide and fks_step of this context interpolate f* (the trigonometric
+ * interpolant; a Nyquist coefficient split between +-n/2) onto the 2n grid
+ * of the same box, run the operator there without projection, keep the modes
+ * |k| <= n/2 (+-n/2 folded back onto the Nyquist index) on the n grid and
+ * project.  Needs a spectral FP32 or FP64 context with n = 8 or 16, else
+ * FKS_ERR_UNSUPPORTED.  Allocates an inner context of the 2n grid and two
+ * chunk buffers of up to 2048 cells x (2n)^3 values.  on = 0 releases them. */
+fks_status fks_set_dealias(fks_ctx *ctx, int on);
+
 /* Self-test of the failure detection of the kernels' waits (no GPU fault):
  * one thread waits, with the bounded-wait helper of the collision kernels
  * (bulk-copy and tensor-core completions), on an mbarrier that nothing

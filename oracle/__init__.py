@@ -303,13 +303,16 @@ def transport(f, ncell, bc, delta) -> np.ndarray:
 
 
 class Solver:
-    """Plain FKS time loop: transport, then Euler collision step (Eq. disc_relax)."""
+    """Plain FKS time loop: transport, then Euler collision step (Eq. disc_relax).
+    tab = None: BGK relaxation; variant_b: tab holds the tables of the 2n grid and
+    the collision is the de-aliased operator (collide_b)."""
 
-    def __init__(self, ncell, x0, x1, bc, n, L, tab: Tables, kn: float):
+    def __init__(self, ncell, x0, x1, bc, n, L, tab: Tables, kn: float, variant_b: bool = False):
         self.ncell = tuple(int(c) for c in ncell)
         self.bc = tuple(int(b) for b in bc)
         self.dx = [(x1[a] - x0[a]) / self.ncell[a] for a in range(3)]
         self.n, self.L, self.tab, self.kn = n, L, tab, kn
+        self.variant_b = variant_b
         self.s = np.zeros((3, n))
 
     def transport(self, f, dt):
@@ -320,6 +323,8 @@ class Solver:
         fs = self.transport(f, dt)
         if self.tab is None:   # BGK relaxation
             Q = bgk(fs, self.n, self.L, self.kn, project=True)
+        elif self.variant_b:
+            Q = collide_b(fs, self.tab, self.kn, project=True)
         else:
             Q = collide(fs, self.tab, self.kn, project=True)
         return fs + dt * Q

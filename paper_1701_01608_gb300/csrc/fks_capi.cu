@@ -596,6 +596,7 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
 
 void fks_destroy(fks_ctx* c) {
     if (!c) return;
+    if (c->dealias) fks_set_dealias(c, 0);
     cudaFree(c->tables);
     cudaFree(c->tc_dft);
     cudaFree(c->tc_scratch);
@@ -621,6 +622,7 @@ fks_status fks_set_cluster_size(fks_ctx* c, int C) {
     if (!c) return FKS_ERR_INVALID_ARG;
     if (c->bgk) return fail(c, FKS_ERR_UNSUPPORTED, "the BGK kernel has no cluster size");
     if (c->tc) return fail(c, FKS_ERR_UNSUPPORTED, "the tensor-core kernel has no cluster size");
+    if (c->dealias) return fks_set_cluster_size(c->inner, C);   // the 2n kernel does the transforms
     if (C == c->C) return FKS_OK;
     // tables are laid out per cluster rank: rebuild them for the new size
     CollideVariant v;
@@ -690,6 +692,7 @@ static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const sig
                                  cudaStream_t s) {
     if (c->bgk) return launch_bgk_ctx(c, f, out, delta, dt, mode, s);
     if (c->tc) return launch_tc_ctx(c, f, out, delta, dt, mode, s);
+    if (c->dealias) return launch_dealias(c, f, out, delta, dt, mode, s);
     CollideArgs a;
     a.f = f;
     a.out = out;
@@ -726,6 +729,11 @@ static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const sig
     if (e != cudaSuccess) return cuda_fail(c, e, "collision kernel launch");
     c->launches += 1;
     return FKS_OK;
+}
+
+fks_status fks_internal_fail(fks_ctx* c, fks_status st, const std::string& msg) { return fail(c, st, msg); }
+fks_status fks_internal_collide(fks_ctx* c, const void* f, void* out, int mode, cudaStream_t s) {
+    return launch_collide(c, f, out, nullptr, 0.0, mode, s);
 }
 
 static fks_status launch_offsets(fks_ctx* c, double dt, cudaStream_t s) {

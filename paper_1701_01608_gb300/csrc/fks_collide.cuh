@@ -66,7 +66,7 @@ struct CollideArgs {
     double L;               // velocity box half width
     double inv_kn;
     double dt;              // Euler step (step mode)
-    int mode;               // 0 collide (out = Q), 1 step (out = f* + dt Q)
+    int mode;               // 0 collide (out = Q), 1 step (out = f* + dt Q), 2 collide without projection
     double P[25];           // dv^6 (C C^T)^-1 over the rows phi = (1, v, |v|^2/2)
     const BatchItem* items; // batch mode: ncells items, each a homogeneous problem
 };
@@ -627,7 +627,7 @@ collide_kernel(CollideArgs args) {
                     for (int i = 0; i < 5; ++i) {
                         double acc = 0.0;
                         for (int j = 0; j < 5; ++j) acc += Pm[i * 5 + j] * tot[j];
-                        mu[i] = acc;
+                        mu[i] = args.mode == 2 ? 0.0 : acc;   // mode 2: the caller projects
                     }
                     // correction phi(v).mu = mu0 + mu1 vx + mu2 vy + mu4 (vx^2+vy^2)/2 + [mu3 vz + mu4 vz^2/2]
                     for (int z = 0; z < N; ++z) czt[z] = (T)(mu[3] * vzt[z] + mu[4] * vz2t[z]);

@@ -73,6 +73,14 @@ struct fks_ctx {
     void* tc_dft = nullptr;     // BF16 DFT matrices
     void* tc_scratch = nullptr; // per-CTA spectrum and pass-3 operand scratch
     int tc_grid = 0;
+    // variant B (fks_set_dealias): inner context of the 2n grid, chunk buffers, P and T
+    bool dealias = false;
+    fks_ctx* inner = nullptr;
+    void* d2f = nullptr;
+    void* d2q = nullptr;
+    void* dPm = nullptr;
+    void* dTm = nullptr;
+    long dchunk = 0;
     fks_grid grid;
     fks_vbox vbox;
     fks_kernel kern;
@@ -100,6 +108,16 @@ struct fks_ctx {
     int* s_count = nullptr;
 };
 
+
+// Context helpers shared by the translation units (fks_capi.cu): record an
+// error message and return the status; launch a context's collision kernel
+// (mode 0 collide, 1 step without transport, 2 collide without projection).
+// (C linkage: they are defined beside the C ABI.)
+extern "C" fks_status fks_internal_fail(fks_ctx* c, fks_status st, const std::string& msg);
+extern "C" fks_status fks_internal_collide(fks_ctx* c, const void* f, void* out, int mode, cudaStream_t s);
+// variant B (fks_dealias.cu)
+fks_status launch_dealias(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
+                          cudaStream_t s);
 
 // Surrogate network internals (fks_net.cu) used by the routing path.
 const float* fks_net_forward_internal(fks_net* m, int batch, const float* x, cudaStream_t s, fks_status* st);

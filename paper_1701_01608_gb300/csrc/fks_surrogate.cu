@@ -238,7 +238,7 @@ fks_status fks_surrogate_inputs(int n, double L, long ncells, const float* f, fl
 fks_status fks_surrogate_collide(fks_ctx* c, fks_net* net, const void* f, void* Q, double out_scale,
                                  double ind_scale, double threshold, long* nrouted, void* stream) {
     if (!c || !net || !f || !Q || f == Q) return FKS_ERR_INVALID_ARG;
-    if (c->fp64 || c->bgk || c->tc || fks_net_grid(net) != c->n) {
+    if (c->fp64 || c->bgk || c->tc || c->dealias || fks_net_grid(net) != c->n) {
         c->err = "the surrogate needs an FP32 spectral context with the network's grid";
         return FKS_ERR_UNSUPPORTED;
     }

@@ -64,7 +64,7 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_init", "fks_net_num_params", "fks_net_set_params", "fks_net_get_params", "fks_net_forward",
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
            "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
-           "fks_net_infer", "fks_net_check", "fks_selftest_wait"]
+           "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias"]
 
 
 def lib(build: bool = True):
@@ -134,6 +134,7 @@ def lib(build: bool = True):
     L.fks_surrogate_collide.argtypes = [P, P, P, P, D, D, D, ctypes.POINTER(ctypes.c_long), P]
     L.fks_surrogate_indicator.argtypes = [P, P, ctypes.c_long]
     L.fks_selftest_wait.argtypes = [ctypes.c_long, P]
+    L.fks_set_dealias.argtypes = [P, I]
     L.fks_destroy.argtypes = [P]
     L.fks_destroy.restype = None
     L.fks_last_error.argtypes = [P]
@@ -184,6 +185,7 @@ class Config:
     A2: int = 4
     rule: int = 0
     precision: int = FKS_FP32
+    dealias: bool = False   # variant B: 2n-padded (de-aliased) operator, n = 8 or 16
 
 
 class Context:
@@ -205,6 +207,12 @@ class Context:
             raise FKSError(st, "fks_init")
         self._h = h
         self.dtype = torch.float64 if cfg.precision == FKS_FP64 else torch.float32
+        if cfg.dealias:
+            self.set_dealias(True)
+
+    def set_dealias(self, on: bool = True):
+        """Variant B: the 2n-padded (de-aliased) operator for this context's collisions."""
+        self._check(self._L.fks_set_dealias(self._h, 1 if on else 0), "fks_set_dealias")
 
     def __del__(self):
         h = getattr(self, "_h", None)
