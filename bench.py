@@ -322,6 +322,7 @@ def main():
     ap.add_argument("--no-bgk", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
+    ap.add_argument("--no-varb", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=int(os.environ.get("FKS_CPU_SAMPLE", "1024")))
     ap.add_argument("--grid", default=None, help="nx,ny,nz spatial cells (default 32,32,32); smaller grids "
                     "are for profiling runs, not bench lines")
@@ -476,6 +477,46 @@ def main():
             tcp["err_sample"] = "64 seeded two-stream cells (5 % noise) on the workload's velocity grid, relative L2 of Q"
         del ctxt
 
+    # variant B (de-aliased, 2n transforms) in the paper's own setting: 16^3 modes with 32^3 transforms
+    varb = None
+    if not args.no_varb and ws == 1:
+        from paper_1701_01608_gb300 import inputs as I
+        nb = 16
+        states, which = I.shock_tube_states(nb, LBOX, GRID[0])
+        sb = torch.from_numpy(states).float().to(dev)
+        fb0 = sb.index_select(0, torch.from_numpy(np.repeat(which, GRID[1] * GRID[2])).to(dev)).contiguous()
+        res = {}
+        for name, dealias in (("variant_b", True), ("variant_a", False)):
+            cb = fks.Context(fks.Config(ncell=GRID, bc=(1, 0, 0), n=nb, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
+                                        precision=fks.FKS_FP32, dealias=dealias))
+            tb_, perb_, lb_, bitsb_, _ = time_steps(torch, cb, fb0, args.steps, args.warmup, dt, ws)
+            res[name] = {"ms_per_step": tb_ / args.steps, "value": NCELLS * nb ** 3 * args.steps / (tb_ / 1e3),
+                         "gpu_launches": lb_, "health_bits": bitsb_}
+            del cb
+        # error of FP32 variant B against FP64 variant B on far-from-equilibrium cells
+        fs = torch.from_numpy(I.two_stream((64, 1, 1), nb, LBOX, seed=78, noise=0.05)).to(dev)
+        q64 = torch.empty_like(fs)
+        fks.Context(fks.Config(ncell=(64, 1, 1), n=nb, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
+                               precision=fks.FKS_FP64, dealias=True)).collide(fs, q64)
+        q32 = torch.empty_like(fs, dtype=torch.float32)
+        fks.Context(fks.Config(ncell=(64, 1, 1), n=nb, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
+                               precision=fks.FKS_FP32, dealias=True)).collide(fs.float(), q32)
+        d = ((q32.double() - q64).flatten(1).norm(dim=1) / q64.flatten(1).norm(dim=1)).cpu().numpy()
+        ms_b = res["variant_b"]["ms_per_step"]
+        fl2 = flops_per_cell(2 * nb, M) * NCELLS
+        varb = {"value": res["variant_b"]["value"], "unit": "pts/s (N_v = 16^3)", "ms_per_step": ms_b,
+                "variant_a_same_grid": res["variant_a"],
+                "roofline": {"bound": "alu", "achieved": fl2 / (ms_b / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                             "unit": "TFLOP/s", "frac": fl2 / (ms_b / 1e3) / 1e12 / FP32_PEAK_TFLOPS, "traffic": None,
+                             "algorithmic_flops_per_launch": fl2,
+                             "peak_note": "operator flops at the 2n = 32 grid; derived FP32 peak"},
+                "gpu_launches": res["variant_b"]["gpu_launches"],
+                "err_fp32_vs_fp64": {"max": float(d.max()), "median": float(np.median(d))},
+                "note": "shock tube %dx%dx%d cells x 16^3 velocities, FP32, fks_step with fks_set_dealias: "
+                        "interpolation to 32^3, the 32^3 collision without projection, truncation to "
+                        "|k| <= 8 and projection (per 2048-cell chunk: 3 launches)" % GRID}
+        del fb0, sb
+
     learned = None
     if not args.no_learned and ws == 1:
         learned = learned_path(torch, fks, dev, args)
@@ -516,6 +557,7 @@ def main():
         "fp64_spectral": fp64,
         "bgk_step": bgk,
         "bf16x3_tensor_core": tcp,
+        "variant_b_16v": varb,
         "learned": learned,
     }
     print(json.dumps(out), flush=True)

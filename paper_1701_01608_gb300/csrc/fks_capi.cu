@@ -211,10 +211,152 @@ __global__ void offsets_kernel(int n, double L, double3 dx3, double dt, double* 
 
 // ------------------------------------------------------------------ transport
 // f_out[j][k] = f[j - delta_k][k'] : one thread per output element
+// One CTA per cell (persistent over cells), rows of N/V lanes: lane group t
+// owns velocity indices z0 .. z0+V-1 (V = 16 bytes / sizeof T) of the rows
+// (x, y) = t / (N/V) + RPI j.  The source offsets of the transported cell are
+// tabulated per axis in shared memory; where the thread's V source elements
+// are one aligned run they move as one 16-byte access.
 template <typename T>
-__global__ void transport_kernel(int n, int ncx, int ncy, int ncz, int bcx, int bcy, int bcz,
-                                 const signed char* __restrict__ delta, const T* __restrict__ f,
-                                 T* __restrict__ out, long total) {
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+};
+
+// transport gather f*[j][k] = f[j - delta_k][k'] (Sec. 2.1, exact shift)
+template <typename T, int N>
+__global__ void __launch_bounds__(256) transport_kernel(int ncx, int ncy, int ncz, int bcx, int bcy, int bcz,
+                                                        const signed char* __restrict__ delta, const T* __restrict__ f,
+                                                        T* __restrict__ out, long ncells) {
+    constexpr int BS = 256, V = 16 / (int)sizeof(T), LPR = N / V, RPI = BS / LPR;
+    constexpr int ROWS = (N * N + RPI - 1) / RPI;
+    constexpr long N3 = (long)N * N * N;
+    using VT = typename Vec16<T>::type;
+    __shared__ long src_x[N], src_y[N], src_z[N];
+    const int tid = threadIdx.x;
+    const bool lane_ok = tid < LPR * RPI;
+    const int z0 = (tid % LPR) * V, r0 = tid / LPR;
+    for (long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
+        const int cx = (int)(cell / ((long)ncy * ncz)), cy = (int)((cell / ncz) % ncy), cz = (int)(cell % ncz);
+        __syncthreads();   // the previous cell's readers of the tables are done
+        for (int i = tid; i < 3 * N; i += BS) {
+            const int ax = i / N, k = i % N;
+            const int c0 = ax == 0 ? cx : (ax == 1 ? cy : cz);
+            const int len = ax == 0 ? ncx : (ax == 1 ? ncy : ncz);
+            const int bc = ax == 0 ? bcx : (ax == 1 ? bcy : bcz);
+            int fl = 0;
+            const int sc = fold_cell(c0 - delta[i], len, bc, fl);
+            const int q = fl ? N - 1 - k : k;
+            if (ax == 0) src_x[k] = (long)sc * ncy * ncz * N3 + (long)q * N * N;
+            else if (ax == 1) src_y[k] = (long)sc * ncz * N3 + (long)q * N;
+            else src_z[k] = (long)sc * N3 + q;
+        }
+        __syncthreads();
+        if (!lane_ok) continue;
+        long zo[V];
+        bool vec = true;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            zo[k] = src_z[z0 + k];
+            vec &= zo[k] == zo[0] + k;
+        }
+        vec &= (zo[0] % V) == 0;
+        T* oc = out + cell * N3 + z0;
+#pragma unroll 4
+        for (int j = 0; j < ROWS; ++j) {
+            const int r = r0 + RPI * j;
+            if (r >= N * N) break;
+            const long rb = src_x[r / N] + src_y[r % N];
+            VT w;
+            if (vec) {
+                w = __ldcs(reinterpret_cast<const VT*>(f + rb + zo[0]));
+            } else {
+                T* pw = reinterpret_cast<T*>(&w);
+#pragma unroll
+                for (int k = 0; k < V; ++k) pw[k] = __ldcs(f + rb + zo[k]);
+            }
+            __stcs(reinterpret_cast<VT*>(oc + (long)r * N), w);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ moments
+// U = dv^3 sum phi(v) f, phi = (1, v, |v|^2/2), in FP64 with three FP64
+// operations per element: along a 16-byte run the sums of f, f v_z and
+// f v_z^2/2, then per row the factors v_x, v_y.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) moments_kernel(double L, long ncells, const T* __restrict__ f,
+                                                      double* __restrict__ U) {
+    constexpr int BS = 256, V = 16 / (int)sizeof(T), LPR = N / V, RPI = BS / LPR;
+    constexpr int ROWS = (N * N + RPI - 1) / RPI;
+    constexpr long N3 = (long)N * N * N;
+    using VT = typename Vec16<T>::type;
+    __shared__ double red[BS / 32][5];
+    __shared__ double vg[N];
+    const int tid = threadIdx.x;
+    const double dv = 2.0 * L / N;
+    if (tid < N) vg[tid] = ((double)tid + 0.5 - 0.5 * N) * dv;
+    __syncthreads();
+    const bool lane_ok = tid < LPR * RPI;
+    const int z0 = (tid % LPR) * V, r0 = tid / LPR;
+    double vz[V], vz2[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        vz[k] = vg[(z0 + k) % N];
+        vz2[k] = 0.5 * vz[k] * vz[k];
+    }
+    for (long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
+        double s[5] = {0, 0, 0, 0, 0};
+        if (lane_ok) {
+            const T* fc = f + cell * N3 + z0;
+#pragma unroll 4
+            for (int j = 0; j < ROWS; ++j) {
+                const int r = r0 + RPI * j;
+                if (r >= N * N) break;
+                const VT w = __ldcs(reinterpret_cast<const VT*>(fc + (long)r * N));
+                const T* pw = reinterpret_cast<const T*>(&w);
+                double t0 = 0.0, tz = 0.0, tzz = 0.0;
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const double m = (double)pw[k];
+                    t0 += m;
+                    tz = fma(m, vz[k], tz);
+                    tzz = fma(m, vz2[k], tzz);
+                }
+                const double vx = vg[r / N], vy = vg[r % N];
+                s[0] += t0;
+                s[1] = fma(t0, vx, s[1]);
+                s[2] = fma(t0, vy, s[2]);
+                s[3] += tz;
+                s[4] = fma(t0, 0.5 * (vx * vx + vy * vy), s[4]) + tzz;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s[i] += __shfl_xor_sync(0xffffffffu, s[i], off);
+        const int warp = tid >> 5;
+        if ((tid & 31) == 0)
+            for (int i = 0; i < 5; ++i) red[warp][i] = s[i];
+        __syncthreads();
+        if (tid < 5) {
+            double acc = 0.0;
+            for (int w = 0; w < BS / 32; ++w) acc += red[w][tid];
+            U[cell * 5 + tid] = acc * dv * dv * dv;
+        }
+        __syncthreads();
+    }
+}
+
+// the same gather for any n and any alignment, one element per thread
+template <typename T>
+__global__ void transport_any_kernel(int n, int ncx, int ncy, int ncz, int bcx, int bcy, int bcz,
+                                     const signed char* __restrict__ delta, const T* __restrict__ f,
+                                     T* __restrict__ out, long total) {
     const long n3 = (long)n * n * n;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
         const long cell = i / n3;
@@ -234,44 +376,54 @@ __global__ void transport_kernel(int n, int ncx, int ncy, int ncz, int bcx, int 
     }
 }
 
-// ------------------------------------------------------------------ moments
-template <typename T, int BS>
-__global__ void __launch_bounds__(BS) moments_kernel(int n, double L, long ncells, const T* __restrict__ f,
-                                                     double* __restrict__ U) {
-    __shared__ double red[BS / 32][5];
-    const long n3 = (long)n * n * n;
-    const double dv = 2.0 * L / n;
-    const double dv3 = dv * dv * dv;
-    for (long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
-        const T* fc = f + cell * n3;
-        double s[5] = {0, 0, 0, 0, 0};
-        for (long k = threadIdx.x; k < n3; k += BS) {
-            const int kz = (int)(k % n), ky = (int)((k / n) % n), kx = (int)(k / ((long)n * n));
-            const double vx = ((double)kx + 0.5 - 0.5 * n) * dv;
-            const double vy = ((double)ky + 0.5 - 0.5 * n) * dv;
-            const double vz = ((double)kz + 0.5 - 0.5 * n) * dv;
-            const double m = (double)fc[k];
-            s[0] += m;
-            s[1] += m * vx;
-            s[2] += m * vy;
-            s[3] += m * vz;
-            s[4] += m * 0.5 * (vx * vx + vy * vy + vz * vz);
+// transport of ncells cells: the run kernel for n = 8, 16, 24, 32 and 16-byte
+// aligned arrays, the element kernel otherwise
+template <typename T>
+static cudaError_t launch_transport(int n, const fks_grid& g, const signed char* delta, const void* f, void* out,
+                                    cudaStream_t s) {
+    const long ncells = (long)g.nx * g.ny * g.nz;
+    const bool al = ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+    const long grid = ncells < 152L * 8 ? ncells : 152L * 8;
+    const T* fi = static_cast<const T*>(f);
+    T* fo = static_cast<T*>(out);
+#define FKS_TRANSPORT_RUN(NN)                                                                                   \
+    case NN:                                                                                                    \
+        transport_kernel<T, NN><<<(unsigned)grid, 256, 0, s>>>(g.nx, g.ny, g.nz, g.bc[0], g.bc[1], g.bc[2], delta, \
+                                                               fi, fo, ncells);                                 \
+        return cudaGetLastError();
+    if (al) {
+        switch (n) {
+            FKS_TRANSPORT_RUN(8)
+            FKS_TRANSPORT_RUN(16)
+            FKS_TRANSPORT_RUN(24)
+            FKS_TRANSPORT_RUN(32)
         }
-#pragma unroll
-        for (int i = 0; i < 5; ++i)
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s[i] += __shfl_xor_sync(0xffffffffu, s[i], off);
-        const int warp = threadIdx.x >> 5;
-        if ((threadIdx.x & 31) == 0)
-            for (int i = 0; i < 5; ++i) red[warp][i] = s[i];
-        __syncthreads();
-        if (threadIdx.x < 5) {
-            double acc = 0.0;
-            for (int w = 0; w < BS / 32; ++w) acc += red[w][threadIdx.x];
-            U[cell * 5 + threadIdx.x] = acc * dv3;
-        }
-        __syncthreads();
     }
+#undef FKS_TRANSPORT_RUN
+    const long total = ncells * n * n * n;
+    long blocks = (total + 255) / 256;
+    if (blocks > 152L * 64) blocks = 152L * 64;
+    if (blocks < 1) blocks = 1;
+    transport_any_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(n, g.nx, g.ny, g.nz, g.bc[0], g.bc[1], g.bc[2], delta, fi,
+                                                             fo, total);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+static cudaError_t launch_moments_n(const fks_ctx* c, const void* f, double* U, cudaStream_t s) {
+    const long grid = c->ncells < 152L * 8 ? c->ncells : 152L * 8;
+    moments_kernel<T, N><<<(unsigned)grid, 256, 0, s>>>(c->vbox.L, c->ncells, static_cast<const T*>(f), U);
+    return cudaGetLastError();
+}
+template <typename T>
+static cudaError_t launch_moments_t(const fks_ctx* c, const void* f, double* U, cudaStream_t s) {
+    switch (c->n) {
+        case 8: return launch_moments_n<T, 8>(c, f, U, s);
+        case 16: return launch_moments_n<T, 16>(c, f, U, s);
+        case 24: return launch_moments_n<T, 24>(c, f, U, s);
+        case 32: return launch_moments_n<T, 32>(c, f, U, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 int default_cluster_size(bool fp64, int N) {
@@ -763,18 +915,10 @@ fks_status fks_transport(fks_ctx* c, const void* f, void* f_out, double dt, void
     cudaStream_t s = (cudaStream_t)stream;
     fks_status st = launch_offsets(c, dt, s);
     if (st != FKS_OK) return st;
-    const long total = c->ncells * (long)c->n * c->n * c->n;
-    const int bs = 256;
-    long blocks = (total + bs - 1) / bs;
-    if (blocks > 152L * 64) blocks = 152L * 64;
-    if (c->fp64)
-        transport_kernel<double><<<(unsigned)blocks, bs, 0, s>>>(c->n, c->grid.nx, c->grid.ny, c->grid.nz, c->grid.bc[0],
-                                                               c->grid.bc[1], c->grid.bc[2], c->d_delta,
-                                                               (const double*)f, (double*)f_out, total);
-    else
-        transport_kernel<float><<<(unsigned)blocks, bs, 0, s>>>(c->n, c->grid.nx, c->grid.ny, c->grid.nz, c->grid.bc[0],
-                                                              c->grid.bc[1], c->grid.bc[2], c->d_delta,
-                                                              (const float*)f, (float*)f_out, total);
+    if (c->ncells == 0) return FKS_OK;
+    const cudaError_t e0 = c->fp64 ? launch_transport<double>(c->n, c->grid, c->d_delta, f, f_out, s)
+                                   : launch_transport<float>(c->n, c->grid, c->d_delta, f, f_out, s);
+    if (e0 != cudaSuccess) return cuda_fail(c, e0, "transport kernel launch");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "transport kernel launch");
     c->launches += 1;
@@ -797,11 +941,8 @@ fks_status fks_moments(fks_ctx* c, const void* f, double* U, void* stream) {
     if (!f || !U) return fail(c, FKS_ERR_INVALID_ARG, "null pointer");
     if (c->ncells == 0) return FKS_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    long blocks = c->ncells < 152L * 16 ? c->ncells : 152L * 16;
-    if (c->fp64)
-        moments_kernel<double, 256><<<(unsigned)blocks, 256, 0, s>>>(c->n, c->vbox.L, c->ncells, (const double*)f, U);
-    else
-        moments_kernel<float, 256><<<(unsigned)blocks, 256, 0, s>>>(c->n, c->vbox.L, c->ncells, (const float*)f, U);
+    const cudaError_t e0 = c->fp64 ? launch_moments_t<double>(c, f, U, s) : launch_moments_t<float>(c, f, U, s);
+    if (e0 != cudaSuccess) return cuda_fail(c, e0, "moments kernel launch");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel launch");
     c->launches += 1;
@@ -1340,18 +1481,9 @@ extern "C" fks_status fks_transport_noalloc(const fks_grid* grid, const fks_vbox
     cudaStream_t cs = (cudaStream_t)stream;
     if (cudaMemsetAsync(d_flags, 0, sizeof(int), cs) != cudaSuccess) return FKS_ERR_CUDA;
     offsets_kernel<<<dim3(1, 3), n / 2, 0, cs>>>(n, vbox->L, make_double3(dx[0], dx[1], dx[2]), dt, s, d_delta, d_flags);
-    const long total = (long)grid->nx * grid->ny * grid->nz * n * n * n;
-    const int bs = 256;
-    long blocks = (total + bs - 1) / bs;
-    if (blocks > 152L * 64) blocks = 152L * 64;
-    if (blocks < 1) blocks = 1;
-    if (precision == FKS_FP64)
-        transport_kernel<double><<<(unsigned)blocks, bs, 0, cs>>>(n, grid->nx, grid->ny, grid->nz, grid->bc[0],
-                                                                grid->bc[1], grid->bc[2], d_delta, (const double*)f,
-                                                                (double*)f_out, total);
-    else
-        transport_kernel<float><<<(unsigned)blocks, bs, 0, cs>>>(n, grid->nx, grid->ny, grid->nz, grid->bc[0],
-                                                               grid->bc[1], grid->bc[2], d_delta, (const float*)f,
-                                                               (float*)f_out, total);
+    if ((long)grid->nx * grid->ny * grid->nz == 0) return FKS_OK;
+    const cudaError_t e0 = precision == FKS_FP64 ? launch_transport<double>(n, *grid, d_delta, f, f_out, cs)
+                                                 : launch_transport<float>(n, *grid, d_delta, f, f_out, cs);
+    if (e0 != cudaSuccess) return FKS_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? FKS_OK : FKS_ERR_CUDA;
 }
