@@ -227,6 +227,15 @@ def learned_path(torch, fks, dev, args, sample=1216, threshold=1e-3):
         d = (Q.double() - Q64).flatten(1).norm(dim=1) / Q64.flatten(1).norm(dim=1)
         return float(d.max().item()), float(d.median().item())
 
+    # the learned + split-BF16 path: routed cells recomputed on the tensor cores
+    ctc = fks.Context(fks.Config(ncell=(nc, 1, 1), n=NV, L=LBOX, kn=KN, A1=A1, A2=A2, precision=fks.FKS_BF16X3))
+    Qt, Qlt = torch.empty_like(f), torch.empty_like(f)
+    t_tc = timed(lambda: ctc.collide(f, Qt))
+    routed_t = [0]
+    t_learn_tc = timed(lambda: routed_t.__setitem__(0, ctc.surrogate_collide(sur.net, f, Qlt, sur.out_scale,
+                                                                              sur.ind_scale, threshold)))
+    elt, mlt = err(Qlt)
+    del ctc
     el, ml = err(Ql)
     es, ms = err(Qs)
     pts = nc * NV ** 3
@@ -235,6 +244,10 @@ def learned_path(torch, fks, dev, args, sample=1216, threshold=1e-3):
             "err_vs_fp64": {"max": el, "median": ml},
             "spectral_fp32_collide": {"value": pts / (t_spec / 1e3), "ms": t_spec, "err_vs_fp64": {"max": es, "median": ms}},
             "speedup_vs_spectral_fp32": t_spec / t_learn,
+            "learned_bf16x3": {"value": pts / (t_learn_tc / 1e3), "ms": t_learn_tc, "routed_fraction": routed_t[0] / nc,
+                               "err_vs_fp64": {"max": elt, "median": mlt},
+                               "spectral_bf16x3_collide_ms": t_tc,
+                               "note": "routed cells recomputed by the split-BF16 tensor-core operator"},
             "train_seconds": train_s, "train_loss_last": sur.train_loss[-1], "calibration": sur.calib,
             "note": "collision operator only (the part the surrogate replaces), same sample for both paths; "
                     "net: 6 x conv3d 3^3, 32 ch, BF16 weights and activations, FP32 accumulation; inference on "

@@ -234,11 +234,13 @@ void fks_net_destroy(fks_net *net);
 fks_status fks_surrogate_inputs(int n, double L, long ncells, const float *f, float *x, double *rho, float *dist,
                                 void *stream);
 
-/* Q for every cell of an FP32 spectral context by the surrogate: Q = rho^2 y
- * out_scale / Kn, projected onto the conservation constraints; indicator =
- * ind_scale (dist + relative moment defect of the raw output); cells whose
- * indicator exceeds `threshold` (or is not finite) are recomputed with the
- * spectral operator.  Synchronises `stream` once (to read the routed count,
+/* Q for every cell of an FP32 or split-BF16 (FKS_BF16X3) spectral context
+ * (variant A) by the surrogate: Q = rho^2 y out_scale / Kn, projected onto
+ * the conservation constraints; indicator = ind_scale (dist + relative moment
+ * defect of the raw output); cells whose indicator exceeds `threshold` (or
+ * is not finite) are recomputed with the context's spectral operator (the
+ * FP32 cluster kernel, or the split-BF16 tensor-core kernel on the list of
+ * routed cells).  Synchronises `stream` once (to read the routed count,
  * stored in *nrouted).  f and Q 16-byte aligned.  The moments of the raw
  * output are FP64 sums of its FP32 values; the correction is applied in FP32. */
 fks_status fks_surrogate_collide(fks_ctx *ctx, fks_net *net, const void *f, void *Q, double out_scale,

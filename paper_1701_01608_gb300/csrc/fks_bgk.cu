@@ -32,9 +32,8 @@ struct Vec<double> {
     using type = double2;
 };
 
-template <typename T, int N>
-__global__ void __launch_bounds__(256, 4) bgk_kernel(BgkArgs a) {
-    constexpr int BS = 256;
+template <typename T, int N, int BS>
+__global__ void __launch_bounds__(BS, 1024 / BS) bgk_kernel(BgkArgs a) {
     constexpr int V = 16 / (int)sizeof(T);          // elements per 16-byte access
     constexpr int LPR = N / V;                       // lanes per row
     constexpr int RPI = BS / LPR;                    // rows per iteration
@@ -245,8 +244,10 @@ __global__ void __launch_bounds__(256, 4) bgk_kernel(BgkArgs a) {
 
 template <typename T, int N>
 static cudaError_t launch_n(const BgkArgs& a, cudaStream_t s) {
-    long grid = a.ncells < 152L * 8 ? a.ncells : 152L * 8;
-    bgk_kernel<T, N><<<(unsigned)grid, 256, 0, s>>>(a);
+    // 128-thread CTAs, 8 per SM: eight cells in flight per SM
+    constexpr int BS = N >= 16 ? 128 : 256;
+    long grid = a.ncells < 152L * 16 ? a.ncells : 152L * 16;
+    bgk_kernel<T, N, BS><<<(unsigned)grid, BS, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -760,6 +760,7 @@ void fks_destroy(fks_ctx* c) {
     cudaFree(c->s_dist);
     cudaFree(c->s_ind);
     cudaFree(c->s_items);
+    cudaFree(c->s_cells);
     cudaFree(c->s_count);
     delete c;
 }
@@ -813,7 +814,7 @@ static fks_status launch_bgk_ctx(fks_ctx* c, const void* f, void* out, const sig
 }
 
 static fks_status launch_tc_ctx(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
-                                cudaStream_t s) {
+                                cudaStream_t s, const int* cells = nullptr, long ncells = -1) {
     TcLaunch l;
     l.f = f;
     l.out = out;
@@ -822,7 +823,8 @@ static fks_status launch_tc_ctx(fks_ctx* c, const void* f, void* out, const sign
     l.scratch = c->tc_scratch;
     l.delta = delta;
     l.flags = c->d_flags;
-    l.ncells = c->ncells;
+    l.ncells = ncells >= 0 ? ncells : c->ncells;
+    l.cells = cells;
     l.nc[0] = c->grid.nx;
     l.nc[1] = c->grid.ny;
     l.nc[2] = c->grid.nz;
@@ -884,6 +886,11 @@ static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const sig
 }
 
 fks_status fks_internal_fail(fks_ctx* c, fks_status st, const std::string& msg) { return fail(c, st, msg); }
+fks_status fks_internal_collide_cells(fks_ctx* c, const void* f, void* out, const int* cells, long ncells,
+                                      cudaStream_t s) {
+    if (!c->tc) return fail(c, FKS_ERR_UNSUPPORTED, "cell lists need a tensor-core context");
+    return launch_tc_ctx(c, f, out, nullptr, 0.0, 0, s, cells, ncells);
+}
 fks_status fks_internal_collide(fks_ctx* c, const void* f, void* out, int mode, cudaStream_t s) {
     return launch_collide(c, f, out, nullptr, 0.0, mode, s);
 }

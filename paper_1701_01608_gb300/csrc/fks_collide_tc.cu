@@ -214,7 +214,8 @@ struct Args {
     unsigned char* a3;          // [gridDim.x][A3_CELL] pass-3 operands of the CTA's current cell
     const signed char* delta;   // [3][N] cell shifts of the transport (step mode) or nullptr
     int* flags;                 // health bits
-    long ncells;
+    long ncells;                // cells to process (entries of `cells`, if given)
+    const int* cells;           // optional list of cell indices (routed cells), else 0 .. ncells-1
     int nc[3], bc[3];
     int M;
     double L, inv_kn, dt;
@@ -317,7 +318,8 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
         commit(bar);
     };
 
-    for (long cell = blockIdx.x; cell < a.ncells; cell += gridDim.x) {
+    for (long item = blockIdx.x; item < a.ncells; item += gridDim.x) {
+        const long cell = a.cells ? (long)a.cells[item] : item;
         const int cx = (int)(cell / ((long)ncy * ncz)), cy = (int)((cell / ncz) % ncy), cz = (int)(cell % ncz);
         if (tid < N) {
             if (!transport) {
@@ -706,6 +708,7 @@ cudaError_t launch_collide_tc(int n, const TcLaunch& l, cudaStream_t s) {
     a.delta = l.delta;
     a.flags = l.flags;
     a.ncells = l.ncells;
+    a.cells = l.cells;
     for (int i = 0; i < 3; ++i) {
         a.nc[i] = l.nc[i];
         a.bc[i] = l.bc[i];

@@ -53,6 +53,7 @@ struct TcLaunch {
     const signed char* delta;   // transport shifts (step) or nullptr
     int* flags;
     long ncells;
+    const int* cells = nullptr; // optional device list of cell indices (the cells to process)
     int nc[3], bc[3];
     int M;
     double L, inv_kn, dt;
@@ -105,6 +106,7 @@ struct fks_ctx {
     float* s_dist = nullptr;
     float* s_ind = nullptr;
     fks::BatchItem* s_items = nullptr;
+    int* s_cells = nullptr;     // routed cell indices (tensor-core contexts)
     int* s_count = nullptr;
 };
 
@@ -115,6 +117,9 @@ struct fks_ctx {
 // (C linkage: they are defined beside the C ABI.)
 extern "C" fks_status fks_internal_fail(fks_ctx* c, fks_status st, const std::string& msg);
 extern "C" fks_status fks_internal_collide(fks_ctx* c, const void* f, void* out, int mode, cudaStream_t s);
+// collide (projected) only the listed cells of a tensor-core context
+extern "C" fks_status fks_internal_collide_cells(fks_ctx* c, const void* f, void* out, const int* cells, long ncells,
+                                                 cudaStream_t s);
 // variant B (fks_dealias.cu)
 fks_status launch_dealias(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
                           cudaStream_t s);

@@ -11,6 +11,7 @@
 //
 // Weight layout of layer l: W[co][ci][27], tap t = (dx+1)*9 + (dy+1)*3 + (dz+1),
 // then bias[co]; the layers are packed in one flat FP32 master vector.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -267,7 +268,8 @@ static void layer_wgrad(int l, int n, int batch, const float* x, const float* g,
 //
 // Implicit-GEMM convolution on the 5th-generation tensor cores (tcgen05, BF16
 // operands, FP32 accumulation in tensor memory), used for inference.
-// Activations are BF16 "channels-last" ([b][voxel][CP], CP = 16 or 32).
+// Activations are BF16 in chunks of 8 channels: [b][chunk][voxel][8] (2 or 4
+// chunks), so that the halo of one chunk is a TMA box of contiguous voxels.
 // A tile is 1 x 16 x 8 output voxels (x, y, z) = 128 rows of D; D[m][co] =
 // sum_t sum_ci A_t[m][ci] B_t[ci][co] over the 27 taps t.  The tile's input
 // halo (3 x 18 x 10 voxels) is stored as [k-chunk j][halo row r][8 channels]
@@ -301,6 +303,10 @@ __host__ __device__ constexpr uint32_t instr_desc() {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+__device__ __forceinline__ void fence_async_shared_cta() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_init1(uint64_t* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -314,96 +320,147 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+constexpr uint32_t HPLANE = 8704;             // 128-aligned k-chunk plane of a halo tile (540 x 16 B = 8640)
+
+// bounded wait; on a timeout record bit 3 and set *abort, after which no wait
+// is taken again (the kernel runs to its end without waiting)
+__device__ __forceinline__ void wait_bounded(uint64_t* bar, uint32_t parity, int* flags, volatile int* abort) {
+    if (*abort) return;
+    bool ok = false;
+    for (long it = 0; it < (1L << 26) && !ok; ++it) ok = mbar_try(bar, parity);
+    if (!ok) {
+        atomicOr(flags, 8);
+        *abort = 1;
+    }
+}
+
+// Implicit-GEMM 3^3 convolution on the tensor cores, one tile of 1 x 16 x 8
+// voxels (M = 128) per MMA group.  Activations are BF16 in chunks of 8
+// channels, [cell][chunk][x][y][z][8].  The halo of a tile (3 x 18 x 10
+// voxels, zero outside the grid) arrives by TMA as KC boxes (one per chunk,
+// contiguous 16-byte voxels), one 16-byte row per voxel, so that tap t's A operand is
+// the plane of k-chunk j shifted by the tap's row offset: a K-major descriptor
+// with LBO = the plane stride and SBO = 10 rows (next y).  B: the tap's
+// [KC][NP][16 B] weight block.  Per CTA the tiles are pipelined: halos and
+// TMEM accumulators are double-buffered, the MMAs of tile i+1 run beside the
+// epilogue of tile i.
 template <int KC, int NP, bool RELU, bool OUT_F32>
-__global__ void __launch_bounds__(NTHR, 1) conv_tc_kernel(int n, int batch, const __nv_bfloat16* __restrict__ x,
+__global__ void __launch_bounds__(NTHR, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap xmap, int n, int batch,
                                                           const __nv_bfloat16* __restrict__ wpk,
                                                           const float* __restrict__ bias, void* __restrict__ y,
                                                           int cout, int* flags) {
-    constexpr int CP = KC * 8;                           // input channels (padded)
-    constexpr uint32_t HALO_BYTES = KC * HROWS * 16;
+    constexpr uint32_t HALO_BYTES = KC * HPLANE;
     constexpr uint32_t W_BYTES = 27 * KC * NP * 16;
     constexpr uint32_t IDESC = instr_desc<128, NP>();
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* halo = smem;                          // [KC][HROWS][16 B]
-    unsigned char* wsm = smem + HALO_BYTES;              // [27][KC][NP][16 B]
-    __shared__ uint64_t mbar;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations on 128-byte boundaries (the launch adds 128 bytes of slack)
+    unsigned char* smem = smem_raw + ((128u - (saddr(smem_raw) & 127u)) & 127u);
+    unsigned char* halo = smem;                          // [2][KC][HPLANE]
+    unsigned char* wsm = smem + 2 * HALO_BYTES;          // [27][KC][NP][16 B]
+    __shared__ uint64_t bar_ld[2], bar_mma[2];
     __shared__ uint32_t tmem_base;
     __shared__ float sbias[32];
+    __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // weights -> shared memory (16-byte chunks), bias
     for (uint32_t i = tid; i < W_BYTES / 16; i += NTHR)
         reinterpret_cast<uint4*>(wsm)[i] = reinterpret_cast<const uint4*>(wpk)[i];
     if (tid < 32) sbias[tid] = tid < cout ? bias[tid] : 0.f;
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(saddr(&tmem_base))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;\n" ::"r"(saddr(&tmem_base))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    if (tid == 0) mbar_init1(&mbar);
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init1(&bar_ld[i]);
+            mbar_init1(&bar_mma[i]);
+        }
+        s_abort = 0;
+    }
+    fence_async_shared_cta();   // the weights (generic stores) before the tensor core reads them
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_base;
-    uint32_t phase = 0;
 
     const int ny = n / TY, nz = n / TZ;
     const long tiles = (long)batch * n * ny * nz;
+    const long mine = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;   // tiles of this CTA
     const long n3 = (long)n * n * n;
-    for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int zb = (int)(tile % nz), yb = (int)((tile / nz) % ny), x0 = (int)((tile / ((long)nz * ny)) % n);
-        const int b = (int)(tile / ((long)nz * ny * n));
-        const int y0 = yb * TY, z0 = zb * TZ;
-        // halo rows -> shared memory (zero outside the grid)
-        for (int i = tid; i < KC * HROWS; i += NTHR) {
-            const int j = i / HROWS, r = i % HROWS;
-            const int hx = r / (HY * HZ), hy = (r / HZ) % HY, hz = r % HZ;
-            const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n)
-                v = *reinterpret_cast<const uint4*>(x + (((long)b * n3 + ((long)gx * n + gy) * n + gz) * CP + 8 * j));
-            reinterpret_cast<uint4*>(halo)[(long)j * HROWS + r] = v;
+    auto coords = [&](long i, int& b, int& x0, int& y0, int& z0) {
+        const long tile = blockIdx.x + i * gridDim.x;
+        z0 = (int)(tile % nz) * TZ;
+        y0 = (int)((tile / nz) % ny) * TY;
+        x0 = (int)((tile / ((long)nz * ny)) % n);
+        b = (int)(tile / ((long)nz * ny * n));
+    };
+    auto load = [&](long i) {   // thread 0: the halo of tile i into buffer i & 1 (zero fill outside the grid)
+        int b, x0, y0, z0;
+        coords(i, b, x0, y0, z0);
+        uint64_t* bar = &bar_ld[i & 1];
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(bar)), "r"(KC * 8640u)
+                     : "memory");
+        for (int j = 0; j < KC; ++j) {
+            const uint32_t dst = saddr(halo + (i & 1) * HALO_BYTES + j * HPLANE);
+            asm volatile(
+                "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4, %5, %6}], [%7];\n" ::"r"(dst),
+                "l"(reinterpret_cast<uint64_t>(&xmap)), "r"(0), "r"(z0 - 1), "r"(y0 - 1), "r"(x0 - 1), "r"(b * KC + j),
+                "r"(saddr(bar))
+                : "memory");
         }
-        // generic-proxy writes of the halo before the tensor core reads it
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t hbase = saddr(halo), wbase = saddr(wsm);
-            int k = 0;
-#pragma unroll 1
-            for (int t = 0; t < 27; ++t) {
-                const int dx = t / 9, dy = (t / 3) % 3, dz = t % 3;
-                const uint32_t r0 = (uint32_t)((dx * HY + dy) * HZ + dz);
-#pragma unroll
-                for (int s2 = 0; s2 < KC / 2; ++s2) {
-                    const uint64_t ad = smem_desc(hbase + (2u * s2 * HROWS + r0) * 16u, HROWS * 16u, HZ * 16u);
-                    const uint64_t bd = smem_desc(wbase + (uint32_t)((t * KC + 2 * s2) * NP) * 16u, NP * 16u, 128u);
-                    const uint32_t acc = k > 0 ? 1u : 0u;
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
-                        : "memory");
-                    ++k;
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             saddr(&mbar))
-                         : "memory");
-        }
-        // bounded wait for the tile's MMAs
-        {
-            bool done = false;
-            for (long it = 0; it < (1L << 26) && !done; ++it) done = mbar_try(&mbar, phase);
-            if (!done && tid == 0) atomicOr(flags, 8);
-            phase ^= 1u;
-        }
+    };
+    auto wait_halo = [&](long i) {   // thread 0: the halo of tile i has landed
+        wait_bounded(&bar_ld[i & 1], (uint32_t)((i >> 1) & 1), flags, &s_abort);
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    };
+    auto mma = [&](long i) {   // thread 0: 27 taps x KC/2 k-steps of tile i into TMEM (i & 1) * 32
+        // descriptors of base + off are the base descriptors + off / 16 (addresses < 2^18 bytes:
+        // no carry out of the start-address field); every offset is a compile-time constant
+        const uint64_t a0 = smem_desc(saddr(halo + (i & 1) * HALO_BYTES), HPLANE, HZ * 16u);
+        const uint64_t b0 = smem_desc(saddr(wsm), NP * 16u, 128u);
+        const uint32_t d = tmem + (uint32_t)(i & 1) * 32u;
+#pragma unroll
+        for (int t = 0; t < 27; ++t) {
+            const uint32_t r0 = (uint32_t)(((t / 9) * HY + (t / 3) % 3) * HZ + t % 3);
+#pragma unroll
+            for (int s2 = 0; s2 < KC / 2; ++s2) {
+                const uint64_t ad = a0 + ((2u * s2 * HPLANE + r0 * 16u) >> 4);
+                const uint64_t bd = b0 + ((uint32_t)((t * KC + 2 * s2) * NP) * 16u >> 4);
+                const uint32_t acc = (t > 0 || s2 > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                    "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                    : "memory");
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         saddr(&bar_mma[i & 1]))
+                     : "memory");
+    };
+    if (tid == 0 && mine > 0) {
+        load(0);
+        if (mine > 1) load(1);
+        wait_halo(0);
+        mma(0);
+    }
+#pragma unroll 1
+    for (long i = 0; i < mine; ++i) {
+        if (tid == 0 && i + 1 < mine) {   // accumulator (i+1) & 1 was read by tile i-1
+            wait_halo(i + 1);
+            mma(i + 1);
+        }
+        wait_bounded(&bar_mma[i & 1], (uint32_t)((i >> 1) & 1), flags, &s_abort);
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (tid == 0 && i + 2 < mine) load(i + 2);   // halo buffer i & 1: the MMAs of tile i are done
         // epilogue: warp w reads D rows 32w .. 32w+31 (one voxel per thread)
+        int b, x0, y0, z0;
+        coords(i, b, x0, y0, z0);
         float v[NP];
         {
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+            const uint32_t taddr = tmem + (uint32_t)(i & 1) * 32u + ((uint32_t)(32 * warp) << 16);
             uint32_t r[NP];
             if constexpr (NP == 32) {
                 asm volatile(
@@ -429,28 +486,30 @@ __global__ void __launch_bounds__(NTHR, 1) conv_tc_kernel(int n, int batch, cons
             for (int c = 0; c < NP; ++c) v[c] = __uint_as_float(r[c]);
         }
         const int m = 32 * warp + lane;
-        const long vox = (long)b * n3 + ((long)x0 * n + (y0 + m / TZ)) * n + (z0 + m % TZ);
+        const long vloc = ((long)x0 * n + (y0 + m / TZ)) * n + (z0 + m % TZ);   // voxel within the cell
         if constexpr (OUT_F32) {
-            static_cast<float*>(y)[vox] = v[0] + sbias[0];
+            static_cast<float*>(y)[(long)b * n3 + vloc] = v[0] + sbias[0];
         } else {
-            __nv_bfloat16* yo = static_cast<__nv_bfloat16*>(y) + vox * 32;
+            // chunk c of 8 channels at [cell][c][voxel][8]: consecutive voxels are 16 bytes apart
 #pragma unroll
-            for (int c = 0; c < 32; c += 8) {
+            for (int c = 0; c < 4; ++c) {
                 __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    float a = (c + e < NP) ? v[c + e] + sbias[c + e] : 0.f;
+                    float a = (8 * c + e < NP) ? v[8 * c + e] + sbias[8 * c + e] : 0.f;
                     if (RELU) a = fmaxf(a, 0.f);
                     h[e] = __float2bfloat16_rn(a);
                 }
-                *reinterpret_cast<uint4*>(yo + c) = *reinterpret_cast<const uint4*>(h);
+                __nv_bfloat16* yo = static_cast<__nv_bfloat16*>(y) + (((long)b * 4 + c) * n3 + vloc) * 8;
+                *reinterpret_cast<uint4*>(yo) = *reinterpret_cast<const uint4*>(h);
             }
         }
-        // every thread's TMEM reads are done before the next tile's MMAs overwrite D
+        // every thread's TMEM reads are done before tile i+2's MMAs overwrite accumulator i & 1
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
     }
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(tmem) : "memory");
 }
 
 // FP32 master weights of one layer -> [27][KC][NP][8] BF16 (zero padding)
@@ -464,29 +523,62 @@ __global__ void pack_weights_kernel(int cin, int cout, int KC, int NP, const flo
     }
 }
 
-// FP32 [b][2][n^3] -> BF16 channels-last [b][n^3][16] (channels 2..15 zero)
+// FP32 [b][2][n^3] -> BF16 [b][2 chunks][n^3][8] (channels 2..15 zero)
 __global__ void input_pack_kernel(long nvox, long n3, const float* __restrict__ x, __nv_bfloat16* __restrict__ out) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nvox; i += (long)gridDim.x * blockDim.x) {
         const long b = i / n3, p = i % n3;
-        __align__(16) __nv_bfloat16 h[16];
-        for (int c = 0; c < 16; ++c) h[c] = __float2bfloat16_rn(c < 2 ? x[(b * 2 + c) * n3 + p] : 0.f);
-        reinterpret_cast<uint4*>(out + i * 16)[0] = reinterpret_cast<const uint4*>(h)[0];
-        reinterpret_cast<uint4*>(out + i * 16)[1] = reinterpret_cast<const uint4*>(h)[1];
+        __align__(16) __nv_bfloat16 h[8];
+        for (int c = 0; c < 8; ++c) h[c] = __float2bfloat16_rn(c < 2 ? x[(b * 2 + c) * n3 + p] : 0.f);
+        reinterpret_cast<uint4*>(out)[(b * 2) * n3 + p] = *reinterpret_cast<const uint4*>(h);
+        reinterpret_cast<uint4*>(out)[(b * 2 + 1) * n3 + p] = make_uint4(0u, 0u, 0u, 0u);
     }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// tensor map of a BF16 activation in chunks of 8 channels, [batch][KC][n][n][n][8]
+// (the chunk index folded into the last dimension), with a halo box of
+// 8 channels x 10 (z) x 18 (y) x 3 (x) x 1 chunk: contiguous 16-byte voxels
+static bool halo_map(CUtensorMap* m, const __nv_bfloat16* x, int n, int batch, int KC) {
+    EncodeTiled enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[5] = {8, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)batch * KC};
+    const cuuint64_t strides[4] = {16, 16ull * n, 16ull * n * n, 16ull * n * n * n};
+    const cuuint32_t box[5] = {8, HZ, HY, HX, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(x), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int KC, int NP, bool RELU, bool OUT_F32>
 static cudaError_t launch_tc(int n, int batch, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias,
                              void* y, int cout, int* flags, cudaStream_t s) {
-    // exact size: the last byte any descriptor reaches is the last byte of
-    // the halo (A) or of the weight block (B) for every tap
-    const size_t smem = (size_t)KC * HROWS * 16 + (size_t)27 * KC * NP * 16;
+    alignas(64) CUtensorMap xmap;
+    if (!halo_map(&xmap, x, n, batch, KC)) return cudaErrorInvalidValue;
+    // two halo buffers and the weights; one CTA per SM (64 TMEM columns)
+    const size_t smem = (size_t)2 * KC * HPLANE + (size_t)27 * KC * NP * 16 + 128;
     auto k = conv_tc_kernel<KC, NP, RELU, OUT_F32>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long tiles = (long)batch * n * (n / TY) * (n / TZ);
-    const long grid = tiles < 2L * 152 ? tiles : 2L * 152;
-    k<<<(unsigned)grid, NTHR, smem, s>>>(n, batch, x, w, bias, y, cout, flags);
+    const long grid = tiles < 152 ? tiles : 152;
+    k<<<(unsigned)grid, NTHR, smem, s>>>(xmap, n, batch, w, bias, y, cout, flags);
     return cudaGetLastError();
 }
 
@@ -513,7 +605,7 @@ struct fks_net {
     int ib = 0;
     float* xbuf = nullptr;            // [ib][2][n^3] input workspace of the routing path
     float* yinf = nullptr;            // [ib][n^3] network output
-    // tensor-core inference: packed BF16 weights per layer, BF16 channels-last activations
+    // tensor-core inference: packed BF16 weights per layer, BF16 activations in 8-channel chunks
     __nv_bfloat16* wpk[NL] = {};
     __nv_bfloat16* tact[2] = {};
     int* tflags = nullptr;

@@ -217,6 +217,13 @@ __global__ void route_kernel(long ncells, const float* __restrict__ ind, float t
     }
 }
 
+// indices of the cells whose indicator exceeds the threshold (tensor-core contexts)
+__global__ void route_list_kernel(long ncells, const float* __restrict__ ind, float threshold, int* __restrict__ cells,
+                                  int* __restrict__ count) {
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncells; c += (long)gridDim.x * blockDim.x)
+        if (!(ind[c] <= threshold)) cells[atomicAdd(count, 1)] = (int)c;
+}
+
 }  // namespace surr
 }  // namespace fks
 
@@ -238,8 +245,8 @@ fks_status fks_surrogate_inputs(int n, double L, long ncells, const float* f, fl
 fks_status fks_surrogate_collide(fks_ctx* c, fks_net* net, const void* f, void* Q, double out_scale,
                                  double ind_scale, double threshold, long* nrouted, void* stream) {
     if (!c || !net || !f || !Q || f == Q) return FKS_ERR_INVALID_ARG;
-    if (c->fp64 || c->bgk || c->tc || c->dealias || fks_net_grid(net) != c->n) {
-        c->err = "the surrogate needs an FP32 spectral context with the network's grid";
+    if (c->fp64 || c->bgk || c->dealias || fks_net_grid(net) != c->n) {
+        c->err = "the surrogate needs an FP32 or split-BF16 spectral context (variant A) with the network's grid";
         return FKS_ERR_UNSUPPORTED;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -250,7 +257,7 @@ fks_status fks_surrogate_collide(fks_ctx* c, fks_net* net, const void* f, void* 
     if (!c->s_rho) {
         if (cudaMalloc(&c->s_rho, sizeof(double) * nc) != cudaSuccess || cudaMalloc(&c->s_dist, sizeof(float) * nc) ||
             cudaMalloc(&c->s_ind, sizeof(float) * nc) || cudaMalloc(&c->s_items, sizeof(BatchItem) * nc) ||
-            cudaMalloc(&c->s_count, sizeof(int))) {
+            cudaMalloc(&c->s_count, sizeof(int)) || cudaMalloc(&c->s_cells, sizeof(int) * (nc > 0 ? nc : 1))) {
             c->err = "surrogate workspace";
             return FKS_ERR_OOM;
         }
@@ -276,14 +283,21 @@ fks_status fks_surrogate_collide(fks_ctx* c, fks_net* net, const void* f, void* 
         c->launches += 2;
     }
     if (cudaMemsetAsync(c->s_count, 0, sizeof(int), s) != cudaSuccess) return FKS_ERR_CUDA;
-    surr::route_kernel<<<256, 256, 0, s>>>(nc, c->s_ind, (float)threshold, n, fin, Qo, c->tables, c->d_P,
-                                          1.0 / c->kern.knudsen, c->vbox.L, c->s_items, c->s_count);
+    if (c->tc)
+        surr::route_list_kernel<<<256, 256, 0, s>>>(nc, c->s_ind, (float)threshold, c->s_cells, c->s_count);
+    else
+        surr::route_kernel<<<256, 256, 0, s>>>(nc, c->s_ind, (float)threshold, n, fin, Qo, c->tables, c->d_P,
+                                              1.0 / c->kern.knudsen, c->vbox.L, c->s_items, c->s_count);
     c->launches += 1;
     int count = 0;
     if (cudaMemcpyAsync(&count, c->s_count, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return FKS_ERR_CUDA;
     if (nrouted) *nrouted = count;
+    if (count > 0 && c->tc) {
+        // split-BF16 tensor-core operator (projected) on the routed cells
+        return fks_internal_collide_cells(c, f, Q, c->s_cells, count, s);
+    }
     if (count > 0) {
         // spectral operator (projected) on the routed cells, in batch mode
         CollideArgs a;

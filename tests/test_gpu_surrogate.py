@@ -190,3 +190,27 @@ def ctx_indicators(fks, ctx, sur, f):
     tmp = torch.empty_like(f)
     ctx.surrogate_collide(sur.net, f, tmp, sur.out_scale, 1.0, 1e30)
     return ctx.indicator()
+
+
+def test_routed_surrogate_collide_to_tensor_cores(fks):
+    """The learned + split-BF16 path: routed cells are recomputed by the
+    tensor-core operator, the others keep the surrogate's output."""
+    n, L, kn, nc = 16, 8.0, 0.3, 40
+    ctx = fks.Context(fks.Config(ncell=(nc, 1, 1), n=n, L=L, kn=kn, A1=4, A2=4, precision=fks.FKS_BF16X3))
+    net = fks.Net(n, 2, seed=11)
+    fd = torch.from_numpy(I.two_stream((nc, 1, 1), n, L, seed=6, noise=0.05).astype(np.float32)).cuda()
+    Qs = torch.empty_like(fd)
+    ctx.collide(fd, Qs)
+    Q = torch.empty_like(fd)
+    assert ctx.surrogate_collide(net, fd, Q, 1.0, 1.0, -1.0) == nc    # every cell routed
+    assert torch.equal(Q, Qs)
+    Qn = torch.empty_like(fd)
+    assert ctx.surrogate_collide(net, fd, Qn, 2.5, 1.0, 1e30) == 0    # none routed
+    ind = ctx.indicator()
+    thr = float(np.median(ind))
+    Qm = torch.empty_like(fd)
+    routed = ctx.surrogate_collide(net, fd, Qm, 2.5, 1.0, thr)
+    assert 0 < routed < nc
+    for c in range(nc):
+        want = Qs[c] if not ind[c] <= thr else Qn[c]
+        assert torch.equal(Qm[c], want), c
