@@ -282,8 +282,7 @@ namespace tc {
 
 constexpr int TY = 16, TZ = 8;                  // tile: 1 x 16 x 8 voxels
 constexpr int HX = 3, HY = TY + 2, HZ = TZ + 2;
-constexpr int HROWS = HX * HY * HZ;             // 540 halo rows
-constexpr int NTHR = 128;                       // 4 warps: TMEM lanes 0..127
+constexpr int NTHR = 160;                       // warps 0-3: epilogue (TMEM lanes 0..127); warp 4: TMA + MMA
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -341,9 +340,10 @@ __device__ __forceinline__ void wait_bounded(uint64_t* bar, uint32_t parity, int
 // contiguous 16-byte voxels), one 16-byte row per voxel, so that tap t's A operand is
 // the plane of k-chunk j shifted by the tap's row offset: a K-major descriptor
 // with LBO = the plane stride and SBO = 10 rows (next y).  B: the tap's
-// [KC][NP][16 B] weight block.  Per CTA the tiles are pipelined: halos and
-// TMEM accumulators are double-buffered, the MMAs of tile i+1 run beside the
-// epilogue of tile i.
+// [KC][NP][16 B] weight block.  Warp-specialised pipeline per CTA: warp 4
+// loads the halos (TMA, double-buffered) and issues the MMAs into two TMEM
+// accumulators; warps 0-3 read an accumulator, release it (an mbarrier of 128
+// arrivals) and store the tile, while the next tile's MMAs run.
 template <int KC, int NP, bool RELU, bool OUT_F32>
 __global__ void __launch_bounds__(NTHR, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap xmap, int n, int batch,
                                                           const __nv_bfloat16* __restrict__ wpk,
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(NTHR, 1) conv_tc_kernel(const __grid_constant_
     unsigned char* smem = smem_raw + ((128u - (saddr(smem_raw) & 127u)) & 127u);
     unsigned char* halo = smem;                          // [2][KC][HPLANE]
     unsigned char* wsm = smem + 2 * HALO_BYTES;          // [27][KC][NP][16 B]
-    __shared__ uint64_t bar_ld[2], bar_mma[2];
+    __shared__ uint64_t bar_ld[2], bar_mma[2], bar_free[2];   // halo landed, MMAs done, accumulator read
     __shared__ uint32_t tmem_base;
     __shared__ float sbias[32];
     __shared__ int s_abort;
@@ -375,7 +375,9 @@ __global__ void __launch_bounds__(NTHR, 1) conv_tc_kernel(const __grid_constant_
         for (int i = 0; i < 2; ++i) {
             mbar_init1(&bar_ld[i]);
             mbar_init1(&bar_mma[i]);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(saddr(&bar_free[i])) : "memory");
         }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         s_abort = 0;
     }
     fence_async_shared_cta();   // the weights (generic stores) before the tensor core reads them
@@ -440,21 +442,30 @@ __global__ void __launch_bounds__(NTHR, 1) conv_tc_kernel(const __grid_constant_
                          saddr(&bar_mma[i & 1]))
                      : "memory");
     };
-    if (tid == 0 && mine > 0) {
-        load(0);
-        if (mine > 1) load(1);
-        wait_halo(0);
-        mma(0);
-    }
+    if (warp == 4) {
+        // producer: lane 0 loads halos and issues MMAs; the MMAs of tile i queue behind
+        // those of tile i-1, whose completion frees the halo buffer for tile i+1
+        if (lane == 0 && mine > 0) {
+            load(0);
+            if (mine > 1) load(1);
+#pragma unroll 1
+            for (long i = 0; i < mine; ++i) {
+                wait_halo(i);
+                if (i >= 2)   // the epilogue of tile i-2 has read accumulator i & 1
+                    wait_bounded(&bar_free[i & 1], (uint32_t)(((i - 2) >> 1) & 1), flags, &s_abort);
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                mma(i);
+                if (i >= 1) {
+                    wait_bounded(&bar_mma[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1), flags, &s_abort);
+                    if (i + 1 < mine) load(i + 1);   // into the buffer of tile i-1
+                }
+            }
+        }
+    } else {
 #pragma unroll 1
     for (long i = 0; i < mine; ++i) {
-        if (tid == 0 && i + 1 < mine) {   // accumulator (i+1) & 1 was read by tile i-1
-            wait_halo(i + 1);
-            mma(i + 1);
-        }
         wait_bounded(&bar_mma[i & 1], (uint32_t)((i >> 1) & 1), flags, &s_abort);
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (tid == 0 && i + 2 < mine) load(i + 2);   // halo buffer i & 1: the MMAs of tile i are done
         // epilogue: warp w reads D rows 32w .. 32w+31 (one voxel per thread)
         int b, x0, y0, z0;
         coords(i, b, x0, y0, z0);
@@ -485,6 +496,9 @@ __global__ void __launch_bounds__(NTHR, 1) conv_tc_kernel(const __grid_constant_
 #pragma unroll
             for (int c = 0; c < NP; ++c) v[c] = __uint_as_float(r[c]);
         }
+        // this thread's reads of accumulator i & 1 are done: release it to the producer
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(&bar_free[i & 1])) : "memory");
         const int m = 32 * warp + lane;
         const long vloc = ((long)x0 * n + (y0 + m / TZ)) * n + (z0 + m % TZ);   // voxel within the cell
         if constexpr (OUT_F32) {
@@ -504,10 +518,10 @@ __global__ void __launch_bounds__(NTHR, 1) conv_tc_kernel(const __grid_constant_
                 *reinterpret_cast<uint4*>(yo) = *reinterpret_cast<const uint4*>(h);
             }
         }
-        // every thread's TMEM reads are done before tile i+2's MMAs overwrite accumulator i & 1
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();
     }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();   // every MMA has completed and been read
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(tmem) : "memory");
 }
