@@ -54,9 +54,9 @@ BF16_PEAK_TFLOPS, BF16_PEAK_KIND = _bf16_peak()
 # ncu capture on the 16x16x8 = 2048-cell shock tube, divided by 2048; traffic grows with
 # the cells of a launch).  Valid for the kernels as profiled; None once a kernel changes.
 DRAM_BYTES_PER_CELL = {
-    "collide_f32": (274375424 + 221985792) / 2048,   # collide_kernel<float, 32, 4>
-    "bgk_f32": (315430656 + 209028864) / 2048,       # bgk_kernel<float, 32>
-    "collide_tc": (635289344 + 1520071000) / 2048,   # collide_tc_kernel<32> (scratch written back from L2)
+    "collide_f32": (273574656 + 221917696) / 2048,   # collide_kernel<float, 32, 4>
+    "bgk_f32": (443623936 + 208807680) / 2048,       # bgk_kernel<float, 32, 128> (part of the second pass misses L2)
+    "collide_tc": (635715072 + 1520406000) / 2048,   # collide_tc_kernel<32> (scratch written back from L2)
 }
 
 
@@ -248,6 +248,10 @@ def learned_path(torch, fks, dev, args, sample=1216, threshold=1e-3):
                                "err_vs_fp64": {"max": elt, "median": mlt},
                                "spectral_bf16x3_collide_ms": t_tc,
                                "note": "routed cells recomputed by the split-BF16 tensor-core operator"},
+            "err_note": "relative L2 of Q against the FP64 operator on this sample, which includes nearly "
+                        "Maxwellian shock-tube cells: there ||L|| / ||Q|| is large and the error is bounded on the "
+                        "loss scale (FP32 2.5e-7 ||L||, split BF16 2.5e-5 ||L||); far from equilibrium see "
+                        "bf16x3_tensor_core.err_vs_fp64",
             "train_seconds": train_s, "train_loss_last": sur.train_loss[-1], "calibration": sur.calib,
             "note": "collision operator only (the part the surrogate replaces), same sample for both paths; "
                     "net: 6 x conv3d 3^3, 32 ch, BF16 weights and activations, FP32 accumulation; inference on "
