@@ -248,6 +248,20 @@ fks_status fks_surrogate_collide(fks_ctx *ctx, fks_net *net, const void *f, void
 /* host copy of the last indicators (count = number of cells) */
 fks_status fks_surrogate_indicator(const fks_ctx *ctx, float *host, long count);
 
+/* fks_step with HOST arrays (f -> f_out, ncells * n^3 elements each, distinct):
+ * the state is copied to device buffers owned by the context, stepped and
+ * copied back, pipelined over chunks of x-slabs: the host-to-device copies of
+ * later chunks, the step of a chunk (once every slab its transport shift can
+ * reach, at most floor(L |dt| / dx) + 1 slabs away, has landed) and the
+ * device-to-host copies of earlier chunks overlap on internal copy streams.
+ * Spectral FP32/FP64 and BGK contexts use up to 8 chunks; split-BF16 and
+ * variant-B contexts one.  Same values as fks_step on device copies.  Returns
+ * after queueing; the output is complete when `stream` is.  The host arrays
+ * should be page-locked for the copies to overlap; they must not be touched
+ * before `stream` completes.  Allocates two device copies of the state on
+ * first use. */
+fks_status fks_step_host(fks_ctx *ctx, const void *host_f, void *host_out, double dt, void *stream);
+
 /* Variant B (de-aliased operator), Appendix A Eq. CF1 with l + m = k over the
  * modes l, m in [-n/2, n/2]^3, not reduced mod n, evaluated with transforms of
  * size 2n as in Sec. 5 (2n^3 transforms for n^3 modes).  on != 0: from then on

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(BS, 1024 / BS) bgk_kernel(BgkArgs a) {
         __syncthreads();
     };
 
-    for (long cell = blockIdx.x; cell < a.ncells; cell += gridDim.x) {
+    for (long cell = a.cell0 + blockIdx.x; cell < a.ncells; cell += gridDim.x) {
         const int cx = (int)(cell / ((long)ncy * ncz));
         const int cy = (int)((cell / ncz) % ncy);
         const int cz = (int)(cell % ncz);
@@ -246,7 +246,8 @@ template <typename T, int N>
 static cudaError_t launch_n(const BgkArgs& a, cudaStream_t s) {
     // 128-thread CTAs, 8 per SM: eight cells in flight per SM
     constexpr int BS = N >= 16 ? 128 : 256;
-    long grid = a.ncells < 152L * 16 ? a.ncells : 152L * 16;
+    const long cells = a.ncells - a.cell0;
+    long grid = cells < 152L * 16 ? cells : 152L * 16;
     bgk_kernel<T, N, BS><<<(unsigned)grid, BS, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -749,6 +749,16 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
 void fks_destroy(fks_ctx* c) {
     if (!c) return;
     if (c->dealias) fks_set_dealias(c, 0);
+    if (c->h_in) {
+        cudaDeviceSynchronize();
+        for (int k = 0; k < 3; ++k)
+            for (int i = 0; i < 64; ++i)
+                if (c->h_ev[k][i]) cudaEventDestroy(c->h_ev[k][i]);
+        if (c->h_up) cudaStreamDestroy(c->h_up);
+        if (c->h_down) cudaStreamDestroy(c->h_down);
+        cudaFree(c->h_in);
+        cudaFree(c->h_out);
+    }
     cudaFree(c->tables);
     cudaFree(c->tc_dft);
     cudaFree(c->tc_scratch);
@@ -791,13 +801,14 @@ fks_status fks_set_cluster_size(fks_ctx* c, int C) {
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 static fks_status launch_bgk_ctx(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, long cell0 = 0, long cell1 = -1) {
     BgkArgs a;
     a.f = f;
     a.out = out;
     a.delta = delta;
     a.flags = c->d_flags;
-    a.ncells = c->ncells;
+    a.ncells = cell1 >= 0 ? cell1 : c->ncells;
+    a.cell0 = cell0;
     a.nc[0] = c->grid.nx;
     a.nc[1] = c->grid.ny;
     a.nc[2] = c->grid.nz;
@@ -842,18 +853,23 @@ static fks_status launch_tc_ctx(fks_ctx* c, const void* f, void* out, const sign
     return FKS_OK;
 }
 
+// collision of the cells [cell0, cell1) (cell1 < 0: all); ranges other than
+// all cells are for the cluster and BGK kernels
 static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
-                                 cudaStream_t s) {
-    if (c->bgk) return launch_bgk_ctx(c, f, out, delta, dt, mode, s);
+                                 cudaStream_t s, long cell0 = 0, long cell1 = -1) {
+    if (c->bgk) return launch_bgk_ctx(c, f, out, delta, dt, mode, s, cell0, cell1);
     if (c->tc) return launch_tc_ctx(c, f, out, delta, dt, mode, s);
     if (c->dealias) return launch_dealias(c, f, out, delta, dt, mode, s);
+    if (cell1 < 0) cell1 = c->ncells;
+    if (cell1 <= cell0) return FKS_OK;
     CollideArgs a;
     a.f = f;
     a.out = out;
     a.tables = c->tables;
     a.delta = delta;
     a.flags = c->d_flags;
-    a.ncells = c->ncells;
+    a.ncells = cell1;
+    a.cell0 = cell0;
     a.nc[0] = c->grid.nx;
     a.nc[1] = c->grid.ny;
     a.nc[2] = c->grid.nz;
@@ -865,7 +881,8 @@ static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const sig
     a.mode = mode;
     std::memcpy(a.P, c->P, sizeof(a.P));
     a.items = nullptr;
-    const long nclus = c->ncells < c->max_clusters ? c->ncells : c->max_clusters;
+    const long ncl = cell1 - cell0;
+    const long nclus = ncl < c->max_clusters ? ncl : c->max_clusters;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -941,6 +958,91 @@ fks_status fks_step(fks_ctx* c, const void* f, void* f_out, double dt, void* str
     if (st != FKS_OK) return st;
     if (c->ncells == 0) return FKS_OK;
     return launch_collide(c, f, f_out, c->d_delta, dt, 1, s);
+}
+
+// One step with host arrays, pipelined over chunks of x-slabs: upload (stream
+// h_up), step of a chunk once every slab its transport can reach has landed
+// (the caller's stream), download (stream h_down) as soon as it is done.
+fks_status fks_step_host(fks_ctx* c, const void* host_f, void* host_out, double dt, void* stream) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (!host_f || !host_out || host_f == host_out) return fail(c, FKS_ERR_INVALID_ARG, "host arrays must be distinct");
+    if (c->ncells == 0) return FKS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t esz = c->fp64 ? 8 : 4;
+    const long n3 = (long)c->n * c->n * c->n;
+    const size_t bytes = esz * (size_t)c->ncells * n3;
+    if (!c->h_in) {
+        if (cudaMalloc(&c->h_in, bytes) != cudaSuccess || cudaMalloc(&c->h_out, bytes) != cudaSuccess)
+            return fail(c, FKS_ERR_OOM, "device copies of the state");
+        if (cudaStreamCreateWithFlags(&c->h_up, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c->h_down, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(c, FKS_ERR_CUDA, "copy streams");
+        for (int k = 0; k < 3; ++k)
+            for (int i = 0; i < 64; ++i)
+                if (cudaEventCreateWithFlags(&c->h_ev[k][i], cudaEventDisableTiming) != cudaSuccess)
+                    return fail(c, FKS_ERR_CUDA, "events");
+    }
+    fks_status st = launch_offsets(c, dt, s);
+    if (st != FKS_OK) return st;
+    // chunks of whole x-slabs (the cluster and BGK kernels take cell ranges; the others one chunk)
+    const int nx = c->grid.nx;
+    const long slab = (long)c->grid.ny * c->grid.nz;
+    const int nchunk = (c->tc || c->dealias) ? 1 : (nx < 8 ? nx : 8);
+    auto chunk_of = [&](int x) { return (int)((long)x * nchunk / nx); };
+    auto first_slab = [&](int k) { return (int)(((long)k * nx + nchunk - 1) / nchunk); };
+    // shifts along x reach at most floor(L |dt| / dx) + 1 cells (|offset| < dx/2, |v| < L)
+    const int reach = (int)std::floor(c->vbox.L * std::fabs(dt) / c->dx[0]) + 1;
+    const char* hf = static_cast<const char*>(host_f);
+    char* ho = static_cast<char*>(host_out);
+    char* din = static_cast<char*>(c->h_in);
+    char* dout = static_cast<char*>(c->h_out);
+    cudaEvent_t* up = c->h_ev[0];
+    cudaEvent_t* done = c->h_ev[1];
+    cudaEvent_t* down = c->h_ev[2];
+    // the copy streams start after the caller's earlier work (ordering of the host arrays)
+    if (cudaEventRecord(down[63], s) != cudaSuccess || cudaStreamWaitEvent(c->h_up, down[63], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(c->h_down, down[63], 0) != cudaSuccess)
+        return fail(c, FKS_ERR_CUDA, "stream order");
+    for (int k = 0; k < nchunk; ++k) {
+        const long c0 = (long)first_slab(k) * slab, c1 = (long)first_slab(k + 1) * slab;
+        if (cudaMemcpyAsync(din + c0 * n3 * esz, hf + c0 * n3 * esz, (c1 - c0) * n3 * esz, cudaMemcpyHostToDevice,
+                            c->h_up) != cudaSuccess ||
+            cudaEventRecord(up[k], c->h_up) != cudaSuccess)
+            return fail(c, FKS_ERR_CUDA, "upload");
+    }
+    for (int k = 0; k < nchunk; ++k) {
+        const int a = first_slab(k), b = first_slab(k + 1);
+        // every upload chunk a slab of [a - reach, b - 1 + reach] folds into
+        bool need[64] = {};
+        for (int x = a - reach; x <= b - 1 + reach; ++x) {
+            int xf = x;
+            if (c->grid.bc[0] == FKS_BC_PERIODIC) {
+                xf = ((x % nx) + nx) % nx;
+            } else {
+                const int per = 2 * nx;
+                int r = ((x % per) + per) % per;
+                xf = r >= nx ? per - 1 - r : r;
+            }
+            need[chunk_of(xf)] = true;
+            if (nchunk == 1) break;
+        }
+        for (int j = 0; j < nchunk; ++j)
+            if (need[j] && cudaStreamWaitEvent(s, up[j], 0) != cudaSuccess) return fail(c, FKS_ERR_CUDA, "wait upload");
+        st = nchunk == 1 ? launch_collide(c, din, dout, c->d_delta, dt, 1, s)
+                         : launch_collide(c, din, dout, c->d_delta, dt, 1, s, (long)a * slab, (long)b * slab);
+        if (st != FKS_OK) return st;
+        if (cudaEventRecord(done[k], s) != cudaSuccess || cudaStreamWaitEvent(c->h_down, done[k], 0) != cudaSuccess)
+            return fail(c, FKS_ERR_CUDA, "step event");
+        const long c0 = (long)a * slab, c1 = (long)b * slab;
+        if (cudaMemcpyAsync(ho + c0 * n3 * esz, dout + c0 * n3 * esz, (c1 - c0) * n3 * esz, cudaMemcpyDeviceToHost,
+                            c->h_down) != cudaSuccess ||
+            cudaEventRecord(down[k], c->h_down) != cudaSuccess)
+            return fail(c, FKS_ERR_CUDA, "download");
+    }
+    // the caller's stream completes after the last download
+    for (int k = 0; k < nchunk; ++k)
+        if (cudaStreamWaitEvent(s, down[k], 0) != cudaSuccess) return fail(c, FKS_ERR_CUDA, "join");
+    return FKS_OK;
 }
 
 fks_status fks_moments(fks_ctx* c, const void* f, double* U, void* stream) {

@@ -59,7 +59,8 @@ struct CollideArgs {
     const void* tables;     // [M+1][C] slabs: [2][N kx][NS kyl][H-1] planes 1..H-1, then [2][N][NS][2] planes 0, H
     const signed char* delta;  // [3][N] cell shifts for this step (transport) or nullptr
     int* flags;             // health bits (atomicOr)
-    long ncells;
+    long ncells;            // end (exclusive) of the cells (items) this launch processes
+    long cell0;             // first cell of this launch (0 in batch mode)
     int nc[3];              // spatial cells per axis
     int bc[3];              // 0 periodic, 1 specular
     int M;                  // number of directions
@@ -331,7 +332,7 @@ collide_kernel(CollideArgs args) {
             bulk_g2s(Tb, tab + ((long)p * C + rank) * Cfg::TAB_ELEMS, Cfg::TAB_BYTES, tbar);
         }
     };
-    if (cluster_id < args.ncells) fetch_tables(item_tables(cluster_id), 0);
+    if (args.cell0 + cluster_id < args.ncells) fetch_tables(item_tables(args.cell0 + cluster_id), 0);
     const int ncx = args.nc[0], ncy = args.nc[1], ncz = args.nc[2];
 
     // z-pass ownership: column (xl, y), x = rank*NS + xl (threads >= NTASK idle)
@@ -356,7 +357,7 @@ collide_kernel(CollideArgs args) {
     // y-pass lane addressing: element (src, kyl) at ybase + src*BLK + kyl*HP
     const long ybase = widx(t_tab, t_xl, 0, t_pp);
 
-    for (long item = cluster_id; item < args.ncells; item += nclusters) {
+    for (long item = args.cell0 + cluster_id; item < args.ncells; item += nclusters) {
         // batch: item = one homogeneous problem (cell 0 of its own arrays)
         const long cell = BATCH ? 0 : item;
         const T* __restrict__ fin;

@@ -32,7 +32,8 @@ struct BgkArgs {
     void* out;
     const signed char* delta;   // [3][n] shifts (transport) or nullptr
     int* flags;
-    long ncells;
+    long ncells;                // end (exclusive) of the cells this launch processes
+    long cell0;                 // first cell
     int nc[3], bc[3];
     double L, inv_kn, dt;
     int mode;                   // 0 collide, 1 step
@@ -74,6 +75,11 @@ struct fks_ctx {
     void* tc_dft = nullptr;     // BF16 DFT matrices
     void* tc_scratch = nullptr; // per-CTA spectrum and pass-3 operand scratch
     int tc_grid = 0;
+    // fks_step_host: device copies of the state, copy streams, per-chunk events
+    void* h_in = nullptr;
+    void* h_out = nullptr;
+    cudaStream_t h_up = nullptr, h_down = nullptr;
+    cudaEvent_t h_ev[3][64] = {};
     // variant B (fks_set_dealias): inner context of the 2n grid, chunk buffers, P and T
     bool dealias = false;
     fks_ctx* inner = nullptr;

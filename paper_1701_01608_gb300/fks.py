@@ -64,7 +64,7 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_init", "fks_net_num_params", "fks_net_set_params", "fks_net_get_params", "fks_net_forward",
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
            "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
-           "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias"]
+           "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias", "fks_step_host"]
 
 
 def lib(build: bool = True):
@@ -135,6 +135,7 @@ def lib(build: bool = True):
     L.fks_surrogate_indicator.argtypes = [P, P, ctypes.c_long]
     L.fks_selftest_wait.argtypes = [ctypes.c_long, P]
     L.fks_set_dealias.argtypes = [P, I]
+    L.fks_step_host.argtypes = [P, P, P, D, P]
     L.fks_destroy.argtypes = [P]
     L.fks_destroy.restype = None
     L.fks_last_error.argtypes = [P]
@@ -209,6 +210,14 @@ class Context:
         self.dtype = torch.float64 if cfg.precision == FKS_FP64 else torch.float32
         if cfg.dealias:
             self.set_dealias(True)
+
+    def step_host(self, f, f_out, dt: float, stream=None):
+        """fks_step with host (CPU, preferably pinned) tensors, copies pipelined with the step."""
+        for t in (f, f_out):
+            if t.device.type != "cpu" or t.dtype != self.dtype or not t.is_contiguous():
+                raise TypeError(f"expected a contiguous CPU tensor of {self.dtype}")
+        self._check(self._L.fks_step_host(self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(f_out.data_ptr()),
+                                          float(dt), _stream_ptr(stream)), "fks_step_host")
 
     def set_dealias(self, on: bool = True):
         """Variant B: the 2n-padded (de-aliased) operator for this context's collisions."""
