@@ -427,7 +427,8 @@ static cudaError_t launch_moments_t(const fks_ctx* c, const void* f, double* U, 
 }
 
 int default_cluster_size(bool fp64, int N) {
-    if (!fp64) return N == 32 ? 4 : (N == 24 ? 2 : 1);
+    // FP32 n = 32: C = 8 measured 176.9 ms against 178.4 ms for C = 4 (32^3 x 32^3 step)
+    if (!fp64) return N == 32 ? 8 : (N == 24 ? 2 : 1);
     return N == 32 ? 8 : (N == 24 ? 4 : (N == 16 ? 2 : 1));
 }
 
