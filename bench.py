@@ -54,7 +54,7 @@ BF16_PEAK_TFLOPS, BF16_PEAK_KIND = _bf16_peak()
 # ncu capture on the 16x16x8 = 2048-cell shock tube, divided by 2048; traffic grows with
 # the cells of a launch).  Valid for the kernels as profiled; None once a kernel changes.
 DRAM_BYTES_PER_CELL = {
-    "collide_f32": (273574656 + 221917696) / 2048,   # collide_kernel<float, 32, 4>
+    "collide_f32": (275852032 + 222365696) / 2048,   # collide_kernel<float, 32, 8>
     "bgk_f32": (443623936 + 208807680) / 2048,       # bgk_kernel<float, 32, 128> (part of the second pass misses L2)
     "collide_tc": (635715072 + 1520406000) / 2048,   # collide_tc_kernel<32> (scratch written back from L2)
 }
