@@ -19,6 +19,11 @@ Functions and the passage each follows:
   pad, truncate,
   collide_b, galerkin_b  -- variant B: Eq. CF1 with l + m = k not reduced mod n,
                             evaluated with 2n transforms (Sec. 5); brute force
+  vhs_h, vhs_gain_loss,
+  collide_vhs,
+  galerkin_vhs           -- variable hard spheres B = C|g|^alpha: the non-separable
+                            Carleman kernel of Eq. Btilde_pl, B_F(l, m) by a product
+                            radial quadrature (Appendix A); brute force
 
 Pins: every function is checked against values fixed outside this module by
 tests/test_oracle_*.py (numpy.fft, scipy quadrature / Bessel functions, closed
@@ -89,6 +94,10 @@ def _L():
             lib.or_truncate.argtypes = [I, P, P]
             lib.or_collide_b.argtypes = [I, D, I, P, P, P, P, D, I, Lg, P, P]
             lib.or_galerkin_b.argtypes = [I, D, I, D, I, I, I, D, P, P]
+            lib.or_vhs_h.argtypes = [D, D, D, D, D]
+            lib.or_vhs_h.restype = D
+            lib.or_vhs_gain_loss.argtypes = [I, D, D, D, I, I, I, Lg, P, P, P]
+            lib.or_vhs_galerkin.argtypes = [I, D, D, D, I, I, I, D, P, P]
             _lib = lib
     return _lib
 
@@ -256,6 +265,43 @@ def galerkin_b(f, n: int, L: float, ktype=HARD_SPHERE, C=0.25, A1=4, A2=4, rule=
     f = _f64(f).reshape(n, n, n)
     Q = np.empty_like(f)
     _L().or_galerkin_b(n, L, ktype, C, A1, A2, rule, 1.0 / kn, _p(f), _p(Q))
+    return Q
+
+
+def vhs_h(alpha: float, C: float, R: float, t: float, u: float) -> float:
+    """Direction factor H(t, u) of the VHS kernel B = C|g|^alpha (product radial quadrature)."""
+    return _L().or_vhs_h(alpha, C, R, t, u)
+
+
+def vhs_gain_loss(f, n: int, L: float, alpha: float, C=0.25, A1=4, A2=4, rule=0):
+    """Gain and loss of the VHS operator for every n^3 cell of f (no projection, no 1/Kn)."""
+    f = _f64(f)
+    shp = f.shape
+    assert shp[-3:] == (n, n, n)
+    nc = int(np.prod(shp[:-3])) if len(shp) > 3 else 1
+    G = np.empty_like(f)
+    Lo = np.empty_like(f)
+    _L().or_vhs_gain_loss(n, L, alpha, C, A1, A2, rule, nc, _p(f), _p(G), _p(Lo))
+    return G, Lo
+
+
+def collide_vhs(f, n: int, L: float, alpha: float, C=0.25, A1=4, A2=4, rule=0, kn: float = 1.0,
+                project: bool = True) -> np.ndarray:
+    """VHS Q(f)/Kn for every cell, then (optionally) the conservation projection."""
+    G, Lo = vhs_gain_loss(f, n, L, alpha, C, A1, A2, rule)
+    Q = np.ascontiguousarray((G - Lo) / kn)
+    if project:
+        Qc = Q.reshape(-1, n, n, n)
+        for c in range(Qc.shape[0]):
+            _L().or_project(n, L, _p(Qc[c]))
+    return Q
+
+
+def galerkin_vhs(f, n: int, L: float, alpha: float, C=0.25, A1=4, A2=4, rule=0, kn: float = 1.0) -> np.ndarray:
+    """Brute-force Eq. CF1 with the VHS B_F of one n^3 cell (unprojected); n <= 8."""
+    f = _f64(f).reshape(n, n, n)
+    Q = np.empty_like(f)
+    _L().or_vhs_galerkin(n, L, alpha, C, A1, A2, rule, 1.0 / kn, _p(f), _p(Q))
     return Q
 
 

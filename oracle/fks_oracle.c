@@ -25,7 +25,10 @@
  * Parity status of every exported function: pinned by tests/test_oracle_*.py
  * (FFT against numpy.fft, kernel transforms against scipy quadrature and
  * scipy.special.j1, Galerkin identity, conservation, Q(M)=0, closed-form
- * loss frequency of a Maxwellian, BKW shape, transport permutation).
+ * loss frequency of a Maxwellian, BKW shape, transport permutation; the
+ * variable-hard-sphere operator against scipy's double quadrature, the hard-
+ * sphere operator at alpha = 1, the closed-form loss frequency of a
+ * Maxwellian for every alpha and BKW for Maxwell molecules).
  */
 #include <complex.h>
 #include <math.h>
@@ -795,4 +798,261 @@ void or_galerkin_b(int n, double L, int ktype, double C, int A1, int A2, int rul
     or_fft3d(Qc, n, +1);
     for (long j = 0; j < n3; ++j) Q[j] = creal(Qc[j]) * inv_kn;
     free(e); free(w); free(F); free(g); free(a); free(b); free(Qc);
+}
+
+/* ------------------------------------------------------------------ */
+/* variable hard spheres: the non-separable kernel of Eq. Btilde_pl     */
+/* ------------------------------------------------------------------ */
+
+/* For the collision kernel B = C |g|^alpha the Carleman kernel is
+ *   B~(r, r') = 4C (r^2 + r'^2)^((alpha - 1)/2),   r = |x|, r' = |y|
+ * (Appendix A, Eq. Btilde_pl).  Only alpha = 1 makes it a product a(r) b(r');
+ * for any other alpha the direction-p factor of B_F(l, m) stays the double
+ * radial integral
+ *   H(t, u) = int_0^R int_0^R [2 r cos(r t)] B~(r, r') [2 pi r' J_0(r' u)] dr dr'
+ * (the phi and psi integrals of the separable case, here with B~ inside), and
+ *   B_F(l, m) = sum_p w_p H(xi_l . e_p, |xi_m - (xi_m . e_p) e_p|).
+ * The oracle evaluates H by a product quadrature in (r, r') on a composite
+ * Gauss-Legendre rule: 20 nodes on each of [R/3, 2R/3] and [2R/3, R], and
+ * 12 nodes on each of 16 panels of [0, R/3] that halve towards 0 (the last
+ * one reaching 0), which resolves the corner r = r' = 0 where B~ is singular
+ * for alpha < 1. */
+enum { VHS_TOP = 20, VHS_LOW = 12, VHS_LEVELS = 16, VHS_NQ = 2 * VHS_TOP + VHS_LEVELS * VHS_LOW };
+
+static void vhs_rule(double R, double *r, double *wr)
+{
+    double xt[VHS_TOP], wt[VHS_TOP], xl[VHS_LOW], wl[VHS_LOW];
+    gauss_legendre(VHS_TOP, xt, wt);
+    gauss_legendre(VHS_LOW, xl, wl);
+    int q = 0;
+    for (int j = 1; j <= 2; ++j) {
+        double a = j * R / 3.0, b = (j + 1) * R / 3.0;
+        for (int i = 0; i < VHS_TOP; ++i, ++q) {
+            r[q] = a + 0.5 * (b - a) * (xt[i] + 1.0);
+            wr[q] = 0.5 * (b - a) * wt[i];
+        }
+    }
+    double b = R / 3.0;
+    for (int lev = 0; lev < VHS_LEVELS; ++lev) {
+        double a = lev < VHS_LEVELS - 1 ? 0.5 * b : 0.0;
+        for (int i = 0; i < VHS_LOW; ++i, ++q) {
+            r[q] = a + 0.5 * (b - a) * (xl[i] + 1.0);
+            wr[q] = 0.5 * (b - a) * wl[i];
+        }
+        b = a;
+    }
+}
+
+/* B~ on the node pairs: Bt[i * NQ + j] = 4C (r_i^2 + r_j^2)^((alpha-1)/2) */
+static void vhs_kernel_matrix(double alpha, double C, const double *r, double *Bt)
+{
+    for (int i = 0; i < VHS_NQ; ++i)
+        for (int j = 0; j < VHS_NQ; ++j)
+            Bt[i * VHS_NQ + j] = 4.0 * C * pow(r[i] * r[i] + r[j] * r[j], 0.5 * (alpha - 1.0));
+}
+
+double or_vhs_h(double alpha, double C, double R, double t, double u)
+{
+    double r[VHS_NQ], wr[VHS_NQ], c[VHS_NQ], d[VHS_NQ];
+    vhs_rule(R, r, wr);
+    for (int i = 0; i < VHS_NQ; ++i) {
+        c[i] = 2.0 * wr[i] * r[i] * cos(r[i] * t);
+        d[i] = 2.0 * OR_PI * wr[i] * r[i] * bessel_j(0, r[i] * u);
+    }
+    double s = 0.0;
+    for (int i = 0; i < VHS_NQ; ++i)
+        for (int j = 0; j < VHS_NQ; ++j)
+            s += c[i] * 4.0 * C * pow(r[i] * r[i] + r[j] * r[j], 0.5 * (alpha - 1.0)) * d[j];
+    return s;
+}
+
+/* Radial factors of direction p on the DFT index grid, each the mean over
+ * the sign choices of the Nyquist components (as in or_tables):
+ *   c[i][k] = 2 w_i r_i cos(r_i xi_k . e_p)
+ *   D[i][k] = sum_j B~(r_i, r_j) 2 pi w_j r_j J_0(r_j |xi_k - (xi_k . e_p) e_p|)
+ * so that sum_i c[i][l] D[i][m] = H(xi_l . e_p, |xi_m x e_p|). */
+static void vhs_direction_factors(int n, double L, const double *ep, const double *r, const double *wr,
+                                  const double *Bt, double *c, double *D)
+{
+    long n3 = (long)n * n * n;
+    double h = OR_PI / L;
+    int nyq = (n % 2 == 0) ? n / 2 : -1;
+#pragma omp parallel
+    {
+        double *ca = (double *)malloc(sizeof(double) * VHS_NQ);
+        double *da = (double *)malloc(sizeof(double) * VHS_NQ);
+#pragma omp for schedule(dynamic)
+        for (long k = 0; k < n3; ++k) {
+            int kk[3] = {(int)(k / ((long)n * n)), (int)((k / n) % n), (int)(k % n)};
+            int nflip = 0, fl[3];
+            for (int a = 0; a < 3; ++a) if (kk[a] == nyq) fl[nflip++] = a;
+            int ncomb = 1 << nflip;
+            for (int i = 0; i < VHS_NQ; ++i) ca[i] = da[i] = 0.0;
+            for (int cmb = 0; cmb < ncomb; ++cmb) {
+                double xi[3];
+                for (int a = 0; a < 3; ++a) xi[a] = h * kappa(kk[a], n);
+                for (int b = 0; b < nflip; ++b)
+                    if (cmb & (1 << b)) xi[fl[b]] = -xi[fl[b]];
+                double de = xi[0] * ep[0] + xi[1] * ep[1] + xi[2] * ep[2];
+                double q2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2] - de * de;
+                double sp = sqrt(q2 > 0 ? q2 : 0.0);
+                for (int i = 0; i < VHS_NQ; ++i) {
+                    ca[i] += 2.0 * wr[i] * r[i] * cos(r[i] * de);
+                    da[i] += 2.0 * OR_PI * wr[i] * r[i] * bessel_j(0, r[i] * sp);
+                }
+            }
+            for (int i = 0; i < VHS_NQ; ++i) {
+                double s = 0.0;
+                for (int j = 0; j < VHS_NQ; ++j) s += Bt[i * VHS_NQ + j] * da[j];
+                c[(long)i * n3 + k] = ca[i] / ncomb;
+                D[(long)i * n3 + k] = s / ncomb;
+            }
+        }
+        free(ca); free(da);
+    }
+}
+
+/* Gain and loss of the VHS operator for every cell (no projection, no 1/Kn):
+ *   G = sum_p w_p sum_i IDFT(c_{p,i} F) IDFT(D_{p,i} F) / n^6
+ *   L = f IDFT(betaL F) / n^3,  betaL(k) = sum_p w_p sum_i c_{p,i}(k) D_{p,i}(k)
+ * i.e. the Galerkin sum of Eq. CF1 with B_F(l, m) = sum_p w_p H_p(l, m),
+ * written as a sum of products because H_p is a finite sum over quadrature
+ * nodes of functions of l times functions of m. */
+void or_vhs_gain_loss(int n, double L, double alpha, double C, int A1, int A2, int rule,
+                      long ncells, const double *f, double *G, double *Lo)
+{
+    int M = A1 * A2;
+    long n3 = (long)n * n * n;
+    double *e = (double *)malloc(sizeof(double) * 3 * M), *w = (double *)malloc(sizeof(double) * M);
+    or_directions(A1, A2, rule, e, w);
+    double R = 2.0 / (3.0 + sqrt(2.0)) * L;
+    double r[VHS_NQ], wr[VHS_NQ];
+    vhs_rule(R, r, wr);
+    double *Bt = (double *)malloc(sizeof(double) * VHS_NQ * VHS_NQ);
+    vhs_kernel_matrix(alpha, C, r, Bt);
+    double *c = (double *)malloc(sizeof(double) * VHS_NQ * n3);
+    double *D = (double *)malloc(sizeof(double) * VHS_NQ * n3);
+    double *betaL = (double *)calloc(n3, sizeof(double));
+    double *P = (double *)malloc(sizeof(double) * VHS_NQ * n3);
+    cplx *F = (cplx *)malloc(sizeof(cplx) * n3 * ncells);
+    for (long cl = 0; cl < ncells; ++cl) {
+        for (long k = 0; k < n3; ++k) F[cl * n3 + k] = f[cl * n3 + k];
+        or_fft3d(F + cl * n3, n, -1);
+    }
+    for (long k = 0; k < n3 * ncells; ++k) G[k] = 0.0;
+    for (int p = 0; p < M; ++p) {
+        vhs_direction_factors(n, L, e + 3 * p, r, wr, Bt, c, D);
+        for (long k = 0; k < n3; ++k) {
+            double s = 0.0;
+            for (int i = 0; i < VHS_NQ; ++i) s += c[(long)i * n3 + k] * D[(long)i * n3 + k];
+            betaL[k] += w[p] * s;
+        }
+        for (long cl = 0; cl < ncells; ++cl) {
+            const cplx *Fc = F + cl * n3;
+#pragma omp parallel
+            {
+                cplx *A = (cplx *)malloc(sizeof(cplx) * n3);
+                cplx *B = (cplx *)malloc(sizeof(cplx) * n3);
+#pragma omp for schedule(dynamic)
+                for (int i = 0; i < VHS_NQ; ++i) {
+                    for (long k = 0; k < n3; ++k) {
+                        A[k] = c[(long)i * n3 + k] * Fc[k];
+                        B[k] = D[(long)i * n3 + k] * Fc[k];
+                    }
+                    or_fft3d(A, n, +1);
+                    or_fft3d(B, n, +1);
+                    for (long k = 0; k < n3; ++k) P[(long)i * n3 + k] = (creal(A[k]) / n3) * (creal(B[k]) / n3);
+                }
+                free(A); free(B);
+            }
+            /* sum over the nodes in a fixed order (deterministic) */
+            double *Gc = G + cl * n3;
+#pragma omp parallel for
+            for (long k = 0; k < n3; ++k) {
+                double s = 0.0;
+                for (int i = 0; i < VHS_NQ; ++i) s += P[(long)i * n3 + k];
+                Gc[k] += w[p] * s;
+            }
+        }
+    }
+    cplx *A = (cplx *)malloc(sizeof(cplx) * n3);
+    for (long cl = 0; cl < ncells; ++cl) {
+        for (long k = 0; k < n3; ++k) A[k] = betaL[k] * F[cl * n3 + k];
+        or_fft3d(A, n, +1);
+        for (long k = 0; k < n3; ++k) Lo[cl * n3 + k] = f[cl * n3 + k] * creal(A[k]) / n3;
+    }
+    free(A); free(P); free(e); free(w); free(Bt); free(c); free(D); free(betaL); free(F);
+}
+
+/* Brute-force Eq. CF1 for the VHS kernel (one cell, unprojected):
+ * Q^_k = n^-3 sum_{l+m=k mod n} [B_F(l,m) - B_F(m,m)] F_l F_m with
+ * B_F(l,m) = sum_p w_p sum_i c_{p,i}(l) D_{p,i}(m), F by the direct DFT sum,
+ * Q = IDFT(Q^)/n^3 by the direct sum, times inv_kn.  O(n^6 M NQ): n <= 8. */
+void or_vhs_galerkin(int n, double L, double alpha, double C, int A1, int A2, int rule, double inv_kn,
+                     const double *f, double *Q)
+{
+    int M = A1 * A2;
+    long n3 = (long)n * n * n;
+    double *e = (double *)malloc(sizeof(double) * 3 * M), *w = (double *)malloc(sizeof(double) * M);
+    or_directions(A1, A2, rule, e, w);
+    double R = 2.0 / (3.0 + sqrt(2.0)) * L;
+    double r[VHS_NQ], wr[VHS_NQ];
+    vhs_rule(R, r, wr);
+    double *Bt = (double *)malloc(sizeof(double) * VHS_NQ * VHS_NQ);
+    vhs_kernel_matrix(alpha, C, r, Bt);
+    double *c = (double *)malloc(sizeof(double) * (long)M * VHS_NQ * n3);
+    double *D = (double *)malloc(sizeof(double) * (long)M * VHS_NQ * n3);
+    /* node factors of every direction, stored [p][k][i] (node index fastest) */
+    double *tc = (double *)malloc(sizeof(double) * VHS_NQ * n3), *tD = (double *)malloc(sizeof(double) * VHS_NQ * n3);
+    for (int p = 0; p < M; ++p) {
+        vhs_direction_factors(n, L, e + 3 * p, r, wr, Bt, tc, tD);
+        for (long k = 0; k < n3; ++k)
+            for (int i = 0; i < VHS_NQ; ++i) {
+                c[((long)p * n3 + k) * VHS_NQ + i] = tc[(long)i * n3 + k];
+                D[((long)p * n3 + k) * VHS_NQ + i] = tD[(long)i * n3 + k];
+            }
+    }
+    free(tc); free(tD);
+    cplx *F = (cplx *)malloc(sizeof(cplx) * n3);
+    cplx *Qh = (cplx *)calloc(n3, sizeof(cplx));
+    for (long k = 0; k < n3; ++k) {
+        int kx = (int)(k / (n * n)), ky = (int)((k / n) % n), kz = (int)(k % n);
+        cplx s = 0;
+        for (long j = 0; j < n3; ++j) {
+            int jx = (int)(j / (n * n)), jy = (int)((j / n) % n), jz = (int)(j % n);
+            double ang = -2.0 * OR_PI * (double)(kx * jx + ky * jy + kz * jz) / n;
+            s += f[j] * (cos(ang) + I * sin(ang));
+        }
+        F[k] = s;
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (long k = 0; k < n3; ++k) {
+        int kx = (int)(k / (n * n)), ky = (int)((k / n) % n), kz = (int)(k % n);
+        cplx acc = 0;
+        for (long l = 0; l < n3; ++l) {
+            int lx = (int)(l / (n * n)), ly = (int)((l / n) % n), lz = (int)(l % n);
+            long m = (((long)((kx - lx + n) % n) * n) + (ky - ly + n) % n) * n + (kz - lz + n) % n;
+            double beta = 0.0;
+            for (int p = 0; p < M; ++p) {
+                const double *cl = c + ((long)p * n3 + l) * VHS_NQ, *cm = c + ((long)p * n3 + m) * VHS_NQ;
+                const double *Dm = D + ((long)p * n3 + m) * VHS_NQ;
+                double s = 0.0;
+                for (int i = 0; i < VHS_NQ; ++i) s += (cl[i] - cm[i]) * Dm[i];
+                beta += w[p] * s;
+            }
+            acc += beta * F[l] * F[m];
+        }
+        Qh[k] = acc;
+    }
+    for (long j = 0; j < n3; ++j) {
+        int jx = (int)(j / (n * n)), jy = (int)((j / n) % n), jz = (int)(j % n);
+        cplx s = 0;
+        for (long k = 0; k < n3; ++k) {
+            int kx = (int)(k / (n * n)), ky = (int)((k / n) % n), kz = (int)(k % n);
+            double ang = 2.0 * OR_PI * (double)(kx * jx + ky * jy + kz * jz) / n;
+            s += Qh[k] * (cos(ang) + I * sin(ang));
+        }
+        Q[j] = creal(s) / ((double)n3 * n3) * inv_kn;
+    }
+    free(e); free(w); free(Bt); free(c); free(D); free(F); free(Qh);
 }
