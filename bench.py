@@ -340,6 +340,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
     ap.add_argument("--no-varb", action="store_true")
+    ap.add_argument("--no-vhs", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=int(os.environ.get("FKS_CPU_SAMPLE", "1024")))
     ap.add_argument("--grid", default=None, help="nx,ny,nz spatial cells (default 32,32,32); smaller grids "
                     "are for profiling runs, not bench lines")
@@ -530,6 +531,40 @@ def main():
                         "|k| <= 8 and projection (per 2048-cell chunk: 3 launches)" % GRID}
         del fb0, sb
 
+    # variable hard spheres B = C|g|^alpha (non-separable Carleman kernel, expanded into
+    # separable terms): Maxwell molecules, alpha = 0, on the same workload
+    vhs = None
+    if not args.no_vhs and ws == 1:
+        from paper_1701_01608_gb300 import inputs as I
+        alpha = 0.0
+        _, S, trunc = fks.vhs_factor(alpha, 0.25, LBOX, NV, fks.FKS_FP32, 0, 0.0, 0.0)
+        cv = fks.Context(fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=fks.VHS, C=0.25, kn=KN,
+                                    A1=A1, A2=A2, precision=fks.FKS_FP32, alpha=alpha))
+        ks, kw = min(args.steps, 3), max(1, min(args.warmup, 3))
+        tv, perv, lv, bitsv, _ = time_steps(torch, cv, f0, ks, kw, dt, ws)
+        del cv
+        msv = float(np.mean(perv))
+        flv = flops_per_cell(NV, M * S) * NCELLS
+        fs = torch.from_numpy(I.two_stream((8, 1, 1), NV, LBOX, seed=79, noise=0.05)).to(dev)
+        q64 = torch.empty_like(fs)
+        fks.Context(fks.Config(ncell=(8, 1, 1), n=NV, L=LBOX, kernel=fks.VHS, C=0.25, kn=KN, A1=A1, A2=A2,
+                               precision=fks.FKS_FP64, alpha=alpha)).collide(fs, q64)
+        q32 = torch.empty_like(fs, dtype=torch.float32)
+        fks.Context(fks.Config(ncell=(8, 1, 1), n=NV, L=LBOX, kernel=fks.VHS, C=0.25, kn=KN, A1=A1, A2=A2,
+                               precision=fks.FKS_FP32, alpha=alpha)).collide(fs.float(), q32)
+        d = ((q32.double() - q64).flatten(1).norm(dim=1) / q64.flatten(1).norm(dim=1)).cpu().numpy()
+        vhs = {"value": PTS * ks / (tv / 1e3), "unit": "pts/s", "ms_per_step": tv / ks, "steps": ks,
+               "alpha": alpha, "terms": S, "truncation": trunc,
+               "roofline": {"bound": "alu", "achieved": flv / (msv / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                            "unit": "TFLOP/s", "frac": flv / (msv / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                            "traffic": None, "algorithmic_flops_per_launch": flv,
+                            "peak_note": "operator flops with M x terms table pairs; derived FP32 peak"},
+               "gpu_launches": lv, "health_bits": bitsv,
+               "err_fp32_vs_fp64": {"max": float(d.max()), "median": float(np.median(d))},
+               "note": "fks_step, FKS_VHS alpha = 0 (Maxwell molecules, B = C): the radial factor of the "
+                       "Carleman kernel 4C (|x|^2+|y|^2)^-1/2 expanded into %d separable terms, "
+                       "%d table pairs per cell; same shock tube, FP32" % (S, M * S)}
+
     learned = None
     if not args.no_learned and ws == 1:
         learned = learned_path(torch, fks, dev, args)
@@ -571,6 +606,7 @@ def main():
         "bgk_step": bgk,
         "bf16x3_tensor_core": tcp,
         "variant_b_16v": varb,
+        "vhs_maxwell": vhs,
         "learned": learned,
     }
     print(json.dumps(out), flush=True)

@@ -50,7 +50,7 @@ enum { FKS_BC_PERIODIC = 0, FKS_BC_SPECULAR = 1 };
  * hi*hi + lo*hi + hi*lo accumulated in FP32); n = 16 or 32, spectral kernels
  * only (not BGK, not batches). */
 enum { FKS_FP64 = 0, FKS_FP32 = 1, FKS_BF16X3 = 2 };
-enum { FKS_HARD_SPHERE = 0, FKS_MAXWELL = 1, FKS_BGK = 2 };
+enum { FKS_HARD_SPHERE = 0, FKS_MAXWELL = 1, FKS_BGK = 2, FKS_VHS = 3 };
 
 /* Spatial grid: nx*ny*nz cells on the box [x0, x1]; bc[a] applies to both
  * walls of axis a.  nx = ny = nz = 1 is the space-homogeneous problem. */
@@ -71,15 +71,29 @@ typedef struct {
  *   FKS_MAXWELL:     B~(|x|,|y|) = 4C (|x||y|)^-1/2, a separable kernel whose
  *                    collision kernel B = C (sin(theta)/2)^-1/2 does not
  *                    depend on |g| (Maxwell type).
+ *   FKS_VHS:         variable hard spheres B = C |g|^alpha, -1 <= alpha <= 1
+ *                    (alpha = 0: Maxwell molecules, alpha = 1: hard spheres):
+ *                    B~(|x|,|y|) = 4C (|x|^2 + |y|^2)^((alpha-1)/2), which is
+ *                    not a product a(|x|) b(|y|) for alpha != 1.  The library
+ *                    expands the radial factor of B_F(l, m) into `terms`
+ *                    separable terms (eigen-decomposition of the kernel on a
+ *                    radial quadrature; terms = 0 picks the smallest count whose
+ *                    error on the grid's frequencies is below 1e-7 (FP32,
+ *                    BF16X3) or 1e-12 (FP64) of the factor), each term one more
+ *                    pair of tables per direction: the cost grows with the
+ *                    count.  Not available in batches.
  * The operator returned is Q / knudsen.
  *   FKS_BGK:         the BGK relaxation nu (M[f] - f) of Sec. 2 with the
  *                    cell's Maxwellian M[f] and nu = rho / knudsen (C unused),
  *                    followed by the same conservation projection; not
- *                    available in batches. */
+ *                    available in batches.
+ * alpha and terms are read for FKS_VHS only (terms <= 64). */
 typedef struct {
     int type;
     double C;
     double knudsen;
+    double alpha;
+    int terms;
 } fks_kernel;
 
 /* Collision directions (Appendix A): M = A1*A2 half-sphere directions
@@ -150,6 +164,17 @@ long fks_launch_count(const fks_ctx *ctx);
  * (R = 2L/(3+sqrt 2)) evaluated on the host by the same code the table
  * kernel runs on the device.  Needs no GPU. */
 fks_status fks_kernel_transform(int ktype, double C, double L, double s, double *phi, double *psi);
+
+/* Diagnostic: the radial factor H(t, u) of one direction of the FKS_VHS kernel
+ * (alpha, C, box [-L, L]^3 with n^3 points) as the library's expansion gives
+ * it: sum over the separable terms of phi_s(t) psi_s(u), where the exact factor is
+ *   H(t, u) = int_0^R int_0^R 2r cos(rt) B~(r, r') 2 pi r' J0(r'u) dr dr',
+ * R = 2L/(3 + sqrt 2) (Appendix A).  Returns the term count in *S and the
+ * truncation error estimate (max over the check grid, relative) in *trunc_err
+ * (either may be NULL).  precision selects the automatic tolerance; terms as in
+ * fks_kernel.  Runs on the host; needs no GPU. */
+fks_status fks_vhs_factor(double alpha, double C, double L, int n, int precision, int terms, double t, double u,
+                          double *H, int *S, double *trunc_err);
 
 /* ---------------------------------------------------------------- batches
  * Independent space-homogeneous problems (one cell each, no transport) of

@@ -351,14 +351,17 @@ def transport(f, ncell, bc, delta) -> np.ndarray:
 class Solver:
     """Plain FKS time loop: transport, then Euler collision step (Eq. disc_relax).
     tab = None: BGK relaxation; variant_b: tab holds the tables of the 2n grid and
-    the collision is the de-aliased operator (collide_b)."""
+    the collision is the de-aliased operator (collide_b); vhs = (alpha, C, A1, A2,
+    rule): the variable-hard-sphere operator (collide_vhs), tab unused."""
 
-    def __init__(self, ncell, x0, x1, bc, n, L, tab: Tables, kn: float, variant_b: bool = False):
+    def __init__(self, ncell, x0, x1, bc, n, L, tab: Tables, kn: float, variant_b: bool = False,
+                 vhs: tuple | None = None):
         self.ncell = tuple(int(c) for c in ncell)
         self.bc = tuple(int(b) for b in bc)
         self.dx = [(x1[a] - x0[a]) / self.ncell[a] for a in range(3)]
         self.n, self.L, self.tab, self.kn = n, L, tab, kn
         self.variant_b = variant_b
+        self.vhs = vhs
         self.s = np.zeros((3, n))
 
     def transport(self, f, dt):
@@ -367,7 +370,9 @@ class Solver:
 
     def step(self, f, dt):
         fs = self.transport(f, dt)
-        if self.tab is None:   # BGK relaxation
+        if self.vhs is not None:
+            Q = collide_vhs(fs, self.n, self.L, *self.vhs, kn=self.kn, project=True)
+        elif self.tab is None:   # BGK relaxation
             Q = bgk(fs, self.n, self.L, self.kn, project=True)
         elif self.variant_b:
             Q = collide_b(fs, self.tab, self.kn, project=True)

@@ -40,6 +40,11 @@ struct TableParams {
     const double* glt_w;           //                               weights
     const double* glu_x;           // Gauss-Legendre on [0, sqrt(R)]: nodes
     const double* glu_w;           //                                  weights
+    // variable hard spheres (ktype 3): table pair p is term p % vS of direction p / vS
+    int vS, vQ;
+    const double* vr;              // [vQ] radial nodes
+    const double* vca;             // [vS][vQ] phi_s coefficients
+    const double* vcb;             // [vS][vQ] psi_s coefficients
 };
 
 // phi for hard spheres in closed form: 2 c4 [R sin(Rs)/s + (cos(Rs) - 1)/s^2]
@@ -95,8 +100,15 @@ __host__ __device__ inline void mode_tables(const TableParams& tp, int p, int kx
             if (c & (1 << b)) xi[nyq_axes[b]] = -xi[nyq_axes[b]];
         const double d = xi[0] * ex + xi[1] * ey + xi[2] * ez;
         const double q2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2] - d * d;
-        sa += phi_any(tp, d);
-        sb += psi_any(tp, sqrt(q2 > 0.0 ? q2 : 0.0));
+        const double u = sqrt(q2 > 0.0 ? q2 : 0.0);
+        if (tp.ktype == 3) {
+            const int term = p % tp.vS;
+            sa += vhs_phi(tp.vca + (long)term * tp.vQ, tp.vr, tp.vQ, d);
+            sb += vhs_psi(tp.vcb + (long)term * tp.vQ, tp.vr, tp.vQ, u);
+        } else {
+            sa += phi_any(tp, d);
+            sb += psi_any(tp, u);
+        }
     }
     *a_out = sa / ncomb;
     *b_out = sb / ncomb;
@@ -516,22 +528,33 @@ static fks_status configure_variant(fks_ctx* c, int C) {
 // Spectral tables of one (n, L, kernel, directions) in the collision kernel's
 // layout for cluster size C, built on the device in FP64 and stored in the
 // working precision.  *out is a new device allocation.
+// vx (FKS_VHS only): the separable terms; table pair p * S + s is term s of
+// direction p (M = A1 A2 S pairs).
 static fks_status build_tables_raw(int n, const fks_dirs& dirs, double L, int ktype, double Ck, int C, bool fp64,
-                                   void** out, std::string* err, bool full = false) {
-    const int M = dirs.A1 * dirs.A2, HF = n / 2 + 1;
+                                   void** out, std::string* err, bool full = false,
+                                   const VhsExpansion* vx = nullptr) {
+    const int S = (ktype == FKS_VHS && vx) ? vx->S : 1;
+    const int M = dirs.A1 * dirs.A2 * S, HF = n / 2 + 1;
     const double pi = 3.14159265358979323846;
     std::vector<double> e(3 * M), w(M);
     for (int p = 0; p < dirs.A1; ++p) {
         const double t = (dirs.rule == 0 ? (p + 0.5) : (double)p) * pi / dirs.A1;
         for (int q = 0; q < dirs.A2; ++q) {
             const double fi = q * pi / dirs.A2;
-            const int m = p * dirs.A2 + q;
-            e[3 * m] = std::sin(t) * std::cos(fi);
-            e[3 * m + 1] = std::sin(t) * std::sin(fi);
-            e[3 * m + 2] = std::cos(t);
-            w[m] = pi * pi / ((double)dirs.A1 * dirs.A2) * std::sin(t);
+            for (int term = 0; term < S; ++term) {
+                const int m = (p * dirs.A2 + q) * S + term;
+                e[3 * m] = std::sin(t) * std::cos(fi);
+                e[3 * m + 1] = std::sin(t) * std::sin(fi);
+                e[3 * m + 2] = std::cos(t);
+                w[m] = pi * pi / ((double)dirs.A1 * dirs.A2) * std::sin(t);
+            }
         }
     }
+    if (ktype == FKS_VHS && (!vx || vx->S < 1)) {
+        *err = "VHS tables need the separable expansion";
+        return FKS_ERR_INVALID_ARG;
+    }
+    const size_t nv = ktype == FKS_VHS ? vx->r.size() + vx->ca.size() + vx->cb.size() : 0;
     const double R = 2.0 / (3.0 + std::sqrt(2.0)) * L;
     std::vector<double> gl(4 * kGL);
     gl_rule(kGL, 0.0, 0.5 * pi, gl.data(), gl.data() + kGL);
@@ -543,7 +566,7 @@ static fks_status build_tables_raw(int n, const fks_dirs& dirs, double L, int kt
     const size_t esz = fp64 ? 8 : 4;
     fks_status st = FKS_OK;
     *out = nullptr;
-    cudaError_t e1 = cudaMalloc(&d_e, sizeof(double) * (3 * M + M));
+    cudaError_t e1 = cudaMalloc(&d_e, sizeof(double) * (3 * M + M + nv));
     cudaError_t e2 = cudaMalloc(&d_gl, sizeof(double) * 4 * kGL);
     cudaError_t e3 = cudaMalloc(&d_A, sizeof(double) * half);
     cudaError_t e4 = cudaMalloc(&d_B, sizeof(double) * half);
@@ -553,8 +576,15 @@ static fks_status build_tables_raw(int n, const fks_dirs& dirs, double L, int kt
         st = FKS_ERR_OOM;
     } else {
         d_w = d_e + 3 * M;
+        double* d_v = d_w + M;
         cudaMemcpy(d_e, e.data(), sizeof(double) * 3 * M, cudaMemcpyHostToDevice);
         cudaMemcpy(d_w, w.data(), sizeof(double) * M, cudaMemcpyHostToDevice);
+        if (nv) {
+            cudaMemcpy(d_v, vx->r.data(), sizeof(double) * vx->r.size(), cudaMemcpyHostToDevice);
+            cudaMemcpy(d_v + vx->r.size(), vx->ca.data(), sizeof(double) * vx->ca.size(), cudaMemcpyHostToDevice);
+            cudaMemcpy(d_v + vx->r.size() + vx->ca.size(), vx->cb.data(), sizeof(double) * vx->cb.size(),
+                       cudaMemcpyHostToDevice);
+        }
         cudaMemcpy(d_gl, gl.data(), sizeof(double) * 4 * kGL, cudaMemcpyHostToDevice);
         TableParams tp;
         tp.n = n;
@@ -570,6 +600,11 @@ static fks_status build_tables_raw(int n, const fks_dirs& dirs, double L, int kt
         tp.glt_w = d_gl + kGL;
         tp.glu_x = d_gl + 2 * kGL;
         tp.glu_w = d_gl + 3 * kGL;
+        tp.vS = S;
+        tp.vQ = nv ? (int)vx->r.size() : 0;
+        tp.vr = d_v;
+        tp.vca = d_v + tp.vQ;
+        tp.vcb = d_v + tp.vQ + (nv ? vx->ca.size() : 0);
         tables_kernel<<<1024, 128>>>(tp, d_A, d_B);
         if (full)
             pack_tables_full_kernel<<<1024, 256>>>(n, M, HF, d_A, d_B, d_w, (float2*)*out);
@@ -597,7 +632,7 @@ static fks_status build_tables_raw(int n, const fks_dirs& dirs, double L, int kt
 static fks_status build_tables(fks_ctx* c) {
     std::string err;
     fks_status st = build_tables_raw(c->n, c->dirs, c->vbox.L, c->kern.type, c->kern.C, c->C, c->fp64, &c->tables, &err,
-                                     c->tc);
+                                     c->tc, &c->vhs);
     c->launches += 2;
     if (st != FKS_OK) return fail(c, st, err);
     return FKS_OK;
@@ -689,7 +724,11 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
     }
     if (!(vbox->L > 0.0) || !std::isfinite(vbox->L)) return FKS_ERR_INVALID_ARG;
     if (vbox->n != 8 && vbox->n != 16 && vbox->n != 24 && vbox->n != 32) return FKS_ERR_UNSUPPORTED;
-    if (kernel->type != FKS_HARD_SPHERE && kernel->type != FKS_MAXWELL && kernel->type != FKS_BGK)
+    if (kernel->type != FKS_HARD_SPHERE && kernel->type != FKS_MAXWELL && kernel->type != FKS_BGK &&
+        kernel->type != FKS_VHS)
+        return FKS_ERR_INVALID_ARG;
+    if (kernel->type == FKS_VHS &&
+        (!(kernel->alpha >= -1.0 && kernel->alpha <= 1.0) || kernel->terms < 0 || kernel->terms > kVhsMaxTerms))
         return FKS_ERR_INVALID_ARG;
     if (!(kernel->C > 0.0) || !(kernel->knudsen > 0.0)) return FKS_ERR_INVALID_ARG;
     if (dirs->A1 < 1 || dirs->A2 < 1 || dirs->A1 * dirs->A2 > 4096 || (dirs->rule != 0 && dirs->rule != 1))
@@ -714,6 +753,18 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
     c->bgk = kernel->type == FKS_BGK;
     c->tc = precision == FKS_BF16X3;
     fks_status st = FKS_OK;
+    if (kernel->type == FKS_VHS) {
+        // the separable terms, each one more table pair per direction
+        st = vhs_expand(kernel->alpha, kernel->C, vbox->L, vbox->n, vhs_tolerance(precision), kernel->terms, &c->vhs,
+                        &c->err);
+        if (st == FKS_OK && (long)c->M * c->vhs.S > 4096) st = fail(c, FKS_ERR_UNSUPPORTED, "A1 A2 x VHS terms > 4096");
+        if (st == FKS_OK) c->M *= c->vhs.S;
+    }
+    if (st != FKS_OK) {
+        std::fprintf(stderr, "fks_init: %s\n", c->err.c_str());
+        fks_destroy(c);
+        return st;
+    }
     if (c->tc) {
         c->C = 1;
         st = build_tables(c);
@@ -1317,7 +1368,7 @@ fks_status fks_batch_init(int nprob, const int* n, const double* L, const int* k
         return FKS_ERR_INVALID_ARG;
     for (int i = 0; i < nprob; ++i) {
         if (n[i] != 8 && n[i] != 16 && n[i] != 24 && n[i] != 32) return FKS_ERR_UNSUPPORTED;
-        if (ktype[i] == FKS_BGK) return FKS_ERR_UNSUPPORTED;
+        if (ktype[i] == FKS_BGK || ktype[i] == FKS_VHS) return FKS_ERR_UNSUPPORTED;
         if (!(L[i] > 0.0) || !std::isfinite(L[i]) || (ktype[i] != 0 && ktype[i] != 1) || !(C[i] > 0.0) ||
             !(knudsen[i] > 0.0))
             return FKS_ERR_INVALID_ARG;

@@ -66,6 +66,32 @@ cudaError_t launch_collide_tc(int n, const TcLaunch& l, cudaStream_t s);
 long tc_scratch_per_cta(int n);
 void tc_dft_matrices(int n, std::vector<uint16_t>& out);
 
+// Separable expansion of the variable-hard-sphere kernel (fks_vhs.cu):
+// H(t, u) ~ sum_{s<S} phi_s(t) psi_s(u), phi_s(t) = sum_i ca[s][i] cos(r_i t),
+// psi_s(u) = sum_i cb[s][i] J0(r_i u) over Q radial nodes r_i.
+constexpr int kVhsMaxTerms = 64;
+struct VhsExpansion {
+    int S = 0, Q = 0;
+    double err = 0.0;               // max |H_S - H| / max |H| on the check grid
+    std::vector<double> r, ca, cb;  // [Q], [S][Q], [S][Q]
+    std::vector<double> lambda;     // [S] eigenvalues kept
+};
+// truncation target of the automatic term count: the rounding scale of the precision
+inline double vhs_tolerance(int precision) { return precision == FKS_FP64 ? 1e-12 : 1e-7; }
+__host__ __device__ inline double vhs_phi(const double* ca, const double* r, int Q, double t) {
+    double acc = 0.0;
+    for (int i = 0; i < Q; ++i) acc += ca[i] * cos(r[i] * t);
+    return acc;
+}
+__host__ __device__ inline double vhs_psi(const double* cb, const double* r, int Q, double u) {
+    double acc = 0.0;
+    for (int i = 0; i < Q; ++i) acc += cb[i] * j0(r[i] * u);
+    return acc;
+}
+// terms = 0: the smallest S meeting tol on the frequencies of the n^3 grid
+fks_status vhs_expand(double alpha, double C, double L, int n, double tol, int terms, VhsExpansion* out,
+                      std::string* err);
+
 }  // namespace fks
 
 // Context state (fks_capi.cu); visible to the other translation units.
@@ -91,6 +117,7 @@ struct fks_ctx {
     fks_grid grid;
     fks_vbox vbox;
     fks_kernel kern;
+    fks::VhsExpansion vhs;      // FKS_VHS: the separable terms (M = A1 A2 S table pairs)
     fks_dirs dirs;
     bool fp64;
     int n, M, C;

@@ -21,6 +21,7 @@ FKS_BF16X3 = 2   # split-BF16 tensor-core transforms, FP32 storage
 HARD_SPHERE = 0
 MAXWELL = 1
 BGK = 2
+VHS = 3          # variable hard spheres B = C|g|^alpha (Config.alpha, Config.terms)
 PERIODIC = 0
 SPECULAR = 1
 
@@ -44,7 +45,8 @@ class _VBox(ctypes.Structure):
 
 
 class _Kernel(ctypes.Structure):
-    _fields_ = [("type", ctypes.c_int), ("C", ctypes.c_double), ("knudsen", ctypes.c_double)]
+    _fields_ = [("type", ctypes.c_int), ("C", ctypes.c_double), ("knudsen", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("terms", ctypes.c_int)]
 
 
 class _Dirs(ctypes.Structure):
@@ -64,7 +66,7 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_init", "fks_net_num_params", "fks_net_set_params", "fks_net_get_params", "fks_net_forward",
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
            "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
-           "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias", "fks_step_host"]
+           "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias", "fks_step_host", "fks_vhs_factor"]
 
 
 def lib(build: bool = True):
@@ -97,6 +99,7 @@ def lib(build: bool = True):
     L.fks_launch_count.argtypes = [P]
     L.fks_launch_count.restype = ctypes.c_long
     L.fks_kernel_transform.argtypes = [I, D, D, D, ctypes.POINTER(D), ctypes.POINTER(D)]
+    L.fks_vhs_factor.argtypes = [D, D, D, I, I, I, D, D, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D)]
     L.fks_transport_noalloc.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_VBox), I, P, D, P, P, P]
     PP = ctypes.POINTER(ctypes.c_void_p)
     PD = ctypes.POINTER(ctypes.c_double)
@@ -156,6 +159,19 @@ def kernel_transform(ktype: int, C: float, L: float, s: float) -> tuple[float, f
     return phi.value, psi.value
 
 
+def vhs_factor(alpha: float, C: float, L: float, n: int, precision: int, terms: int, t: float,
+               u: float) -> tuple[float, int, float]:
+    """(H(t, u), term count, truncation estimate) of the library's VHS expansion (host)."""
+    H = ctypes.c_double()
+    S = ctypes.c_int()
+    e = ctypes.c_double()
+    st = lib().fks_vhs_factor(alpha, C, L, n, precision, terms, t, u, ctypes.byref(H), ctypes.byref(S),
+                              ctypes.byref(e))
+    if st != 0:
+        raise FKSError(st, "fks_vhs_factor")
+    return H.value, S.value, e.value
+
+
 def _stream_ptr(stream) -> int:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -187,6 +203,8 @@ class Config:
     rule: int = 0
     precision: int = FKS_FP32
     dealias: bool = False   # variant B: 2n-padded (de-aliased) operator, n = 8 or 16
+    alpha: float = 1.0      # VHS exponent (kernel=VHS only)
+    terms: int = 0          # VHS separable terms, 0 = automatic
 
 
 class Context:
@@ -199,7 +217,7 @@ class Context:
         g = _Grid(cfg.ncell[0], cfg.ncell[1], cfg.ncell[2], (ctypes.c_double * 3)(*cfg.x0),
                   (ctypes.c_double * 3)(*cfg.x1), (ctypes.c_int * 3)(*cfg.bc))
         vb = _VBox(cfg.n, cfg.L)
-        k = _Kernel(cfg.kernel, cfg.C, cfg.kn)
+        k = _Kernel(cfg.kernel, cfg.C, cfg.kn, cfg.alpha, cfg.terms)
         d = _Dirs(cfg.A1, cfg.A2, cfg.rule)
         h = ctypes.c_void_p()
         st = self._L.fks_init(ctypes.byref(g), ctypes.byref(vb), ctypes.byref(k), ctypes.byref(d),

@@ -42,3 +42,36 @@ def test_status_strings(fks):
     lib = fks.lib()
     assert lib.fks_status_string(0) == b"ok"
     assert lib.fks_status_string(1) == b"invalid argument"
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.5, 0.0, -1.0])
+@pytest.mark.parametrize("prec,tol", [(1, 1e-7), (0, 1e-10)])
+def test_vhs_expansion_matches_oracle_factor(fks, oracle, alpha, prec, tol):
+    """The library's separable expansion of the VHS radial factor H(t, u)
+    (eigen-decomposition on its own radial rule, truncated at the precision's
+    tolerance) against the oracle's product quadrature of the definition, on
+    frequencies of the 32^3 grid of [-10, 10]^3."""
+    L, n = 10.0, 32
+    R = 2.0 / (3.0 + np.sqrt(2.0)) * L
+    tmax = np.pi / L * (n / 2) * np.sqrt(3.0)
+    href = abs(oracle.vhs_h(alpha, 0.25, R, 0.0, 0.0))
+    rng = np.random.default_rng(7)
+    pts = [(0.0, 0.0), (tmax, tmax), (0.0, tmax)] + [tuple(rng.uniform(0, tmax, 2)) for _ in range(6)]
+    for t, u in pts:
+        H, S, est = fks.vhs_factor(alpha, 0.25, L, n, prec, 0, t, u)
+        assert abs(H - oracle.vhs_h(alpha, 0.25, R, t, u)) <= tol * href, (t, u, S)
+    # hard spheres are one separable term; the others need several
+    assert (S == 1) == (alpha == 1.0)
+
+
+def test_vhs_expansion_term_count_and_errors(fks):
+    L, n = 10.0, 32
+    H8, S8, e8 = fks.vhs_factor(0.0, 0.25, L, n, 1, 8, 0.5, 0.5)
+    H4, S4, e4 = fks.vhs_factor(0.0, 0.25, L, n, 1, 4, 0.5, 0.5)
+    assert (S8, S4) == (8, 4) and e8 < e4
+    Ha, Sa, ea = fks.vhs_factor(0.0, 0.25, L, n, 1, 0, 0.5, 0.5)
+    Hd, Sd, ed = fks.vhs_factor(0.0, 0.25, L, n, 0, 0, 0.5, 0.5)
+    assert ea <= 1e-7 and ed <= 1e-12 and Sd > Sa
+    for bad in ((1.5, 0), (-1.5, 0), (0.0, 65), (0.0, -1)):
+        with pytest.raises(fks.FKSError):
+            fks.vhs_factor(bad[0], 0.25, L, n, 1, bad[1], 0.5, 0.5)

@@ -1,0 +1,170 @@
+"""GPU parity of the variable-hard-sphere operator (FKS_VHS, B = C|g|^alpha,
+the non-separable Carleman kernel of Eq. Btilde_pl expanded into separable
+terms by the library) against the oracle, which evaluates the kernel's
+definition by a product radial quadrature.  Bounds: FP64 1e-10 and FP32 1e-5
+relative L2 of Q (the expansion is truncated at 1e-12 / 1e-7 of the radial
+factor, below those bounds), split-BF16 the tensor-core bound."""
+import numpy as np
+import pytest
+from conftest import bf16_within
+
+from paper_1701_01608_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fks():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_01608_gb300 import fks
+    fks.lib()
+    return fks
+
+
+TOL = {0: 1e-10, 1: 1e-5}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def vhs_ctx(fks, ncell, n, L, alpha, A, prec, kn=0.3, bc=(0, 0, 0), terms=0):
+    return fks.Context(fks.Config(ncell=tuple(ncell), bc=tuple(bc), n=n, L=L, kernel=fks.VHS, C=0.25, kn=kn,
+                                  A1=A[0], A2=A[1], precision=prec, alpha=alpha, terms=terms))
+
+
+def dev(f, ctx):
+    return torch.from_numpy(np.ascontiguousarray(f)).to(device="cuda", dtype=ctx.dtype).contiguous()
+
+
+def host64(t):
+    return t.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("n,prec,alpha,L,A,nc", [
+    (8, 0, 0.5, 6.0, (4, 4), 3),
+    (8, 0, -1.0, 6.0, (4, 4), 2),
+    (16, 0, 0.0, 8.0, (2, 4), 2),
+    (8, 1, 0.0, 6.0, (4, 4), 5),
+    (16, 1, 0.0, 8.0, (4, 4), 3),
+    (16, 1, -1.0, 8.0, (2, 4), 2),
+    (32, 1, 0.0, 10.0, (2, 4), 1),
+])
+def test_vhs_collide_matches_oracle(fks, oracle, n, prec, alpha, L, A, nc):
+    ctx = vhs_ctx(fks, (nc, 1, 1), n, L, alpha, A, prec)
+    f = I.two_stream((nc, 1, 1), n, L, seed=21 + n, noise=0.05)
+    fd = dev(f, ctx)
+    Q = torch.empty_like(fd)
+    ctx.collide(fd, Q)
+    assert ctx.check() == 0
+    Qo = oracle.collide_vhs(host64(fd), n, L, alpha, 0.25, A[0], A[1], 0, kn=0.3, project=True)
+    Qg = host64(Q)
+    for c in range(nc):
+        assert rel(Qg[c], Qo[c]) < TOL[prec], (c, rel(Qg[c], Qo[c]))
+
+
+def test_vhs_alpha_one_is_hard_spheres(fks):
+    """alpha = 1 expands into one term equal to the hard-sphere tables."""
+    n, L, A = 16, 8.0, (4, 4)
+    f = I.two_stream((4, 1, 1), n, L, seed=5, noise=0.05)
+    cv = vhs_ctx(fks, (4, 1, 1), n, L, 1.0, A, 1)
+    ch = fks.Context(fks.Config(ncell=(4, 1, 1), n=n, L=L, kernel=fks.HARD_SPHERE, C=0.25, kn=0.3, A1=4, A2=4,
+                                precision=1))
+    fd = dev(f, cv)
+    Qv, Qh = torch.empty_like(fd), torch.empty_like(fd)
+    cv.collide(fd, Qv)
+    ch.collide(fd, Qh)
+    assert rel(host64(Qv), host64(Qh)) < 1e-6
+
+
+def test_vhs_split_bf16(fks, oracle):
+    n, L, A, nc = 16, 8.0, (4, 4), 3
+    ctx = vhs_ctx(fks, (nc, 1, 1), n, L, 0.0, A, fks.FKS_BF16X3)
+    f = I.two_stream((nc, 1, 1), n, L, seed=4, noise=0.05)
+    fd = dev(f, ctx)
+    Q = torch.empty_like(fd)
+    ctx.collide(fd, Q)
+    assert ctx.check() == 0
+    fin = host64(fd)
+    G, Lo = oracle.vhs_gain_loss(fin, n, L, 0.0, 0.25, A[0], A[1], 0)
+    Qo = oracle.collide_vhs(fin, n, L, 0.0, 0.25, A[0], A[1], 0, kn=0.3, project=True)
+    Qg = host64(Q)
+    for c in range(nc):
+        assert bf16_within(Qg[c], Qo[c], Lo[c] / 0.3), c
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_vhs_steps_specular(fks, oracle, prec):
+    """Transport + VHS collision + projection + Euler, 3 steps on a ragged grid."""
+    ncell, n, L, bc = (3, 2, 2), 8, 5.0, (1, 0, 0)
+    ctx = vhs_ctx(fks, ncell, n, L, 0.0, (4, 4), prec, kn=0.5, bc=bc)
+    sol = oracle.Solver(ncell, (0, 0, 0), (1, 1, 1), bc, n, L, None, 0.5, vhs=(0.0, 0.25, 4, 4, 0))
+    f = I.two_stream(ncell, n, L, seed=9, noise=0.1)
+    fd = dev(f, ctx)
+    f = host64(fd)
+    out = torch.empty_like(fd)
+    dt = 0.7 * (1.0 / 3) / L
+    for _ in range(3):
+        ctx.step(fd, out, dt)
+        fd, out = out, fd
+        f = sol.step(f, dt)
+    assert ctx.check() & 1 == 0
+    assert rel(host64(fd), f) < (1e-10 if prec == 0 else 2e-5)
+
+
+def test_vhs_variant_b(fks, oracle):
+    """Variant B (2n padding) with the VHS kernel: pad, the 2n operator, truncate, project."""
+    n, L, A, nc = 8, 6.0, (4, 4), 2
+    ctx = vhs_ctx(fks, (nc, 1, 1), n, L, 0.0, A, 0)
+    ctx.set_dealias(True)
+    f = I.two_stream((nc, 1, 1), n, L, seed=6, noise=0.05)
+    fd = dev(f, ctx)
+    Q = torch.empty_like(fd)
+    ctx.collide(fd, Q)
+    fin = host64(fd)
+    for c in range(nc):
+        f2 = oracle.pad(fin[c], n)
+        G2, L2 = oracle.vhs_gain_loss(f2, 2 * n, L, 0.0, 0.25, A[0], A[1], 0)
+        Qo = oracle.project(oracle.truncate((G2 - L2) / 0.3, n), n, L)
+        assert rel(host64(Q)[c], Qo) < 1e-10
+
+
+def test_vhs_rejected_where_unsupported(fks):
+    with pytest.raises(fks.FKSError):
+        vhs_ctx(fks, (1, 1, 1), 8, 6.0, 1.5, (4, 4), 1)
+    with pytest.raises(fks.FKSError):
+        fks.Batch([dict(n=16, L=8.0, kernel=fks.VHS, C=0.25, kn=1.0)])
+
+
+@pytest.mark.slow
+def test_vhs_full_size_step_sampled(fks, oracle):
+    """The benchmark's VHS step (32^3 cells x 32^3 velocities, FP32, M = 32
+    directions, Maxwell molecules, specular x walls) checked on sampled cells:
+    transport (bit-exact) followed by the oracle's projected VHS operator and
+    the Euler update."""
+    from paper_1701_01608_gb300 import inputs as I
+    n, L, kn, A = 32, 10.0, 0.01, (4, 8)
+    ctx = vhs_ctx(fks, (32, 32, 32), n, L, 0.0, A, 1, kn=kn, bc=(1, 0, 0))
+    states, which = I.shock_tube_states(n, L, 32)
+    st = torch.from_numpy(states).float().cuda()
+    f0 = st.index_select(0, torch.from_numpy(np.repeat(which, 1024)).cuda()).contiguous()
+    g = torch.Generator(device="cuda").manual_seed(3)
+    f0 *= 1.0 + 0.05 * (2.0 * torch.rand(f0.shape, generator=g, device="cuda", dtype=torch.float32) - 1.0)
+    f1 = torch.empty_like(f0)
+    dt = 1e-3
+    ctx.step(f0, f1, dt)
+    assert ctx.check() & 1 == 0
+    # the transport of the same step by a fresh context (its offsets start where ctx's did)
+    fs = torch.empty_like(f0)
+    ctx2 = vhs_ctx(fks, (32, 32, 32), n, L, 0.0, A, 1, kn=kn, bc=(1, 0, 0))
+    ctx2.transport(f0, fs, dt)
+    sample = [16 * 1024 + 5 * 32 + 7, 32767]
+    fsh = fs[sample].double().cpu().numpy()
+    Qo = oracle.collide_vhs(fsh, n, L, 0.0, 0.25, A[0], A[1], 0, kn=kn, project=True)
+    got = f1[sample].double().cpu().numpy()
+    for i in range(len(sample)):
+        inc_err = np.linalg.norm(got[i] - fsh[i] - dt * Qo[i]) / np.linalg.norm(dt * Qo[i])
+        assert inc_err < 1e-4, (sample[i], inc_err)
