@@ -16,7 +16,7 @@ from . import fks
 
 # cluster sizes compiled for each (precision, n)
 CANDIDATES = {
-    (fks.FKS_FP32, 8): [1, 2], (fks.FKS_FP32, 16): [1, 2], (fks.FKS_FP32, 24): [2, 4], (fks.FKS_FP32, 32): [4, 8],
+    (fks.FKS_FP32, 8): [1, 2], (fks.FKS_FP32, 16): [1, 2], (fks.FKS_FP32, 24): [2, 4], (fks.FKS_FP32, 32): [4, 8, 16],
     (fks.FKS_FP64, 8): [1, 2], (fks.FKS_FP64, 16): [2, 4], (fks.FKS_FP64, 24): [4], (fks.FKS_FP64, 32): [8],
 }
 

@@ -496,6 +496,10 @@ static cudaError_t query_variant(bool fp64, int n, int C, CollideVariant* v, int
     if (!*found) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(v->func_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem);
+    if (e == cudaSuccess && C > 8) {   // clusters of 16 are an opt-in size
+        e = cudaFuncSetAttribute(v->func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(v->func_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];

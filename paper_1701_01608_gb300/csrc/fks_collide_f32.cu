@@ -26,6 +26,7 @@ bool find_collide_variant_f32(int N, int C, CollideVariant* out) {
         case 24 * 16 + 4: return variant<24, 4>(out);
         case 32 * 16 + 4: return variant<32, 4>(out);
         case 32 * 16 + 8: return variant<32, 8>(out);
+        case 32 * 16 + 16: return variant<32, 16>(out);
         default: return false;
     }
 }

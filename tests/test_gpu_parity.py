@@ -70,9 +70,9 @@ def test_collide_matches_oracle(fks, oracle, n, prec, kernel, L, A, ncell):
         assert rel(Qg[c], Qo[c]) < TOL[prec], (c, rel(Qg[c], Qo[c]))
 
 
-@pytest.mark.parametrize("prec,C", [(1, 8), (1, 2), (0, 4), (1, 4)])
+@pytest.mark.parametrize("prec,C", [(1, 16), (1, 8), (1, 2), (0, 4), (1, 4)])
 def test_cluster_size_variants(fks, oracle, prec, C):
-    n = {(1, 8): 32, (1, 2): 16, (0, 4): 16, (1, 4): 24}[(prec, C)]
+    n = {(1, 16): 32, (1, 8): 32, (1, 2): 16, (0, 4): 16, (1, 4): 24}[(prec, C)]
     L, A = 10.0, (4, 4)
     ctx = make_ctx(fks, (3, 1, 1), n, L, A=A, prec=prec)
     ctx.set_cluster_size(C)
