@@ -341,6 +341,7 @@ def main():
     ap.add_argument("--no-tc", action="store_true")
     ap.add_argument("--no-varb", action="store_true")
     ap.add_argument("--no-vhs", action="store_true")
+    ap.add_argument("--no-strang", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=int(os.environ.get("FKS_CPU_SAMPLE", "1024")))
     ap.add_argument("--grid", default=None, help="nx,ny,nz spatial cells (default 32,32,32); smaller grids "
                     "are for profiling runs, not bench lines")
@@ -565,6 +566,31 @@ def main():
                        "Carleman kernel 4C (|x|^2+|y|^2)^-1/2 expanded into %d separable terms, "
                        "%d table pairs per cell; same shock tube, FP32" % (S, M * S)}
 
+    # second-order step (Strang splitting, Heun collision sub-step) on the same workload
+    strang = None
+    if not args.no_strang and ws == 1:
+        cs = fks.Context(cfg)
+        fa, fb, fw = f0.clone(), torch.empty_like(f0), torch.empty_like(f0)
+        ks, kw = min(args.steps, 5), max(1, min(args.warmup, 3))
+        for _ in range(kw):
+            cs.step_strang(fa, fb, fw, dt)
+            fa, fb = fb, fa
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = cs.launches
+        e0.record()
+        for _ in range(ks):
+            cs.step_strang(fa, fb, fw, dt)
+            fa, fb = fb, fa
+        e1.record()
+        torch.cuda.synchronize()
+        tsr = e0.elapsed_time(e1)
+        strang = {"value": PTS * ks / (tsr / 1e3), "unit": "pts/s", "ms_per_step": tsr / ks, "steps": ks,
+                  "gpu_launches": cs.launches - l0, "health_bits": cs.check(),
+                  "note": "fks_step_strang: T(dt/2), Heun collision (two projected operator evaluations), "
+                          "T(dt/2); second order in dt; FP32, same workload and dt"}
+        del cs, fa, fb, fw
+
     learned = None
     if not args.no_learned and ws == 1:
         learned = learned_path(torch, fks, dev, args)
@@ -607,6 +633,7 @@ def main():
         "bf16x3_tensor_core": tcp,
         "variant_b_16v": varb,
         "vhs_maxwell": vhs,
+        "strang_second_order": strang,
         "learned": learned,
     }
     print(json.dumps(out), flush=True)

@@ -130,6 +130,18 @@ fks_status fks_transport(fks_ctx *ctx, const void *f, void *f_out, double dt, vo
  * kernel per cell (f* never goes to memory).  f and f_out must not overlap. */
 fks_status fks_step(fks_ctx *ctx, const void *f, void *f_out, double dt, void *stream);
 
+/* A second-order step (the higher-order splitting the paper allows in Sec. 2.1):
+ * Strang splitting T(dt/2) C(dt) T(dt/2) of transport T and collision C, the
+ * collision sub-step integrated by Heun's method, the second-order explicit
+ * Runge-Kutta counterpart of Eq. disc_relax:
+ *   a = T(dt/2) f,  b = a + dt Q(a),  c = (a + b + dt Q(b)) / 2,  f_out = T(dt/2) c,
+ * Q projected as in fks_collide.  Advances the offsets by dt (two half steps).
+ * work: a caller-owned device array of the size of f (scratch; overwritten).
+ * f, f_out and work must be distinct.  FKS_FP64 and FKS_FP32 spectral
+ * contexts and BGK contexts; FKS_ERR_UNSUPPORTED for FKS_BF16X3 and
+ * variant-B contexts. */
+fks_status fks_step_strang(fks_ctx *ctx, const void *f, void *f_out, void *work, double dt, void *stream);
+
 /* U[cell][0..4] = sum_k (1, vx, vy, vz, |v|^2/2) f[cell][k] dv^3, accumulated
  * in FP64 (Sec. 3).  U: device array of ncells * 5 doubles. */
 fks_status fks_moments(fks_ctx *ctx, const void *f, double *U, void *stream);

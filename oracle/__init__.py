@@ -16,6 +16,7 @@ Functions and the passage each follows:
   project                -- conservation correction (collision invariants, Sec. 2)
   bgk                    -- BGK relaxation nu (M[f] - f) (Sec. 2, BGK approximation)
   step                   -- Eq. disc_relax: transport, then f = f* + dt Q(f*)
+  step_strang            -- second-order splitting (Sec. 2.1 allows it): T(dt/2), Heun, T(dt/2)
   pad, truncate,
   collide_b, galerkin_b  -- variant B: Eq. CF1 with l + m = k not reduced mod n,
                             evaluated with 2n transforms (Sec. 5); brute force
@@ -379,3 +380,22 @@ class Solver:
         else:
             Q = collide(fs, self.tab, self.kn, project=True)
         return fs + dt * Q
+
+    def collision(self, f):
+        """Q(f)/Kn, projected, with this solver's operator."""
+        if self.vhs is not None:
+            return collide_vhs(f, self.n, self.L, *self.vhs, kn=self.kn, project=True)
+        if self.tab is None:
+            return bgk(f, self.n, self.L, self.kn, project=True)
+        if self.variant_b:
+            return collide_b(f, self.tab, self.kn, project=True)
+        return collide(f, self.tab, self.kn, project=True)
+
+    def step_strang(self, f, dt):
+        """Second-order step (Sec. 2.1 allows higher-order splitting): Strang splitting
+        T(dt/2) C(dt) T(dt/2) with the collision sub-step by Heun's method, the
+        second-order Runge-Kutta counterpart of Eq. disc_relax."""
+        a = self.transport(f, 0.5 * dt)
+        b = a + dt * self.collision(a)
+        c = 0.5 * (a + b + dt * self.collision(b))
+        return self.transport(c, 0.5 * dt)

@@ -211,8 +211,10 @@ __global__ void __launch_bounds__(BS, 1024 / BS) bgk_kernel(BgkArgs a) {
                 czz[k] = m3 * vz[k] + (T)0.5 * m4 * vz[k] * vz[k];
             }
             const T tdt = (T)a.dt;
-            const bool stepm = a.mode == 1;
+            const bool heun = a.mode == 3;
+            const bool stepm = a.mode == 1 || heun;
             T* oc = fout + cell * N3 + z0;
+            const T* bc = static_cast<const T*>(a.base) + cell * N3 + z0;   // Heun: base, read before the store
             bool bad = false, neg = false;
 #pragma unroll 4
             for (int j = 0; j < ROWS; ++j) {
@@ -223,11 +225,18 @@ __global__ void __launch_bounds__(BS, 1024 / BS) bgk_kernel(BgkArgs a) {
                 const T vx = vgT[r / N], vy = vgT[r % N];
                 const T gxy = gx[r / N] * gy[r % N];
                 const T cxy = m0 + m1 * vx + m2 * vy + (T)0.5 * m4 * (vx * vx + vy * vy);
-                T o[V];
+                T o[V], b[V];
+                if (heun) {
+                    const VT w = *reinterpret_cast<const VT*>(bc + (long)r * N);
+                    const T* pw = reinterpret_cast<const T*>(&w);
+#pragma unroll
+                    for (int k = 0; k < V; ++k) b[k] = pw[k];
+                }
 #pragma unroll
                 for (int k = 0; k < V; ++k) {
                     const T q = tnu * (gxy * gzz[k] - v[k]) - (cxy + czz[k]);
                     o[k] = stepm ? v[k] + tdt * q : q;
+                    if (heun) o[k] = (T)0.5 * (o[k] + b[k]);
                     bad |= !isfinite(o[k]);
                     neg |= stepm && o[k] < T(0);
                 }

@@ -857,8 +857,9 @@ fks_status fks_set_cluster_size(fks_ctx* c, int C) {
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 static fks_status launch_bgk_ctx(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
-                                 cudaStream_t s, long cell0 = 0, long cell1 = -1) {
+                                 cudaStream_t s, long cell0 = 0, long cell1 = -1, const void* base = nullptr) {
     BgkArgs a;
+    a.base = base;
     a.f = f;
     a.out = out;
     a.delta = delta;
@@ -912,13 +913,14 @@ static fks_status launch_tc_ctx(fks_ctx* c, const void* f, void* out, const sign
 // collision of the cells [cell0, cell1) (cell1 < 0: all); ranges other than
 // all cells are for the cluster and BGK kernels
 static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
-                                 cudaStream_t s, long cell0 = 0, long cell1 = -1) {
-    if (c->bgk) return launch_bgk_ctx(c, f, out, delta, dt, mode, s, cell0, cell1);
+                                 cudaStream_t s, long cell0 = 0, long cell1 = -1, const void* base = nullptr) {
+    if (c->bgk) return launch_bgk_ctx(c, f, out, delta, dt, mode, s, cell0, cell1, base);
     if (c->tc) return launch_tc_ctx(c, f, out, delta, dt, mode, s);
     if (c->dealias) return launch_dealias(c, f, out, delta, dt, mode, s);
     if (cell1 < 0) cell1 = c->ncells;
     if (cell1 <= cell0) return FKS_OK;
     CollideArgs a;
+    a.base = base;
     a.f = f;
     a.out = out;
     a.tables = c->tables;
@@ -989,10 +991,8 @@ fks_status fks_collide(fks_ctx* c, const void* f, void* Q, void* stream) {
     return launch_collide(c, f, Q, nullptr, 0.0, 0, (cudaStream_t)stream);
 }
 
-fks_status fks_transport(fks_ctx* c, const void* f, void* f_out, double dt, void* stream) {
-    if (!c) return FKS_ERR_INVALID_ARG;
-    if (!f || !f_out || f == f_out) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must be distinct device pointers");
-    cudaStream_t s = (cudaStream_t)stream;
+// offsets over dt, then the transport gather f -> f_out
+static fks_status transport_ctx(fks_ctx* c, const void* f, void* f_out, double dt, cudaStream_t s) {
     fks_status st = launch_offsets(c, dt, s);
     if (st != FKS_OK) return st;
     if (c->ncells == 0) return FKS_OK;
@@ -1003,6 +1003,33 @@ fks_status fks_transport(fks_ctx* c, const void* f, void* f_out, double dt, void
     if (e != cudaSuccess) return cuda_fail(c, e, "transport kernel launch");
     c->launches += 1;
     return FKS_OK;
+}
+
+fks_status fks_transport(fks_ctx* c, const void* f, void* f_out, double dt, void* stream) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (!f || !f_out || f == f_out) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must be distinct device pointers");
+    return transport_ctx(c, f, f_out, dt, (cudaStream_t)stream);
+}
+
+// Second-order step: Strang splitting T(dt/2) C(dt) T(dt/2) with the collision
+// sub-step by Heun's method (the second-order explicit Runge-Kutta analogue of
+// Eq. disc_relax):  a = T(dt/2) f,  b = a + dt Q(a),  c = (a + b + dt Q(b)) / 2,
+// f_out = T(dt/2) c.  work holds a and then c (the second stage writes over its
+// own base element by element).
+fks_status fks_step_strang(fks_ctx* c, const void* f, void* f_out, void* work, double dt, void* stream) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (!f || !f_out || !work || !aligned16(f) || !aligned16(f_out) || !aligned16(work))
+        return fail(c, FKS_ERR_INVALID_ARG, "f, f_out and work must be 16-byte aligned device pointers");
+    if (f == f_out || f == work || f_out == work) return fail(c, FKS_ERR_INVALID_ARG, "f, f_out and work must be distinct");
+    if (c->tc || c->dealias)
+        return fail(c, FKS_ERR_UNSUPPORTED, "the Strang step runs on the FP64/FP32 spectral and BGK kernels");
+    if (!std::isfinite(dt)) return fail(c, FKS_ERR_INVALID_ARG, "dt must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    fks_status st = transport_ctx(c, f, work, 0.5 * dt, s);
+    if (st == FKS_OK && c->ncells > 0) st = launch_collide(c, work, f_out, nullptr, dt, 1, s);
+    if (st == FKS_OK && c->ncells > 0) st = launch_collide(c, f_out, work, nullptr, dt, 3, s, 0, -1, work);
+    if (st == FKS_OK) st = transport_ctx(c, work, f_out, 0.5 * dt, s);
+    return st;
 }
 
 fks_status fks_step(fks_ctx* c, const void* f, void* f_out, double dt, void* stream) {

@@ -67,9 +67,11 @@ struct CollideArgs {
     double L;               // velocity box half width
     double inv_kn;
     double dt;              // Euler step (step mode)
-    int mode;               // 0 collide (out = Q), 1 step (out = f* + dt Q), 2 collide without projection
+    int mode;               // 0 collide (out = Q), 1 step (out = f* + dt Q), 2 collide without projection,
+                            // 3 second Heun stage (out = (base + f* + dt Q) / 2; no transport, not batch)
     double P[25];           // dv^6 (C C^T)^-1 over the rows phi = (1, v, |v|^2/2)
     const BatchItem* items; // batch mode: ncells items, each a homogeneous problem
+    const void* base;       // mode 3: the first stage's input, same layout as out (may be out itself)
 };
 
 __device__ __forceinline__ void cluster_arrive() {
@@ -638,19 +640,32 @@ collide_kernel(CollideArgs args) {
                     // corrected Q = r / Kn - phi(v).mu, then out = Q or f* + dt Q
                     const T cxy = (T)(mu[0] + mu[1] * vx + mu[2] * vy + mu[4] * v2xy);
                     const T kn = (T)inv_kn, dt = (T)dt_step;
-                    const bool stepm = args.mode == 1;
+                    const bool heun = !BATCH && args.mode == 3;
+                    const bool stepm = args.mode == 1 || heun;
                     T* dst = fout + cell * N3 + ((long)zx * N + zl_y) * N;
+                    // Heun: base row of this column (read before this thread's own store to it)
+                    const T* brow = static_cast<const T*>(args.base) + cell * N3 + ((long)zx * N + zl_y) * N;
                     bool bad = false, neg = false;
                     constexpr int V = 16 / sizeof(T);
                     static_assert((N * sizeof(T)) % 16 == 0, "rows are whole 16-byte vectors");
 #pragma unroll
                     for (int z0 = 0; z0 < N; z0 += V) {
-                        T res[V];
+                        T res[V], bv[V];
+                        if (heun) {
+                            if constexpr (sizeof(T) == 4) {
+                                const float4 w = *reinterpret_cast<const float4*>(brow + z0);
+                                bv[0] = w.x; bv[1] = w.y; bv[2] = w.z; bv[3] = w.w;
+                            } else {
+                                const double2 w = *reinterpret_cast<const double2*>(brow + z0);
+                                bv[0] = w.x; bv[1] = w.y;
+                            }
+                        }
 #pragma unroll
                         for (int j = 0; j < V; ++j) {
                             const int z = z0 + j;
                             const T q = fma(rval(z), kn, -(cxy + czt[z]));
-                            const T o = stepm ? fma(dt, q, col[z]) : q;
+                            T o = stepm ? fma(dt, q, col[z]) : q;
+                            if (heun) o = T(0.5) * (o + bv[j]);
                             bad |= !isfinite(o);
                             neg |= stepm && (o < T(0));
                             res[j] = o;

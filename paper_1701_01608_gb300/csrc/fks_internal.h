@@ -36,8 +36,9 @@ struct BgkArgs {
     long cell0;                 // first cell
     int nc[3], bc[3];
     double L, inv_kn, dt;
-    int mode;                   // 0 collide, 1 step
+    int mode;                   // 0 collide, 1 step, 3 second Heun stage (out = (base + f* + dt Q) / 2)
     double P[25];
+    const void* base = nullptr; // mode 3: the first stage's input (may be out itself)
 };
 cudaError_t launch_bgk(bool fp64, int n, const BgkArgs& a, cudaStream_t s);
 
