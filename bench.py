@@ -55,7 +55,7 @@ BF16_PEAK_TFLOPS, BF16_PEAK_KIND = _bf16_peak()
 # the cells of a launch).  Valid for the kernels as profiled; None once a kernel changes.
 DRAM_BYTES_PER_CELL = {
     "collide_f32": (275852032 + 222365696) / 2048,   # collide_kernel<float, 32, 8>
-    "bgk_f32": (443623936 + 208807680) / 2048,       # bgk_kernel<float, 32, 128> (part of the second pass misses L2)
+    "bgk_f32": (268547328 + 215617792) / 2048,       # bgk_cluster_kernel<float, 32, 4> (f* read once)
     "collide_tc": (635715072 + 1520406000) / 2048,   # collide_tc_kernel<32> (scratch written back from L2)
 }
 

@@ -52,8 +52,9 @@ enum { FKS_BC_PERIODIC = 0, FKS_BC_SPECULAR = 1 };
 enum { FKS_FP64 = 0, FKS_FP32 = 1, FKS_BF16X3 = 2 };
 enum { FKS_HARD_SPHERE = 0, FKS_MAXWELL = 1, FKS_BGK = 2, FKS_VHS = 3 };
 
-/* Spatial grid: nx*ny*nz cells on the box [x0, x1]; bc[a] applies to both
- * walls of axis a.  nx = ny = nz = 1 is the space-homogeneous problem. */
+/* Spatial grid: nx*ny*nz cells (fewer than 2^31) on the box [x0, x1]; bc[a]
+ * applies to both walls of axis a.  nx = ny = nz = 1 is the space-homogeneous
+ * problem. */
 typedef struct {
     int nx, ny, nz;
     double x0[3], x1[3];

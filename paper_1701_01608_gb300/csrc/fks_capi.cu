@@ -253,7 +253,8 @@ __global__ void __launch_bounds__(256) transport_kernel(int ncx, int ncy, int nc
     const bool lane_ok = tid < LPR * RPI;
     const int z0 = (tid % LPR) * V, r0 = tid / LPR;
     for (long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
-        const int cx = (int)(cell / ((long)ncy * ncz)), cy = (int)((cell / ncz) % ncy), cz = (int)(cell % ncz);
+        int cx, cy, cz;
+        cell_coords(cell, ncy, ncz, cx, cy, cz);
         __syncthreads();   // the previous cell's readers of the tables are done
         for (int i = tid; i < 3 * N; i += BS) {
             const int ax = i / N, k = i % N;
@@ -374,9 +375,8 @@ __global__ void transport_any_kernel(int n, int ncx, int ncy, int ncz, int bcx, 
         const long cell = i / n3;
         const int k = (int)(i - cell * n3);
         const int kz = k % n, ky = (k / n) % n, kx = k / (n * n);
-        const int cz = (int)(cell % ncz);
-        const int cy = (int)((cell / ncz) % ncy);
-        const int cx = (int)(cell / ((long)ncy * ncz));
+        int cx, cy, cz;
+        cell_coords(cell, ncy, ncz, cx, cy, cz);
         int fx, fy, fz;
         const int sx = fold_cell(cx - delta[kx], ncx, bcx, fx);
         const int sy = fold_cell(cy - delta[n + ky], ncy, bcy, fy);
@@ -722,6 +722,7 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
     if (out) *out = nullptr;
     if (!grid || !vbox || !kernel || !dirs || !out) return FKS_ERR_INVALID_ARG;
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return FKS_ERR_INVALID_ARG;
+    if ((long)grid->nx * grid->ny * grid->nz >= (1L << 31)) return FKS_ERR_INVALID_ARG;   // 32-bit cell indices
     for (int a = 0; a < 3; ++a) {
         if (!(grid->x1[a] > grid->x0[a])) return FKS_ERR_INVALID_ARG;
         if (grid->bc[a] != FKS_BC_PERIODIC && grid->bc[a] != FKS_BC_SPECULAR) return FKS_ERR_INVALID_ARG;
@@ -1650,6 +1651,7 @@ extern "C" fks_status fks_transport_noalloc(const fks_grid* grid, const fks_vbox
                                             double dt, const void* f, void* f_out, void* stream) {
     if (!grid || !vbox || !s || !f || !f_out || f == f_out) return FKS_ERR_INVALID_ARG;
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return FKS_ERR_INVALID_ARG;
+    if ((long)grid->nx * grid->ny * grid->nz >= (1L << 31)) return FKS_ERR_INVALID_ARG;   // 32-bit cell indices
     for (int a = 0; a < 3; ++a) {
         if (!(grid->x1[a] > grid->x0[a])) return FKS_ERR_INVALID_ARG;
         if (grid->bc[a] != FKS_BC_PERIODIC && grid->bc[a] != FKS_BC_SPECULAR) return FKS_ERR_INVALID_ARG;

@@ -143,6 +143,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
+// cell index -> (cx, cy, cz) in 32-bit unsigned arithmetic (a context holds fewer
+// than 2^31 cells; 64-bit division is a long emulated sequence, run by every thread)
+__device__ __forceinline__ void cell_coords(long cell, int ncy, int ncz, int& cx, int& cy, int& cz) {
+    const unsigned c = (unsigned)cell, nyz = (unsigned)ncy * (unsigned)ncz;
+    const unsigned r = c % nyz;
+    cx = (int)(c / nyz);
+    cy = (int)(r / (unsigned)ncz);
+    cz = (int)(r % (unsigned)ncz);
+}
+
 // fold a source cell coordinate: periodic wrap or specular reflection
 __device__ __forceinline__ int fold_cell(int u, int len, int specular, int& flip) {
     if (!specular) {
@@ -388,9 +398,8 @@ collide_kernel(CollideArgs args) {
             inv_kn = args.inv_kn;
             dt_step = args.dt;
         }
-        const int cx = (int)(cell / ((long)ncy * ncz));
-        const int cy = (int)((cell / ncz) % ncy);
-        const int cz = (int)(cell % ncz);
+        int cx, cy, cz;
+        cell_coords(cell, ncy, ncz, cx, cy, cz);
         // gather offsets along z for this cell (relative to the (x, y) source row)
         if (tid < N) {
             if (!transport) {

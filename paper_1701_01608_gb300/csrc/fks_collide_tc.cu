@@ -320,7 +320,8 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
 
     for (long item = blockIdx.x; item < a.ncells; item += gridDim.x) {
         const long cell = a.cells ? (long)a.cells[item] : item;
-        const int cx = (int)(cell / ((long)ncy * ncz)), cy = (int)((cell / ncz) % ncy), cz = (int)(cell % ncz);
+        int cx, cy, cz;
+        cell_coords(cell, ncy, ncz, cx, cy, cz);
         if (tid < N) {
             if (!transport) {
                 zoff[tid] = cell * N3 + tid;

@@ -53,7 +53,8 @@ __device__ __forceinline__ T fstar(const Args& a, const int* dsm, long cell, int
     const T* f = static_cast<const T*>(a.f);
     if (!a.delta) return f[cell * N3 + ((long)x * N + y) * N + z];
     const int ncy = a.nc[1], ncz = a.nc[2];
-    const int cx = (int)(cell / ((long)ncy * ncz)), cy = (int)((cell / ncz) % ncy), cz = (int)(cell % ncz);
+    int cx, cy, cz;
+    cell_coords(cell, ncy, ncz, cx, cy, cz);
     int fx, fy, fz;
     const int sx = fold_cell(cx - dsm[x], a.nc[0], a.bc[0], fx);
     const int sy = fold_cell(cy - dsm[N + y], ncy, a.bc[1], fy);
