@@ -54,9 +54,9 @@ BF16_PEAK_TFLOPS, BF16_PEAK_KIND = _bf16_peak()
 # ncu capture on the 16x16x8 = 2048-cell shock tube, divided by 2048; traffic grows with
 # the cells of a launch).  Valid for the kernels as profiled; None once a kernel changes.
 DRAM_BYTES_PER_CELL = {
-    "collide_f32": (275852032 + 222365696) / 2048,   # collide_kernel<float, 32, 8>
+    "collide_f32": (273924096 + 221965312) / 2048,   # collide_kernel<float, 32, 8>
     "bgk_f32": (268547328 + 215617792) / 2048,       # bgk_cluster_kernel<float, 32, 4> (f* read once)
-    "collide_tc": (635715072 + 1520406000) / 2048,   # collide_tc_kernel<32> (scratch written back from L2)
+    "collide_tc": (634375680 + 1517931008) / 2048,   # collide_tc_kernel<32> (scratch written back from L2)
 }
 
 
@@ -207,16 +207,17 @@ def learned_path(torch, fks, dev, args, sample=1216, threshold=1e-3):
     Qs = torch.empty_like(f)
     Ql = torch.empty_like(f)
 
-    def timed(fn, reps=3):
+    def timed(fn, reps=5):
+        """median over reps of the per-call device time (one call includes a host sync)"""
         fn()
         torch.cuda.synchronize()
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record()
-        for _ in range(reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+        ev[0].record()
+        for i in range(reps):
             fn()
-        e.record()
+            ev[i + 1].record()
         torch.cuda.synchronize()
-        return s.elapsed_time(e) / reps
+        return float(np.median([ev[i].elapsed_time(ev[i + 1]) for i in range(reps)]))
 
     t_spec = timed(lambda: c32.collide(f, Qs))
     routed = [0]
@@ -415,23 +416,23 @@ def main():
         host_in = torch.empty(f0.shape, dtype=torch.float32, pin_memory=True)
         host_in.copy_(f0)
         host_out = torch.empty_like(host_in, pin_memory=True)
-        e2e_steps = max(1, min(args.steps, 3))
+        e2e_steps = max(1, min(args.steps, 5))
         # fks_step_host: the library copies the step's input in, steps and copies the result out,
         # pipelined over x-slab chunks (every step: H2D of the whole state, the step, D2H)
         ctx.step_host(host_in, host_out, dt)
         torch.cuda.synchronize()
         barrier(ws)
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record()
-        for _ in range(e2e_steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
+        evs[0].record()
+        for i in range(e2e_steps):
             ctx.step_host(host_in, host_out, dt)
-        s1.record()
+            evs[i + 1].record()
         torch.cuda.synchronize()
-        e2e_ms = max_over_ranks(s0.elapsed_time(s1), ws)
+        e2e_ms = max_over_ranks(evs[0].elapsed_time(evs[e2e_steps]), ws)
+        e2e_each = [round(evs[i].elapsed_time(evs[i + 1]), 2) for i in range(e2e_steps)]
         nbytes = f0.numel() * 4
         e2e = {"value": ws * PTS * e2e_steps / (e2e_ms / 1e3), "unit": "pts/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
+               "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "ms_each": e2e_each,
                "api": "fks_step_host (pinned host arrays; copies overlapped with the step over 8 x-slab chunks)"}
         del host_in, host_out
 

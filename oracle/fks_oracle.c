@@ -632,6 +632,11 @@ void or_bgk(int n, double L, double inv_kn, int project, long ncells, const doub
         double rho = U[0];
         double u[3] = {U[1] / rho, U[2] / rho, U[3] / rho};
         double T = (U[4] - 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2])) / (1.5 * rho);
+        if (!(rho > 0.0) || !(T > 0.0)) {
+            /* no Maxwellian exists (vacuum or a degenerate cell): the cell does not relax */
+            for (long k = 0; k < n3; ++k) Q[c * n3 + k] = 0.0;
+            continue;
+        }
         double nu = rho * inv_kn;
         double pre = rho * pow(2.0 * OR_PI * T, -1.5);
         for (int i = 0; i < n; ++i)

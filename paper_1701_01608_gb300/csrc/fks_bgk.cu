@@ -151,12 +151,16 @@ __global__ void __launch_bounds__(BS, 1024 / BS) bgk_kernel(BgkArgs a) {
             block_sum5(s);
         }
         if (tid < N) {
-            // cell moments and the Maxwellian's one-axis factors (in T)
+            // cell moments and the Maxwellian's one-axis factors (in T); no Maxwellian exists
+            // for rho <= 0 or T <= 0 (vacuum, degenerate cells): then M = 0 and nu = 0, Q = 0
             const double dv3 = dv * dv * dv;
             const double rho = cell5[0] * dv3;
-            const double ux = cell5[1] * dv3 / rho, uy = cell5[2] * dv3 / rho, uz = cell5[3] * dv3 / rho;
-            const double Tt = (cell5[4] * dv3 - 0.5 * rho * (ux * ux + uy * uy + uz * uz)) / (1.5 * rho);
-            const T A = (T)(rho / (2.0 * 3.14159265358979323846 * Tt * sqrt(2.0 * 3.14159265358979323846 * Tt)));
+            double ux = cell5[1] * dv3 / rho, uy = cell5[2] * dv3 / rho, uz = cell5[3] * dv3 / rho;
+            double Tt = (cell5[4] * dv3 - 0.5 * rho * (ux * ux + uy * uy + uz * uz)) / (1.5 * rho);
+            const bool ok = rho > 0.0 && Tt > 0.0;
+            if (!ok) ux = uy = uz = 0.0, Tt = 1.0;
+            const T A = ok ? (T)(rho / (2.0 * 3.14159265358979323846 * Tt * sqrt(2.0 * 3.14159265358979323846 * Tt)))
+                           : T(0);
             const T i2T = (T)(0.5 / Tt);
             const T dx = vgT[tid] - (T)ux, dy = vgT[tid] - (T)uy, dz = vgT[tid] - (T)uz;
             gx[tid] = A * exp(-dx * dx * i2T);
@@ -187,7 +191,8 @@ __global__ void __launch_bounds__(BS, 1024 / BS) bgk_kernel(BgkArgs a) {
                     Z[k] = (double)acc[6 + k];
                 }
                 const double dv3 = dv * dv * dv;
-                const double nu = cell5[0] * dv3 * a.inv_kn;
+                const bool live = X[0] > 0.0;   // A > 0: the cell has a Maxwellian
+                const double nu = live ? cell5[0] * dv3 * a.inv_kn : 0.0;
                 const double sM[5] = {X[0] * Y[0] * Z[0], X[1] * Y[0] * Z[0], X[0] * Y[1] * Z[0], X[0] * Y[0] * Z[1],
                                       0.5 * (X[2] * Y[0] * Z[0] + X[0] * Y[2] * Z[0] + X[0] * Y[0] * Z[2])};
                 if (tid < 5) {
@@ -415,10 +420,13 @@ __global__ void __launch_bounds__(256, 3) bgk_cluster_kernel(BgkArgs a) {
             const double rho = m[0] * dv3, irho = 1.0 / rho;
             const double ux = m[1] * dv3 * irho, uy = m[2] * dv3 * irho, uz = m[3] * dv3 * irho;
             const double Tt = (m[4] * dv3 * irho - 0.5 * (ux * ux + uy * uy + uz * uz)) * (2.0 / 3.0);
-            const float tf = (float)Tt, i2T = 0.5f / tf;
-            const float A = (float)rho * rsqrtf(2.0f * 3.14159265358979f * tf) / (2.0f * 3.14159265358979f * tf);
+            // no Maxwellian for rho <= 0 or T <= 0 (vacuum, degenerate cells): M = 0, nu = 0, Q = 0
+            const bool ok = rho > 0.0 && Tt > 0.0;
+            const float tf = ok ? (float)Tt : 1.0f, i2T = 0.5f / tf;
+            const float A = ok ? (float)rho * rsqrtf(2.0f * 3.14159265358979f * tf) / (2.0f * 3.14159265358979f * tf)
+                               : 0.0f;
             const T w = vgT[lane];
-            const T dx = w - (float)ux, dy = w - (float)uy, dz = w - (float)uz;
+            const T dx = w - (ok ? (float)ux : 0.0f), dy = w - (ok ? (float)uy : 0.0f), dz = w - (ok ? (float)uz : 0.0f);
             const T g0 = A * exp(-dx * dx * i2T), g1 = exp(-dy * dy * i2T), g2 = exp(-dz * dz * i2T);
             gx[lane] = g0;
             gy[lane] = g1;
@@ -432,7 +440,7 @@ __global__ void __launch_bounds__(256, 3) bgk_cluster_kernel(BgkArgs a) {
                 const double X[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
                 const double Y[3] = {(double)acc[3], (double)acc[4], (double)acc[5]};
                 const double Z[3] = {(double)acc[6], (double)acc[7], (double)acc[8]};
-                const double nu = rho * a.inv_kn;
+                const double nu = ok ? rho * a.inv_kn : 0.0;
                 const double sM[5] = {X[0] * Y[0] * Z[0], X[1] * Y[0] * Z[0], X[0] * Y[1] * Z[0], X[0] * Y[0] * Z[1],
                                       0.5 * (X[2] * Y[0] * Z[0] + X[0] * Y[2] * Z[0] + X[0] * Y[0] * Z[2])};
                 if (lane < 5) {

@@ -86,3 +86,26 @@ def test_bgk_full_size_fp32_sampled(fks, oracle):
     for i in range(len(sample)):
         err = np.linalg.norm(got[i] - (fsh[i] + dt * Qo[i]))
         assert err < 1e-5 * np.linalg.norm(dt * Qo[i]) + 2e-7 * np.linalg.norm(fsh[i])
+
+
+@pytest.mark.parametrize("n,prec", [(32, 1), (16, 0), (32, 0)])
+def test_bgk_vacuum_cell_does_not_relax(fks, oracle, n, prec):
+    """A vacuum cell (f = 0) has no Maxwellian: Q = 0 there, the other cells as usual."""
+    L = 8.0
+    c = ctx(fks, (3, 1, 1), n, L, prec)
+    f = I.two_stream((3, 1, 1), n, L, seed=7, noise=0.05)
+    f[1] = 0.0
+    fd = torch.from_numpy(f).to("cuda", c.dtype).contiguous()
+    Q = torch.empty_like(fd)
+    c.collide(fd, Q)
+    assert c.check() & 1 == 0
+    Qg = Q.double().cpu().numpy()
+    assert np.all(Qg[1] == 0.0)
+    Qo = oracle.bgk(fd.double().cpu().numpy(), n, L, kn=0.2)
+    assert np.all(Qo[1] == 0.0)
+    for i in (0, 2):
+        if prec == 0:
+            assert rel(Qg[i], Qo[i]) < 1e-12
+        else:
+            fin = fd.double().cpu().numpy()[i]
+            assert fp32_within(Qg[i], Qo[i], fin * fin.sum() * (2 * L / n) ** 3 / 0.2)

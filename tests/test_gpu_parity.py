@@ -320,3 +320,14 @@ def test_step_host_equals_device_step(fks, prec, kernel, n, bc, ncell, dt_scale,
         fd, od = od, fd
         h_in.copy_(h_out)
     assert a.check() & 1 == 0 and b.check() & 1 == 0
+
+
+@pytest.mark.parametrize("n,prec", [(8, 0), (32, 1), (16, 2)])
+def test_zero_distribution_collides_to_zero(fks, n, prec):
+    """Q is quadratic: f = 0 gives Q = 0 exactly (transforms, products, projection)."""
+    ctx = make_ctx(fks, (2, 1, 1), n, 10.0, prec=prec)
+    f = torch.zeros((2, n, n, n), dtype=ctx.dtype, device="cuda")
+    Q = torch.full_like(f, 7.0)
+    ctx.collide(f, Q)
+    assert ctx.check() == 0
+    assert bool((Q == 0).all())

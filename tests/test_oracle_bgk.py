@@ -35,3 +35,18 @@ def test_bgk_conserves_after_projection(oracle):
     for c in range(3):
         m = phi @ Q[c].ravel()
         assert np.all(np.abs(m) <= 1e-12 * (np.abs(phi) @ np.abs(Q[c].ravel())))
+
+
+def test_bgk_vacuum_and_degenerate_cells_do_not_relax(oracle):
+    """BGK's Maxwellian needs rho > 0 and T > 0: a vacuum cell (f = 0) and a cell
+    whose mass sits on one grid velocity (T = 0) have Q = 0; their neighbours in
+    the same call are unaffected."""
+    n, L = 8, 6.0
+    f = I.two_stream((3, 1, 1), n, L, seed=4, noise=0.05)
+    f[1] = 0.0
+    f[2] = 0.0
+    f[2][3, 4, 5] = 2.0
+    Q = oracle.bgk(f, n, L, kn=0.5)
+    assert np.all(Q[1] == 0.0) and np.all(Q[2] == 0.0)
+    Q0 = oracle.bgk(f[:1], n, L, kn=0.5)
+    assert np.array_equal(Q[0], Q0[0])
