@@ -26,6 +26,7 @@ GRID = (NX, NX, NX)
 NCELLS = NX ** 3
 PTS = NCELLS * NV ** 3
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA lanes x FMA x max SM clock (1.26 TFLOP/s)
 
 
 def _hbm_peak():
@@ -431,8 +432,20 @@ def main():
         e2e_ms = max_over_ranks(evs[0].elapsed_time(evs[e2e_steps]), ws)
         e2e_each = [round(evs[i].elapsed_time(evs[i + 1]), 2) for i in range(e2e_steps)]
         nbytes = f0.numel() * 4
+        # this box's plain copy rates (one full-state copy each way), to read the e2e line against
+        dtmp = torch.empty_like(f0)
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        c0.record()
+        dtmp.copy_(host_in, non_blocking=True)
+        c1.record()
+        host_out.copy_(dtmp, non_blocking=True)
+        c2.record()
+        torch.cuda.synchronize()
+        copy_gbs = {"h2d": nbytes / (c0.elapsed_time(c1) / 1e3) / 1e9,
+                    "d2h": nbytes / (c1.elapsed_time(c2) / 1e3) / 1e9}
+        del dtmp
         e2e = {"value": ws * PTS * e2e_steps / (e2e_ms / 1e3), "unit": "pts/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "ms_each": e2e_each,
+               "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "ms_each": e2e_each, "copy_gbs": copy_gbs,
                "api": "fks_step_host (pinned host arrays; copies overlapped with the step over 8 x-slab chunks)"}
         del host_in, host_out
 
@@ -586,7 +599,11 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         tsr = e0.elapsed_time(e1)
+        fls = 2 * flops_per_cell() * NCELLS / (tsr / ks / 1e3) / 1e12
         strang = {"value": PTS * ks / (tsr / 1e3), "unit": "pts/s", "ms_per_step": tsr / ks, "steps": ks,
+                  "roofline": {"bound": "alu", "achieved": fls, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": fls / FP32_PEAK_TFLOPS, "traffic": None,
+                               "peak_note": "two operator evaluations per step; derived FP32 peak"},
                   "gpu_launches": cs.launches - l0, "health_bits": cs.check(),
                   "note": "fks_step_strang: T(dt/2), Heun collision (two projected operator evaluations), "
                           "T(dt/2); second order in dt; FP32, same workload and dt"}
@@ -603,7 +620,12 @@ def main():
         ctx64 = fks.Context(cfg64)
         f64 = build_state(torch, torch.float64, dev)
         t64, per64, _, _, _ = time_steps(torch, ctx64, f64, 1, 1, dt, ws)
+        fl64 = flops_per_cell() * NCELLS / (t64 / 1e3) / 1e12
         fp64 = {"value": PTS / (t64 / 1e3), "unit": "pts/s", "ms_per_step": t64,
+                "roofline": {"bound": "alu", "achieved": fl64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": fl64 / FP64_PEAK_TFLOPS, "traffic": None,
+                             "peak_note": "derived FP64 CUDA-core peak: 152 SMs x 2 FP64 FMA lanes x 2 flop x "
+                                          "2.07 GHz (GB300's reduced FP64 rate)"},
                 "note": "same workload and step through the FP64 kernels (1 timed step after 1 warm-up)"}
         del f64, ctx64
 
