@@ -143,6 +143,33 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
+// bulk prefetch of a global range into L2 (16-byte aligned address, size a multiple of 16)
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// double-float helpers (hi, lo) for compensated FP32 sums: add a float, add two pairs,
+// multiply two pairs (error-free transformations with FMA; the lo parts are not renormalised
+// beyond what the sums need)
+__device__ __forceinline__ float2 df_add1(float2 a, float b) {
+    const float t = __fadd_rn(a.x, b);
+    const float bb = __fsub_rn(t, a.x);
+    const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, bb)), __fsub_rn(b, bb));
+    return make_float2(t, __fadd_rn(a.y, e));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float2 s = df_add1(a, b.x);
+    return make_float2(s.x, __fadd_rn(s.y, b.y));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    const float e = fmaf(a.x, b.x, -p);
+    return make_float2(p, fmaf(a.x, b.y, fmaf(a.y, b.x, e)));
+}
+__device__ __forceinline__ float2 df_shfl_xor(float2 v, int off) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off));
+}
+
 // cell index -> (cx, cy, cz) in 32-bit unsigned arithmetic (a context holds fewer
 // than 2^31 cells; 64-bit division is a long emulated sequence, run by every thread)
 __device__ __forceinline__ void cell_coords(long cell, int ncy, int ncz, int& cx, int& cy, int& cz) {
@@ -218,15 +245,16 @@ struct CollideCfg {
     static constexpr unsigned TAB_BYTES = (unsigned)(sizeof(T) * TAB_ELEMS);
     static constexpr long G_ELEMS = G_REG ? 0 : (long)NTASK * N;    // FP64 gain [N z][NTASK]
     static constexpr size_t SMEM_BASE = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS + S_ELEMS) + sizeof(T) * G_ELEMS +
-                                        sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N) + sizeof(T) * N +
-                                        sizeof(long) * N + 2 * sizeof(uint64_t) + 3 * N + 4 * NT + 64;
+                                        sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N) + sizeof(float) * (4 * N + 8) +
+                                        sizeof(T) * N + sizeof(long) * N + 2 * sizeof(uint64_t) + 3 * N + 4 * NT + 64;
     // the table slab is staged in shared memory (bulk-copy prefetch) when it fits
     static constexpr bool TAB_SMEM = SMEM_BASE + sizeof(T) * TAB_ELEMS <= 227u * 1024u;
     static constexpr long TB_ELEMS = TAB_SMEM ? TAB_ELEMS : 0;
     static constexpr size_t SMEM_BYTES = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS + S_ELEMS) +
                                          sizeof(T) * (TB_ELEMS + G_ELEMS) +
-                                         sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N) + sizeof(T) * N +
-                                         sizeof(long) * N + 2 * sizeof(uint64_t) + 3 * N + 4 * NT + 64;
+                                         sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N) +
+                                         sizeof(float) * (4 * N + 8) + sizeof(T) * N + sizeof(long) * N +
+                                         2 * sizeof(uint64_t) + 3 * N + 4 * NT + 64;
     static_assert(N % C == 0, "cluster size must divide N");
     static_assert(TAB_BYTES % 16 == 0 && BLK_BYTES % 16 == 0, "bulk copies move whole 16-byte units");
     static_assert(STG_ELEMS <= W_ELEMS, "forward staging fits in W");
@@ -293,7 +321,9 @@ collide_kernel(CollideArgs args) {
     double* mu = redw + (NT / 32) * 5;                                 // [8] correction coefficients
     double* vzt = mu + 8;                                              // [N] v_z
     double* vz2t = vzt + N;                                            // [N] v_z^2 / 2
-    T* czt = reinterpret_cast<T*>(vz2t + N);                          // [N] projection correction along z
+    float* vzf = reinterpret_cast<float*>(vz2t + N);                  // [4][N] v_z, v_z^2/2 as FP32 (hi, lo)
+    float* muf = vzf + 4 * N;                                          // [8] mu in FP32
+    T* czt = reinterpret_cast<T*>(muf + 8);                           // [N] projection correction along z
     long* zoff = reinterpret_cast<long*>(czt + N + (N & 1));          // [N] gather offsets along z
     uint64_t* tbar = reinterpret_cast<uint64_t*>(zoff + N);           // table-slab mbarrier
     uint64_t* xbar = tbar + 1;                                         // exchange mbarrier
@@ -323,10 +353,17 @@ collide_kernel(CollideArgs args) {
     double dv = 2.0 * args.L / N;
     // velocity of grid index i: (i + 1/2 - N/2) dv
     auto vel = [&dv](int i) { return ((double)i + 0.5 - 0.5 * N) * dv; };
-    for (int i = tid; i < N; i += NT) {
+    // v_z and v_z^2/2 as FP32 pairs hi + lo (the compensated FP32 moment sums)
+    auto set_vel = [&](int i) {
         vzt[i] = vel(i);
         vz2t[i] = 0.5 * vel(i) * vel(i);
-    }
+        const float h1 = (float)vzt[i], h2 = (float)vz2t[i];
+        vzf[i] = h1;
+        vzf[N + i] = (float)(vzt[i] - (double)h1);
+        vzf[2 * N + i] = h2;
+        vzf[3 * N + i] = (float)(vz2t[i] - (double)h2);
+    };
+    for (int i = tid; i < N; i += NT) set_vel(i);
     if (tid == 0) {
         mbar_init(tbar, 1);
         mbar_init(xbar, 1);
@@ -372,6 +409,13 @@ collide_kernel(CollideArgs args) {
     for (long item = args.cell0 + cluster_id; item < args.ncells; item += nclusters) {
         // batch: item = one homogeneous problem (cell 0 of its own arrays)
         const long cell = BATCH ? 0 : item;
+        if constexpr (!BATCH) {
+            // the x-planes of this cluster's next cell towards L2 while this one is processed
+            // (its forward pass then starts on L2 hits; with transport most sources are the cell itself)
+            if (tid == 0 && item + nclusters < args.ncells)
+                prefetch_l2(static_cast<const T*>(args.f) + (item + nclusters) * N3 + (long)rank * NS * N * N,
+                            (unsigned)(sizeof(T) * NS * N * N));
+        }
         const T* __restrict__ fin;
         T* __restrict__ fout;
         const T* __restrict__ tab = item_tables(item);
@@ -387,10 +431,7 @@ collide_kernel(CollideArgs args) {
             // velocity tables of this problem's box (read after the barrier below;
             // the previous item's last reads precede its final cluster barrier)
             dv = 2.0 * bi.L / N;
-            if (tid < N) {
-                vzt[tid] = vel(tid);
-                vz2t[tid] = 0.5 * vel(tid) * vel(tid);
-            }
+            if (tid < N) set_vel(tid);
         } else {
             fin = static_cast<const T*>(args.f);
             fout = static_cast<T*>(args.out);
@@ -577,8 +618,7 @@ collide_kernel(CollideArgs args) {
             } else {
                 // loss: r = G - f* l by one fused multiply-add (the product is exact,
                 // one rounding of the difference: relative to r itself), Q = r / Kn;
-                // the five moments of Q from three FP64 sums per column
-                double s5[5] = {0, 0, 0, 0, 0};
+                // the five moments of Q from three sums per column
                 const double vx = vel(zx), vy = vel(zl_y);
                 const double v2xy = 0.5 * (vx * vx + vy * vy);
                 T col[N];
@@ -592,62 +632,119 @@ collide_kernel(CollideArgs args) {
                     else g = Gcol[(long)z * NTASK];
                     return fma(-col[z], av[z], g);
                 };
-                if (has_col) {
-                    double s0 = 0.0, sz = 0.0, szz = 0.0;
-#pragma unroll
-                    for (int z = 0; z < N; ++z) {
-                        const double r = (double)rval(z);
-                        s0 += r;
-                        sz = fma(r, vzt[z], sz);
-                        szz = fma(r, vz2t[z], szz);
-                    }
-                    const double k = inv_kn;
-                    s5[0] = s0 * k;
-                    s5[1] = vx * s0 * k;
-                    s5[2] = vy * s0 * k;
-                    s5[3] = sz * k;
-                    s5[4] = (v2xy * s0 + szz) * k;
-                }
-                // block reduction of the five moments (fixed order: deterministic)
-#pragma unroll
-                for (int i = 0; i < 5; ++i) {
-                    double v = s5[i];
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                    s5[i] = v;
-                }
                 const int warp = tid >> 5, lane = tid & 31;
-                if (lane == 0) {
+                if constexpr (sizeof(T) == 4) {
+                    // FP32: compensated sums (hi, lo) with exact products (FMA), carried as pairs
+                    // through the warp and block reductions, FP64 from the block totals on (the
+                    // FP64 pipe of this part is slow: per-element FP64 sums dominated the epilogue)
+                    float2 m5[5];
 #pragma unroll
-                    for (int i = 0; i < 5; ++i) redw[warp * 5 + i] = s5[i];
-                }
-                __syncthreads();
-                if (tid == 0) {
+                    for (int i = 0; i < 5; ++i) m5[i] = make_float2(0.f, 0.f);
+                    if (has_col) {
+                        float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0;
+#pragma unroll
+                        for (int z = 0; z < N; ++z) {
+                            const float r = rval(z);
+                            a0 = df_add1(a0, r);
+                            const float p = r * vzf[z];
+                            const float pe = fmaf(r, vzf[N + z], fmaf(r, vzf[z], -p));
+                            a1 = df_add1(a1, p);
+                            a1.y += pe;
+                            const float q = r * vzf[2 * N + z];
+                            const float qe = fmaf(r, vzf[3 * N + z], fmaf(r, vzf[2 * N + z], -q));
+                            a2 = df_add1(a2, q);
+                            a2.y += qe;
+                        }
+                        const float2 v2 = df_add(make_float2(vzf[2 * N + zx], vzf[3 * N + zx]),
+                                                 make_float2(vzf[2 * N + zl_y], vzf[3 * N + zl_y]));
+                        m5[0] = a0;
+                        m5[1] = df_mul(a0, make_float2(vzf[zx], vzf[N + zx]));
+                        m5[2] = df_mul(a0, make_float2(vzf[zl_y], vzf[N + zl_y]));
+                        m5[3] = a1;
+                        m5[4] = df_add(df_mul(a0, v2), a2);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 5; ++i)
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) m5[i] = df_add(m5[i], df_shfl_xor(m5[i], off));
+                    float2* redw2 = reinterpret_cast<float2*>(redw);
+                    if (lane == 0) {
+#pragma unroll
+                        for (int i = 0; i < 5; ++i) redw2[warp * 5 + i] = m5[i];
+                    }
+                    __syncthreads();
+                    if (tid < 5) {
+                        float2 acc = make_float2(0.f, 0.f);
+                        for (int w = 0; w < NT / 32; ++w) acc = df_add(acc, redw2[w * 5 + tid]);
+                        red[tid] = ((double)acc.x + (double)acc.y) * inv_kn;
+                    }
+                } else {
+                    double s5[5] = {0, 0, 0, 0, 0};
+                    if (has_col) {
+                        double s0 = 0.0, sz = 0.0, szz = 0.0;
+#pragma unroll
+                        for (int z = 0; z < N; ++z) {
+                            const double r = (double)rval(z);
+                            s0 += r;
+                            sz = fma(r, vzt[z], sz);
+                            szz = fma(r, vz2t[z], szz);
+                        }
+                        const double k = inv_kn;
+                        s5[0] = s0 * k;
+                        s5[1] = vx * s0 * k;
+                        s5[2] = vy * s0 * k;
+                        s5[3] = sz * k;
+                        s5[4] = (v2xy * s0 + szz) * k;
+                    }
+                    // block reduction of the five moments (fixed order: deterministic)
+#pragma unroll
                     for (int i = 0; i < 5; ++i) {
+                        double v = s5[i];
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                        s5[i] = v;
+                    }
+                    if (lane == 0) {
+#pragma unroll
+                        for (int i = 0; i < 5; ++i) redw[warp * 5 + i] = s5[i];
+                    }
+                    __syncthreads();
+                    if (tid < 5) {
                         double acc = 0.0;
-                        for (int w = 0; w < NT / 32; ++w) acc += redw[w * 5 + i];
-                        red[i] = acc;
+                        for (int w = 0; w < NT / 32; ++w) acc += redw[w * 5 + tid];
+                        red[tid] = acc;
                     }
                 }
                 cluster_sync_all();
-                if (tid == 0) {
-                    double tot[5] = {0, 0, 0, 0, 0};
-                    for (int r = 0; r < C; ++r) {
-                        const double* rr = cluster.map_shared_rank(red, r);
-                        for (int i = 0; i < 5; ++i) tot[i] += rr[i];
-                    }
-                    for (int i = 0; i < 5; ++i) {
+                if (tid < 32) {
+                    // warp 0: cluster totals (lane i: moment i over the ranks, in rank order),
+                    // mu = P tot, the z part of the correction
+                    double tot = 0.0;
+                    if (lane < 5)
+                        for (int r = 0; r < C; ++r) tot += cluster.map_shared_rank(red, r)[lane];
+                    double t5[5];
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) t5[i] = __shfl_sync(0xffffffffu, tot, i);
+                    if (lane < 5) {
                         double acc = 0.0;
-                        for (int j = 0; j < 5; ++j) acc += Pm[i * 5 + j] * tot[j];
-                        mu[i] = args.mode == 2 ? 0.0 : acc;   // mode 2: the caller projects
+                        for (int j = 0; j < 5; ++j) acc += Pm[lane * 5 + j] * t5[j];
+                        acc = args.mode == 2 ? 0.0 : acc;   // mode 2: the caller projects
+                        mu[lane] = acc;
+                        muf[lane] = (float)acc;
                     }
+                    __syncwarp();
                     // correction phi(v).mu = mu0 + mu1 vx + mu2 vy + mu4 (vx^2+vy^2)/2 + [mu3 vz + mu4 vz^2/2]
-                    for (int z = 0; z < N; ++z) czt[z] = (T)(mu[3] * vzt[z] + mu[4] * vz2t[z]);
+                    for (int z = lane; z < N; z += 32) czt[z] = (T)(mu[3] * vzt[z] + mu[4] * vz2t[z]);
                 }
                 cluster_sync_all();   // every CTA has read the partials; mu and czt are visible
                 if (has_col) {
                     // corrected Q = r / Kn - phi(v).mu, then out = Q or f* + dt Q
-                    const T cxy = (T)(mu[0] + mu[1] * vx + mu[2] * vy + mu[4] * v2xy);
+                    T cxy;
+                    if constexpr (sizeof(T) == 4)
+                        cxy = muf[0] + muf[1] * vzf[zx] + muf[2] * vzf[zl_y] +
+                              muf[4] * (vzf[2 * N + zx] + vzf[2 * N + zl_y]);
+                    else
+                        cxy = (T)(mu[0] + mu[1] * vx + mu[2] * vy + mu[4] * v2xy);
                     const T kn = (T)inv_kn, dt = (T)dt_step;
                     const bool heun = !BATCH && args.mode == 3;
                     const bool stepm = args.mode == 1 || heun;
