@@ -408,7 +408,8 @@ def main():
                   "moments_ms": ev_ms(lambda: ctx.moments(f0, U)),
                   "collide_ms": ev_ms(lambda: ctx.collide(f0, tmp)),
                   "step_ms": step_ms,
-                  "note": "FP32; transport = offsets + gather kernel (2 x 4 B per point), moments = FP64 sums"}
+                  "note": "FP32; transport = offsets + gather kernel (2 x 4 B per point), moments = compensated "
+                          "FP32 sums (FP64-equivalent), 4 B per point"}
         del tmp, U
 
     e2e = None

@@ -298,9 +298,10 @@ __global__ void __launch_bounds__(256) transport_kernel(int ncx, int ncy, int nc
 }
 
 // ------------------------------------------------------------------ moments
-// U = dv^3 sum phi(v) f, phi = (1, v, |v|^2/2), in FP64 with three FP64
-// operations per element: along a 16-byte run the sums of f, f v_z and
-// f v_z^2/2, then per row the factors v_x, v_y.
+// U = dv^3 sum phi(v) f, phi = (1, v, |v|^2/2): along a 16-byte run the sums of
+// f, f v_z and f v_z^2/2, then per row the factors v_x, v_y.  FP64 input: FP64
+// sums.  FP32 input: compensated FP32 sums (FP64-equivalent accuracy; GB300's
+// FP64 pipe made the FP64 version FP64-bound at 3 operations per element).
 template <typename T, int N>
 __global__ void __launch_bounds__(256) moments_kernel(double L, long ncells, const T* __restrict__ f,
                                                       double* __restrict__ U) {
@@ -321,6 +322,79 @@ __global__ void __launch_bounds__(256) moments_kernel(double L, long ncells, con
     for (int k = 0; k < V; ++k) {
         vz[k] = vg[(z0 + k) % N];
         vz2[k] = 0.5 * vz[k] * vz[k];
+    }
+    if constexpr (sizeof(T) == 4) {
+        // FP32 input: compensated FP32 sums (hi, lo) with exact products by FMA, as accurate
+        // as FP64 accumulation, off GB300's slow FP64 pipe (FP64 from the block totals on)
+        __shared__ float vgf[2][N], vg2f[2][N];   // v and v^2/2 as FP32 pairs hi + lo
+        if (tid < N) {
+            const double w = vg[tid], w2 = 0.5 * w * w;
+            vgf[0][tid] = (float)w;
+            vgf[1][tid] = (float)(w - (double)(float)w);
+            vg2f[0][tid] = (float)w2;
+            vg2f[1][tid] = (float)(w2 - (double)(float)w2);
+        }
+        __syncthreads();
+        float vzh[V], vzl[V], vz2h[V], vz2l[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int z = (z0 + k) % N;
+            vzh[k] = vgf[0][z];
+            vzl[k] = vgf[1][z];
+            vz2h[k] = vg2f[0][z];
+            vz2l[k] = vg2f[1][z];
+        }
+        __shared__ float2 redf[BS / 32][5];
+        for (long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
+            float2 sm[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) sm[i] = make_float2(0.f, 0.f);
+            if (lane_ok) {
+                const T* fc = f + cell * N3 + z0;
+#pragma unroll 4
+                for (int j = 0; j < ROWS; ++j) {
+                    const int r = r0 + RPI * j;
+                    if (r >= N * N) break;
+                    const VT w = __ldcs(reinterpret_cast<const VT*>(fc + (long)r * N));
+                    const float* pw = reinterpret_cast<const float*>(&w);
+                    float2 t0 = make_float2(0.f, 0.f), tz = t0, tzz = t0;
+#pragma unroll
+                    for (int k = 0; k < V; ++k) {
+                        const float m = pw[k];
+                        t0 = df_add1(t0, m);
+                        const float p = m * vzh[k];
+                        tz = df_add1(tz, p);
+                        tz.y += fmaf(m, vzl[k], fmaf(m, vzh[k], -p));
+                        const float q = m * vz2h[k];
+                        tzz = df_add1(tzz, q);
+                        tzz.y += fmaf(m, vz2l[k], fmaf(m, vz2h[k], -q));
+                    }
+                    const int ix = r / N, iy = r % N;
+                    const float2 vx = make_float2(vgf[0][ix], vgf[1][ix]), vy = make_float2(vgf[0][iy], vgf[1][iy]);
+                    const float2 v2 = df_add(make_float2(vg2f[0][ix], vg2f[1][ix]), make_float2(vg2f[0][iy], vg2f[1][iy]));
+                    sm[0] = df_add(sm[0], t0);
+                    sm[1] = df_add(sm[1], df_mul(t0, vx));
+                    sm[2] = df_add(sm[2], df_mul(t0, vy));
+                    sm[3] = df_add(sm[3], tz);
+                    sm[4] = df_add(sm[4], df_add(df_mul(t0, v2), tzz));
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) sm[i] = df_add(sm[i], df_shfl_xor(sm[i], off));
+            const int warp = tid >> 5;
+            if ((tid & 31) == 0)
+                for (int i = 0; i < 5; ++i) redf[warp][i] = sm[i];
+            __syncthreads();
+            if (tid < 5) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int w2 = 0; w2 < BS / 32; ++w2) acc = df_add(acc, redf[w2][tid]);
+                U[cell * 5 + tid] = ((double)acc.x + (double)acc.y) * dv * dv * dv;
+            }
+            __syncthreads();
+        }
+        return;
     }
     for (long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
         double s[5] = {0, 0, 0, 0, 0};
