@@ -12,6 +12,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -344,6 +345,8 @@ def main():
     ap.add_argument("--no-varb", action="store_true")
     ap.add_argument("--no-vhs", action="store_true")
     ap.add_argument("--no-strang", action="store_true")
+    ap.add_argument("--clocks-log", default=None, help="keep the raw nvidia-smi clock samples of the timed "
+                                                        "region in this CSV file")
     ap.add_argument("--cpu-sample", type=int, default=int(os.environ.get("FKS_CPU_SAMPLE", "1024")))
     ap.add_argument("--grid", default=None, help="nx,ny,nz spatial cells (default 32,32,32); smaller grids "
                     "are for profiling runs, not bench lines")
@@ -375,8 +378,8 @@ def main():
     ctx = fks.Context(cfg)
     f0 = build_state(torch, torch.float32, dev)
 
-    clk = Clocks(torch.cuda.current_device(), os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/fks_clocks_{os.getpid()}.csv")
+    clk = Clocks(torch.cuda.current_device(),
+                 args.clocks_log or os.path.join(tempfile.gettempdir(), f"fks_clocks_{os.getpid()}_{rank}.csv"))
     total_ms, per, launches, bits, _ = time_steps(torch, ctx, f0, args.steps, args.warmup, dt, ws)
     clocks = clk.stop()
     total_ms = max_over_ranks(total_ms, ws)
@@ -433,7 +436,8 @@ def main():
         e2e_ms = max_over_ranks(evs[0].elapsed_time(evs[e2e_steps]), ws)
         e2e_each = [round(evs[i].elapsed_time(evs[i + 1]), 2) for i in range(e2e_steps)]
         nbytes = f0.numel() * 4
-        # this box's plain copy rates (one full-state copy each way), to read the e2e line against
+        # plain copy rates between the pinned host arrays and the device (one full-state copy each
+        # way), to read the e2e line against
         dtmp = torch.empty_like(f0)
         c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         c0.record()
