@@ -161,6 +161,19 @@ def barrier(ws: int):
         dist.barrier()
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip() + " (" + platform.machine() + ")"
+    except Exception:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(sample_cells: int = 16, fp32_input=None) -> dict:
     """The oracle as it stands, on `sample_cells` cells of the workload, on
     this host's cores (OpenMP over cells)."""
@@ -180,7 +193,7 @@ def cpu_baseline(sample_cells: int = 16, fp32_input=None) -> dict:
     _ = f + dt * Q
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": sample_cells * NV ** 3 / el, "unit": "pts/s", "cores": cores, "kind": "oracle",
+    return {"value": sample_cells * NV ** 3 / el, "unit": "pts/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
             "sample": f"{sample_cells} seeded cells of the 32^3x32^3 shock tube, collision + Euler "
                       f"(transport gather is a copy, excluded); tables {t_tab:.1f}s excluded",
             "seconds": el}
@@ -291,7 +304,7 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "hs_shocktube_32x32x32c_32v (sampled cells)", "cells_per_step": sample,
                       "n_v": NV ** 3, "M": M, "note": "CPU oracle (plain FP64 C, OpenMP over cells)"},
-           "cpu_baseline": {"value": val, "unit": "pts/s", "cores": cores, "kind": "oracle",
+           "cpu_baseline": {"value": val, "unit": "pts/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                             "sample": f"{sample} seeded cells per step"},
            "e2e": {"value": val, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -377,6 +390,9 @@ def main():
                      A1=A1, A2=A2, precision=fks.FKS_FP32)
     ctx = fks.Context(cfg)
     f0 = build_state(torch, torch.float32, dev)
+    # measured FMA throughput of the FP32 and FP64 pipes (a second denominator beside the derived one)
+    alu32 = fks.alu_peak(fks.FKS_FP32)
+    alu64 = fks.alu_peak(fks.FKS_FP64)
 
     clk = Clocks(torch.cuda.current_device(),
                  args.clocks_log or os.path.join(tempfile.gettempdir(), f"fks_clocks_{os.getpid()}_{rank}.csv"))
@@ -628,7 +644,8 @@ def main():
         fl64 = flops_per_cell() * NCELLS / (t64 / 1e3) / 1e12
         fp64 = {"value": PTS / (t64 / 1e3), "unit": "pts/s", "ms_per_step": t64,
                 "roofline": {"bound": "alu", "achieved": fl64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": fl64 / FP64_PEAK_TFLOPS, "traffic": None,
+                             "frac": fl64 / FP64_PEAK_TFLOPS, "traffic": None, "peak_measured": alu64,
+                             "frac_of_measured": fl64 / alu64 if alu64 else None,
                              "peak_note": "derived FP64 CUDA-core peak: 152 SMs x 2 FP64 FMA lanes x 2 flop x "
                                           "2.07 GHz (GB300's reduced FP64 rate)"},
                 "note": "same workload and step through the FP64 kernels (1 timed step after 1 warm-up)"}
@@ -649,7 +666,9 @@ def main():
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic("collide_f32"),
                      "traffic_note": "dram bytes of one ncu capture on 2048 cells, scaled by the cells of a launch",
                      "algorithmic_flops_per_launch": flops_launch,
-                     "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived, not measured)"},
+                     "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
+                     "peak_measured": alu32, "frac_of_measured": achieved / alu32 if alu32 else None,
+                     "peak_measured_note": "FMA-chain kernel (fks_alu_peak), this run"},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "e2e": e2e,

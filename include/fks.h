@@ -321,6 +321,13 @@ fks_status fks_set_dealias(fks_ctx *ctx, int on);
  * FKS_ERR_OOM on a CUDA failure.  The device stays usable. */
 fks_status fks_selftest_wait(long polls, void *stream);
 
+/* Measurement helper: the device's FMA throughput in TFLOP/s (2 flop per FMA)
+ * for precision FKS_FP32 (the FP32 pipe) or FKS_FP64 (the FP64 pipe), from a
+ * kernel of independent FMA chains (8 per thread, 8 CTAs of 256 threads per
+ * SM), timed with CUDA events after one warm-up launch.  Synchronises
+ * `stream`.  The roofline denominator of the CUDA-core collision kernels. */
+fks_status fks_alu_peak(int precision, double *tflops, void *stream);
+
 /* fks_transport_noalloc -- the transport of fks_transport for callers that
  * cannot allocate device memory.  It is an addition of this library; the
  * paper has no counterpart.

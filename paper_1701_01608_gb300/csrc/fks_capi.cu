@@ -512,6 +512,24 @@ static cudaError_t launch_moments_t(const fks_ctx* c, const void* f, double* U, 
     return cudaErrorInvalidValue;
 }
 
+// FMA-chain throughput: eight independent chains per thread keep the FMA (or
+// FP64) pipe full; the sum is stored only if it hits an impossible value, so
+// the chains stay live.
+template <typename T>
+__global__ void __launch_bounds__(256) fma_peak_kernel(T b, T c, int iters, T* sink) {
+    T a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (T)(threadIdx.x + k) * (T)1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+    }
+    T sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += a[k];
+    if (sum == (T)-12345.0) sink[0] = sum;
+}
+
 int default_cluster_size(bool fp64, int N) {
     // FP32 n = 32: C = 8 measured 176.9 ms against 178.4 ms for C = 4 (32^3 x 32^3 step)
     if (!fp64) return N == 32 ? 8 : (N == 24 ? 2 : 1);
@@ -1249,6 +1267,39 @@ fks_status fks_selftest_wait(long polls, void* stream) {
     cudaFree(d);
     if (e != cudaSuccess) return FKS_ERR_CUDA;
     return (h & 8) ? FKS_ERR_TIMEOUT : FKS_OK;
+}
+
+fks_status fks_alu_peak(int precision, double* tflops, void* stream) {
+    if (!tflops || (precision != FKS_FP64 && precision != FKS_FP32)) return FKS_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return FKS_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    void* sink = nullptr;
+    if (cudaMalloc(&sink, 16) != cudaSuccess) return FKS_ERR_OOM;
+    const bool fp64 = precision == FKS_FP64;
+    const int iters = fp64 ? 1024 : 32768;
+    const dim3 grid((unsigned)(sms * 8)), block(256);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first launch warms up
+        e = cudaEventRecord(e0, s);
+        if (fp64) fma_peak_kernel<double><<<grid, block, 0, s>>>(0.999999, 1e-7, iters, (double*)sink);
+        else fma_peak_kernel<float><<<grid, block, 0, s>>>(0.999999f, 1e-7f, iters, (float*)sink);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess || !(ms > 0.f)) return FKS_ERR_CUDA;
+    *tflops = 2.0 * 8.0 * iters * (double)grid.x * block.x / (ms * 1e-3) / 1e12;
+    return FKS_OK;
 }
 
 fks_status fks_get_offsets(fks_ctx* c, double* s) {

@@ -67,7 +67,7 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
            "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
            "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias", "fks_step_host", "fks_vhs_factor",
-           "fks_step_strang"]
+           "fks_step_strang", "fks_alu_peak"]
 
 
 def lib(build: bool = True):
@@ -139,6 +139,7 @@ def lib(build: bool = True):
     L.fks_surrogate_collide.argtypes = [P, P, P, P, D, D, D, ctypes.POINTER(ctypes.c_long), P]
     L.fks_surrogate_indicator.argtypes = [P, P, ctypes.c_long]
     L.fks_selftest_wait.argtypes = [ctypes.c_long, P]
+    L.fks_alu_peak.argtypes = [I, ctypes.POINTER(D), P]
     L.fks_set_dealias.argtypes = [P, I]
     L.fks_step_host.argtypes = [P, P, P, D, P]
     L.fks_destroy.argtypes = [P]
@@ -473,6 +474,15 @@ def surrogate_inputs(n: int, L: float, f, x, rho, dist, stream=None):
                                     _dptr(rho, torch.float64), _dptr(dist, torch.float32), _stream_ptr(stream))
     if st != 0:
         raise FKSError(st, "fks_surrogate_inputs")
+
+
+def alu_peak(precision: int, stream=None) -> float:
+    """Measured FMA throughput (TFLOP/s) of the FP32 or FP64 pipe."""
+    t = ctypes.c_double()
+    st = lib().fks_alu_peak(precision, ctypes.byref(t), _stream_ptr(stream))
+    if st != 0:
+        raise FKSError(st, "fks_alu_peak")
+    return t.value
 
 
 def selftest_wait(polls: int = 4096, stream=None) -> int:

@@ -331,3 +331,13 @@ def test_zero_distribution_collides_to_zero(fks, n, prec):
     ctx.collide(f, Q)
     assert ctx.check() == 0
     assert bool((Q == 0).all())
+
+
+def test_alu_peak_measurement_is_plausible(fks):
+    """fks_alu_peak: the FMA-chain throughput of the FP32 and FP64 pipes (the
+    roofline's measured denominators) lies near GB300's unit counts x clock
+    (80.5 and 1.26 TFLOP/s at 2.07 GHz)."""
+    t32 = fks.alu_peak(fks.FKS_FP32)
+    t64 = fks.alu_peak(fks.FKS_FP64)
+    assert 40.0 < t32 < 90.0, t32
+    assert 0.5 < t64 < 2.0, t64
