@@ -124,13 +124,21 @@ __global__ void __launch_bounds__(BS) trunc_kernel(const Args a) {
     T* Bp = Cp + N * M2 * M2;               // [N][N][M2]
     __shared__ int dsm[3 * N];
     __shared__ double vg[N];
+    __shared__ float vgf[N], vgl[N], vg2f[N], vg2l[N];   // v and v^2/2 as FP32 pairs hi + lo
     __shared__ double red[BS / 32][5];
     __shared__ double mu[5];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < N * M2; i += BS) Tm[i] = static_cast<const T*>(a.T)[i];
     for (int i = tid; i < 3 * N; i += BS) dsm[i] = a.delta ? (int)a.delta[i] : 0;
     const double dv = 2.0 * a.L / N;
-    if (tid < N) vg[tid] = ((double)tid + 0.5 - 0.5 * N) * dv;
+    if (tid < N) {
+        vg[tid] = ((double)tid + 0.5 - 0.5 * N) * dv;
+        const double h = 0.5 * vg[tid] * vg[tid];
+        vgf[tid] = (float)vg[tid];
+        vgl[tid] = (float)(vg[tid] - (double)vgf[tid]);
+        vg2f[tid] = (float)h;
+        vg2l[tid] = (float)(h - (double)vg2f[tid]);
+    }
     __syncthreads();
     for (long cell = a.c0 + blockIdx.x; cell < a.c0 + a.k; cell += gridDim.x) {
         const T* src = static_cast<const T*>(a.q2) + (cell - a.c0) * (long)M2 * M2 * M2;
@@ -156,24 +164,55 @@ __global__ void __launch_bounds__(BS) trunc_kernel(const Args a) {
         __syncthreads();
         T* Q = Cp;   // the x-pass result is no longer needed
         double s[5] = {0, 0, 0, 0, 0};
-        for (int e = tid; e < N * N * N; e += BS) {   // along z, and the moment sums (FP64)
-            const int xy = e / N, z = e % N;
-            T acc = 0;
-            for (int z2 = 0; z2 < M2; ++z2) acc += Tm[z * M2 + z2] * Bp[xy * M2 + z2];
-            Q[e] = acc;
-            const double q = (double)acc, vx = vg[xy / N], vy = vg[xy % N], vz = vg[z];
-            s[0] += q;
-            s[1] = fma(q, vx, s[1]);
-            s[2] = fma(q, vy, s[2]);
-            s[3] = fma(q, vz, s[3]);
-            s[4] = fma(q, 0.5 * (vx * vx + vy * vy + vz * vz), s[4]);
-        }
+        if constexpr (sizeof(T) == 4) {
+            // FP32: compensated FP32 moment sums (hi, lo pairs, exact products by FMA), FP64
+            // from the warp totals on (per-element FP64 work is slow on this part)
+            float2 sf[5];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            double v = s[i];
+            for (int i = 0; i < 5; ++i) sf[i] = make_float2(0.f, 0.f);
+            for (int e = tid; e < N * N * N; e += BS) {   // along z, and the moment sums
+                const int xy = e / N, z = e % N;
+                T acc = 0;
+                for (int z2 = 0; z2 < M2; ++z2) acc += Tm[z * M2 + z2] * Bp[xy * M2 + z2];
+                Q[e] = acc;
+                const int x = xy / N, y = xy % N;
+                const float q = acc;
+                sf[0] = df_add1(sf[0], q);
+                sf[1] = df_add(sf[1], df_mul(make_float2(q, 0.f), make_float2(vgf[x], vgl[x])));
+                sf[2] = df_add(sf[2], df_mul(make_float2(q, 0.f), make_float2(vgf[y], vgl[y])));
+                sf[3] = df_add(sf[3], df_mul(make_float2(q, 0.f), make_float2(vgf[z], vgl[z])));
+                const float2 w = df_add(df_add(make_float2(vg2f[x], vg2l[x]), make_float2(vg2f[y], vg2l[y])),
+                                        make_float2(vg2f[z], vg2l[z]));
+                sf[4] = df_add(sf[4], df_mul(make_float2(q, 0.f), w));
+            }
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (lane == 0) red[warp][i] = v;
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) sf[i] = df_add(sf[i], df_shfl_xor(sf[i], off));
+#pragma unroll
+            for (int i = 0; i < 5; ++i) s[i] = (double)sf[i].x + (double)sf[i].y;
+            if (lane == 0)
+                for (int i = 0; i < 5; ++i) red[warp][i] = s[i];
+        } else {
+            for (int e = tid; e < N * N * N; e += BS) {   // along z, and the moment sums (FP64)
+                const int xy = e / N, z = e % N;
+                T acc = 0;
+                for (int z2 = 0; z2 < M2; ++z2) acc += Tm[z * M2 + z2] * Bp[xy * M2 + z2];
+                Q[e] = acc;
+                const double q = (double)acc, vx = vg[xy / N], vy = vg[xy % N], vz = vg[z];
+                s[0] += q;
+                s[1] = fma(q, vx, s[1]);
+                s[2] = fma(q, vy, s[2]);
+                s[3] = fma(q, vz, s[3]);
+                s[4] = fma(q, 0.5 * (vx * vx + vy * vy + vz * vz), s[4]);
+            }
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                double v = s[i];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if (lane == 0) red[warp][i] = v;
+            }
         }
         __syncthreads();
         if (tid < 5) {
@@ -187,13 +226,23 @@ __global__ void __launch_bounds__(BS) trunc_kernel(const Args a) {
         __syncthreads();
         T* out = static_cast<T*>(a.out);
         bool bad = false, neg = false;
+        const float muf[5] = {(float)mu[0], (float)mu[1], (float)mu[2], (float)mu[3], (float)mu[4]};
         for (int e = tid; e < N * N * N; e += BS) {
             const int x = e / (N * N), y = (e / N) % N, z = e % N;
-            const double vx = vg[x], vy = vg[y], vz = vg[z];
-            const double corr = mu[0] + mu[1] * vx + mu[2] * vy + mu[3] * vz + mu[4] * 0.5 * (vx * vx + vy * vy + vz * vz);
-            const T q = (T)((double)Q[e] - corr);
+            T q;
+            if constexpr (sizeof(T) == 4) {
+                // the correction in FP32 (a small term next to Q)
+                const float corr = muf[0] + muf[1] * vgf[x] + muf[2] * vgf[y] + muf[3] * vgf[z] +
+                                   muf[4] * (vg2f[x] + vg2f[y] + vg2f[z]);
+                q = Q[e] - corr;
+            } else {
+                const double vx = vg[x], vy = vg[y], vz = vg[z];
+                const double corr =
+                    mu[0] + mu[1] * vx + mu[2] * vy + mu[3] * vz + mu[4] * 0.5 * (vx * vx + vy * vy + vz * vz);
+                q = (T)((double)Q[e] - corr);
+            }
             const T o = a.mode == 1 ? fstar<T, N>(a, dsm, cell, x, y, z) + (T)a.dt * q : q;
-            bad |= !isfinite((double)o);
+            bad |= !isfinite(o);
             neg |= a.mode == 1 && o < T(0);
             out[cell * N3 + e] = o;
         }
