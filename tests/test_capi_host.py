@@ -75,3 +75,44 @@ def test_vhs_expansion_term_count_and_errors(fks):
     for bad in ((1.5, 0), (-1.5, 0), (0.0, 65), (0.0, -1)):
         with pytest.raises(fks.FKSError):
             fks.vhs_factor(bad[0], 0.25, L, n, 1, bad[1], 0.5, 0.5)
+
+
+def test_null_context_is_rejected_before_any_device_work(fks):
+    """Every context call checks its handle first (FKS_ERR_INVALID_ARG, no CUDA call)."""
+    import ctypes
+    lib = fks.lib()
+    bits = ctypes.c_int()
+    assert lib.fks_collide(None, None, None, None) == 1
+    assert lib.fks_transport(None, None, None, 0.0, None) == 1
+    assert lib.fks_step(None, None, None, 0.0, None) == 1
+    assert lib.fks_step_strang(None, None, None, None, 0.0, None) == 1
+    assert lib.fks_step_host(None, None, None, 0.0, None) == 1
+    assert lib.fks_moments(None, None, None, None) == 1
+    assert lib.fks_check(None, None, ctypes.byref(bits)) == 1
+    assert lib.fks_set_cluster_size(None, 8) == 1
+    assert lib.fks_get_offsets(None, None) == 1
+    assert lib.fks_set_offsets(None, None) == 1
+    lib.fks_destroy(None)   # a no-op
+
+
+@pytest.mark.parametrize("change,status", [
+    (dict(nx=0), 1), (dict(nx=2048, ny=2048, nz=1024), 1), (dict(n=12), 2), (dict(ktype=7), 1),
+    (dict(ktype=3, alpha=1.5), 1), (dict(ktype=3, alpha=-1.5), 1), (dict(ktype=3, terms=65), 1),
+    (dict(knudsen=0.0), 1), (dict(A1=128, A2=64), 1), (dict(rule=2), 1), (dict(prec=9), 2),
+    (dict(prec=2, ktype=2), 2), (dict(prec=2, n=8), 2), (dict(L=-1.0), 1), (dict(bc=3), 1),
+])
+def test_init_rejects_invalid_configurations_before_any_device_work(fks, change, status):
+    """fks_init validates every argument before it touches the device (no GPU needed)."""
+    import ctypes
+    p = dict(nx=2, ny=2, nz=2, n=16, L=8.0, ktype=0, C=0.25, knudsen=1.0, alpha=1.0, terms=0,
+             A1=4, A2=4, rule=0, prec=1, bc=0)
+    p.update(change)
+    g = fks._Grid(p["nx"], p["ny"], p["nz"], (ctypes.c_double * 3)(0, 0, 0), (ctypes.c_double * 3)(1, 1, 1),
+                  (ctypes.c_int * 3)(p["bc"], 0, 0))
+    vb = fks._VBox(p["n"], p["L"])
+    k = fks._Kernel(p["ktype"], p["C"], p["knudsen"], p["alpha"], p["terms"])
+    d = fks._Dirs(p["A1"], p["A2"], p["rule"])
+    h = ctypes.c_void_p()
+    st = fks.lib().fks_init(ctypes.byref(g), ctypes.byref(vb), ctypes.byref(k), ctypes.byref(d), p["prec"],
+                            ctypes.byref(h))
+    assert st == status and not h.value
