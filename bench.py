@@ -485,7 +485,25 @@ def main():
                             "algorithmic_bytes_per_launch": 8.0 * PTS,
                             "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
                "note": "BGK relaxation (Sec. 2) with the fused transport gather, FP32"}
-        del ctxb
+        # the stiff (exponential) BGK step at Kn = 1e-6, nu dt ~ 1e3, where the Euler step diverges
+        ctxe = fks.Context(fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=fks.BGK, kn=1e-6,
+                                      precision=fks.FKS_FP32))
+        fa, fb = f0.clone(), torch.empty_like(f0)
+        for _ in range(max(1, min(args.warmup, 3))):
+            ctxe.step_exp(fa, fb, dt)
+            fa, fb = fb, fa
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            ctxe.step_exp(fa, fb, dt)
+            fa, fb = fb, fa
+        e1.record()
+        torch.cuda.synchronize()
+        bgk["stiff_exp_step"] = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "knudsen": 1e-6,
+                                 "health_bits": ctxe.check(),
+                                 "note": "fks_step_exp: transport + exact BGK relaxation over dt (stable at any nu dt)"}
+        del ctxb, ctxe, fa, fb
 
     # the same step with every DFT on the tensor cores (split BF16)
     tcp = None

@@ -131,6 +131,16 @@ fks_status fks_transport(fks_ctx *ctx, const void *f, void *f_out, double dt, vo
  * kernel per cell (f* never goes to memory).  f and f_out must not overlap. */
 fks_status fks_step(fks_ctx *ctx, const void *f, void *f_out, double dt, void *stream);
 
+/* A stiff step for BGK contexts (Sec. 2.1 asks for care in the stiff limit):
+ * transport over dt, then the exact solution of the BGK relaxation
+ * df/dt = nu (M[f*] - f) - phi.mu from f*, whose Maxwellian, rate nu = rho/Kn
+ * and projection term stay fixed over the step (the relaxation conserves
+ * rho, rho u, E):  f_out = f* + (1 - e^{-nu dt}) / nu * Q(f*).  Stable for any
+ * nu dt and equal to M[f*] (plus the projection correction) as Kn -> 0; tends
+ * to fks_step as nu dt -> 0.  dt >= 0.  FKS_ERR_UNSUPPORTED for spectral
+ * contexts.  f and f_out must not overlap. */
+fks_status fks_step_exp(fks_ctx *ctx, const void *f, void *f_out, double dt, void *stream);
+
 /* A second-order step (the higher-order splitting the paper allows in Sec. 2.1):
  * Strang splitting T(dt/2) C(dt) T(dt/2) of transport T and collision C, the
  * collision sub-step integrated by Heun's method, the second-order explicit

@@ -391,6 +391,20 @@ class Solver:
             return collide_b(f, self.tab, self.kn, project=True)
         return collide(f, self.tab, self.kn, project=True)
 
+    def step_exp(self, f, dt):
+        """Stiff BGK step (Sec. 2.1: care in the stiff limit): transport, then the exact solution
+        of the BGK relaxation with the cell's Maxwellian, rate nu = rho/Kn and projection term
+        fixed: f* + (1 - exp(-nu dt)) / nu * Q(f*) per cell (dt where nu = 0)."""
+        assert self.tab is None and self.vhs is None, "BGK solvers only"
+        fs = self.transport(f, dt)
+        Q = bgk(fs, self.n, self.L, self.kn, project=True)
+        dv3 = (2.0 * self.L / self.n) ** 3
+        shp = fs.shape
+        fc = fs.reshape(-1, self.n ** 3)
+        nu = fc.sum(axis=1) * dv3 / self.kn
+        w = np.where(nu > 0, -np.expm1(-nu * dt) / np.where(nu > 0, nu, 1.0), dt)
+        return (fc + w[:, None] * Q.reshape(fc.shape)).reshape(shp)
+
     def step_strang(self, f, dt):
         """Second-order step (Sec. 2.1 allows higher-order splitting): Strang splitting
         T(dt/2) C(dt) T(dt/2) with the collision sub-step by Heun's method, the

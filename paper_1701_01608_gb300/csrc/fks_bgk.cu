@@ -201,6 +201,8 @@ __global__ void __launch_bounds__(BS, 1024 / BS) bgk_kernel(BgkArgs a) {
                     mu[tid] = m;
                 } else {
                     mu[5] = nu;
+                    // mode 4: exponential step weight (1 - e^{-nu dt}) / nu (dt as nu -> 0)
+                    mu[6] = nu > 0.0 ? -expm1(-nu * a.dt) / nu : a.dt;
                 }
             }
         }
@@ -215,9 +217,9 @@ __global__ void __launch_bounds__(BS, 1024 / BS) bgk_kernel(BgkArgs a) {
                 gzz[k] = gz[z0 + k];
                 czz[k] = m3 * vz[k] + (T)0.5 * m4 * vz[k] * vz[k];
             }
-            const T tdt = (T)a.dt;
+            const T tdt = (T)(a.mode == 4 ? mu[6] : a.dt);
             const bool heun = a.mode == 3;
-            const bool stepm = a.mode == 1 || heun;
+            const bool stepm = a.mode == 1 || heun || a.mode == 4;
             T* oc = fout + cell * N3 + z0;
             const T* bc = static_cast<const T*>(a.base) + cell * N3 + z0;   // Heun: base, read before the store
             bool bad = false, neg = false;
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(256, 3) bgk_cluster_kernel(BgkArgs a) {
     for (int i = tid; i < 3 * N; i += NT) dsm[i] = transport ? a.delta[i] : 0;
     const int ncx = a.nc[0], ncy = a.nc[1], ncz = a.nc[2];
     const bool heun = a.mode == 3;
-    const bool stepm = a.mode == 1 || heun;
+    const bool stepm = a.mode == 1 || heun || a.mode == 4;
     // run j of this thread: row r = (xl, y) and z0 inside the CTA's planes
     auto run_row = [&](int j) { return (j * NT + tid) / LPR; };
     auto run_z0 = [&](int j) { return ((j * NT + tid) % LPR) * V; };
@@ -449,6 +451,8 @@ __global__ void __launch_bounds__(256, 3) bgk_cluster_kernel(BgkArgs a) {
                     mu[lane] = nu * mm;
                 } else {
                     mu[5] = nu;
+                    // mode 4: exponential step weight (1 - e^{-nu dt}) / nu (dt as nu -> 0)
+                    mu[6] = nu > 0.0 ? -expm1(-nu * a.dt) / nu : a.dt;
                 }
             }
         }
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(256, 3) bgk_cluster_kernel(BgkArgs a) {
         {
             const T tnu = (T)mu[5];
             const T m0 = (T)mu[0], m1 = (T)mu[1], m2 = (T)mu[2], m3 = (T)mu[3], m4 = (T)mu[4];
-            const T tdt = (T)a.dt;
+            const T tdt = (T)(a.mode == 4 ? mu[6] : a.dt);
             T* oc = fout + cell * N3 + (long)rank * PP * N * N;
             const T* bc = static_cast<const T*>(a.base) + cell * N3 + (long)rank * PP * N * N;
             bool bad = false, neg = false;

@@ -1125,6 +1125,22 @@ fks_status fks_step_strang(fks_ctx* c, const void* f, void* f_out, void* work, d
     return st;
 }
 
+// Exponential BGK step: the relaxation df/dt = Q(f) = nu (M[f] - f) - phi.mu keeps M[f], nu and the
+// projection term fixed over the step (collision invariants), so its exact solution from f* is
+// f* + (1 - e^{-nu dt}) / nu Q(f*): stable for any nu dt, and it reaches M[f*] as Kn -> 0.
+fks_status fks_step_exp(fks_ctx* c, const void* f, void* f_out, double dt, void* stream) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (!f || !f_out || !aligned16(f) || !aligned16(f_out)) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must be 16-byte aligned device pointers");
+    if (f == f_out) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must not alias");
+    if (!c->bgk) return fail(c, FKS_ERR_UNSUPPORTED, "the exponential step needs a BGK context");
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(c, FKS_ERR_INVALID_ARG, "dt must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    fks_status st = launch_offsets(c, dt, s);
+    if (st != FKS_OK) return st;
+    if (c->ncells == 0) return FKS_OK;
+    return launch_collide(c, f, f_out, c->d_delta, dt, 4, s);
+}
+
 fks_status fks_step(fks_ctx* c, const void* f, void* f_out, double dt, void* stream) {
     if (!c) return FKS_ERR_INVALID_ARG;
     if (!f || !f_out || !aligned16(f) || !aligned16(f_out)) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must be 16-byte aligned device pointers");

@@ -36,7 +36,8 @@ struct BgkArgs {
     long cell0;                 // first cell
     int nc[3], bc[3];
     double L, inv_kn, dt;
-    int mode;                   // 0 collide, 1 step, 3 second Heun stage (out = (base + f* + dt Q) / 2)
+    int mode;                   // 0 collide, 1 step, 3 second Heun stage (out = (base + f* + dt Q) / 2),
+                                // 4 exponential step (out = f* + (1 - e^{-nu dt}) / nu Q)
     double P[25];
     const void* base = nullptr; // mode 3: the first stage's input (may be out itself)
 };

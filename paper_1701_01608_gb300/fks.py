@@ -67,7 +67,7 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
            "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
            "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias", "fks_step_host", "fks_vhs_factor",
-           "fks_step_strang", "fks_alu_peak"]
+           "fks_step_strang", "fks_alu_peak", "fks_step_exp"]
 
 
 def lib(build: bool = True):
@@ -89,6 +89,7 @@ def lib(build: bool = True):
     L.fks_transport.argtypes = [P, P, P, D, P]
     L.fks_step.argtypes = [P, P, P, D, P]
     L.fks_step_strang.argtypes = [P, P, P, P, D, P]
+    L.fks_step_exp.argtypes = [P, P, P, D, P]
     L.fks_moments.argtypes = [P, P, P, P]
     L.fks_check.argtypes = [P, P, ctypes.POINTER(I)]
     L.fks_get_offsets.argtypes = [P, P]
@@ -280,6 +281,11 @@ class Context:
     def step(self, f, f_out, dt: float, stream=None):
         self._check(self._L.fks_step(self._h, _dptr(f, self.dtype), _dptr(f_out, self.dtype), float(dt),
                                      _stream_ptr(stream)), "fks_step")
+
+    def step_exp(self, f, f_out, dt: float, stream=None):
+        """Stiff BGK step: transport, then the exact BGK relaxation over dt (BGK contexts)."""
+        self._check(self._L.fks_step_exp(self._h, _dptr(f, self.dtype), _dptr(f_out, self.dtype), float(dt),
+                                         _stream_ptr(stream)), "fks_step_exp")
 
     def step_strang(self, f, f_out, work, dt: float, stream=None):
         """Second-order step: Strang splitting with a Heun collision sub-step (work: scratch like f)."""

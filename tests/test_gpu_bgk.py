@@ -109,3 +109,32 @@ def test_bgk_vacuum_cell_does_not_relax(fks, oracle, n, prec):
         else:
             fin = fd.double().cpu().numpy()[i]
             assert fp32_within(Qg[i], Qo[i], fin * fin.sum() * (2 * L / n) ** 3 / 0.2)
+
+
+@pytest.mark.parametrize("n,prec,kn", [(16, 0, 0.1), (32, 1, 0.01), (32, 1, 1e-6), (16, 0, 1e-6)])
+def test_bgk_exponential_step_matches_oracle(fks, oracle, n, prec, kn):
+    """fks_step_exp (transport + exact BGK relaxation) against the oracle's solver, 3 steps on a
+    ragged specular grid; Kn = 1e-6 is the stiff case (nu dt ~ 1e3, where the Euler step diverges)."""
+    ncell, L, bc = (3, 2, 2), 8.0, (1, 0, 0)
+    c = ctx(fks, ncell, n, L, prec, kn=kn, bc=bc)
+    sol = oracle.Solver(ncell, (0, 0, 0), (1, 1, 1), bc, n, L, None, kn)
+    f = I.two_stream(ncell, n, L, seed=5, noise=0.1)
+    fd = torch.from_numpy(f).to("cuda", c.dtype).contiguous()
+    f = fd.double().cpu().numpy()
+    out = torch.empty_like(fd)
+    dt = 1e-3
+    for _ in range(3):
+        c.step_exp(fd, out, dt)
+        fd, out = out, fd
+        f = sol.step_exp(f, dt)
+    assert c.check() & 1 == 0
+    got = fd.double().cpu().numpy()
+    assert rel(got, f) < (1e-11 if prec == 0 else 3e-6)
+
+
+def test_bgk_exponential_step_unsupported_for_spectral(fks):
+    c = fks.Context(fks.Config(ncell=(2, 1, 1), n=16, L=8.0, kernel=0, precision=1))
+    f = torch.zeros((2, 16, 16, 16), device="cuda")
+    with pytest.raises(fks.FKSError) as e:
+        c.step_exp(f, torch.empty_like(f), 0.01)
+    assert e.value.status == 2
