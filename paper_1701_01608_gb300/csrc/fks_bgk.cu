@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(BS, 1024 / BS) bgk_kernel(BgkArgs a) {
                 } else {
                     mu[5] = nu;
                     // mode 4: exponential step weight (1 - e^{-nu dt}) / nu (dt as nu -> 0)
-                    mu[6] = nu > 0.0 ? -expm1(-nu * a.dt) / nu : a.dt;
+                    if (a.mode == 4) mu[6] = nu > 0.0 ? -expm1(-nu * a.dt) / nu : a.dt;
                 }
             }
         }
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(256, 3) bgk_cluster_kernel(BgkArgs a) {
                 } else {
                     mu[5] = nu;
                     // mode 4: exponential step weight (1 - e^{-nu dt}) / nu (dt as nu -> 0)
-                    mu[6] = nu > 0.0 ? -expm1(-nu * a.dt) / nu : a.dt;
+                    if (a.mode == 4) mu[6] = nu > 0.0 ? -expm1(-nu * a.dt) / nu : a.dt;
                 }
             }
         }
