@@ -8,11 +8,12 @@ import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLD = os.path.join(HERE, "golden", "oracle_q_n8_two_stream.txt")
+GOLD_VHS = os.path.join(HERE, "golden", "oracle_q_vhs_alpha0_n8_two_stream.txt")
 
 
-def load():
+def load(path=GOLD):
     case, arrays = {}, {}
-    for line in open(GOLD):
+    for line in open(path):
         if line.startswith("#"):
             case = dict(kv.split("=") for kv in line[1:].split())
         else:
@@ -52,3 +53,27 @@ def test_fp64_gpu_matches_the_frozen_output():
     ctx.collide(fd, out)
     got = out[0].cpu().numpy()
     assert np.linalg.norm(got - Q) <= 1e-10 * np.linalg.norm(Q)
+
+
+def test_oracle_reproduces_the_frozen_vhs_output(oracle):
+    case, f, Q = load(GOLD_VHS)
+    got = oracle.collide_vhs(f[None], int(case["n"]), float(case["L"]), float(case["alpha"]), float(case["C"]),
+                             int(case["A1"]), int(case["A2"]), int(case["rule"]), kn=float(case["kn"]),
+                             project=True)[0]
+    assert np.linalg.norm(got - Q) <= 1e-13 * np.linalg.norm(Q)
+
+
+@pytest.mark.gpu
+def test_fp64_gpu_vhs_matches_the_frozen_output():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_01608_gb300 import fks
+    case, f, Q = load(GOLD_VHS)
+    ctx = fks.Context(fks.Config(ncell=(1, 1, 1), n=8, L=float(case["L"]), kernel=fks.VHS, alpha=float(case["alpha"]),
+                                 C=float(case["C"]), kn=float(case["kn"]), A1=int(case["A1"]), A2=int(case["A2"]),
+                                 rule=int(case["rule"]), precision=fks.FKS_FP64))
+    fd = torch.from_numpy(f[None].copy()).cuda()
+    out = torch.empty_like(fd)
+    ctx.collide(fd, out)
+    assert np.linalg.norm(out[0].cpu().numpy() - Q) <= 1e-10 * np.linalg.norm(Q)
