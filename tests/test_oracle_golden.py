@@ -35,7 +35,8 @@ def test_stored_input_is_the_seeded_input():
     case, f, _ = load()
     g = I.two_stream((1, 1, 1), int(case["n"]), float(case["L"]), seed=int(case["seed"]),
                      noise=float(case["noise"]))[0]
-    assert np.array_equal(g, f)
+    # to the last bits of the platform's exp (the stored file was written on x86-64)
+    assert np.allclose(g, f, rtol=1e-14, atol=0.0)
 
 
 @pytest.mark.gpu
