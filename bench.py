@@ -466,7 +466,8 @@ def main():
                     "d2h": nbytes / (c1.elapsed_time(c2) / 1e3) / 1e9}
         del dtmp
         e2e = {"value": ws * PTS * e2e_steps / (e2e_ms / 1e3), "unit": "pts/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "ms_each": e2e_each, "copy_gbs": copy_gbs,
+               "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "ms_each": e2e_each,
+               "ms_median": float(np.median(e2e_each)), "copy_gbs": copy_gbs,
                "api": "fks_step_host (pinned host arrays; copies overlapped with the step over 8 x-slab chunks)"}
         del host_in, host_out
 
