@@ -372,6 +372,10 @@ collide_kernel(CollideArgs args) {
     // every CTA of the cluster is running before any distributed-shared access
     cluster_sync_all();
     unsigned tphase = 0, xphase = 0;
+    // after a wait has run out (bit 3 recorded), this thread's further waits poll once: the launch
+    // then finishes its cells quickly; every CTA of a cluster keeps the same barrier sequence, so
+    // none leaves while a peer may still address its shared memory
+    bool tmo = false;
     // table slab of direction p (p = M: loss) for this CTA, fetched by one thread
     auto fetch_tables = [&](const T* tab, int p) {
         if (Cfg::TAB_SMEM && tid == 0) {
@@ -517,7 +521,7 @@ collide_kernel(CollideArgs args) {
             const bool active_y = has_col && (!loss || t_tab == 0);
             cpx<T> a[N];
             if constexpr (Cfg::TAB_SMEM) {
-                mbar_wait_bounded(tbar, tphase, args.flags);   // table slab of direction p has landed
+                tmo |= !mbar_wait_bounded(tbar, tphase, args.flags, tmo ? 1L : (1L << 26));   // table slab of direction p has landed
                 tphase ^= 1u;
             }
             if (active) {
@@ -577,7 +581,7 @@ collide_kernel(CollideArgs args) {
                 else if (item + nclusters < args.ncells) fetch_tables(item_tables(item + nclusters), 0);
             }
             if constexpr (C > 1) {
-                mbar_wait_bounded(xbar, xphase, args.flags);   // every peer's block has landed
+                tmo |= !mbar_wait_bounded(xbar, xphase, args.flags, tmo ? 1L : (1L << 26));   // every peer's block has landed
                 xphase ^= 1u;
             }
             // ---- y-pass in place
