@@ -14,9 +14,11 @@
 //   for p < M:  a = IDFT(alpha_p F) / N^3,  b = IDFT(w_p alphap_p F) / N^3,
 //               G += a b                            (gain, Appendix A)
 //   l   = IDFT(betaL F) / N^3,  L = f* l             (loss: the B_F(m,m) term)
-//   Q   = (G - L) / Kn                               (difference in FP64)
-//   Q  -= C^T (C C^T)^-1 C Q                         (FP64 conservation projection)
-//   out = Q  or  f* + dt Q
+//   Q   = (G - L) / Kn                               (G - f* l by one FMA: one rounding)
+//   Q  -= C^T (C C^T)^-1 C Q                         (conservation projection: moment sums in FP64,
+//                                                     or in compensated FP32 pairs for FP32 data;
+//                                                     the coefficients in FP64)
+//   out = Q, f* + dt Q, or the second Heun stage (base + f* + dt Q) / 2
 //
 // Inverse-pass packing: the kz' = 0 and kz' = N/2 planes of a real field are
 // each 2-D Hermitian, so they travel together as one complex plane
