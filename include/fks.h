@@ -153,8 +153,10 @@ fks_status fks_step_exp(fks_ctx *ctx, const void *f, void *f_out, double dt, voi
  * variant-B contexts. */
 fks_status fks_step_strang(fks_ctx *ctx, const void *f, void *f_out, void *work, double dt, void *stream);
 
-/* U[cell][0..4] = sum_k (1, vx, vy, vz, |v|^2/2) f[cell][k] dv^3, accumulated
- * in FP64 (Sec. 3).  U: device array of ncells * 5 doubles. */
+/* U[cell][0..4] = sum_k (1, vx, vy, vz, |v|^2/2) f[cell][k] dv^3 (Sec. 3),
+ * accumulated in FP64 (FP64 states) or in compensated FP32 pairs with exact
+ * products (FP32 states; as accurate as FP64 accumulation), returned in FP64.
+ * U: device array of ncells * 5 doubles. */
 fks_status fks_moments(fks_ctx *ctx, const void *f, double *U, void *stream);
 
 /* Synchronises `stream`, reads and clears the health bits of the kernels
