@@ -114,8 +114,10 @@ fks_status fks_init(const fks_grid *grid, const fks_vbox *vbox, const fks_kernel
                     const fks_dirs *dirs, int precision, fks_ctx **out);
 
 /* Q[cell] = Q(f[cell]) / Kn for every cell (Appendix A), followed by the
- * FP64 conservation projection Q <- Q - C^T (C C^T)^-1 C Q onto the space
- * orthogonal to the collision invariants (1, v, |v|^2/2).
+ * conservation projection Q <- Q - C^T (C C^T)^-1 C Q onto the space
+ * orthogonal to the collision invariants (1, v, |v|^2/2): FP64 coefficients
+ * from moment sums in FP64 (FP64 states) or in compensated FP32 pairs (FP32
+ * states), so the stored Q conserves to the rounding of its own values.
  * f, Q: device arrays of ncells * n^3 elements; f and Q must not overlap. */
 fks_status fks_collide(fks_ctx *ctx, const void *f, void *Q, void *stream);
 
