@@ -17,6 +17,7 @@ Functions and the passage each follows:
   bgk                    -- BGK relaxation nu (M[f] - f) (Sec. 2, BGK approximation)
   step                   -- Eq. disc_relax: transport, then f = f* + dt Q(f*)
   step_strang            -- second-order splitting (Sec. 2.1 allows it): T(dt/2), Heun, T(dt/2)
+  step_exp               -- stiff BGK step (Sec. 2.1, the stiff limit): exact BGK relaxation over dt
   pad, truncate,
   collide_b, galerkin_b  -- variant B: Eq. CF1 with l + m = k not reduced mod n,
                             evaluated with 2n transforms (Sec. 5); brute force
