@@ -10,6 +10,7 @@
 // (persistent over cells), two passes whose second one mostly hits L2.
 #include <cuda_runtime.h>
 
+#include "fks_df.cuh"
 #include "fks_internal.h"
 
 
@@ -277,13 +278,6 @@ struct BgkClusterCfg {
     static_assert(N % CL == 0 && (PP * N * N) % (NT * V) == 0, "whole 16-byte runs per thread");
 };
 
-// compensated FP32 addition: (hi, lo) + (hi2, lo2), hi = rounded sum, lo = the error terms
-__device__ __forceinline__ float2 two_sum_add(float2 x, float2 y) {
-    const float t = __fadd_rn(x.x, y.x);
-    const float bb = __fsub_rn(t, x.x);
-    const float e = __fadd_rn(__fsub_rn(x.x, __fsub_rn(t, bb)), __fsub_rn(y.x, bb));
-    return make_float2(t, __fadd_rn(__fadd_rn(x.y, y.y), e));
-}
 __device__ __forceinline__ float2 shfl_xor_f2(float2 v, int off) {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off));
 }

@@ -38,6 +38,7 @@
 #include <cooperative_groups.h>
 #include <cstdint>
 
+#include "fks_df.cuh"
 #include "fks_fft.cuh"
 
 namespace cg = cooperative_groups;
@@ -151,24 +152,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// double-float helpers (hi, lo) for compensated FP32 sums: add a float, add two pairs,
-// multiply two pairs (error-free transformations with FMA; the lo parts are not renormalised
-// beyond what the sums need)
-__device__ __forceinline__ float2 df_add1(float2 a, float b) {
-    const float t = __fadd_rn(a.x, b);
-    const float bb = __fsub_rn(t, a.x);
-    const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, bb)), __fsub_rn(b, bb));
-    return make_float2(t, __fadd_rn(a.y, e));
-}
-__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
-    const float2 s = df_add1(a, b.x);
-    return make_float2(s.x, __fadd_rn(s.y, b.y));
-}
-__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
-    const float p = __fmul_rn(a.x, b.x);
-    const float e = fmaf(a.x, b.x, -p);
-    return make_float2(p, fmaf(a.x, b.y, fmaf(a.y, b.x, e)));
-}
+// double-float helpers (df_add1, df_add, df_mul) for the compensated FP32 sums: fks_df.cuh
 __device__ __forceinline__ float2 df_shfl_xor(float2 v, int off) {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off));
 }
