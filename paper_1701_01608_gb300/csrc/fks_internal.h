@@ -94,6 +94,20 @@ __host__ __device__ inline double vhs_psi(const double* cb, const double* r, int
 fks_status vhs_expand(double alpha, double C, double L, int n, double tol, int terms, VhsExpansion* out,
                       std::string* err);
 
+// Helpers of the context API (fks_capi.cu) that the uneven batches (fks_batch.cu) share.
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+// Look up the (precision, n, C) instantiation, raise its shared-memory limit and count how many
+// clusters can be resident at once (*found = false: no such instantiation).
+cudaError_t query_variant(bool fp64, int n, int C, CollideVariant* v, int* max_clusters, bool* found);
+// Spectral tables of one (n, L, kernel, directions) in the collision kernel's layout for cluster
+// size C (full: the unsplit layout of the split-BF16 kernel), built on the device in FP64 and
+// stored in the working precision; *out is a new device allocation.  vx (FKS_VHS only): the
+// separable terms, table pair p * S + s being term s of direction p.
+fks_status build_tables_raw(int n, const fks_dirs& dirs, double L, int ktype, double Ck, int C, bool fp64,
+                            void** out, std::string* err, bool full = false, const VhsExpansion* vx = nullptr);
+// P = (sum_k phi(v_k) phi(v_k)^T)^-1 over the n^3 grid on [-L, L)^3, phi = (1, v, |v|^2/2)
+void projection_matrix(int n, double L, double* P);
+
 }  // namespace fks
 
 // Context state (fks_capi.cu); visible to the other translation units.
