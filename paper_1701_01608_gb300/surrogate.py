@@ -1,7 +1,7 @@
 """Training and calibration of the learned collision surrogate.
 
 The surrogate replaces the fast spectral operator on cells near equilibrium;
-the spectral operator is its fallback and the judge of its error.  This module
+the spectral operator is its fallback and the measure of its error.  This module
 drives the library's kernels (fks.Net, fks.surrogate_inputs,
 Context.surrogate_collide): it generates (f, Q) pairs with the spectral solver
 itself, trains the network (own BF16 forward/backward/Adam kernels), and
