@@ -116,3 +116,19 @@ def test_init_rejects_invalid_configurations_before_any_device_work(fks, change,
     st = fks.lib().fks_init(ctypes.byref(g), ctypes.byref(vb), ctypes.byref(k), ctypes.byref(d), p["prec"],
                             ctypes.byref(h))
     assert st == status and not h.value
+
+
+def test_no_cpu_fallback_without_a_gpu(fks):
+    """With no CUDA device the product path fails loudly: a valid context, batch or network cannot be
+    created (FKS_ERR_CUDA from the library, raised by the binding), and the binding accepts only CUDA
+    tensors.  Nothing computes on the CPU instead."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(fks.FKSError) as e:
+        fks.Context(fks.Config(ncell=(2, 1, 1), n=16, L=8.0, precision=fks.FKS_FP32))
+    assert e.value.status in (3, 4)   # the first device call fails: no memory / CUDA error
+    with pytest.raises(TypeError):
+        fks._dptr(torch.zeros(16 ** 3), torch.float32)
+    with pytest.raises(fks.FKSError):
+        fks.Net(16, 2, seed=0)
