@@ -38,8 +38,8 @@ typedef enum {
     FKS_OK = 0,
     FKS_ERR_INVALID_ARG = 1,
     FKS_ERR_UNSUPPORTED = 2,
-    FKS_ERR_OOM = 3,
-    FKS_ERR_CUDA = 4,
+    FKS_ERR_OOM = 3,        /* a device allocation failed for lack of memory */
+    FKS_ERR_CUDA = 4,       /* any other CUDA error (no device, driver, launch, copy) */
     FKS_ERR_NUMERIC = 5,
     FKS_ERR_TIMEOUT = 6
 } fks_status;

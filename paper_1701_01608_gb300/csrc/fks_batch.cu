@@ -135,7 +135,7 @@ static fks_status batch_items(fks_batch* b, const void* const* f, void* const* o
     s.f.assign(f, f + b->nprob);
     s.o.assign(o, o + b->nprob);
     s.dt.assign(dt, dt + b->nprob);
-    if (cudaMalloc(&s.d, sizeof(BatchItem) * b->nprob) != cudaSuccess) return bfail(b, FKS_ERR_OOM, "item descriptors");
+    if (cudaMalloc(&s.d, sizeof(BatchItem) * b->nprob) != cudaSuccess) return bfail(b, alloc_failure(), "item descriptors");
     if (cudaMemcpy(s.d, h.data(), sizeof(BatchItem) * b->nprob, cudaMemcpyHostToDevice) != cudaSuccess)
         return bfail(b, FKS_ERR_CUDA, "item upload");
     b->items.push_back(s);
@@ -229,7 +229,7 @@ fks_status fks_batch_init(int nprob, const int* n, const double* L, const int* k
             double P[25];
             projection_matrix(n[i], L[i], P);
             if (cudaMalloc(&ts.P, sizeof(P)) != cudaSuccess || cudaMemcpy(ts.P, P, sizeof(P), cudaMemcpyHostToDevice))
-                st = FKS_ERR_OOM;
+                st = alloc_failure();
             b->tsets.push_back(ts);
             found = (int)b->tsets.size() - 1;
         }
@@ -249,7 +249,7 @@ fks_status fks_batch_init(int nprob, const int* n, const double* L, const int* k
     }
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) st = FKS_ERR_CUDA;
     if (cudaMalloc(&b->d_flags, sizeof(int)) != cudaSuccess || cudaMemset(b->d_flags, 0, sizeof(int)) != cudaSuccess)
-        st = FKS_ERR_OOM;
+        st = alloc_failure();
     for (BatchClass& cl : b->classes) {
         if (st != FKS_OK) break;
         if (cudaStreamCreateWithFlags(&cl.stream, cudaStreamNonBlocking) != cudaSuccess ||

@@ -663,7 +663,7 @@ fks_status fks::build_tables_raw(int n, const fks_dirs& dirs, double L, int ktyp
     cudaError_t e5 = cudaMalloc(out, esz * packed);
     if (e1 || e2 || e3 || e4 || e5) {
         *err = "cudaMalloc of spectral tables failed";
-        st = FKS_ERR_OOM;
+        st = alloc_failure();
     } else {
         d_w = d_e + 3 * M;
         double* d_v = d_w + M;
@@ -772,7 +772,7 @@ static fks_status setup_tc(fks_ctx* c) {
     const size_t scratch = (size_t)c->tc_grid * tc_scratch_per_cta(c->n);
     if (cudaMalloc(&c->tc_dft, h.size() * sizeof(uint16_t)) != cudaSuccess ||
         cudaMalloc(&c->tc_scratch, scratch) != cudaSuccess)
-        return fail(c, FKS_ERR_OOM, "tensor-core scratch");
+        return fail(c, alloc_failure(), "tensor-core scratch");
     if (cudaMemcpy(c->tc_dft, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(c, FKS_ERR_CUDA, "DFT matrix upload");
     return FKS_OK;
@@ -869,7 +869,7 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
     if (st == FKS_OK) {
         if (cudaMalloc(&c->d_s, sizeof(double) * 3 * c->n) != cudaSuccess ||
             cudaMalloc(&c->d_delta, 3 * c->n) != cudaSuccess || cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess)
-            st = FKS_ERR_OOM;
+            st = alloc_failure();
         else if (cudaMemset(c->d_s, 0, sizeof(double) * 3 * c->n) != cudaSuccess ||
                  cudaMemset(c->d_delta, 0, 3 * c->n) != cudaSuccess || cudaMemset(c->d_flags, 0, sizeof(int)) != cudaSuccess)
             st = FKS_ERR_CUDA;
@@ -882,8 +882,9 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
     projection_matrix(c->n, c->vbox.L, c->P);
     if (cudaMalloc(&c->d_P, sizeof(c->P)) != cudaSuccess ||
         cudaMemcpy(c->d_P, c->P, sizeof(c->P), cudaMemcpyHostToDevice) != cudaSuccess) {
+        const fks_status st2 = alloc_failure();
         fks_destroy(c);
-        return FKS_ERR_OOM;
+        return st2;
     }
     *out = c;
     return FKS_OK;
@@ -1158,7 +1159,7 @@ fks_status fks_step_host(fks_ctx* c, const void* host_f, void* host_out, double 
     const size_t bytes = esz * (size_t)c->ncells * n3;
     if (!c->h_in) {
         if (cudaMalloc(&c->h_in, bytes) != cudaSuccess || cudaMalloc(&c->h_out, bytes) != cudaSuccess)
-            return fail(c, FKS_ERR_OOM, "device copies of the state");
+            return fail(c, alloc_failure(), "device copies of the state");
         if (cudaStreamCreateWithFlags(&c->h_up, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&c->h_down, cudaStreamNonBlocking) != cudaSuccess)
             return fail(c, FKS_ERR_CUDA, "copy streams");
@@ -1263,7 +1264,7 @@ fks_status fks_check(fks_ctx* c, void* stream, int* bits) {
 fks_status fks_selftest_wait(long polls, void* stream) {
     if (polls < 1 || polls > (1L << 26)) return FKS_ERR_INVALID_ARG;
     int* d = nullptr;
-    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return FKS_ERR_OOM;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return alloc_failure();
     cudaStream_t s = (cudaStream_t)stream;
     int h = 0;
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
@@ -1286,7 +1287,7 @@ fks_status fks_alu_peak(int precision, double* tflops, void* stream) {
         return FKS_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     void* sink = nullptr;
-    if (cudaMalloc(&sink, 16) != cudaSuccess) return FKS_ERR_OOM;
+    if (cudaMalloc(&sink, 16) != cudaSuccess) return alloc_failure();
     const bool fp64 = precision == FKS_FP64;
     const int iters = fp64 ? 1024 : 32768;
     const dim3 grid((unsigned)(sms * 8)), block(256);

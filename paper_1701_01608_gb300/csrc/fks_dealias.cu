@@ -404,8 +404,9 @@ extern "C" fks_status fks_set_dealias(fks_ctx* c, int on) {
     c->inner = in;
     c->dealias = true;
     if (!ok) {
+        const fks_status st = alloc_failure();
         fks_set_dealias(c, 0);
-        return fks_internal_fail(c, FKS_ERR_OOM, "variant B buffers");
+        return fks_internal_fail(c, st, "variant B buffers");
     }
     return FKS_OK;
 }

@@ -94,6 +94,13 @@ __host__ __device__ inline double vhs_psi(const double* cb, const double* r, int
 fks_status vhs_expand(double alpha, double C, double L, int n, double tol, int terms, VhsExpansion* out,
                       std::string* err);
 
+// Status after a failed device allocation (or the copy that follows it): FKS_ERR_OOM when the
+// device ran out of memory, FKS_ERR_CUDA for any other CUDA error (no device, driver).  Reads and
+// clears the runtime's last error, so that a later launch check does not report it again.
+inline fks_status alloc_failure() {
+    return cudaGetLastError() == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
+}
+
 // Helpers of the context API (fks_capi.cu) that the uneven batches (fks_batch.cu) share.
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 // Look up the (precision, n, C) instantiation, raise its shared-memory limit and count how many

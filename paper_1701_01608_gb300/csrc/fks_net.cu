@@ -714,7 +714,7 @@ static fks_status ensure_infer(fks_net* m) {
             ok = cudaMalloc(&m->wpk[l], sizeof(__nv_bfloat16) * 27 * KC * NP * 8) == cudaSuccess;
         }
     }
-    if (!ok) return nfail(m, FKS_ERR_OOM, "inference workspace");
+    if (!ok) return nfail(m, alloc_failure(), "inference workspace");
     m->ib = ib;
     return FKS_OK;
 }
@@ -793,8 +793,9 @@ fks_status fks_net_init(int n, int max_batch, unsigned long long seed, fks_net**
     for (int l = 1; l <= NL && ok; ++l) ok = cudaMalloc(&m->act[l], sizeof(float) * max_batch * CH[l] * n3) == cudaSuccess;
     for (int i = 0; i < 2 && ok; ++i) ok = cudaMalloc(&m->gbuf[i], sizeof(float) * max_batch * 32 * n3) == cudaSuccess;
     if (!ok) {
+        const fks_status st = alloc_failure();
         fks_net_destroy(m);
-        return FKS_ERR_OOM;
+        return st;
     }
     // He initialisation (normal, std sqrt(2 / fan_in)), zero biases
     std::vector<float> h(NPARAM, 0.f);

@@ -259,7 +259,7 @@ fks_status fks_surrogate_collide(fks_ctx* c, fks_net* net, const void* f, void* 
             cudaMalloc(&c->s_ind, sizeof(float) * nc) || cudaMalloc(&c->s_items, sizeof(BatchItem) * nc) ||
             cudaMalloc(&c->s_count, sizeof(int)) || cudaMalloc(&c->s_cells, sizeof(int) * (nc > 0 ? nc : 1))) {
             c->err = "surrogate workspace";
-            return FKS_ERR_OOM;
+            return alloc_failure();
         }
     }
     if (((uintptr_t)f & 15) || ((uintptr_t)Q & 15)) return FKS_ERR_INVALID_ARG;

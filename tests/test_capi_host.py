@@ -127,8 +127,9 @@ def test_no_cpu_fallback_without_a_gpu(fks):
         pytest.skip("a CUDA device is present")
     with pytest.raises(fks.FKSError) as e:
         fks.Context(fks.Config(ncell=(2, 1, 1), n=16, L=8.0, precision=fks.FKS_FP32))
-    assert e.value.status in (3, 4)   # the first device call fails: no memory / CUDA error
+    assert e.value.status == 4   # the first device call fails with a CUDA error
     with pytest.raises(TypeError):
         fks._dptr(torch.zeros(16 ** 3), torch.float32)
-    with pytest.raises(fks.FKSError):
+    with pytest.raises(fks.FKSError) as e:
         fks.Net(16, 2, seed=0)
+    assert e.value.status == 4   # a failed allocation reports its CUDA cause, not "out of memory"
