@@ -16,14 +16,14 @@ def test_bessel_matches_scipy(oracle, x):
 def _phi_quad(ktype, C, s):
     a = (lambda r: np.sqrt(4 * C)) if ktype == 0 else (lambda r: np.sqrt(4 * C) / np.sqrt(r))
     # phi(s) = int_{-R}^{R} |rho| a(|rho|) cos(rho s) d rho
-    return 2 * integrate.quad(lambda r: r * a(r) * np.cos(r * s), 0, R, limit=400, epsabs=1e-14, epsrel=1e-13)[0]
+    return 2 * integrate.quad(lambda r: r * a(r) * np.cos(r * s), 0, R, limit=400, epsabs=1e-13, epsrel=1e-12)[0]
 
 
 def _psi_quad(ktype, C, s):
     b = (lambda r: np.sqrt(4 * C)) if ktype == 0 else (lambda r: np.sqrt(4 * C) / np.sqrt(r))
     # psi(s) = int_{disc radius R} b(|y|) exp(i s y_1) dy = 2 pi int_0^R r b(r) J0(r s) dr
     return 2 * np.pi * integrate.quad(lambda r: r * b(r) * special.j0(r * s), 0, R, limit=400,
-                                      epsabs=1e-14, epsrel=1e-13)[0]
+                                      epsabs=1e-13, epsrel=1e-12)[0]
 
 
 @pytest.mark.parametrize("ktype", [0, 1])
