@@ -121,6 +121,28 @@ fks_status fks_init(const fks_grid *grid, const fks_vbox *vbox, const fks_kernel
  * f, Q: device arrays of ncells * n^3 elements; f and Q must not overlap. */
 fks_status fks_collide(fks_ctx *ctx, const void *f, void *Q, void *stream);
 
+/* Precision escalation of FKS_FP32 and FKS_BF16X3 contexts (the FP64 kept for
+ * the gain-loss subtraction near equilibrium).  Near equilibrium the gain G
+ * and the loss L = f* IDFT(betaL F) of Appendix A cancel to a few digits, and
+ * the rounding of the transforms (not of the subtraction itself) bounds the
+ * error of Q at about c ||L|| / Kn: c ~ 2.4e-7 in FP32, ~5e-6 for the split-BF16
+ * tensor cores.  After its projection, each cell whose bound
+ * c ||L|| / Kn exceeds tol ||Q|| (c: 5e-7 FP32, 1.5e-5 split BF16, with a margin)
+ * is not written by the context's kernel but listed on the device and
+ * recomputed by the next tier: FKS_FP32 contexts -> FP64 arithmetic over the
+ * FP32 state; FKS_BF16X3 -> FP32 (with the same test) -> FP64.  Every cell of
+ * fks_collide, fks_step, fks_step_strang and fks_surrogate_collide then meets
+ * relative L2 <= tol of Q against the FP64 operator, with no host
+ * synchronisation (the tiers read the device counts).  Default tol: 1e-5
+ * (FP32), 1e-3 (BF16X3); tol = 0 switches it off (the raw FP32 / split-BF16
+ * result).  FKS_ERR_UNSUPPORTED for a positive tol on FP64, BGK and FKS_VHS
+ * contexts (no tiers).  Synchronises the device. */
+fks_status fks_set_escalation(fks_ctx *ctx, double tol);
+/* The tolerance in force and, if counts != NULL, the cells sent to each tier
+ * (counts[0]: first tier, counts[1]: second) by the last collision or step
+ * call (synchronous device read). */
+fks_status fks_get_escalation(const fks_ctx *ctx, double *tol, long *counts);
+
 /* Exact shift transport over time dt (Sec. 2.1): advances the generic-cell
  * particle offsets (FP64, s <- s + v dt, cell shift delta = floor((s + dx/2)/dx))
  * and writes f_out[j][k] = f[j - delta_k][k'] (k' = k mirrored along an axis
@@ -233,6 +255,17 @@ fks_status fks_batch_run(fks_batch *b, void *const *fa, void *const *fb, const d
 /* As fks_check, for the batch kernels. */
 fks_status fks_batch_check(fks_batch *b, void *stream, int *bits);
 
+/* Precision escalation of FP32 batches, as fks_set_escalation: a problem whose
+ * error bound 5e-7 ||L|| / Kn exceeds tol ||Q|| is recomputed in FP64
+ * arithmetic over its FP32 arrays by a second persistent launch of its class
+ * (device-side list and count: graph-capturable).  Default tol 1e-5; 0: off.
+ * FKS_ERR_UNSUPPORTED for a positive tol on FP64 batches.  Drops the captured
+ * graphs; synchronises the device. */
+fks_status fks_batch_set_escalation(fks_batch *b, double tol);
+/* The tolerance and, if count != NULL, the problems escalated by the last
+ * launch (synchronous device read). */
+fks_status fks_batch_get_escalation(const fks_batch *b, double *tol, long *count);
+
 /* Cluster size used for the class of velocity grid n (-1 if none); the
  * setter rebuilds that class's tables (used by the autotuner). */
 int fks_batch_cluster_size(const fks_batch *b, int n);
@@ -292,8 +325,9 @@ fks_status fks_surrogate_inputs(int n, double L, long ncells, const float *f, fl
  * defect of the raw output); cells whose indicator exceeds `threshold` (or
  * is not finite) are recomputed with the context's spectral operator (the
  * FP32 cluster kernel, or the split-BF16 tensor-core kernel on the list of
- * routed cells).  Synchronises `stream` once (to read the routed count,
- * stored in *nrouted).  f and Q 16-byte aligned.  The moments of the raw
+ * routed cells, each with the context's precision escalation).  The routed
+ * cells are listed on the device; `stream` is synchronised only if nrouted
+ * != NULL (to read the routed count into *nrouted).  f and Q 16-byte aligned.  The moments of the raw
  * output are FP64 sums of its FP32 values; the correction is applied in FP32. */
 fks_status fks_surrogate_collide(fks_ctx *ctx, fks_net *net, const void *f, void *Q, double out_scale,
                                  double ind_scale, double threshold, long *nrouted, void *stream);

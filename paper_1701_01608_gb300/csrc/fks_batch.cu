@@ -29,12 +29,14 @@ struct TableSet {
     int n, ktype;
     double L, Ck;
     void* tables = nullptr;
+    void* tables64 = nullptr;   // FP64 tables of the escalation tier (FP32 batches)
     double* P = nullptr;   // device, 25 doubles
 };
 
 struct BatchClass {
     int n = 0, C = 0, max_clusters = 0;
     CollideVariant var{};
+    EscTier esc{};               // FP32 batches: FP64 arithmetic over the FP32 state (tables in the TableSets)
     std::vector<int> probs;      // problem indices, in item order
     long first = 0;              // offset of this class in an item array
     cudaStream_t stream = nullptr;
@@ -46,6 +48,7 @@ struct ItemSet {
     std::vector<void*> o;
     std::vector<double> dt;
     BatchItem* d = nullptr;
+    BatchItem* d64 = nullptr;    // the same items with the FP64 tables (escalation tier)
 };
 
 struct GraphEntry {
@@ -71,6 +74,11 @@ struct fks_batch {
     int* d_flags = nullptr;
     long launches = 0;
     std::string err;
+    // precision escalation of FP32 batches (as for contexts): problems whose error bound exceeds
+    // esc_tol are listed per class and recomputed in FP64 arithmetic
+    double esc_tol = 0.0;
+    int* esc_lists = nullptr;    // [nprob], class k at its item offset
+    int* esc_counts = nullptr;   // [classes]
 };
 
 static fks_status bfail(fks_batch* b, fks_status s, const std::string& m) {
@@ -87,6 +95,39 @@ static fks_status batch_build_class_tables(fks_batch* b, BatchClass& cl) {
         ts.tables = nullptr;
         std::string err;
         fks_status st = build_tables_raw(ts.n, b->dirs, ts.L, ts.ktype, ts.Ck, cl.C, b->fp64, &ts.tables, &err);
+        if (st != FKS_OK) return bfail(b, st, err);
+        b->launches += 2;
+    }
+    return FKS_OK;
+}
+
+// FP64 escalation tier of an FP32 class: the mixed-precision batch kernel and FP64 tables of every
+// table set of the class
+static fks_status batch_setup_escalation(fks_batch* b, BatchClass& cl) {
+    EscTier& t = cl.esc;
+    t.fp64 = true;
+    t.C = default_cluster_size(true, cl.n);
+    if (!find_collide_variant_mixed(cl.n, t.C, &t.var)) return bfail(b, FKS_ERR_UNSUPPORTED, "no escalation kernel");
+    cudaError_t e = cudaFuncSetAttribute(t.var.func_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.var.smem);
+    if (e != cudaSuccess) return bfail(b, FKS_ERR_CUDA, cudaGetErrorString(e));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = t.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(t.C, 1, 1);
+    cfg.blockDim = dim3(t.var.NT, 1, 1);
+    cfg.dynamicSmemBytes = t.var.smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaOccupancyMaxActiveClusters(&t.max_clusters, t.var.func_batch, &cfg);
+    if (e != cudaSuccess) return bfail(b, FKS_ERR_CUDA, cudaGetErrorString(e));
+    if (t.max_clusters <= 0) return bfail(b, FKS_ERR_UNSUPPORTED, "escalation kernel cannot be resident");
+    for (TableSet& ts : b->tsets) {
+        if (ts.n != cl.n || ts.tables64) continue;
+        std::string err;
+        const fks_status st = build_tables_raw(ts.n, b->dirs, ts.L, ts.ktype, ts.Ck, t.C, true, &ts.tables64, &err);
         if (st != FKS_OK) return bfail(b, st, err);
         b->launches += 2;
     }
@@ -138,16 +179,57 @@ static fks_status batch_items(fks_batch* b, const void* const* f, void* const* o
     if (cudaMalloc(&s.d, sizeof(BatchItem) * b->nprob) != cudaSuccess) return bfail(b, alloc_failure(), "item descriptors");
     if (cudaMemcpy(s.d, h.data(), sizeof(BatchItem) * b->nprob, cudaMemcpyHostToDevice) != cudaSuccess)
         return bfail(b, FKS_ERR_CUDA, "item upload");
+    if (!b->fp64) {
+        for (const BatchClass& cl : b->classes)
+            for (size_t j = 0; j < cl.probs.size(); ++j) h[cl.first + j].tables = b->tsets[b->tset[cl.probs[j]]].tables64;
+        if (cudaMalloc(&s.d64, sizeof(BatchItem) * b->nprob) != cudaSuccess) {
+            cudaFree(s.d);
+            return bfail(b, alloc_failure(), "item descriptors");
+        }
+        if (cudaMemcpy(s.d64, h.data(), sizeof(BatchItem) * b->nprob, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bfail(b, FKS_ERR_CUDA, "item upload");
+    }
     b->items.push_back(s);
     *out = s.d;
     return FKS_OK;
 }
 
+// the FP64-table copy of an item array (escalation tier)
+static BatchItem* batch_items64(const fks_batch* b, const BatchItem* d) {
+    for (const ItemSet& s : b->items)
+        if (s.d == d) return s.d64;
+    return nullptr;
+}
+
 // enqueue one collide (mode 0) or Euler step (mode 1) of every problem on s
+static cudaError_t batch_kernel(const CollideVariant& var, int C, int max_clusters, const CollideArgs& a,
+                                cudaStream_t cs) {
+    const long nclus = a.ncells < max_clusters ? a.ncells : max_clusters;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(nclus * C), 1, 1);
+    cfg.blockDim = dim3(var.NT, 1, 1);
+    cfg.dynamicSmemBytes = var.smem;
+    cfg.stream = cs;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CollideArgs arg = a;
+    void* args[] = {&arg};
+    return cudaLaunchKernelExC(&cfg, var.func_batch, args);
+}
+
 static fks_status batch_launch(fks_batch* b, BatchItem* d_items, int mode, cudaStream_t s) {
     const bool fork = b->classes.size() > 1;
+    BatchItem* d64 = (!b->fp64 && b->esc_tol > 0.0) ? batch_items64(b, d_items) : nullptr;
+    if (d64 && cudaMemsetAsync(b->esc_counts, 0, sizeof(int) * b->classes.size(), s) != cudaSuccess)
+        return bfail(b, FKS_ERR_CUDA, "escalation counts");
     if (fork && cudaEventRecord(b->fork, s) != cudaSuccess) return bfail(b, FKS_ERR_CUDA, "fork event");
-    for (BatchClass& cl : b->classes) {
+    for (size_t k = 0; k < b->classes.size(); ++k) {
+        BatchClass& cl = b->classes[k];
         cudaStream_t cs = fork ? cl.stream : s;
         if (fork && cudaStreamWaitEvent(cs, b->fork, 0) != cudaSuccess) return bfail(b, FKS_ERR_CUDA, "fork wait");
         CollideArgs a;
@@ -159,23 +241,27 @@ static fks_status batch_launch(fks_batch* b, BatchItem* d_items, int mode, cudaS
         a.L = b->L[cl.probs[0]];
         a.mode = mode;
         a.flags = b->d_flags;
-        const long nclus = a.ncells < cl.max_clusters ? a.ncells : cl.max_clusters;
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cl.C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3((unsigned)(nclus * cl.C), 1, 1);
-        cfg.blockDim = dim3(cl.var.NT, 1, 1);
-        cfg.dynamicSmemBytes = cl.var.smem;
-        cfg.stream = cs;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        void* args[] = {&a};
-        cudaError_t e = cudaLaunchKernelExC(&cfg, cl.var.func_batch, args);
+        if (d64) {
+            a.esc_list = b->esc_lists + cl.first;
+            a.esc_count = b->esc_counts + k;
+            a.esc_c2 = kEscFp32 * kEscFp32;
+            a.esc_tol2 = b->esc_tol * b->esc_tol;
+        }
+        cudaError_t e = batch_kernel(cl.var, cl.C, cl.max_clusters, a, cs);
         if (e != cudaSuccess) return bfail(b, FKS_ERR_CUDA, std::string("batch kernel launch: ") + cudaGetErrorString(e));
         b->launches += 1;
+        if (d64) {
+            // the listed problems again, in FP64 arithmetic (the count is read on the device)
+            a.items = d64 + cl.first;
+            a.list = b->esc_lists + cl.first;
+            a.list_count = b->esc_counts + k;
+            a.esc_list = nullptr;
+            a.esc_count = nullptr;
+            e = batch_kernel(cl.esc.var, cl.esc.C, cl.esc.max_clusters, a, cs);
+            if (e != cudaSuccess)
+                return bfail(b, FKS_ERR_CUDA, std::string("escalation kernel launch: ") + cudaGetErrorString(e));
+            b->launches += 1;
+        }
         if (fork) {
             if (cudaEventRecord(cl.done, cs) != cudaSuccess || cudaStreamWaitEvent(s, cl.done, 0) != cudaSuccess)
                 return bfail(b, FKS_ERR_CUDA, "join");
@@ -259,6 +345,15 @@ fks_status fks_batch_init(int nprob, const int* n, const double* L, const int* k
         }
         st = batch_configure_class(b, cl, default_cluster_size(b->fp64, cl.n));
         if (st == FKS_OK) st = batch_build_class_tables(b, cl);
+        if (st == FKS_OK && !b->fp64) st = batch_setup_escalation(b, cl);
+    }
+    if (st == FKS_OK && !b->fp64) {
+        if (cudaMalloc(&b->esc_lists, sizeof(int) * nprob) != cudaSuccess ||
+            cudaMalloc(&b->esc_counts, sizeof(int) * b->classes.size()) != cudaSuccess)
+            st = alloc_failure();
+        else if (cudaMemset(b->esc_counts, 0, sizeof(int) * b->classes.size()) != cudaSuccess)
+            st = FKS_ERR_CUDA;
+        b->esc_tol = 1e-5;   // the stated FP32 bound (relative L2 of Q)
     }
     if (st != FKS_OK) {
         std::fprintf(stderr, "fks_batch_init: %s\n", b->err.c_str());
@@ -274,11 +369,17 @@ void fks_batch_destroy(fks_batch* b) {
     cudaDeviceSynchronize();
     for (GraphEntry& g : b->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
-    for (ItemSet& s : b->items) cudaFree(s.d);
+    for (ItemSet& s : b->items) {
+        cudaFree(s.d);
+        cudaFree(s.d64);
+    }
     for (TableSet& t : b->tsets) {
         cudaFree(t.tables);
+        cudaFree(t.tables64);
         cudaFree(t.P);
     }
+    cudaFree(b->esc_lists);
+    cudaFree(b->esc_counts);
     for (BatchClass& cl : b->classes) {
         if (cl.stream) cudaStreamDestroy(cl.stream);
         if (cl.done) cudaEventDestroy(cl.done);
@@ -312,7 +413,10 @@ fks_status fks_batch_set_cluster_size(fks_batch* b, int n, int C) {
         for (GraphEntry& g : b->graphs)
             if (g.exec) cudaGraphExecDestroy(g.exec);
         b->graphs.clear();
-        for (ItemSet& s : b->items) cudaFree(s.d);
+        for (ItemSet& s : b->items) {
+            cudaFree(s.d);
+            cudaFree(s.d64);
+        }
         b->items.clear();
         return FKS_OK;
     }
@@ -391,6 +495,34 @@ fks_status fks_batch_run(fks_batch* b, void* const* fa, void* const* fb, const d
     }
     cudaError_t e = cudaGraphLaunch(g->exec, s);
     if (e != cudaSuccess) return bfail(b, FKS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    return FKS_OK;
+}
+
+fks_status fks_batch_set_escalation(fks_batch* b, double tol) {
+    if (!b) return FKS_ERR_INVALID_ARG;
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return bfail(b, FKS_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    if (tol > 0.0 && b->fp64) return bfail(b, FKS_ERR_UNSUPPORTED, "FP64 batches have no escalation tier");
+    cudaDeviceSynchronize();
+    // captured graphs hold the launches of the old setting
+    for (GraphEntry& g : b->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+    b->esc_tol = tol;
+    return FKS_OK;
+}
+
+fks_status fks_batch_get_escalation(const fks_batch* b, double* tol, long* count) {
+    if (!b) return FKS_ERR_INVALID_ARG;
+    if (tol) *tol = b->esc_tol;
+    if (count) {
+        *count = 0;
+        if (b->esc_counts) {
+            std::vector<int> h(b->classes.size());
+            if (cudaMemcpy(h.data(), b->esc_counts, sizeof(int) * h.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return FKS_ERR_CUDA;
+            for (int v : h) *count += v;
+        }
+    }
     return FKS_OK;
 }
 

@@ -728,6 +728,57 @@ static fks_status build_tables(fks_ctx* c) {
     return FKS_OK;
 }
 
+// Precision escalation of an FP32 or split-BF16 context: the tiers that recompute the cells whose
+// error bound exceeds the tolerance (FP32 context: FP64 arithmetic; split-BF16 context: FP32, then
+// FP64), each with its own tables, and the device lists that connect them.  Kernels without tiers
+// (BGK, the separable VHS expansion, variant B's inner grid) keep their own arithmetic.
+static fks_status setup_escalation(fks_ctx* c) {
+    if (c->fp64 || c->bgk || c->kern.type == FKS_VHS) return FKS_OK;
+    int k = 0;
+    auto add_tier = [&](bool fp64) -> fks_status {
+        EscTier& t = c->esc[k];
+        t.fp64 = fp64;
+        t.C = default_cluster_size(fp64, c->n);
+        const bool found = fp64 ? find_collide_variant_mixed(c->n, t.C, &t.var) : find_collide_variant_f32(c->n, t.C, &t.var);
+        if (!found) return fail(c, FKS_ERR_UNSUPPORTED, "no escalation kernel for this n");
+        cudaError_t e = cudaFuncSetAttribute(t.var.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.var.smem);
+        if (e == cudaSuccess && t.C > 8) e = cudaFuncSetAttribute(t.var.func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return cuda_fail(c, e, "escalation kernel attributes");
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = t.C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(t.C, 1, 1);
+        cfg.blockDim = dim3(t.var.NT, 1, 1);
+        cfg.dynamicSmemBytes = t.var.smem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaOccupancyMaxActiveClusters(&t.max_clusters, t.var.func, &cfg);
+        if (e != cudaSuccess) return cuda_fail(c, e, "escalation kernel occupancy");
+        if (t.max_clusters <= 0) return fail(c, FKS_ERR_UNSUPPORTED, "escalation kernel cannot be resident");
+        std::string err;
+        const fks_status st = build_tables_raw(c->n, c->dirs, c->vbox.L, c->kern.type, c->kern.C, t.C, fp64, &t.tables,
+                                               &err, false, nullptr);
+        if (st != FKS_OK) return fail(c, st, err);
+        ++k;
+        return FKS_OK;
+    };
+    fks_status st = FKS_OK;
+    if (c->tc) st = add_tier(false);
+    if (st == FKS_OK) st = add_tier(true);
+    if (st != FKS_OK) return st;
+    const long nl = c->ncells > 0 ? c->ncells : 1;
+    if (cudaMalloc(&c->esc_lists, sizeof(int) * 2 * nl) != cudaSuccess ||
+        cudaMalloc(&c->esc_counts, sizeof(int) * 2) != cudaSuccess)
+        return fail(c, alloc_failure(), "escalation lists");
+    if (cudaMemset(c->esc_counts, 0, sizeof(int) * 2) != cudaSuccess) return fail(c, FKS_ERR_CUDA, "escalation lists");
+    c->esc_ntier = k;
+    c->esc_tol = c->tc ? 1e-3 : 1e-5;   // the stated relative L2 bounds of Q (split BF16, FP32)
+    return FKS_OK;
+}
+
 // P = (sum_k phi(v_k) phi(v_k)^T)^-1, phi = (1, v, |v|^2/2): the projection
 // Q -= C^T (C C^T)^-1 C Q with C = dv^3 phi^T becomes Q -= phi^T P (phi^T Q)
 void fks::projection_matrix(int n, double L, double* P) {
@@ -866,6 +917,7 @@ fks_status fks_init(const fks_grid* grid, const fks_vbox* vbox, const fks_kernel
     } else {
         c->C = 1;
     }
+    if (st == FKS_OK) st = setup_escalation(c);
     if (st == FKS_OK) {
         if (cudaMalloc(&c->d_s, sizeof(double) * 3 * c->n) != cudaSuccess ||
             cudaMalloc(&c->d_delta, 3 * c->n) != cudaSuccess || cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess)
@@ -913,9 +965,11 @@ void fks_destroy(fks_ctx* c) {
     cudaFree(c->s_rho);
     cudaFree(c->s_dist);
     cudaFree(c->s_ind);
-    cudaFree(c->s_items);
     cudaFree(c->s_cells);
     cudaFree(c->s_count);
+    for (int i = 0; i < 2; ++i) cudaFree(c->esc[i].tables);
+    cudaFree(c->esc_lists);
+    cudaFree(c->esc_counts);
     delete c;
 }
 
@@ -968,9 +1022,19 @@ static fks_status launch_bgk_ctx(fks_ctx* c, const void* f, void* out, const sig
     return FKS_OK;
 }
 
+static bool esc_on(const fks_ctx* c) { return c->esc_tol > 0.0 && c->esc_ntier > 0; }
+
 static fks_status launch_tc_ctx(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
-                                cudaStream_t s, const int* cells = nullptr, long ncells = -1) {
+                                cudaStream_t s, const int* cells = nullptr, long ncells = -1,
+                                const int* cells_count = nullptr) {
     TcLaunch l;
+    l.cells_count = cells_count;
+    if (esc_on(c)) {
+        l.esc_list = c->esc_lists;
+        l.esc_count = c->esc_counts;
+        l.esc_c2 = kEscBf16 * kEscBf16;
+        l.esc_tol2 = c->esc_tol * c->esc_tol;
+    }
     l.f = f;
     l.out = out;
     l.tables = c->tables;
@@ -997,20 +1061,15 @@ static fks_status launch_tc_ctx(fks_ctx* c, const void* f, void* out, const sign
     return FKS_OK;
 }
 
-// collision of the cells [cell0, cell1) (cell1 < 0: all); ranges other than
-// all cells are for the cluster and BGK kernels
-static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
-                                 cudaStream_t s, long cell0 = 0, long cell1 = -1, const void* base = nullptr) {
-    if (c->bgk) return launch_bgk_ctx(c, f, out, delta, dt, mode, s, cell0, cell1, base);
-    if (c->tc) return launch_tc_ctx(c, f, out, delta, dt, mode, s);
-    if (c->dealias) return launch_dealias(c, f, out, delta, dt, mode, s);
-    if (cell1 < 0) cell1 = c->ncells;
-    if (cell1 <= cell0) return FKS_OK;
+// arguments of the cluster kernel for a context (tables: the context's own or an escalation tier's)
+static CollideArgs cluster_args(const fks_ctx* c, const void* tables, const void* f, void* out, const signed char* delta,
+                                double dt, int mode, long cell0, long cell1, const void* base) {
     CollideArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.base = base;
     a.f = f;
     a.out = out;
-    a.tables = c->tables;
+    a.tables = tables;
     a.delta = delta;
     a.flags = c->d_flags;
     a.ncells = cell1;
@@ -1026,32 +1085,117 @@ static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const sig
     a.mode = mode;
     std::memcpy(a.P, c->P, sizeof(a.P));
     a.items = nullptr;
-    const long ncl = cell1 - cell0;
-    const long nclus = ncl < c->max_clusters ? ncl : c->max_clusters;
+    return a;
+}
+
+// persistent launch of one cluster-kernel instantiation over `work` cells (at most max_clusters clusters)
+static cudaError_t launch_cluster(const CollideVariant& var, int C, int max_clusters, const CollideArgs& a, long work,
+                                  cudaStream_t s) {
+    const long nclus = work < max_clusters ? work : max_clusters;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = c->C;
+    attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)(nclus * c->C), 1, 1);
-    cfg.blockDim = dim3(c->var.NT, 1, 1);
-    cfg.dynamicSmemBytes = c->var.smem;
+    cfg.gridDim = dim3((unsigned)(nclus * C), 1, 1);
+    cfg.blockDim = dim3(var.NT, 1, 1);
+    cfg.dynamicSmemBytes = var.smem;
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    void* args[] = {&a};
-    cudaError_t e = cudaLaunchKernelExC(&cfg, c->var.func, args);
-    if (e != cudaSuccess) return cuda_fail(c, e, "collision kernel launch");
-    c->launches += 1;
+    CollideArgs arg = a;
+    void* args[] = {&arg};
+    return cudaLaunchKernelExC(&cfg, var.func, args);
+}
+
+// the escalation tiers after a launch of the context's own kernel: tier i recomputes the cells the
+// launch before it listed (device count: no host synchronisation) and lists its own failures
+static fks_status launch_esc_tiers(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
+                                   cudaStream_t s, const void* base) {
+    for (int i = 0; i < c->esc_ntier; ++i) {
+        const EscTier& t = c->esc[i];
+        CollideArgs a = cluster_args(c, t.tables, f, out, delta, dt, mode, 0, c->ncells, base);
+        a.list = c->esc_lists + (long)i * c->ncells;
+        a.list_count = c->esc_counts + i;
+        if (i + 1 < c->esc_ntier) {
+            a.esc_list = c->esc_lists + (long)(i + 1) * c->ncells;
+            a.esc_count = c->esc_counts + i + 1;
+            a.esc_c2 = kEscFp32 * kEscFp32;
+            a.esc_tol2 = c->esc_tol * c->esc_tol;
+        }
+        const cudaError_t e = launch_cluster(t.var, t.C, t.max_clusters, a, c->ncells, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "escalation kernel launch");
+        c->launches += 1;
+    }
     return FKS_OK;
 }
 
+static fks_status reset_esc(fks_ctx* c, cudaStream_t s) {
+    if (cudaMemsetAsync(c->esc_counts, 0, sizeof(int) * 2, s) != cudaSuccess)
+        return fail(c, FKS_ERR_CUDA, "escalation counts");
+    return FKS_OK;
+}
+
+// collision of the cells [cell0, cell1) (cell1 < 0: all); ranges other than
+// all cells are for the cluster and BGK kernels
+static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
+                                 cudaStream_t s, long cell0 = 0, long cell1 = -1, const void* base = nullptr) {
+    if (c->bgk) return launch_bgk_ctx(c, f, out, delta, dt, mode, s, cell0, cell1, base);
+    if (c->dealias) return launch_dealias(c, f, out, delta, dt, mode, s);
+    const bool esc = esc_on(c);
+    if (esc) {
+        const fks_status st = reset_esc(c, s);
+        if (st != FKS_OK) return st;
+    }
+    if (c->tc) {
+        const fks_status st = launch_tc_ctx(c, f, out, delta, dt, mode, s);
+        if (st != FKS_OK || !esc) return st;
+        return launch_esc_tiers(c, f, out, delta, dt, mode, s, base);
+    }
+    if (cell1 < 0) cell1 = c->ncells;
+    if (cell1 <= cell0) return FKS_OK;
+    CollideArgs a = cluster_args(c, c->tables, f, out, delta, dt, mode, cell0, cell1, base);
+    if (esc) {
+        a.esc_list = c->esc_lists;
+        a.esc_count = c->esc_counts;
+        a.esc_c2 = kEscFp32 * kEscFp32;
+        a.esc_tol2 = c->esc_tol * c->esc_tol;
+    }
+    const cudaError_t e = launch_cluster(c->var, c->C, c->max_clusters, a, cell1 - cell0, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "collision kernel launch");
+    c->launches += 1;
+    if (!esc) return FKS_OK;
+    return launch_esc_tiers(c, f, out, delta, dt, mode, s, base);
+}
+
 fks_status fks_internal_fail(fks_ctx* c, fks_status st, const std::string& msg) { return fail(c, st, msg); }
-fks_status fks_internal_collide_cells(fks_ctx* c, const void* f, void* out, const int* cells, long ncells,
-                                      cudaStream_t s) {
-    if (!c->tc) return fail(c, FKS_ERR_UNSUPPORTED, "cell lists need a tensor-core context");
-    return launch_tc_ctx(c, f, out, nullptr, 0.0, 0, s, cells, ncells);
+fks_status fks_internal_collide_list(fks_ctx* c, const void* f, void* out, const int* cells, const int* count,
+                                     cudaStream_t s) {
+    if (c->bgk || c->dealias) return fail(c, FKS_ERR_UNSUPPORTED, "cell lists need a spectral context (variant A)");
+    const bool esc = esc_on(c);
+    if (esc) {
+        const fks_status st = reset_esc(c, s);
+        if (st != FKS_OK) return st;
+    }
+    if (c->tc) {
+        const fks_status st = launch_tc_ctx(c, f, out, nullptr, 0.0, 0, s, cells, c->ncells, count);
+        if (st != FKS_OK) return st;
+    } else {
+        CollideArgs a = cluster_args(c, c->tables, f, out, nullptr, 0.0, 0, 0, c->ncells, nullptr);
+        a.list = cells;
+        a.list_count = count;
+        if (esc) {
+            a.esc_list = c->esc_lists;
+            a.esc_count = c->esc_counts;
+            a.esc_c2 = kEscFp32 * kEscFp32;
+            a.esc_tol2 = c->esc_tol * c->esc_tol;
+        }
+        const cudaError_t e = launch_cluster(c->var, c->C, c->max_clusters, a, c->ncells, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "collision kernel launch");
+        c->launches += 1;
+    }
+    return esc ? launch_esc_tiers(c, f, out, nullptr, 0.0, 0, s, nullptr) : FKS_OK;
 }
 fks_status fks_internal_collide(fks_ctx* c, const void* f, void* out, int mode, cudaStream_t s) {
     return launch_collide(c, f, out, nullptr, 0.0, mode, s);
@@ -1309,6 +1453,29 @@ fks_status fks_alu_peak(int precision, double* tflops, void* stream) {
     cudaFree(sink);
     if (e != cudaSuccess || !(ms > 0.f)) return FKS_ERR_CUDA;
     *tflops = 2.0 * 8.0 * iters * (double)grid.x * block.x / (ms * 1e-3) / 1e12;
+    return FKS_OK;
+}
+
+fks_status fks_set_escalation(fks_ctx* c, double tol) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(c, FKS_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    if (tol > 0.0 && c->esc_ntier == 0)
+        return fail(c, FKS_ERR_UNSUPPORTED, "this context has no escalation tiers (FP64, BGK, VHS)");
+    cudaDeviceSynchronize();   // launches in flight keep the tolerance they were issued with
+    c->esc_tol = tol;
+    return FKS_OK;
+}
+
+fks_status fks_get_escalation(const fks_ctx* c, double* tol, long* counts) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (tol) *tol = c->esc_tol;
+    if (counts) {
+        int h[2] = {0, 0};
+        if (c->esc_counts && cudaMemcpy(h, c->esc_counts, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return FKS_ERR_CUDA;
+        counts[0] = h[0];
+        counts[1] = h[1];
+    }
     return FKS_OK;
 }
 

@@ -76,7 +76,22 @@ struct CollideArgs {
     double P[25];           // dv^6 (C C^T)^-1 over the rows phi = (1, v, |v|^2/2)
     const BatchItem* items; // batch mode: ncells items, each a homogeneous problem
     const void* base;       // mode 3: the first stage's input, same layout as out (may be out itself)
+    // list mode: the cells (batch: items) processed are list[cell0 .. *list_count) instead of cell0 .. ncells
+    const int* list;
+    const int* list_count;
+    // precision escalation: a cell whose error bound esc_c * ||L|| / Kn exceeds esc_tol * ||Q|| (Q
+    // projected) is appended to esc_list (count esc_count) and not written; nullptr: every cell is written
+    int* esc_list;
+    int* esc_count;
+    double esc_c2;          // esc_c^2
+    double esc_tol2;        // esc_tol^2
 };
+
+// Error constants of the escalation bound ||dQ|| <= c ||L|| / Kn (L = f* l, the loss term): the
+// transforms' rounding in each arithmetic measured against the FP64 operator, with a margin
+// (FP32 ~2.4e-7, split BF16 ~5e-6 of ||L|| on near-equilibrium and two-stream cells).
+constexpr double kEscFp32 = 5e-7;
+constexpr double kEscBf16 = 1.5e-5;
 
 __device__ __forceinline__ void cluster_arrive() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
@@ -232,14 +247,14 @@ struct CollideCfg {
     static constexpr unsigned TAB_BYTES = (unsigned)(sizeof(T) * TAB_ELEMS);
     static constexpr long G_ELEMS = G_REG ? 0 : (long)NTASK * N;    // FP64 gain [N z][NTASK]
     static constexpr size_t SMEM_BASE = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS + S_ELEMS) + sizeof(T) * G_ELEMS +
-                                        sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N) + sizeof(float) * (4 * N + 8) +
+                                        sizeof(double) * (8 + (NT / 32) * 7 + 8 + 2 * N) + sizeof(float) * (4 * N + 8) +
                                         sizeof(T) * N + sizeof(long) * N + 2 * sizeof(uint64_t) + 3 * N + 4 * NT + 64;
     // the table slab is staged in shared memory (bulk-copy prefetch) when it fits
     static constexpr bool TAB_SMEM = SMEM_BASE + sizeof(T) * TAB_ELEMS <= 227u * 1024u;
     static constexpr long TB_ELEMS = TAB_SMEM ? TAB_ELEMS : 0;
     static constexpr size_t SMEM_BYTES = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS + S_ELEMS) +
                                          sizeof(T) * (TB_ELEMS + G_ELEMS) +
-                                         sizeof(double) * (8 + (NT / 32) * 5 + 8 + 2 * N) +
+                                         sizeof(double) * (8 + (NT / 32) * 7 + 8 + 2 * N) +
                                          sizeof(float) * (4 * N + 8) + sizeof(T) * N + sizeof(long) * N +
                                          2 * sizeof(uint64_t) + 3 * N + 4 * NT + 64;
     static_assert(N % C == 0, "cluster size must divide N");
@@ -283,7 +298,9 @@ __device__ void xpass_task_map(unsigned* map, unsigned char* used) {
     }
 }
 
-template <typename T, int N, int C, bool BATCH = false>
+// T: arithmetic of the transforms; ST: element type of f, out and base in global memory (ST = float
+// with T = double: the FP64 escalation tier of an FP32 state)
+template <typename T, int N, int C, bool BATCH = false, typename ST = T>
 __global__ void __launch_bounds__(CollideCfg<T, N, C>::NT, 1)
 collide_kernel(CollideArgs args) {
     using Cfg = CollideCfg<T, N, C>;
@@ -304,8 +321,8 @@ collide_kernel(CollideArgs args) {
     T* Tb = reinterpret_cast<T*>(S + Cfg::S_ELEMS);                   // table slab
     T* Gs = Tb + Cfg::TB_ELEMS;                                        // FP64 gain [N z][NTASK]
     double* red = reinterpret_cast<double*>(Gs + Cfg::G_ELEMS);       // [8] own partials
-    double* redw = red + 8;                                            // [NT/32][5]
-    double* mu = redw + (NT / 32) * 5;                                 // [8] correction coefficients
+    double* redw = red + 8;                                            // [NT/32][7]
+    double* mu = redw + (NT / 32) * 7;                                 // [8] correction coefficients, [7] escalation
     double* vzt = mu + 8;                                              // [N] v_z
     double* vz2t = vzt + N;                                            // [N] v_z^2 / 2
     float* vzf = reinterpret_cast<float*>(vz2t + N);                  // [4][N] v_z, v_z^2/2 as FP32 (hi, lo)
@@ -369,7 +386,10 @@ collide_kernel(CollideArgs args) {
             bulk_g2s(Tb, tab + ((long)p * C + rank) * Cfg::TAB_ELEMS, Cfg::TAB_BYTES, tbar);
         }
     };
-    if (args.cell0 + cluster_id < args.ncells) fetch_tables(item_tables(args.cell0 + cluster_id), 0);
+    // list mode: the count was written by an earlier launch on the stream
+    const long end = args.list ? (long)*args.list_count : args.ncells;
+    auto item_at = [&](long it) -> long { return args.list ? (long)args.list[it] : it; };
+    if (args.cell0 + cluster_id < end) fetch_tables(item_tables(item_at(args.cell0 + cluster_id)), 0);
     const int ncx = args.nc[0], ncy = args.nc[1], ncz = args.nc[2];
 
     // z-pass ownership: column (xl, y), x = rank*NS + xl (threads >= NTASK idle)
@@ -394,25 +414,27 @@ collide_kernel(CollideArgs args) {
     // y-pass lane addressing: element (src, kyl) at ybase + src*BLK + kyl*HP
     const long ybase = widx(t_tab, t_xl, 0, t_pp);
 
-    for (long item = args.cell0 + cluster_id; item < args.ncells; item += nclusters) {
+    for (long it = args.cell0 + cluster_id; it < end; it += nclusters) {
+        const long item = item_at(it);
+        const bool has_next = it + nclusters < end;
         // batch: item = one homogeneous problem (cell 0 of its own arrays)
         const long cell = BATCH ? 0 : item;
         if constexpr (!BATCH) {
             // the x-planes of this cluster's next cell towards L2 while this one is processed
             // (its forward pass then starts on L2 hits; with transport most sources are the cell itself)
-            if (tid == 0 && item + nclusters < args.ncells)
-                prefetch_l2(static_cast<const T*>(args.f) + (item + nclusters) * N3 + (long)rank * NS * N * N,
-                            (unsigned)(sizeof(T) * NS * N * N));
+            if (tid == 0 && has_next)
+                prefetch_l2(static_cast<const ST*>(args.f) + item_at(it + nclusters) * N3 + (long)rank * NS * N * N,
+                            (unsigned)(sizeof(ST) * NS * N * N));
         }
-        const T* __restrict__ fin;
-        T* __restrict__ fout;
+        const ST* __restrict__ fin;
+        ST* __restrict__ fout;
         const T* __restrict__ tab = item_tables(item);
         const double* Pm;
         double inv_kn, dt_step;
         if constexpr (BATCH) {
             const BatchItem& bi = args.items[item];
-            fin = static_cast<const T*>(bi.f);
-            fout = static_cast<T*>(bi.out);
+            fin = static_cast<const ST*>(bi.f);
+            fout = static_cast<ST*>(bi.out);
             Pm = bi.P;
             inv_kn = bi.inv_kn;
             dt_step = bi.dt;
@@ -421,8 +443,8 @@ collide_kernel(CollideArgs args) {
             dv = 2.0 * bi.L / N;
             if (tid < N) set_vel(tid);
         } else {
-            fin = static_cast<const T*>(args.f);
-            fout = static_cast<T*>(args.out);
+            fin = static_cast<const ST*>(args.f);
+            fout = static_cast<ST*>(args.out);
             Pm = args.P;
             inv_kn = args.inv_kn;
             dt_step = args.dt;
@@ -441,7 +463,7 @@ collide_kernel(CollideArgs args) {
         }
         __syncthreads();
         // base of the f* column (x, y, :) of the transported cell
-        const T* colbase;
+        const ST* colbase;
         if (!transport) {
             colbase = fin + ((long)zx * N + zl_y) * N;
         } else {
@@ -458,7 +480,7 @@ collide_kernel(CollideArgs args) {
         if (has_col) {
             cpx<T> a[N];
 #pragma unroll
-            for (int z = 0; z < N; ++z) a[z] = {colbase[zoff[z]], T(0)};
+            for (int z = 0; z < N; ++z) a[z] = {T(colbase[zoff[z]]), T(0)};
             fft<N, -1>(a);
             cpx<T>* stg = W + ((long)zl_x * N + zl_y) * HF;
 #pragma unroll
@@ -564,7 +586,7 @@ collide_kernel(CollideArgs args) {
             }
             if (tid == 0) {
                 if (!loss) fetch_tables(tab, p + 1);
-                else if (item + nclusters < args.ncells) fetch_tables(item_tables(item + nclusters), 0);
+                else if (has_next) fetch_tables(item_tables(item_at(it + nclusters)), 0);
             }
             if constexpr (C > 1) {
                 tmo |= !mbar_wait_bounded(xbar, xphase, args.flags, tmo ? 1L : (1L << 26));   // every peer's block has landed
@@ -612,7 +634,7 @@ collide_kernel(CollideArgs args) {
                 T col[N];
                 if (has_col) {
 #pragma unroll
-                    for (int z = 0; z < N; ++z) col[z] = colbase[zoff[z]];
+                    for (int z = 0; z < N; ++z) col[z] = T(colbase[zoff[z]]);
                 }
                 auto rval = [&](int z) -> T {
                     T g;
@@ -621,6 +643,9 @@ collide_kernel(CollideArgs args) {
                     return fma(-col[z], av[z], g);
                 };
                 const int warp = tid >> 5, lane = tid & 31;
+                // escalation bound inputs: sum r^2 (r = G - f* l) and sum (f* l)^2 over the cell (FP32: an
+                // estimate of the norms is all the bound needs)
+                float e_qq = 0.f, e_ll = 0.f;
                 if constexpr (sizeof(T) == 4) {
                     // FP32: compensated sums (hi, lo) with exact products (FMA), carried as pairs
                     // through the warp and block reductions, FP64 from the block totals on (the
@@ -633,6 +658,9 @@ collide_kernel(CollideArgs args) {
 #pragma unroll
                         for (int z = 0; z < N; ++z) {
                             const float r = rval(z);
+                            const float lz = col[z] * av[z];
+                            e_qq = fmaf(r, r, e_qq);
+                            e_ll = fmaf(lz, lz, e_ll);
                             a0 = df_add1(a0, r);
                             const float p = r * vzf[z];
                             const float pe = fmaf(r, vzf[N + z], fmaf(r, vzf[z], -p));
@@ -655,16 +683,27 @@ collide_kernel(CollideArgs args) {
                     for (int i = 0; i < 5; ++i)
 #pragma unroll
                         for (int off = 16; off > 0; off >>= 1) m5[i] = df_add(m5[i], df_shfl_xor(m5[i], off));
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        e_qq += __shfl_xor_sync(0xffffffffu, e_qq, off);
+                        e_ll += __shfl_xor_sync(0xffffffffu, e_ll, off);
+                    }
                     float2* redw2 = reinterpret_cast<float2*>(redw);
                     if (lane == 0) {
 #pragma unroll
-                        for (int i = 0; i < 5; ++i) redw2[warp * 5 + i] = m5[i];
+                        for (int i = 0; i < 5; ++i) redw2[warp * 7 + i] = m5[i];
+                        redw[warp * 7 + 5] = (double)e_ll;
+                        redw[warp * 7 + 6] = (double)e_qq;
                     }
                     __syncthreads();
                     if (tid < 5) {
                         float2 acc = make_float2(0.f, 0.f);
-                        for (int w = 0; w < NT / 32; ++w) acc = df_add(acc, redw2[w * 5 + tid]);
+                        for (int w = 0; w < NT / 32; ++w) acc = df_add(acc, redw2[w * 7 + tid]);
                         red[tid] = ((double)acc.x + (double)acc.y) * inv_kn;
+                    } else if (tid < 7) {
+                        double acc = 0.0;
+                        for (int w = 0; w < NT / 32; ++w) acc += redw[w * 7 + tid];
+                        red[tid] = acc;
                     }
                 } else {
                     double s5[5] = {0, 0, 0, 0, 0};
@@ -694,13 +733,15 @@ collide_kernel(CollideArgs args) {
                     }
                     if (lane == 0) {
 #pragma unroll
-                        for (int i = 0; i < 5; ++i) redw[warp * 5 + i] = s5[i];
+                        for (int i = 0; i < 5; ++i) redw[warp * 7 + i] = s5[i];
                     }
                     __syncthreads();
                     if (tid < 5) {
                         double acc = 0.0;
-                        for (int w = 0; w < NT / 32; ++w) acc += redw[w * 5 + tid];
+                        for (int w = 0; w < NT / 32; ++w) acc += redw[w * 7 + tid];
                         red[tid] = acc;
+                    } else if (tid < 7) {
+                        red[tid] = 0.0;   // the FP64 arithmetic is the last escalation tier
                     }
                 }
                 cluster_sync_all();
@@ -708,24 +749,43 @@ collide_kernel(CollideArgs args) {
                     // warp 0: cluster totals (lane i: moment i over the ranks, in rank order),
                     // mu = P tot, the z part of the correction
                     double tot = 0.0;
-                    if (lane < 5)
+                    if (lane < 7)
                         for (int r = 0; r < C; ++r) tot += cluster.map_shared_rank(red, r)[lane];
                     double t5[5];
 #pragma unroll
                     for (int i = 0; i < 5; ++i) t5[i] = __shfl_sync(0xffffffffu, tot, i);
+                    double mval = 0.0;
                     if (lane < 5) {
                         double acc = 0.0;
                         for (int j = 0; j < 5; ++j) acc += Pm[lane * 5 + j] * t5[j];
                         acc = args.mode == 2 ? 0.0 : acc;   // mode 2: the caller projects
                         mu[lane] = acc;
                         muf[lane] = (float)acc;
+                        mval = acc;
+                    }
+                    // escalation: ||Q_proj||^2 = ||Q||^2 - mu . s (s = the moment sums of Q, mu = P s)
+                    double ms = lane < 5 ? mval * tot : 0.0;
+#pragma unroll
+                    for (int off = 4; off > 0; off >>= 1) ms += __shfl_xor_sync(0xffffffffu, ms, off);
+                    const double e_l2 = __shfl_sync(0xffffffffu, tot, 5), e_q2 = __shfl_sync(0xffffffffu, tot, 6);
+                    if (lane == 0) {
+                        bool esc = false;
+                        if (args.esc_list) {
+                            const double k2 = inv_kn * inv_kn, qp = k2 * e_q2 - ms;
+                            esc = args.esc_c2 * k2 * e_l2 > args.esc_tol2 * (qp > 0.0 ? qp : 0.0);
+                        }
+                        mu[7] = esc ? 1.0 : 0.0;
                     }
                     __syncwarp();
                     // correction phi(v).mu = mu0 + mu1 vx + mu2 vy + mu4 (vx^2+vy^2)/2 + [mu3 vz + mu4 vz^2/2]
                     for (int z = lane; z < N; z += 32) czt[z] = (T)(mu[3] * vzt[z] + mu[4] * vz2t[z]);
                 }
-                cluster_sync_all();   // every CTA has read the partials; mu and czt are visible
-                if (has_col) {
+                cluster_sync_all();   // every CTA has read the partials; mu, czt and the decision are visible
+                // an escalated cell is left to the next tier (which reads f, and base in mode 3, again)
+                const bool escalated = mu[7] != 0.0;
+                if (escalated && rank == 0 && tid == 0)
+                    args.esc_list[atomicAdd(args.esc_count, 1)] = (int)(BATCH ? item : cell);
+                if (has_col && !escalated) {
                     // corrected Q = r / Kn - phi(v).mu, then out = Q or f* + dt Q
                     T cxy;
                     if constexpr (sizeof(T) == 4)
@@ -736,22 +796,23 @@ collide_kernel(CollideArgs args) {
                     const T kn = (T)inv_kn, dt = (T)dt_step;
                     const bool heun = !BATCH && args.mode == 3;
                     const bool stepm = args.mode == 1 || heun;
-                    T* dst = fout + cell * N3 + ((long)zx * N + zl_y) * N;
+                    ST* dst = fout + cell * N3 + ((long)zx * N + zl_y) * N;
                     // Heun: base row of this column (read before this thread's own store to it)
-                    const T* brow = static_cast<const T*>(args.base) + cell * N3 + ((long)zx * N + zl_y) * N;
+                    const ST* brow = static_cast<const ST*>(args.base) + cell * N3 + ((long)zx * N + zl_y) * N;
                     bool bad = false, neg = false;
-                    constexpr int V = 16 / sizeof(T);
-                    static_assert((N * sizeof(T)) % 16 == 0, "rows are whole 16-byte vectors");
+                    constexpr int V = 16 / sizeof(ST);
+                    static_assert((N * sizeof(ST)) % 16 == 0, "rows are whole 16-byte vectors");
 #pragma unroll
                     for (int z0 = 0; z0 < N; z0 += V) {
-                        T res[V], bv[V];
+                        ST res[V];
+                        T bv[V];
                         if (heun) {
-                            if constexpr (sizeof(T) == 4) {
+                            if constexpr (sizeof(ST) == 4) {
                                 const float4 w = *reinterpret_cast<const float4*>(brow + z0);
-                                bv[0] = w.x; bv[1] = w.y; bv[2] = w.z; bv[3] = w.w;
+                                bv[0] = T(w.x); bv[1] = T(w.y); bv[2] = T(w.z); bv[3] = T(w.w);
                             } else {
                                 const double2 w = *reinterpret_cast<const double2*>(brow + z0);
-                                bv[0] = w.x; bv[1] = w.y;
+                                bv[0] = T(w.x); bv[1] = T(w.y);
                             }
                         }
 #pragma unroll
@@ -760,11 +821,11 @@ collide_kernel(CollideArgs args) {
                             const T q = fma(rval(z), kn, -(cxy + czt[z]));
                             T o = stepm ? fma(dt, q, col[z]) : q;
                             if (heun) o = T(0.5) * (o + bv[j]);
-                            bad |= !isfinite(o);
-                            neg |= stepm && (o < T(0));
-                            res[j] = o;
+                            res[j] = ST(o);
+                            bad |= !isfinite(res[j]);
+                            neg |= stepm && (res[j] < ST(0));
                         }
-                        if constexpr (sizeof(T) == 4)
+                        if constexpr (sizeof(ST) == 4)
                             *reinterpret_cast<float4*>(dst + z0) = make_float4(res[0], res[1], res[2], res[3]);
                         else
                             *reinterpret_cast<double2*>(dst + z0) = make_double2(res[0], res[1]);

@@ -216,6 +216,10 @@ struct Args {
     int* flags;                 // health bits
     long ncells;                // cells to process (entries of `cells`, if given)
     const int* cells;           // optional list of cell indices (routed cells), else 0 .. ncells-1
+    const int* cells_count;     // optional device count of `cells` (replaces ncells)
+    int* esc_list;              // precision escalation (as in the cluster kernel): cells whose bound
+    int* esc_count;             //   esc_c ||L|| / Kn exceeds esc_tol ||Q|| are listed here, not written
+    double esc_c2, esc_tol2;
     int nc[3], bc[3];
     int M;
     double L, inv_kn, dt;
@@ -240,9 +244,9 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
     __shared__ int dsm[3 * N];
     __shared__ float vg[N];
     __shared__ double vgd[N];
-    __shared__ double red[NTH / 32][5];
+    __shared__ double red[NTH / 32][7];
     __shared__ double mu[5];
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_esc;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, cs = warp >> 2;
@@ -318,7 +322,8 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
         commit(bar);
     };
 
-    for (long item = blockIdx.x; item < a.ncells; item += gridDim.x) {
+    const long nitems = a.cells_count ? (long)*a.cells_count : a.ncells;
+    for (long item = blockIdx.x; item < nitems; item += gridDim.x) {
         const long cell = a.cells ? (long)a.cells[item] : item;
         int cx, cy, cz;
         cell_coords(cell, ncy, ncz, cx, cy, cz);
@@ -343,6 +348,7 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
             return a.f + ((long)sx * ncy + sy) * ncz * N3 + ((long)qx * N + qy) * N;
         };
         double s5[5] = {0, 0, 0, 0, 0};
+        float e_ll = 0.f, e_qq = 0.f;   // escalation bound: sum (f* l)^2, sum q^2
 
         // transform t: -1 forward (f* -> fh), 0..M-1 gain directions, M loss
         for (int t = -1; t <= a.M; ++t) {
@@ -556,6 +562,9 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
                     for (int j = 0; j < ZS; ++j) {
                         const float fv = frow(x0 + j, yy)[zoff[zz]];
                         const float q = fmaf(-fv, dr[j], gv[j]) * kn;
+                        const float lz = fv * dr[j];
+                        e_ll = fmaf(lz, lz, e_ll);
+                        e_qq = fmaf(q, q, e_qq);
                         gv[j] = q;
                         const double qd = (double)q, vx = vgd[x0 + j];
                         sr += qd;
@@ -585,23 +594,50 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
             if (lane == 0) red[warp][i] = v;
         }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            e_ll += __shfl_xor_sync(0xffffffffu, e_ll, off);
+            e_qq += __shfl_xor_sync(0xffffffffu, e_qq, off);
+        }
+        if (lane == 0) {
+            red[warp][5] = (double)e_ll;
+            red[warp][6] = (double)e_qq;
+        }
         __syncthreads();
         if (tid < 5) {
-            double tot[5] = {0, 0, 0, 0, 0};
+            double tot[7] = {0, 0, 0, 0, 0, 0, 0};
             for (int w = 0; w < NTH / 32; ++w)
-                for (int j = 0; j < 5; ++j) tot[j] += red[w][j];
-            double acc = 0.0;
-            for (int j = 0; j < 5; ++j) acc += a.P[tid * 5 + j] * tot[j];
-            mu[tid] = acc;
+                for (int j = 0; j < 7; ++j) tot[j] += red[w][j];
+            double m[5];
+            for (int i = 0; i < 5; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j < 5; ++j) acc += a.P[i * 5 + j] * tot[j];
+                m[i] = acc;
+            }
+            mu[tid] = m[tid];
+            if (tid == 0) {
+                // ||Q_proj||^2 = ||Q||^2 - mu . s (s = the moment sums of Q)
+                bool esc = false;
+                if (a.esc_list) {
+                    double ms = 0.0;
+                    for (int i = 0; i < 5; ++i) ms += m[i] * tot[i];
+                    const double qp = tot[6] - ms, k2 = a.inv_kn * a.inv_kn;
+                    esc = a.esc_c2 * k2 * tot[5] > a.esc_tol2 * (qp > 0.0 ? qp : 0.0);
+                }
+                s_esc = esc ? 1 : 0;
+                if (esc) a.esc_list[atomicAdd(a.esc_count, 1)] = (int)cell;
+            }
         }
         __syncthreads();
         fence_after();
+        // an escalated cell is left to the next tier
+        const bool escalated = s_esc != 0;
         const float m0 = (float)mu[0], m1 = (float)mu[1], m2 = (float)mu[2], m3 = (float)mu[3], m4 = (float)mu[4];
         const bool stepm = a.mode == 1;
         const float dt = (float)a.dt;
         bool bad = false, neg = false;
 #pragma unroll 1
-        for (int T = 0; T < TILES; ++T) {
+        for (int T = 0; T < (escalated ? 0 : TILES); ++T) {
             const int r = 128 * T + 32 * quad + lane, yy = r / N, zz = r % N;
             const int x0 = ZS * cs;
             float gv[ZS];
@@ -710,6 +746,11 @@ cudaError_t launch_collide_tc(int n, const TcLaunch& l, cudaStream_t s) {
     a.flags = l.flags;
     a.ncells = l.ncells;
     a.cells = l.cells;
+    a.cells_count = l.cells_count;
+    a.esc_list = l.esc_list;
+    a.esc_count = l.esc_count;
+    a.esc_c2 = l.esc_c2;
+    a.esc_tol2 = l.esc_tol2;
     for (int i = 0; i < 3; ++i) {
         a.nc[i] = l.nc[i];
         a.bc[i] = l.bc[i];

@@ -388,6 +388,9 @@ extern "C" fks_status fks_set_dealias(fks_ctx* c, int on) {
     fks_ctx* in = nullptr;
     fks_status st = fks_init(&g, &vb, &c->kern, &c->dirs, c->fp64 ? FKS_FP64 : FKS_FP32, &in);
     if (st != FKS_OK) return fks_internal_fail(c, st, "inner 2n context");
+    // the inner grid's unprojected operator keeps its own arithmetic (the escalation bound is
+    // stated for the projected n-grid result)
+    if (!c->fp64) fks_set_escalation(in, 0.0);
     const size_t esz = c->fp64 ? 8 : 4;
     const size_t m3 = (size_t)8 * c->n * c->n * c->n;
     std::vector<double> P, T;

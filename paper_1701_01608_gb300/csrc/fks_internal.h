@@ -25,6 +25,18 @@ struct CollideVariant {
 bool find_collide_variant(bool fp64, int N, int C, CollideVariant* out);
 bool find_collide_variant_f32(int N, int C, CollideVariant* out);
 bool find_collide_variant_f64(int N, int C, CollideVariant* out);
+// FP64 arithmetic over an FP32 state (the last tier of the precision escalation)
+bool find_collide_variant_mixed(int N, int C, CollideVariant* out);
+
+// One tier of the precision escalation: the cluster kernel that recomputes the listed cells of the
+// tier before it (FP32 arithmetic, or FP64 arithmetic over the FP32 state) with its own tables.
+struct EscTier {
+    bool fp64 = false;
+    CollideVariant var{};
+    int C = 0;
+    int max_clusters = 0;
+    void* tables = nullptr;
+};
 
 // Arguments of the BGK relaxation kernel (fks_bgk.cu).
 struct BgkArgs {
@@ -57,6 +69,10 @@ struct TcLaunch {
     int* flags;
     long ncells;
     const int* cells = nullptr; // optional device list of cell indices (the cells to process)
+    const int* cells_count = nullptr;   // optional device count of `cells` (ncells then only sizes the grid)
+    int* esc_list = nullptr;    // precision escalation output (see CollideArgs)
+    int* esc_count = nullptr;
+    double esc_c2 = 0.0, esc_tol2 = 0.0;
     int nc[3], bc[3];
     int M;
     double L, inv_kn, dt;
@@ -161,9 +177,15 @@ struct fks_ctx {
     double* s_rho = nullptr;
     float* s_dist = nullptr;
     float* s_ind = nullptr;
-    fks::BatchItem* s_items = nullptr;
-    int* s_cells = nullptr;     // routed cell indices (tensor-core contexts)
+    int* s_cells = nullptr;     // routed cell indices
     int* s_count = nullptr;
+    // precision escalation (FP32 and split-BF16 contexts): cells whose error bound exceeds esc_tol are
+    // listed by the context's kernel and recomputed by esc[0] (whose own failures go to esc[1])
+    double esc_tol = 0.0;       // 0: off
+    int esc_ntier = 0;
+    fks::EscTier esc[2];
+    int* esc_lists = nullptr;   // [2][ncells]
+    int* esc_counts = nullptr;  // [2]
 };
 
 
@@ -173,9 +195,9 @@ struct fks_ctx {
 // (C linkage: they are defined beside the C ABI.)
 extern "C" fks_status fks_internal_fail(fks_ctx* c, fks_status st, const std::string& msg);
 extern "C" fks_status fks_internal_collide(fks_ctx* c, const void* f, void* out, int mode, cudaStream_t s);
-// collide (projected) only the listed cells of a tensor-core context
-extern "C" fks_status fks_internal_collide_cells(fks_ctx* c, const void* f, void* out, const int* cells, long ncells,
-                                                 cudaStream_t s);
+// collide (projected, with the context's escalation) only the cells cells[0 .. *count) (a device count)
+extern "C" fks_status fks_internal_collide_list(fks_ctx* c, const void* f, void* out, const int* cells, const int* count,
+                                                cudaStream_t s);
 // variant B (fks_dealias.cu)
 fks_status launch_dealias(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
                           cudaStream_t s);

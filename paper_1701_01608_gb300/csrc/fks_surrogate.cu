@@ -7,7 +7,8 @@
 //             indicator = ind_scale (d + defect), defect = relative size of the
 //             raw output's moments
 //   routing : cells whose indicator exceeds the threshold are recomputed by
-//             the spectral kernel (batch mode over the routed cells).
+//             the context's spectral kernel over a device list of the routed
+//             cells (with the context's precision escalation).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -195,29 +196,7 @@ __global__ void __launch_bounds__(BS) output_kernel(int n, double L, long c0, lo
     }
 }
 
-// descriptors of the cells whose indicator exceeds the threshold
-__global__ void route_kernel(long ncells, const float* __restrict__ ind, float threshold, int n, const float* f,
-                             float* Q, const void* tables, const double* P, double inv_kn, double L,
-                             BatchItem* __restrict__ items, int* __restrict__ count) {
-    const long n3 = (long)n * n * n;
-    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncells; c += (long)gridDim.x * blockDim.x) {
-        if (!(ind[c] <= threshold)) {   // NaN indicators are routed too
-            const int slot = atomicAdd(count, 1);
-            BatchItem it;
-            it.f = f + c * n3;
-            it.out = Q + c * n3;
-            it.tables = tables;
-            it.P = P;
-            it.inv_kn = inv_kn;
-            it.dt = 0.0;
-            it.L = L;
-            it.pad_ = 0.0;
-            items[slot] = it;
-        }
-    }
-}
-
-// indices of the cells whose indicator exceeds the threshold (tensor-core contexts)
+// indices of the cells whose indicator exceeds the threshold (NaN indicators are routed too)
 __global__ void route_list_kernel(long ncells, const float* __restrict__ ind, float threshold, int* __restrict__ cells,
                                   int* __restrict__ count) {
     for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncells; c += (long)gridDim.x * blockDim.x)
@@ -256,7 +235,7 @@ fks_status fks_surrogate_collide(fks_ctx* c, fks_net* net, const void* f, void* 
     // per-context surrogate workspace (rho, distance, indicator, routed descriptors, count)
     if (!c->s_rho) {
         if (cudaMalloc(&c->s_rho, sizeof(double) * nc) != cudaSuccess || cudaMalloc(&c->s_dist, sizeof(float) * nc) ||
-            cudaMalloc(&c->s_ind, sizeof(float) * nc) || cudaMalloc(&c->s_items, sizeof(BatchItem) * nc) ||
+            cudaMalloc(&c->s_ind, sizeof(float) * nc) ||
             cudaMalloc(&c->s_count, sizeof(int)) || cudaMalloc(&c->s_cells, sizeof(int) * (nc > 0 ? nc : 1))) {
             c->err = "surrogate workspace";
             return alloc_failure();
@@ -283,52 +262,18 @@ fks_status fks_surrogate_collide(fks_ctx* c, fks_net* net, const void* f, void* 
         c->launches += 2;
     }
     if (cudaMemsetAsync(c->s_count, 0, sizeof(int), s) != cudaSuccess) return FKS_ERR_CUDA;
-    if (c->tc)
-        surr::route_list_kernel<<<256, 256, 0, s>>>(nc, c->s_ind, (float)threshold, c->s_cells, c->s_count);
-    else
-        surr::route_kernel<<<256, 256, 0, s>>>(nc, c->s_ind, (float)threshold, n, fin, Qo, c->tables, c->d_P,
-                                              1.0 / c->kern.knudsen, c->vbox.L, c->s_items, c->s_count);
+    surr::route_list_kernel<<<256, 256, 0, s>>>(nc, c->s_ind, (float)threshold, c->s_cells, c->s_count);
     c->launches += 1;
-    int count = 0;
-    if (cudaMemcpyAsync(&count, c->s_count, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return FKS_ERR_CUDA;
-    if (nrouted) *nrouted = count;
-    if (count > 0 && c->tc) {
-        // split-BF16 tensor-core operator (projected) on the routed cells
-        return fks_internal_collide_cells(c, f, Q, c->s_cells, count, s);
-    }
-    if (count > 0) {
-        // spectral operator (projected) on the routed cells, in batch mode
-        CollideArgs a;
-        std::memset(&a, 0, sizeof(a));
-        a.items = c->s_items;
-        a.ncells = count;
-        a.nc[0] = a.nc[1] = a.nc[2] = 1;
-        a.M = c->M;
-        a.L = c->vbox.L;
-        a.mode = 0;
-        a.flags = c->d_flags;
-        const long nclus = count < c->max_clusters ? count : c->max_clusters;
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = c->C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3((unsigned)(nclus * c->C), 1, 1);
-        cfg.blockDim = dim3(c->var.NT, 1, 1);
-        cfg.dynamicSmemBytes = c->var.smem;
-        cfg.stream = s;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        void* args[] = {&a};
-        cudaError_t e = cudaLaunchKernelExC(&cfg, c->var.func_batch, args);
-        if (e != cudaSuccess) {
-            c->err = std::string("routed spectral launch: ") + cudaGetErrorString(e);
+    // the context's spectral operator (projected, with its precision escalation) on the routed cells;
+    // the kernels read the count on the device
+    const fks_status st = fks_internal_collide_list(c, f, Q, c->s_cells, c->s_count, s);
+    if (st != FKS_OK) return st;
+    if (nrouted) {
+        int count = 0;
+        if (cudaMemcpyAsync(&count, c->s_count, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
             return FKS_ERR_CUDA;
-        }
-        c->launches += 1;
+        *nrouted = count;
     }
     return cudaGetLastError() == cudaSuccess ? FKS_OK : FKS_ERR_CUDA;
 }

@@ -67,7 +67,8 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
            "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
            "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias", "fks_step_host", "fks_vhs_factor",
-           "fks_step_strang", "fks_alu_peak", "fks_step_exp"]
+           "fks_step_strang", "fks_alu_peak", "fks_step_exp", "fks_set_escalation", "fks_get_escalation",
+           "fks_batch_set_escalation", "fks_batch_get_escalation"]
 
 
 def lib(build: bool = True):
@@ -112,6 +113,8 @@ def lib(build: bool = True):
     L.fks_batch_step.argtypes = [P, PP, PP, PD, P]
     L.fks_batch_run.argtypes = [P, PP, PP, PD, I, P]
     L.fks_batch_check.argtypes = [P, P, PI]
+    L.fks_batch_set_escalation.argtypes = [P, D]
+    L.fks_batch_get_escalation.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
     L.fks_batch_cluster_size.argtypes = [P, I]
     L.fks_batch_set_cluster_size.argtypes = [P, I, I]
     L.fks_batch_launch_count.argtypes = [P]
@@ -142,6 +145,8 @@ def lib(build: bool = True):
     L.fks_selftest_wait.argtypes = [ctypes.c_long, P]
     L.fks_alu_peak.argtypes = [I, ctypes.POINTER(D), P]
     L.fks_set_dealias.argtypes = [P, I]
+    L.fks_set_escalation.argtypes = [P, D]
+    L.fks_get_escalation.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
     L.fks_step_host.argtypes = [P, P, P, D, P]
     L.fks_destroy.argtypes = [P]
     L.fks_destroy.restype = None
@@ -240,6 +245,18 @@ class Context:
                 raise TypeError(f"expected a contiguous CPU tensor of {self.dtype}")
         self._check(self._L.fks_step_host(self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(f_out.data_ptr()),
                                           float(dt), _stream_ptr(stream)), "fks_step_host")
+
+    def set_escalation(self, tol: float):
+        """Precision escalation: cells whose error bound exceeds tol * ||Q|| are recomputed at
+        higher precision (0: off)."""
+        self._check(self._L.fks_set_escalation(self._h, float(tol)), "fks_set_escalation")
+
+    def escalation(self) -> tuple[float, tuple[int, int]]:
+        """(tolerance, cells sent to the first and second tier by the last collision or step)."""
+        tol = ctypes.c_double()
+        counts = (ctypes.c_long * 2)()
+        self._check(self._L.fks_get_escalation(self._h, ctypes.byref(tol), counts), "fks_get_escalation")
+        return tol.value, (counts[0], counts[1])
 
     def set_dealias(self, on: bool = True):
         """Variant B: the 2n-padded (de-aliased) operator for this context's collisions."""
@@ -398,6 +415,18 @@ class Batch:
 
     def cluster_size(self, n: int) -> int:
         return self._L.fks_batch_cluster_size(self._h, n)
+
+    def set_escalation(self, tol: float):
+        """Precision escalation of FP32 batches (0: off)."""
+        self._check(self._L.fks_batch_set_escalation(self._h, float(tol)), "fks_batch_set_escalation")
+
+    def escalation(self) -> tuple[float, int]:
+        """(tolerance, problems recomputed in FP64 by the last launch)."""
+        tol = ctypes.c_double()
+        cnt = ctypes.c_long()
+        self._check(self._L.fks_batch_get_escalation(self._h, ctypes.byref(tol), ctypes.byref(cnt)),
+                    "fks_batch_get_escalation")
+        return tol.value, cnt.value
 
     def set_cluster_size(self, n: int, C: int):
         self._check(self._L.fks_batch_set_cluster_size(self._h, n, C), "fks_batch_set_cluster_size")

@@ -1,0 +1,28 @@
+// Host harness of the double-float arithmetic (csrc/fks_dfloat.cuh) of the collision kernel's
+// last escalation tier: one sum or product of two pairs, returned as its (hi, lo) floats.
+#include "fks_dfloat.cuh"
+
+extern "C" {
+
+int fks_test_dd_add(float ahi, float alo, float bhi, float blo, float* out) {
+    const fks::dfloat r = fks::dfloat(ahi, alo) + fks::dfloat(bhi, blo);
+    out[0] = r.hi;
+    out[1] = r.lo;
+    return 0;
+}
+
+int fks_test_dd_mul(float ahi, float alo, float bhi, float blo, float* out) {
+    const fks::dfloat r = fks::dfloat(ahi, alo) * fks::dfloat(bhi, blo);
+    out[0] = r.hi;
+    out[1] = r.lo;
+    return 0;
+}
+
+int fks_test_dd_from_double(double d, float* out) {
+    const fks::dfloat r(d);
+    out[0] = r.hi;
+    out[1] = r.lo;
+    return 0;
+}
+
+}  // extern "C"

@@ -1,8 +1,10 @@
 // Host build of the library's register FFTs (csrc/fks_fft.cuh) for CPU tests:
 // fks_test_fft(n, sign, prec, in, out) transforms one complex vector of length n
-// (interleaved doubles), fks_test_c2r(n, in, out) runs the packed C2R.
+// (interleaved doubles), fks_test_c2r(n, in, out) runs the packed C2R; prec 0 float,
+// 1 double, 2 double-float (csrc/fks_dfloat.cuh).
 #include <cstring>
 
+#include "fks_dfloat.cuh"
 #include "fks_fft.cuh"
 
 template <int N, typename T>
@@ -49,10 +51,12 @@ static int dispatch_c2r(int n, const double* in, double* out) {
     return 1;
 }
 
-extern "C" int fks_test_fft(int n, int sign, int fp64, const double* in, double* out) {
-    return fp64 ? dispatch_fft<double>(n, sign, in, out) : dispatch_fft<float>(n, sign, in, out);
+extern "C" int fks_test_fft(int n, int sign, int prec, const double* in, double* out) {
+    if (prec == 2) return dispatch_fft<fks::dfloat>(n, sign, in, out);
+    return prec ? dispatch_fft<double>(n, sign, in, out) : dispatch_fft<float>(n, sign, in, out);
 }
 
-extern "C" int fks_test_c2r(int n, int fp64, const double* in, double* out) {
-    return fp64 ? dispatch_c2r<double>(n, in, out) : dispatch_c2r<float>(n, in, out);
+extern "C" int fks_test_c2r(int n, int prec, const double* in, double* out) {
+    if (prec == 2) return dispatch_c2r<fks::dfloat>(n, in, out);
+    return prec ? dispatch_c2r<double>(n, in, out) : dispatch_c2r<float>(n, in, out);
 }

@@ -1,5 +1,6 @@
 """The library's register FFTs (csrc/fks_fft.cuh), compiled for the host,
-against numpy.fft: mixed radix 2/3/4/8 transforms and the packed C2R."""
+against numpy.fft: mixed radix 2/3/4/8 transforms and the packed C2R, in float,
+double and double-float (csrc/fks_dfloat.cuh) arithmetic."""
 import ctypes
 import os
 import subprocess
@@ -14,7 +15,7 @@ CSRC = os.path.join(os.path.dirname(HERE), "paper_1701_01608_gb300", "csrc")
 @pytest.fixture(scope="module")
 def harness(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("fft") / "libfft_host.so")
-    cmd = ["nvcc", "-std=c++17", "-O2", "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr",
+    cmd = ["nvcc", "-std=c++17", "-O2", "-Xcompiler", "-fPIC,-ffp-contract=off", "-shared", "--expt-relaxed-constexpr",
            "-I", CSRC, os.path.join(HERE, "harness", "fft_host.cu"), "-o", out]
     subprocess.run(cmd, check=True, capture_output=True)
     lib = ctypes.CDLL(out)
@@ -24,7 +25,10 @@ def harness(tmp_path_factory):
     return lib
 
 
-@pytest.mark.parametrize("fp64", [1, 0])
+TOL = {0: 1e-6, 1: 1e-14, 2: 1e-13}   # float, double, double-float (~48 bits)
+
+
+@pytest.mark.parametrize("fp64", [1, 0, 2])
 @pytest.mark.parametrize("n", [2, 3, 4, 8, 12, 16, 24, 32])
 @pytest.mark.parametrize("sign", [-1, 1])
 def test_fft_matches_numpy(harness, n, sign, fp64):
@@ -36,11 +40,10 @@ def test_fft_matches_numpy(harness, n, sign, fp64):
     got = out.view(np.complex128)
     xin = inp.view(np.complex128) if fp64 else inp.astype(np.float32).astype(np.float64).view(np.complex128)
     want = np.fft.fft(xin) if sign < 0 else n * np.fft.ifft(xin)
-    tol = 1e-14 if fp64 else 1e-6
-    assert np.abs(got - want).max() < tol * np.abs(want).max()
+    assert np.abs(got - want).max() < TOL[fp64] * np.abs(want).max()
 
 
-@pytest.mark.parametrize("fp64", [1, 0])
+@pytest.mark.parametrize("fp64", [1, 0, 2])
 @pytest.mark.parametrize("n", [8, 16, 24, 32])
 def test_c2r_matches_numpy(harness, n, fp64):
     rng = np.random.default_rng(n)
@@ -54,5 +57,4 @@ def test_c2r_matches_numpy(harness, n, fp64):
     out = np.empty(n)
     assert harness.fks_test_c2r(n, fp64, inp.ctypes.data, out.ctypes.data) == 0
     want = n * np.fft.irfft(X, n)
-    tol = 1e-14 if fp64 else 1e-6
-    assert np.abs(out - want).max() < tol * np.abs(want).max()
+    assert np.abs(out - want).max() < TOL[fp64] * np.abs(want).max()

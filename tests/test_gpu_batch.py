@@ -4,7 +4,6 @@ graph replay against step-by-step launches; the autotuner."""
 import numpy as np
 import pytest
 
-from conftest import fp32_within
 from paper_1701_01608_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -52,11 +51,7 @@ def test_batch_collide_and_step_match_oracle(fks, oracle, prec, tol):
         fin = f.double().cpu().numpy()
         t = oracle.tables(p["n"], p["L"], p["kernel"], 0.25, 4, 8, 0)
         Qo = oracle.collide(fin, t, kn=p["kn"])
-        if prec == 0:
-            assert rel(Q.double().cpu().numpy(), Qo) < tol, (p["n"], p["kernel"])
-        else:
-            _, Lo = oracle.gain_loss(fin, t)
-            assert fp32_within(Q.double().cpu().numpy(), Qo, Lo / p["kn"]), (p["n"], p["kernel"])
+        assert rel(Q.double().cpu().numpy(), Qo) < tol, (p["n"], p["kernel"])
         want = fin + dt * Qo
         assert np.linalg.norm(o.double().cpu().numpy() - want) / np.linalg.norm(dt * Qo) < 10 * tol + 1e-6
 
@@ -97,8 +92,7 @@ def test_autotune_keeps_parity(fks, oracle, tmp_path):
         t = oracle.tables(p["n"], p["L"], p["kernel"], 0.25, 4, 8, 0)
         fin = f.double().cpu().numpy()
         Qo = oracle.collide(fin, t, kn=p["kn"])
-        _, Lo = oracle.gain_loss(fin, t)
-        assert fp32_within(Q.double().cpu().numpy(), Qo, Lo / p["kn"])
+        assert rel(Q.double().cpu().numpy(), Qo) < 1e-5
     # a second call reads the cache
     assert autotune.tune_batch(b, fs, Qs, precision=1, cache=str(tmp_path / "tune.json")) == chosen
 

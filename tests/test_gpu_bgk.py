@@ -4,7 +4,6 @@ full 32^3 x 32^3 FP32 step on sampled cells."""
 import numpy as np
 import pytest
 
-from conftest import fp32_within
 from paper_1701_01608_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -42,11 +41,7 @@ def test_bgk_collide_matches_oracle(fks, oracle, n, prec):
     Qo = oracle.bgk(fin, n, L, kn=0.2)
     Qg = Q.double().cpu().numpy()
     for i in range(5):
-        if prec == 0:
-            assert rel(Qg[i], Qo[i]) < 1e-12
-        else:
-            nu_f = fin[i] * fin[i].sum() * (2 * L / n) ** 3 / 0.2
-            assert fp32_within(Qg[i], Qo[i], nu_f)
+        assert rel(Qg[i], Qo[i]) < (1e-12 if prec == 0 else 1e-5), (i, rel(Qg[i], Qo[i]))
 
 
 def test_bgk_steps_ragged_specular(fks, oracle):
@@ -104,11 +99,7 @@ def test_bgk_vacuum_cell_does_not_relax(fks, oracle, n, prec):
     Qo = oracle.bgk(fd.double().cpu().numpy(), n, L, kn=0.2)
     assert np.all(Qo[1] == 0.0)
     for i in (0, 2):
-        if prec == 0:
-            assert rel(Qg[i], Qo[i]) < 1e-12
-        else:
-            fin = fd.double().cpu().numpy()[i]
-            assert fp32_within(Qg[i], Qo[i], fin * fin.sum() * (2 * L / n) ** 3 / 0.2)
+        assert rel(Qg[i], Qo[i]) < (1e-12 if prec == 0 else 1e-5), (i, rel(Qg[i], Qo[i]))
 
 
 @pytest.mark.parametrize("n,prec,kn", [(16, 0, 0.1), (32, 1, 0.01), (32, 1, 1e-6), (16, 0, 1e-6)])

@@ -1,0 +1,144 @@
+"""Precision escalation near equilibrium (the FP64 kept for the gain-loss
+subtraction near equilibrium): the FP32 and split-BF16 paths against the FP64
+oracle at the plain per-cell bounds (relative L2 of Q <= 1e-5 and <= 1e-3) on
+shock-tube cells, n = 32, M = 32, hard spheres, Kn = 0.01:
+  - the exact discrete Maxwellians of the initial state (left rho = 1, T = 1;
+    right rho = 0.125, T = 0.8), where Q is the discrete operator's own
+    residual, ~1e-7 .. 3e-6 of the loss term (||L|| / ||Q|| up to ~1e7);
+  - the left state times (1 + eps U(-1, 1)), eps = 1e-2 .. 1e-5;
+  - cells of the 32-cell tube after 4 and 16 oracle steps (dt = 1e-3).
+Without the escalation the same cells miss the bounds by orders of magnitude."""
+import numpy as np
+import pytest
+
+from conftest import BF16_REL, FP32_REL
+from paper_1701_01608_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+N, L, KN, A = 32, 10.0, 0.01, (4, 8)
+
+
+@pytest.fixture(scope="module")
+def fks():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_01608_gb300 import fks
+    fks.lib()
+    return fks
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def tab(oracle):
+    return oracle.tables(N, L, 0, 0.25, A[0], A[1], 0)
+
+
+@pytest.fixture(scope="module")
+def shock_cells(oracle, tab):
+    """FP32-representable cells (the GPU reads FP32) and their FP64 oracle Q."""
+    w = I.config_shock_tube(ncell=(32, 1, 1), n=N, L=L)
+    cells = [w.f0[3], w.f0[28]]
+    rng = np.random.Generator(np.random.PCG64(11))
+    for eps in (1e-2, 1e-3, 1e-4, 1e-5):
+        cells.append(w.f0[3] * (1.0 + eps * rng.uniform(-1.0, 1.0, size=w.f0[3].shape)))
+    sol = oracle.Solver((32, 1, 1), (0, 0, 0), (1, 1, 1), (1, 0, 0), N, L, tab, KN)
+    f = w.f0.astype(np.float32).astype(np.float64)
+    for k in range(16):
+        f = sol.step(f, 1e-3)
+        if k + 1 in (4, 16):
+            cells += [f[i] for i in (13, 15, 16, 18, 21)]
+    f32 = np.stack(cells).astype(np.float32)
+    f64 = f32.astype(np.float64)
+    Qo = oracle.collide(f64, tab, kn=KN)
+    kappa = np.array([np.linalg.norm(oracle.gain_loss(c, tab)[1]) / KN / np.linalg.norm(q) for c, q in zip(f64, Qo)])
+    return f32, Qo, kappa
+
+
+def make_ctx(fks, nc, prec, bc=(0, 0, 0)):
+    return fks.Context(fks.Config(ncell=(nc, 1, 1), bc=bc, n=N, L=L, kn=KN, A1=A[0], A2=A[1], precision=prec))
+
+
+@pytest.mark.parametrize("prec,tol", [(1, FP32_REL), (2, BF16_REL)])
+def test_near_equilibrium_cells_meet_plain_bound(fks, shock_cells, prec, tol):
+    f32, Qo, kappa = shock_cells
+    # the sample spans the conditioning range of the workload
+    assert kappa.max() > 1e5 and kappa.min() < 100
+    nc = f32.shape[0]
+    ctx = make_ctx(fks, nc, prec)
+    assert ctx.escalation()[0] == tol   # on by default at the stated bound
+    fd = torch.from_numpy(f32).cuda()
+    Q = torch.empty_like(fd)
+    ctx.collide(fd, Q)
+    assert ctx.check() == 0
+    Qg = Q.double().cpu().numpy()
+    errs = [rel(Qg[c], Qo[c]) for c in range(nc)]
+    for c in range(nc):
+        assert errs[c] < tol, (c, kappa[c], errs[c])
+    _, counts = ctx.escalation()
+    assert counts[0] > 0   # the exact Maxwellians at least
+    if prec == 2:
+        assert counts[1] > 0   # cells beyond the FP32 tier's reach go on to FP64
+    # the same cells without escalation: the raw arithmetic misses the bound
+    ctx.set_escalation(0.0)
+    ctx.collide(fd, Q)
+    raw = [rel(Q[c].double().cpu().numpy(), Qo[c]) for c in range(nc)]
+    assert max(raw) > 10 * tol
+    # the escalated result is deterministic (the order of the device list does not matter)
+    ctx.set_escalation(tol)
+    Q2 = torch.empty_like(fd)
+    ctx.collide(fd, Q2)
+    assert torch.equal(Q2, torch.from_numpy(Qg.astype(np.float32)).cuda())
+
+
+def test_escalated_step_fp32(fks, oracle, tab, shock_cells):
+    """One fused transport + collision step of the 32-cell tube after 4 oracle steps: the
+    increment f_out - f* against dt Q of the oracle, per cell, up to the FP32 rounding of the
+    stored state."""
+    w = I.config_shock_tube(ncell=(32, 1, 1), n=N, L=L)
+    sol = oracle.Solver((32, 1, 1), (0, 0, 0), (1, 1, 1), (1, 0, 0), N, L, tab, KN)
+    f = w.f0.astype(np.float32).astype(np.float64)
+    dt = 1e-3
+    for _ in range(4):
+        f = sol.step(f, dt)
+    f32 = f.astype(np.float32)
+    ctx = make_ctx(fks, 32, 1, bc=(1, 0, 0))   # the tube's specular walls in x
+    ctx.set_offsets(sol.s.copy())   # continue from the oracle's offsets
+    fd = torch.from_numpy(f32).cuda()
+    out = torch.empty_like(fd)
+    ctx.step(fd, out, dt)
+    assert ctx.check() & 1 == 0
+    fsh = sol.transport(f32.astype(np.float64), dt)   # f* by the oracle's transport
+    Qo = oracle.collide(fsh, tab, kn=KN)
+    got = out.double().cpu().numpy()
+    for c in range(32):
+        err = np.linalg.norm(got[c] - fsh[c] - dt * Qo[c])
+        assert err <= FP32_REL * np.linalg.norm(dt * Qo[c]) + 2.0 ** -24 * np.linalg.norm(got[c]) * 1.5, c
+    assert ctx.escalation()[1][0] > 0
+
+
+def test_batch_escalation(fks, oracle):
+    """An FP32 batch problem with ||L|| / ||Q|| ~ 270 (two nearby Maxwellians): without the
+    escalation its error is above 1e-5, with it the plain bound holds."""
+    n, Lb, kn = 16, 8.0, 0.05
+    f = 0.5 * (I.maxwellian(n, Lb, u=(0.2, 0.0, 0.0), T=1.0) + I.maxwellian(n, Lb, u=(-0.2, 0.1, 0.0), T=1.05))
+    probs = [dict(n=n, L=Lb, kernel=0, kn=kn, f0=f[None]),
+             dict(n=32, L=10.0, kernel=0, kn=kn, f0=I.maxwellian(32, 10.0, T=0.9)[None])]
+    b = fks.Batch(probs, A1=4, A2=8, precision=1)
+    fs = [torch.from_numpy(p["f0"]).to("cuda", torch.float32).contiguous() for p in probs]
+    Qs = [torch.empty_like(x) for x in fs]
+    b.collide(fs, Qs)
+    assert b.escalation()[1] >= 1
+    ref = []
+    for p, x, Q in zip(probs, fs, Qs):
+        t = oracle.tables(p["n"], p["L"], 0, 0.25, 4, 8, 0)
+        Qo = oracle.collide(x.double().cpu().numpy(), t, kn=kn)
+        ref.append(Qo)
+        assert rel(Q.double().cpu().numpy(), Qo) < FP32_REL
+    b.set_escalation(0.0)
+    b.collide(fs, Qs)
+    assert max(rel(Q.double().cpu().numpy(), Qo) for Q, Qo in zip(Qs, ref)) > FP32_REL

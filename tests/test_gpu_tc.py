@@ -1,12 +1,12 @@
 """GPU parity of the split-BF16 tensor-core collision path (FKS_BF16X3) against
 the oracle: every 3-D DFT as tcgen05 products of BF16 pairs with FP32
 accumulation; table products, loss, projection and Euler step in FP32 with
-FP64 moment sums.  Tolerance: relative L2 of Q <= 1e-3, read with the
-conditioning of Q = G - L (tests/conftest.py::bf16_within)."""
+FP64 moment sums.  Tolerance: relative L2 of Q <= 1e-3 per cell (cells whose
+error bound exceeds it are recomputed by the escalation tiers)."""
 import numpy as np
 import pytest
 
-from conftest import BF16_REL, bf16_within
+from conftest import BF16_REL
 from paper_1701_01608_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -57,15 +57,12 @@ def test_tc_collide_matches_oracle(fks, oracle, n, kernel, L, A, nc, kn):
     Qg = Q.double().cpu().numpy()
     idx = range(nc) if nc <= 16 else list(range(0, nc, 7)) + [nc - 1]
     for c in idx:
-        Lc = oracle.gain_loss(f64[c], tab)[1] / kn
-        assert bf16_within(Qg[c], Qo[c], Lc), (c, rel(Qg[c], Qo[c]))
-        # these cells are far from equilibrium: the plain relative bound holds
-        assert rel(Qg[c], Qo[c]) < BF16_REL
+        assert rel(Qg[c], Qo[c]) < BF16_REL, c
 
 
 def test_tc_near_equilibrium_cell(fks, oracle):
-    """A nearly Maxwellian cell: ||L|| / ||Q|| is large and the error is bounded
-    on the loss scale."""
+    """A nearly Maxwellian cell (||L|| / ||Q|| > 40): the split-BF16 bound alone would miss 1e-3,
+    the escalation recomputes the cell and the plain bound holds."""
     n, L = 16, 8.0
     f = (I.maxwellian(n, L, 1.0, (0.1, 0.0, -0.2), 1.1) * (1 + 1e-3 * np.cos(np.arange(n ** 3).reshape(n, n, n))))
     f = f[None].astype(np.float32)
@@ -77,7 +74,7 @@ def test_tc_near_equilibrium_cell(fks, oracle):
     Qo = oracle.collide(f.astype(np.float64), tab, kn=1.0)
     G, Lo = oracle.gain_loss(f[0].astype(np.float64), tab)
     assert np.linalg.norm(Lo) / np.linalg.norm(Qo[0]) > 40
-    assert bf16_within(Q[0].double().cpu().numpy(), Qo[0], Lo)
+    assert rel(Q[0].double().cpu().numpy(), Qo[0]) < BF16_REL
 
 
 def test_tc_projection_conserves(fks, oracle):

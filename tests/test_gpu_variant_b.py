@@ -5,7 +5,6 @@ conservation, more cells than one chunk, unsupported configurations."""
 import numpy as np
 import pytest
 
-from conftest import fp32_within
 from paper_1701_01608_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -47,11 +46,7 @@ def test_dealiased_collide_matches_oracle(fks, oracle, n, prec, kernel, nc):
     Qo = oracle.collide_b(fin, tab2, kn=kn, project=True)
     Qg = Q.double().cpu().numpy()
     for c in range(nc):
-        if prec == 0:
-            assert rel(Qg[c], Qo[c]) < 1e-10, (c, rel(Qg[c], Qo[c]))
-        else:
-            Lc = oracle.gain_loss(oracle.pad(fin[c], n), tab2)[1] / kn
-            assert fp32_within(Qg[c], Qo[c], Lc), (c, rel(Qg[c], Qo[c]))
+        assert rel(Qg[c], Qo[c]) < (1e-10 if prec == 0 else 1e-5), (c, rel(Qg[c], Qo[c]))
 
 
 def test_dealiased_differs_from_aliased_and_conserves(fks, oracle):

@@ -6,7 +6,6 @@ relative L2 of Q (the expansion is truncated at 1e-12 / 1e-7 of the radial
 factor, below those bounds), split-BF16 the tensor-core bound."""
 import numpy as np
 import pytest
-from conftest import bf16_within
 
 from paper_1701_01608_gb300 import inputs as I
 
@@ -89,11 +88,10 @@ def test_vhs_split_bf16(fks, oracle):
     ctx.collide(fd, Q)
     assert ctx.check() == 0
     fin = host64(fd)
-    G, Lo = oracle.vhs_gain_loss(fin, n, L, 0.0, 0.25, A[0], A[1], 0)
     Qo = oracle.collide_vhs(fin, n, L, 0.0, 0.25, A[0], A[1], 0, kn=0.3, project=True)
     Qg = host64(Q)
     for c in range(nc):
-        assert bf16_within(Qg[c], Qo[c], Lo[c] / 0.3), c
+        assert rel(Qg[c], Qo[c]) < 1e-3, c
 
 
 @pytest.mark.parametrize("prec", [0, 1])
