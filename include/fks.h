@@ -49,7 +49,11 @@ enum { FKS_BC_PERIODIC = 0, FKS_BC_SPECULAR = 1 };
  * the tensor cores as a split-BF16 product (x = hi + lo for both factors,
  * hi*hi + lo*hi + hi*lo accumulated in FP32); n = 16 or 32, spectral kernels
  * only (not BGK, not batches). */
-enum { FKS_FP64 = 0, FKS_FP32 = 1, FKS_BF16X3 = 2 };
+/* FKS_FP32X2: double-float arithmetic (an unevaluated sum of two FP32 values,
+ * about 48 significant bits, on the FP32 pipes); the arithmetic of the last
+ * precision-escalation tier (fks_set_escalation_arith), not a context
+ * precision. */
+enum { FKS_FP64 = 0, FKS_FP32 = 1, FKS_BF16X3 = 2, FKS_FP32X2 = 3 };
 enum { FKS_HARD_SPHERE = 0, FKS_MAXWELL = 1, FKS_BGK = 2, FKS_VHS = 3 };
 
 /* Spatial grid: nx*ny*nz cells (fewer than 2^31) on the box [x0, x1]; bc[a]
@@ -138,6 +142,12 @@ fks_status fks_collide(fks_ctx *ctx, const void *f, void *Q, void *stream);
  * result).  FKS_ERR_UNSUPPORTED for a positive tol on FP64, BGK and FKS_VHS
  * contexts (no tiers).  Synchronises the device. */
 fks_status fks_set_escalation(fks_ctx *ctx, double tol);
+/* Arithmetic of the last escalation tier: FKS_FP32X2 (default; double-float
+ * pairs on the FP32 pipes, relative error ~1e-14 of the loss term, enough for
+ * tol down to ~1e-6 at ||L|| / ||Q|| = 1e7) or FKS_FP64 (GB300's FP64 pipe,
+ * 1/64 of the FP32 rate).  Rebuilds that tier's tables; synchronises the
+ * device.  FKS_ERR_UNSUPPORTED on contexts without tiers. */
+fks_status fks_set_escalation_arith(fks_ctx *ctx, int arith);
 /* The tolerance in force and, if counts != NULL, the cells sent to each tier
  * (counts[0]: first tier, counts[1]: second) by the last collision or step
  * call (synchronous device read). */
@@ -256,7 +266,7 @@ fks_status fks_batch_run(fks_batch *b, void *const *fa, void *const *fb, const d
 fks_status fks_batch_check(fks_batch *b, void *stream, int *bits);
 
 /* Precision escalation of FP32 batches, as fks_set_escalation: a problem whose
- * error bound 5e-7 ||L|| / Kn exceeds tol ||Q|| is recomputed in FP64
+ * error bound 5e-7 ||L|| / Kn exceeds tol ||Q|| is recomputed in double-float
  * arithmetic over its FP32 arrays by a second persistent launch of its class
  * (device-side list and count: graph-capturable).  Default tol 1e-5; 0: off.
  * FKS_ERR_UNSUPPORTED for a positive tol on FP64 batches.  Drops the captured

@@ -29,14 +29,14 @@ struct TableSet {
     int n, ktype;
     double L, Ck;
     void* tables = nullptr;
-    void* tables64 = nullptr;   // FP64 tables of the escalation tier (FP32 batches)
+    void* tables64 = nullptr;   // double-float tables of the escalation tier (FP32 batches)
     double* P = nullptr;   // device, 25 doubles
 };
 
 struct BatchClass {
     int n = 0, C = 0, max_clusters = 0;
     CollideVariant var{};
-    EscTier esc{};               // FP32 batches: FP64 arithmetic over the FP32 state (tables in the TableSets)
+    EscTier esc{};               // FP32 batches: double-float arithmetic over the FP32 state (tables in the TableSets)
     std::vector<int> probs;      // problem indices, in item order
     long first = 0;              // offset of this class in an item array
     cudaStream_t stream = nullptr;
@@ -101,13 +101,14 @@ static fks_status batch_build_class_tables(fks_batch* b, BatchClass& cl) {
     return FKS_OK;
 }
 
-// FP64 escalation tier of an FP32 class: the mixed-precision batch kernel and FP64 tables of every
-// table set of the class
+// escalation tier of an FP32 class: the batch kernel in double-float arithmetic over the FP32
+// state, and double-float tables of every table set of the class
 static fks_status batch_setup_escalation(fks_batch* b, BatchClass& cl) {
     EscTier& t = cl.esc;
     t.fp64 = true;
+    t.dfl = true;
     t.C = default_cluster_size(true, cl.n);
-    if (!find_collide_variant_mixed(cl.n, t.C, &t.var)) return bfail(b, FKS_ERR_UNSUPPORTED, "no escalation kernel");
+    if (!find_collide_variant_dfloat(cl.n, t.C, &t.var)) return bfail(b, FKS_ERR_UNSUPPORTED, "no escalation kernel");
     cudaError_t e = cudaFuncSetAttribute(t.var.func_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.var.smem);
     if (e != cudaSuccess) return bfail(b, FKS_ERR_CUDA, cudaGetErrorString(e));
     cudaLaunchConfig_t cfg = {};
@@ -127,7 +128,8 @@ static fks_status batch_setup_escalation(fks_batch* b, BatchClass& cl) {
     for (TableSet& ts : b->tsets) {
         if (ts.n != cl.n || ts.tables64) continue;
         std::string err;
-        const fks_status st = build_tables_raw(ts.n, b->dirs, ts.L, ts.ktype, ts.Ck, t.C, true, &ts.tables64, &err);
+        const fks_status st = build_tables_raw(ts.n, b->dirs, ts.L, ts.ktype, ts.Ck, t.C, true, &ts.tables64, &err,
+                                               false, nullptr, true);
         if (st != FKS_OK) return bfail(b, st, err);
         b->launches += 2;
     }

@@ -622,7 +622,7 @@ static fks_status configure_variant(fks_ctx* c, int C) {
 
 // (declared in fks_internal.h)
 fks_status fks::build_tables_raw(int n, const fks_dirs& dirs, double L, int ktype, double Ck, int C, bool fp64,
-                                 void** out, std::string* err, bool full, const VhsExpansion* vx) {
+                                 void** out, std::string* err, bool full, const VhsExpansion* vx, bool dfl) {
     const int S = (ktype == FKS_VHS && vx) ? vx->S : 1;
     const int M = dirs.A1 * dirs.A2 * S, HF = n / 2 + 1;
     const double pi = 3.14159265358979323846;
@@ -698,6 +698,8 @@ fks_status fks::build_tables_raw(int n, const fks_dirs& dirs, double L, int ktyp
         tables_kernel<<<1024, 128>>>(tp, d_A, d_B);
         if (full)
             pack_tables_full_kernel<<<1024, 256>>>(n, M, HF, d_A, d_B, d_w, (float2*)*out);
+        else if (dfl)
+            pack_tables_kernel<dfloat><<<1024, 256>>>(n, M, C, HF, d_A, d_B, d_w, (dfloat*)*out);
         else if (fp64)
             pack_tables_kernel<double><<<1024, 256>>>(n, M, C, HF, d_A, d_B, d_w, (double*)*out);
         else
@@ -737,9 +739,14 @@ static fks_status setup_escalation(fks_ctx* c) {
     int k = 0;
     auto add_tier = [&](bool fp64) -> fks_status {
         EscTier& t = c->esc[k];
+        if (t.tables) cudaFree(t.tables);
+        t = EscTier{};
         t.fp64 = fp64;
+        t.dfl = fp64 && c->esc_arith == FKS_FP32X2;
         t.C = default_cluster_size(fp64, c->n);
-        const bool found = fp64 ? find_collide_variant_mixed(c->n, t.C, &t.var) : find_collide_variant_f32(c->n, t.C, &t.var);
+        const bool found = !fp64 ? find_collide_variant_f32(c->n, t.C, &t.var)
+                                 : (t.dfl ? find_collide_variant_dfloat(c->n, t.C, &t.var)
+                                          : find_collide_variant_mixed(c->n, t.C, &t.var));
         if (!found) return fail(c, FKS_ERR_UNSUPPORTED, "no escalation kernel for this n");
         cudaError_t e = cudaFuncSetAttribute(t.var.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.var.smem);
         if (e == cudaSuccess && t.C > 8) e = cudaFuncSetAttribute(t.var.func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -760,7 +767,7 @@ static fks_status setup_escalation(fks_ctx* c) {
         if (t.max_clusters <= 0) return fail(c, FKS_ERR_UNSUPPORTED, "escalation kernel cannot be resident");
         std::string err;
         const fks_status st = build_tables_raw(c->n, c->dirs, c->vbox.L, c->kern.type, c->kern.C, t.C, fp64, &t.tables,
-                                               &err, false, nullptr);
+                                               &err, false, nullptr, t.dfl);
         if (st != FKS_OK) return fail(c, st, err);
         ++k;
         return FKS_OK;
@@ -770,12 +777,15 @@ static fks_status setup_escalation(fks_ctx* c) {
     if (st == FKS_OK) st = add_tier(true);
     if (st != FKS_OK) return st;
     const long nl = c->ncells > 0 ? c->ncells : 1;
-    if (cudaMalloc(&c->esc_lists, sizeof(int) * 2 * nl) != cudaSuccess ||
-        cudaMalloc(&c->esc_counts, sizeof(int) * 2) != cudaSuccess)
-        return fail(c, alloc_failure(), "escalation lists");
-    if (cudaMemset(c->esc_counts, 0, sizeof(int) * 2) != cudaSuccess) return fail(c, FKS_ERR_CUDA, "escalation lists");
+    if (!c->esc_lists) {
+        if (cudaMalloc(&c->esc_lists, sizeof(int) * 2 * nl) != cudaSuccess ||
+            cudaMalloc(&c->esc_counts, sizeof(int) * 2) != cudaSuccess)
+            return fail(c, alloc_failure(), "escalation lists");
+        if (cudaMemset(c->esc_counts, 0, sizeof(int) * 2) != cudaSuccess)
+            return fail(c, FKS_ERR_CUDA, "escalation lists");
+        c->esc_tol = c->tc ? 1e-3 : 1e-5;   // the stated relative L2 bounds of Q (split BF16, FP32)
+    }
     c->esc_ntier = k;
-    c->esc_tol = c->tc ? 1e-3 : 1e-5;   // the stated relative L2 bounds of Q (split BF16, FP32)
     return FKS_OK;
 }
 
@@ -1464,6 +1474,16 @@ fks_status fks_set_escalation(fks_ctx* c, double tol) {
     cudaDeviceSynchronize();   // launches in flight keep the tolerance they were issued with
     c->esc_tol = tol;
     return FKS_OK;
+}
+
+fks_status fks_set_escalation_arith(fks_ctx* c, int arith) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (arith != FKS_FP64 && arith != FKS_FP32X2) return fail(c, FKS_ERR_INVALID_ARG, "arith: FKS_FP64 or FKS_FP32X2");
+    if (c->esc_ntier == 0) return fail(c, FKS_ERR_UNSUPPORTED, "this context has no escalation tiers");
+    if (arith == c->esc_arith) return FKS_OK;
+    cudaDeviceSynchronize();
+    c->esc_arith = arith;
+    return setup_escalation(c);   // rebuilds the tiers (the last one in the new arithmetic)
 }
 
 fks_status fks_get_escalation(const fks_ctx* c, double* tol, long* counts) {

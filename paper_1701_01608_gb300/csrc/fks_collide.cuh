@@ -39,6 +39,7 @@
 #include <cstdint>
 
 #include "fks_df.cuh"
+#include "fks_dfloat.cuh"
 #include "fks_fft.cuh"
 
 namespace cg = cooperative_groups;
@@ -123,6 +124,11 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, cpx<float> v) {
 }
 __device__ __forceinline__ void st_cluster(uint32_t addr, cpx<double> v) {
     asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};\n" ::"r"(addr), "d"(v.x), "d"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, cpx<dfloat> v) {
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(v.x.hi), "f"(v.x.lo),
+                 "f"(v.y.hi), "f"(v.y.lo)
+                 : "memory");
 }
 
 // mbarrier and bulk-copy (TMA) helpers for the per-direction table slab
@@ -298,8 +304,9 @@ __device__ void xpass_task_map(unsigned* map, unsigned char* used) {
     }
 }
 
-// T: arithmetic of the transforms; ST: element type of f, out and base in global memory (ST = float
-// with T = double: the FP64 escalation tier of an FP32 state)
+// T: arithmetic of the transforms (float, double, or dfloat: double-float pairs on the FP32 pipes);
+// ST: element type of f, out and base in global memory (ST = float with T = double or dfloat: the
+// last escalation tier of an FP32 state)
 template <typename T, int N, int C, bool BATCH = false, typename ST = T>
 __global__ void __launch_bounds__(CollideCfg<T, N, C>::NT, 1)
 collide_kernel(CollideArgs args) {

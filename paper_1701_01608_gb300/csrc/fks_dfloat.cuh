@@ -32,6 +32,22 @@ namespace fks {
 #define FKS_DMUL(a, b) ((float)((a) * (b)))
 #endif
 
+// s + e = a + b exactly (any a, b)
+FKS_DD_HD float2 dd_two_sum(float a, float b) {
+    const float s = FKS_DADD(a, b);
+    const float bb = FKS_DSUB(s, a);
+    const float e = FKS_DADD(FKS_DSUB(a, FKS_DSUB(s, bb)), FKS_DSUB(b, bb));
+    return make_float2(s, e);
+}
+// s + e = a + b exactly if |a| >= |b| (or a = 0)
+FKS_DD_HD float2 dd_fast_two_sum(float a, float b) {
+    const float s = FKS_DADD(a, b);
+    const float e = FKS_DSUB(b, FKS_DSUB(s, a));
+    return make_float2(s, e);
+}
+
+// The operations are hidden friends (found by argument-dependent lookup only), so that they do not
+// hide the float and double overloads of fma and isfinite in the code that includes this header.
 struct dfloat {
     float hi, lo;
     dfloat() = default;
@@ -42,47 +58,30 @@ struct dfloat {
     constexpr FKS_DD_HD dfloat(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
     explicit constexpr FKS_DD_HD operator double() const { return (double)hi + (double)lo; }
     explicit FKS_DD_HD operator float() const { return FKS_DADD(hi, lo); }
+
+    friend FKS_DD_HD dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+    friend FKS_DD_HD dfloat operator+(dfloat a, dfloat b) {
+        const float2 s = dd_two_sum(a.hi, b.hi);
+        const float e = FKS_DADD(s.y, FKS_DADD(a.lo, b.lo));
+        const float2 r = dd_fast_two_sum(s.x, e);
+        return dfloat(r.x, r.y);
+    }
+    friend FKS_DD_HD dfloat operator-(dfloat a, dfloat b) { return a + dfloat(-b.hi, -b.lo); }
+    friend FKS_DD_HD dfloat operator*(dfloat a, dfloat b) {
+        const float p = FKS_DMUL(a.hi, b.hi);
+        float e = fmaf(a.hi, b.hi, -p);   // exact: p + e = a.hi b.hi
+        e = fmaf(a.hi, b.lo, e);
+        e = fmaf(a.lo, b.hi, e);
+        const float2 r = dd_fast_two_sum(p, e);
+        return dfloat(r.x, r.y);
+    }
+    friend FKS_DD_HD dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
+    friend FKS_DD_HD dfloat& operator-=(dfloat& a, dfloat b) { return a = a - b; }
+    friend FKS_DD_HD dfloat& operator*=(dfloat& a, dfloat b) { return a = a * b; }
+    // a b + c (one product, one sum)
+    friend FKS_DD_HD dfloat fma(dfloat a, dfloat b, dfloat c) { return a * b + c; }
+    friend FKS_DD_HD bool isfinite(dfloat a) { return ::isfinite(a.hi) && ::isfinite(a.lo); }
 };
-
-// s + e = a + b exactly (any a, b)
-FKS_DD_HD dfloat dd_two_sum(float a, float b) {
-    const float s = FKS_DADD(a, b);
-    const float bb = FKS_DSUB(s, a);
-    const float e = FKS_DADD(FKS_DSUB(a, FKS_DSUB(s, bb)), FKS_DSUB(b, bb));
-    return dfloat(s, e);
-}
-// s + e = a + b exactly if |a| >= |b| (or a = 0)
-FKS_DD_HD dfloat dd_fast_two_sum(float a, float b) {
-    const float s = FKS_DADD(a, b);
-    const float e = FKS_DSUB(b, FKS_DSUB(s, a));
-    return dfloat(s, e);
-}
-
-FKS_DD_HD dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
-
-FKS_DD_HD dfloat operator+(dfloat a, dfloat b) {
-    const dfloat s = dd_two_sum(a.hi, b.hi);
-    const float e = FKS_DADD(s.lo, FKS_DADD(a.lo, b.lo));
-    return dd_fast_two_sum(s.hi, e);
-}
-FKS_DD_HD dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
-
-FKS_DD_HD dfloat operator*(dfloat a, dfloat b) {
-    const float p = FKS_DMUL(a.hi, b.hi);
-    float e = fmaf(a.hi, b.hi, -p);   // exact: p + e = a.hi b.hi
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    return dd_fast_two_sum(p, e);
-}
-
-FKS_DD_HD dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
-FKS_DD_HD dfloat& operator-=(dfloat& a, dfloat b) { return a = a - b; }
-FKS_DD_HD dfloat& operator*=(dfloat& a, dfloat b) { return a = a * b; }
-
-// a b + c (one product, one sum)
-FKS_DD_HD dfloat fma(dfloat a, dfloat b, dfloat c) { return a * b + c; }
-
-FKS_DD_HD bool isfinite(dfloat a) { return ::isfinite(a.hi) && ::isfinite(a.lo); }
 
 #undef FKS_DADD
 #undef FKS_DSUB

@@ -25,13 +25,16 @@ struct CollideVariant {
 bool find_collide_variant(bool fp64, int N, int C, CollideVariant* out);
 bool find_collide_variant_f32(int N, int C, CollideVariant* out);
 bool find_collide_variant_f64(int N, int C, CollideVariant* out);
-// FP64 arithmetic over an FP32 state (the last tier of the precision escalation)
+// FP64 arithmetic over an FP32 state (the last tier of the precision escalation), and the same
+// with double-float arithmetic on the FP32 pipes
 bool find_collide_variant_mixed(int N, int C, CollideVariant* out);
+bool find_collide_variant_dfloat(int N, int C, CollideVariant* out);
 
 // One tier of the precision escalation: the cluster kernel that recomputes the listed cells of the
 // tier before it (FP32 arithmetic, or FP64 arithmetic over the FP32 state) with its own tables.
 struct EscTier {
-    bool fp64 = false;
+    bool fp64 = false;          // FP64-accurate arithmetic (FP64 or double-float)
+    bool dfl = false;           // double-float pairs on the FP32 pipes
     CollideVariant var{};
     int C = 0;
     int max_clusters = 0;
@@ -126,8 +129,10 @@ cudaError_t query_variant(bool fp64, int n, int C, CollideVariant* v, int* max_c
 // size C (full: the unsplit layout of the split-BF16 kernel), built on the device in FP64 and
 // stored in the working precision; *out is a new device allocation.  vx (FKS_VHS only): the
 // separable terms, table pair p * S + s being term s of direction p.
+// dfl: the cluster layout with double-float (hi, lo) elements (fp64 must be true: 8 bytes each)
 fks_status build_tables_raw(int n, const fks_dirs& dirs, double L, int ktype, double Ck, int C, bool fp64,
-                            void** out, std::string* err, bool full = false, const VhsExpansion* vx = nullptr);
+                            void** out, std::string* err, bool full = false, const VhsExpansion* vx = nullptr,
+                            bool dfl = false);
 // P = (sum_k phi(v_k) phi(v_k)^T)^-1 over the n^3 grid on [-L, L)^3, phi = (1, v, |v|^2/2)
 void projection_matrix(int n, double L, double* P);
 
@@ -183,6 +188,7 @@ struct fks_ctx {
     // listed by the context's kernel and recomputed by esc[0] (whose own failures go to esc[1])
     double esc_tol = 0.0;       // 0: off
     int esc_ntier = 0;
+    int esc_arith = FKS_FP32X2; // arithmetic of the last tier: FKS_FP32X2 or FKS_FP64
     fks::EscTier esc[2];
     int* esc_lists = nullptr;   // [2][ncells]
     int* esc_counts = nullptr;  // [2]

@@ -18,6 +18,7 @@ from . import build as _build
 FKS_FP64 = 0
 FKS_FP32 = 1
 FKS_BF16X3 = 2   # split-BF16 tensor-core transforms, FP32 storage
+FKS_FP32X2 = 3   # double-float arithmetic (the last escalation tier)
 HARD_SPHERE = 0
 MAXWELL = 1
 BGK = 2
@@ -67,7 +68,7 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
            "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
            "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias", "fks_step_host", "fks_vhs_factor",
-           "fks_step_strang", "fks_alu_peak", "fks_step_exp", "fks_set_escalation", "fks_get_escalation",
+           "fks_step_strang", "fks_alu_peak", "fks_step_exp", "fks_set_escalation", "fks_get_escalation", "fks_set_escalation_arith",
            "fks_batch_set_escalation", "fks_batch_get_escalation"]
 
 
@@ -146,6 +147,7 @@ def lib(build: bool = True):
     L.fks_alu_peak.argtypes = [I, ctypes.POINTER(D), P]
     L.fks_set_dealias.argtypes = [P, I]
     L.fks_set_escalation.argtypes = [P, D]
+    L.fks_set_escalation_arith.argtypes = [P, I]
     L.fks_get_escalation.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
     L.fks_step_host.argtypes = [P, P, P, D, P]
     L.fks_destroy.argtypes = [P]
@@ -250,6 +252,10 @@ class Context:
         """Precision escalation: cells whose error bound exceeds tol * ||Q|| are recomputed at
         higher precision (0: off)."""
         self._check(self._L.fks_set_escalation(self._h, float(tol)), "fks_set_escalation")
+
+    def set_escalation_arith(self, arith: int):
+        """Arithmetic of the last escalation tier: FKS_FP32X2 (double-float, default) or FKS_FP64."""
+        self._check(self._L.fks_set_escalation_arith(self._h, int(arith)), "fks_set_escalation_arith")
 
     def escalation(self) -> tuple[float, tuple[int, int]]:
         """(tolerance, cells sent to the first and second tier by the last collision or step)."""

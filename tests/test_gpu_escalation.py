@@ -63,14 +63,15 @@ def make_ctx(fks, nc, prec, bc=(0, 0, 0)):
     return fks.Context(fks.Config(ncell=(nc, 1, 1), bc=bc, n=N, L=L, kn=KN, A1=A[0], A2=A[1], precision=prec))
 
 
-@pytest.mark.parametrize("prec,tol", [(1, FP32_REL), (2, BF16_REL)])
-def test_near_equilibrium_cells_meet_plain_bound(fks, shock_cells, prec, tol):
+@pytest.mark.parametrize("prec,tol,arith", [(1, FP32_REL, 3), (2, BF16_REL, 3), (1, FP32_REL, 0)])
+def test_near_equilibrium_cells_meet_plain_bound(fks, shock_cells, prec, tol, arith):
     f32, Qo, kappa = shock_cells
     # the sample spans the conditioning range of the workload
     assert kappa.max() > 1e5 and kappa.min() < 100
     nc = f32.shape[0]
     ctx = make_ctx(fks, nc, prec)
     assert ctx.escalation()[0] == tol   # on by default at the stated bound
+    ctx.set_escalation_arith(arith)   # last tier: double-float (3, the default) or FP64 (0)
     fd = torch.from_numpy(f32).cuda()
     Q = torch.empty_like(fd)
     ctx.collide(fd, Q)
@@ -142,3 +143,25 @@ def test_batch_escalation(fks, oracle):
     b.set_escalation(0.0)
     b.collide(fs, Qs)
     assert max(rel(Q.double().cpu().numpy(), Qo) for Q, Qo in zip(Qs, ref)) > FP32_REL
+
+
+@pytest.mark.parametrize("arith,n", [(3, 32), (0, 32), (3, 16), (3, 8), (3, 24)])
+def test_last_tier_alone_matches_oracle(fks, oracle, arith, n):
+    """A tolerance below any bound sends every cell to the last tier: its arithmetic alone
+    (double-float or FP64 over the FP32 state) against the oracle on far-from-equilibrium
+    cells, where FP64 accuracy is the reference's own."""
+    Ln = 8.0 if n <= 16 else 10.0
+    nc = 7
+    ctx = fks.Context(fks.Config(ncell=(nc, 1, 1), n=n, L=Ln, kn=0.3, A1=4, A2=8, precision=1))
+    ctx.set_escalation(1e-300)
+    ctx.set_escalation_arith(arith)
+    f = I.two_stream((nc, 1, 1), n, Ln, seed=60 + n, noise=0.05).astype(np.float32)
+    fd = torch.from_numpy(f).cuda()
+    Q = torch.empty_like(fd)
+    ctx.collide(fd, Q)
+    assert ctx.check() == 0
+    assert ctx.escalation()[1][0] == nc
+    Qo = oracle.collide(f.astype(np.float64), oracle.tables(n, Ln, 0, 0.25, 4, 8, 0), kn=0.3)
+    for c in range(nc):
+        # the result is stored in FP32: its rounding (6e-8 relative) is the floor
+        assert rel(Q[c].double().cpu().numpy(), Qo[c]) < 2e-7, c
