@@ -165,6 +165,13 @@ fks_status fks_transport(fks_ctx *ctx, const void *f, void *f_out, double dt, vo
  * kernel per cell (f* never goes to memory).  f and f_out must not overlap. */
 fks_status fks_step(fks_ctx *ctx, const void *f, void *f_out, double dt, void *stream);
 
+/* The collision sub-step of Eq. disc_relax alone: f_out = f + dt Q(f) per
+ * cell with the projected Q, no transport and no change to the offsets -- the
+ * explicit Euler step of the space-homogeneous Boltzmann equation, cell by
+ * cell (every cell an independent homogeneous problem).  Same kernels,
+ * precisions and escalation as fks_step.  f and f_out must not overlap. */
+fks_status fks_relax(fks_ctx *ctx, const void *f, void *f_out, double dt, void *stream);
+
 /* A stiff step for BGK contexts (Sec. 2.1 asks for care in the stiff limit):
  * transport over dt, then the exact solution of the BGK relaxation
  * df/dt = nu (M[f*] - f) - phi.mu from f*, whose Maxwellian, rate nu = rho/Kn
@@ -412,8 +419,13 @@ fks_status fks_alu_peak(int precision, double *tflops, void *stream);
  * Every call shares the array and overwrites it (the flag word is cleared at
  * the start of each call), so calls that overlap on the GPU -- on different
  * streams, or from different host threads -- race: serialise them.
- * Returns FKS_ERR_INVALID_ARG for bad arguments, FKS_ERR_CUDA if a CUDA call
- * fails.  It calls no cudaMalloc, cudaFree or allocating routine. */
+ * The call synchronises `stream` at its end to read the flag word: it returns
+ * FKS_ERR_NUMERIC if a cell shift left the range of the shift table
+ * (|delta| > 120), which the check |L dt| <= 100 dx rules out for offsets in
+ * [-dx/2, dx/2) and so signals a corrupted s (f_out then holds an in-range
+ * but wrong permutation).  Returns FKS_ERR_INVALID_ARG for bad arguments,
+ * FKS_ERR_CUDA if a CUDA call fails.  It calls no cudaMalloc, cudaFree or
+ * allocating routine. */
 fks_status fks_transport_noalloc(const fks_grid *grid, const fks_vbox *vbox, int precision, double *s,
                                  double dt, const void *f, void *f_out, void *stream);
 

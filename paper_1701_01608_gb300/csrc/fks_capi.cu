@@ -1289,6 +1289,16 @@ fks_status fks_step_exp(fks_ctx* c, const void* f, void* f_out, double dt, void*
     return launch_collide(c, f, f_out, c->d_delta, dt, 4, s);
 }
 
+// The collision sub-step alone (space-homogeneous cells): f_out = f + dt Q(f), mode 1 without shifts.
+fks_status fks_relax(fks_ctx* c, const void* f, void* f_out, double dt, void* stream) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (!f || !f_out || !aligned16(f) || !aligned16(f_out)) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must be 16-byte aligned device pointers");
+    if (f == f_out) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must not alias");
+    if (!std::isfinite(dt)) return fail(c, FKS_ERR_INVALID_ARG, "dt must be finite");
+    if (c->ncells == 0) return FKS_OK;
+    return launch_collide(c, f, f_out, nullptr, dt, 1, (cudaStream_t)stream);
+}
+
 fks_status fks_step(fks_ctx* c, const void* f, void* f_out, double dt, void* stream) {
     if (!c) return FKS_ERR_INVALID_ARG;
     if (!f || !f_out || !aligned16(f) || !aligned16(f_out)) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must be 16-byte aligned device pointers");
@@ -1604,9 +1614,14 @@ extern "C" fks_status fks_transport_noalloc(const fks_grid* grid, const fks_vbox
     cudaStream_t cs = (cudaStream_t)stream;
     if (cudaMemsetAsync(d_flags, 0, sizeof(int), cs) != cudaSuccess) return FKS_ERR_CUDA;
     offsets_kernel<<<dim3(1, 3), n / 2, 0, cs>>>(n, vbox->L, make_double3(dx[0], dx[1], dx[2]), dt, s, d_delta, d_flags);
-    if ((long)grid->nx * grid->ny * grid->nz == 0) return FKS_OK;
     const cudaError_t e0 = precision == FKS_FP64 ? launch_transport<double>(n, *grid, d_delta, f, f_out, cs)
                                                  : launch_transport<float>(n, *grid, d_delta, f, f_out, cs);
-    if (e0 != cudaSuccess) return FKS_ERR_CUDA;
-    return cudaGetLastError() == cudaSuccess ? FKS_OK : FKS_ERR_CUDA;
+    if (e0 != cudaSuccess || cudaGetLastError() != cudaSuccess) return FKS_ERR_CUDA;
+    // the flag word: bit 2 = a cell shift beyond the range of the shift table.  The host check on
+    // |L dt| keeps it clear for offsets in [-dx/2, dx/2); offsets outside (a corrupted s) set it.
+    int bits = 0;
+    if (cudaMemcpyAsync(&bits, d_flags, sizeof(int), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess)
+        return FKS_ERR_CUDA;
+    return (bits & 4) ? FKS_ERR_NUMERIC : FKS_OK;
 }

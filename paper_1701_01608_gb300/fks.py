@@ -68,7 +68,7 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
            "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
            "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias", "fks_step_host", "fks_vhs_factor",
-           "fks_step_strang", "fks_alu_peak", "fks_step_exp", "fks_set_escalation", "fks_get_escalation", "fks_set_escalation_arith",
+           "fks_step_strang", "fks_alu_peak", "fks_step_exp", "fks_relax", "fks_set_escalation", "fks_get_escalation", "fks_set_escalation_arith",
            "fks_batch_set_escalation", "fks_batch_get_escalation"]
 
 
@@ -90,6 +90,7 @@ def lib(build: bool = True):
         getattr(L, name).argtypes = [P, P, P, P]
     L.fks_transport.argtypes = [P, P, P, D, P]
     L.fks_step.argtypes = [P, P, P, D, P]
+    L.fks_relax.argtypes = [P, P, P, D, P]
     L.fks_step_strang.argtypes = [P, P, P, P, D, P]
     L.fks_step_exp.argtypes = [P, P, P, D, P]
     L.fks_moments.argtypes = [P, P, P, P]
@@ -304,6 +305,11 @@ class Context:
     def step(self, f, f_out, dt: float, stream=None):
         self._check(self._L.fks_step(self._h, _dptr(f, self.dtype), _dptr(f_out, self.dtype), float(dt),
                                      _stream_ptr(stream)), "fks_step")
+
+    def relax(self, f, f_out, dt: float, stream=None):
+        """Collision sub-step alone (space-homogeneous cells): f_out = f + dt Q(f)."""
+        self._check(self._L.fks_relax(self._h, _dptr(f, self.dtype), _dptr(f_out, self.dtype), float(dt),
+                                      _stream_ptr(stream)), "fks_relax")
 
     def step_exp(self, f, f_out, dt: float, stream=None):
         """Stiff BGK step: transport, then the exact BGK relaxation over dt (BGK contexts)."""

@@ -1,0 +1,130 @@
+"""The two batch workloads at their stated sizes on the GPU, against the oracle.
+
+Homogeneous BKW batch: 4096 independent cells, pseudo-Maxwell kernel (Maxwell type), 32^3
+velocities on [-10, 10]^3, M = 32, BKW data at K0 = 0.6 with per-cell temperature U[0.8, 1.2];
+the collision sub-step alone (fks_relax) in FP64, FP32 and split BF16.  Per cell: one step against
+the oracle from the same input; 50 steps against the BKW closed form (a Maxwell-type kernel keeps
+the BKW shape: f(t) = BKW(K(t)), K = 1 - (1 - K0) e^{-lam t}, lam = (1/4) int B sin^2 d omega).
+
+Uneven batch: 96 homogeneous problems, n in {16, 24, 32}, Kn log-uniform in [1e-3, 1], hard
+spheres or pseudo-Maxwell, two-Maxwellian data; 20 steps in one captured CUDA graph
+(fks_batch_run) against the oracle's 20 Euler steps per problem."""
+import numpy as np
+import pytest
+from scipy.special import gamma
+
+from conftest import BF16_REL, FP32_REL
+from paper_1701_01608_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fks():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_01608_gb300 import fks
+    fks.lib()
+    return fks
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+BKW_DT = 0.035
+# BKW rate of the pseudo-Maxwell kernel B = C (sin(theta)/2)^-1/2 with C = 1/4, per unit density
+BKW_LAM = 0.25 * 2 * np.pi * 0.25 * np.sqrt(2) * np.sqrt(np.pi) * gamma(1.75) / gamma(2.25)
+
+
+@pytest.fixture(scope="module")
+def bkw():
+    return I.config_homogeneous_bkw(4096)
+
+
+def bkw_ctx(fks, w, prec, nc=None):
+    nc = nc or w.ncells
+    return fks.Context(fks.Config(ncell=(nc, 1, 1), n=w.n, L=w.L, kernel=fks.MAXWELL, C=w.C, kn=w.kn,
+                                  A1=w.A1, A2=w.A2, precision=prec))
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, FP32_REL), (2, BF16_REL)])
+def test_bkw_batch_one_step_matches_oracle(fks, oracle, bkw, prec, tol):
+    """All 4096 cells stepped once; sampled cells checked against the oracle's operator on the same
+    input: the increment f_out - f = dt Q(f) per cell."""
+    ctx = bkw_ctx(fks, bkw, prec)
+    dtype = torch.float64 if prec == 0 else torch.float32
+    f = torch.from_numpy(bkw.f0).to("cuda", dtype)
+    out = torch.empty_like(f)
+    ctx.relax(f, out, BKW_DT)
+    assert ctx.check() & 1 == 0
+    sample = [0, 1, 2047, 4095]
+    fin = f[sample].double().cpu().numpy()
+    tab = oracle.tables(bkw.n, bkw.L, 1, bkw.C, bkw.A1, bkw.A2, 0)
+    Qo = oracle.collide(fin, tab, kn=bkw.kn)
+    got = out[sample].double().cpu().numpy()
+    for i in range(len(sample)):
+        inc = got[i] - fin[i]
+        floor = 0.0 if prec == 0 else 2.0 ** -24 * np.linalg.norm(got[i]) * 1.5   # FP32 storage of f_out
+        assert np.linalg.norm(inc - BKW_DT * Qo[i]) <= tol * np.linalg.norm(BKW_DT * Qo[i]) + floor, i
+
+
+def test_bkw_batch_50_steps_follow_the_closed_form(fks, bkw):
+    """50 steps of 256 cells in FP64, FP32 and split BF16: each stays within a few per cent of the
+    BKW closed form at t = 50 dt (the operator's discretisation and the Euler step), and the three
+    precisions agree with each other far below that error."""
+    nc, steps = 256, 50
+    T = bkw.T[:nc]
+    t = steps * BKW_DT
+    K = 1.0 - (1.0 - 0.6) * np.exp(-BKW_LAM * t / bkw.kn)
+    exact = np.stack([I.bkw(bkw.n, bkw.L, K, T=Tc) for Tc in T])
+    finals = {}
+    for prec in (0, 1, 2):
+        ctx = bkw_ctx(fks, bkw, prec, nc)
+        dtype = torch.float64 if prec == 0 else torch.float32
+        fa = torch.from_numpy(bkw.f0[:nc]).to("cuda", dtype)
+        fb = torch.empty_like(fa)
+        for _ in range(steps):
+            ctx.relax(fa, fb, BKW_DT)
+            fa, fb = fb, fa
+        assert ctx.check() & 1 == 0
+        finals[prec] = fa.double().cpu().numpy()
+    e64 = np.array([rel(finals[0][c], exact[c]) for c in range(nc)])
+    assert e64.max() < 0.05
+    # the distance travelled, against which the precisions are compared
+    travel = np.array([np.linalg.norm(finals[0][c] - bkw.f0[c]) for c in range(nc)])
+    for prec, tol in ((1, 1e-4), (2, 1e-2)):
+        d = np.array([np.linalg.norm(finals[prec][c] - finals[0][c]) for c in range(nc)])
+        assert (d / travel).max() < tol, prec
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-4)])
+def test_uneven_batch_96_problems_graph_matches_oracle(fks, oracle, prec, tol):
+    probs = I.config_uneven_batch(96)
+    b = fks.Batch(probs, A1=4, A2=8, precision=prec)
+    dtype = torch.float64 if prec == 0 else torch.float32
+    fa = [torch.from_numpy(p["f0"]).to("cuda", dtype).contiguous() for p in probs]
+    fb = [torch.empty_like(x) for x in fa]
+    f0 = [x.double().cpu().numpy() for x in fa]
+    dts = [0.2 * p["kn"] for p in probs]
+    steps = 20
+    b.run(fa, fb, dts, steps)   # one CUDA graph of 20 steps; 20 is even: the result is in fa
+    assert b.check() & 1 == 0
+    got = [x.double().cpu().numpy() for x in fa]
+    # the oracle's 20 Euler steps, problems grouped by their tables (Q / Kn is linear in 1 / Kn)
+    ref = [x.copy() for x in f0]
+    groups = {}
+    for i, p in enumerate(probs):
+        groups.setdefault((p["n"], p["L"], p["kernel"]), []).append(i)
+    for (n, L, kern), idx in groups.items():
+        tab = oracle.tables(n, L, kern, 0.25, 4, 8, 0)
+        for _ in range(steps):
+            Q1 = oracle.collide(np.concatenate([ref[i] for i in idx]), tab, kn=1.0)
+            for j, i in enumerate(idx):
+                ref[i] = ref[i] + dts[i] / probs[i]["kn"] * Q1[j:j + 1]
+    for i in range(len(probs)):
+        inc_ref = ref[i] - f0[i]
+        inc = got[i] - f0[i]
+        floor = 0.0 if prec == 0 else steps * 2.0 ** -24 * np.linalg.norm(got[i])
+        assert np.linalg.norm(inc - inc_ref) <= tol * np.linalg.norm(inc_ref) + floor, (i, probs[i]["n"])

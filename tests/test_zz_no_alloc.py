@@ -71,3 +71,25 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(fks):
                                    0.01, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 2   # FKS_ERR_UNSUPPORTED, before any work
+
+
+def test_noalloc_reports_a_shift_out_of_range(fks):
+    """Offsets far outside [-dx/2, dx/2) (a corrupted s, written by the host) give cell shifts
+    beyond the shift table's range: the call reads its flag word and returns FKS_ERR_NUMERIC;
+    the next call with sane offsets succeeds."""
+    lib = fks.lib()
+    n, ncell, L = 8, (4, 1, 1), 10.0
+    grid = _grid(fks, ncell, (0, 0, 0))
+    vbox = fks._VBox(n, L)
+    f = torch.rand((4, n, n, n), device="cuda", dtype=torch.float32)
+    out = torch.empty_like(f)
+    dx = 1.0 / ncell[0]
+    s = torch.full((3 * n,), 1000.0 * dx, device="cuda", dtype=torch.float64)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = lib.fks_transport_noalloc(ctypes.byref(grid), ctypes.byref(vbox), 1, ctypes.c_void_p(s.data_ptr()), 0.001,
+                                   ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()), stream)
+    assert st == 5   # FKS_ERR_NUMERIC
+    s.zero_()
+    st = lib.fks_transport_noalloc(ctypes.byref(grid), ctypes.byref(vbox), 1, ctypes.c_void_p(s.data_ptr()), 0.001,
+                                   ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()), stream)
+    assert st == 0
