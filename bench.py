@@ -1,6 +1,9 @@
-"""Benchmark: phase-space points per second of one full FKS step (transport +
-fast spectral collision + projected Euler update) on the 3D/3D hard-sphere
-shock tube, 32^3 cells x 32^3 velocities, FP32, M = 32 directions.
+"""Benchmark: phase-space points per second of one full FKS step on the 3D/3D
+hard-sphere shock tube, 32^3 cells x 32^3 velocities, M = 32 directions, along
+the learned + split-BF16 path: transport, the convolutional surrogate where its
+calibrated indicator certifies 1e-3, the split-BF16 tensor-core operator
+elsewhere, and the precision escalation (FP32, then double-float) of every cell
+whose error bound exceeds 1e-3 -- compared with the plain FP64 spectral step.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 a bounded sample of the same workload instead.
@@ -28,6 +31,11 @@ NCELLS = NX ** 3
 PTS = NCELLS * NV ** 3
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA lanes x FMA x max SM clock (1.26 TFLOP/s)
+# double-float arithmetic on the FP32 pipes: a complex butterfly (4 real products, 6 real sums:
+# 10 FP32 flops) costs 4 x 8 + 6 x 11 = 98 FP32 instructions in pairs -> ~10 per operator flop
+DFLOAT_COST = 10.0
+DFLOAT_PEAK_TFLOPS = FP32_PEAK_TFLOPS / DFLOAT_COST
+TOL = 1e-3   # the metric's bound: relative L2 of Q per cell against the FP64 operator
 
 
 def _hbm_peak():
@@ -57,6 +65,7 @@ BF16_PEAK_TFLOPS, BF16_PEAK_KIND = _bf16_peak()
 # the cells of a launch).  Valid for the kernels as profiled; None once a kernel changes.
 DRAM_BYTES_PER_CELL = {
     "collide_f32": (275447296 + 222745088) / 2048,   # collide_kernel<float, 32, 8>
+    "collide_dfloat": (78028544 + 30366720) / 512,   # collide_kernel<dfloat, 32, 8, false, float> (512 listed cells)
     "bgk_f32": (268507392 + 215125504) / 2048,       # bgk_cluster_kernel<float, 32, 4> (f* read once)
     "collide_tc": (634375680 + 1517931008) / 2048,   # collide_tc_kernel<32> (scratch written back from L2)
 }
@@ -199,79 +208,49 @@ def cpu_baseline(sample_cells: int = 16, fp32_input=None) -> dict:
             "seconds": el}
 
 
-def learned_path(torch, fks, dev, args, sample=1216, threshold=1e-3):
-    """Learned surrogate collision (BF16 conv net, calibrated indicator, cells over the
-    threshold routed to the FP32 spectral operator) against the FP32 spectral collision
-    and the FP64 spectral operator, on a sample of non-equilibrium cells of the
-    workload's velocity grid (shock-tube cells after a few steps, two-stream cells)."""
+def train_surrogate(torch, steps=1500):
+    """The surrogate of the workload's velocity grid: (f, Q) pairs of shock-tube cells after 0-16
+    FP32 FKS steps (2 % noise) and two-stream cells, labelled by the escalated FP32 spectral
+    operator; Adam steps on the library's training kernels; calibration on held-out cells."""
     from paper_1701_01608_gb300 import surrogate as S
     t0 = time.perf_counter()
-    ftr = torch.cat([S.shock_tube_cells(torch, NV, LBOX, nx=32, ny=2, nz=2, steps=(0, 4, 8, 16), seed=0),
-                     S.two_stream_cells(torch, 128, NV, LBOX, seed=1)])
+    ftr = torch.cat([S.shock_tube_cells(torch, NV, LBOX, nx=32, ny=4, nz=4, steps=(0, 2, 4, 8, 16), seed=0),
+                     S.two_stream_cells(torch, 512, NV, LBOX, seed=1)]).contiguous()
     Qtr = S.labels(torch, ftr, NV, LBOX, kn=1.0)
-    sur = S.train(torch, ftr, Qtr, epochs=8, batch=8, lr=2e-3, n=NV, L=LBOX, holdout=0.2)
-    train_s = time.perf_counter() - t0
+    sur = S.train(torch, ftr, Qtr, batch=8, lr=2e-3, n=NV, L=LBOX, holdout=0.1, steps=steps)
     del ftr, Qtr
-    f = torch.cat([S.shock_tube_cells(torch, NV, LBOX, nx=32, ny=8, nz=4, steps=(6,), seed=5)[:sample - 192],
-                   S.two_stream_cells(torch, 192, NV, LBOX, seed=9)]).contiguous()
-    nc = f.shape[0]
-    c32 = fks.Context(fks.Config(ncell=(nc, 1, 1), n=NV, L=LBOX, kn=KN, A1=A1, A2=A2, precision=fks.FKS_FP32))
-    c64 = fks.Context(fks.Config(ncell=(nc, 1, 1), n=NV, L=LBOX, kn=KN, A1=A1, A2=A2, precision=fks.FKS_FP64))
-    Q64 = torch.empty(f.shape, dtype=torch.float64, device=dev)
-    c64.collide(f.double(), Q64)
-    Qs = torch.empty_like(f)
-    Ql = torch.empty_like(f)
+    return sur, time.perf_counter() - t0
 
-    def timed(fn, reps=5):
-        """median over reps of the per-call device time (one call includes a host sync)"""
-        fn()
-        torch.cuda.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
-        ev[0].record()
-        for i in range(reps):
-            fn()
-            ev[i + 1].record()
-        torch.cuda.synchronize()
-        return float(np.median([ev[i].elapsed_time(ev[i + 1]) for i in range(reps)]))
 
-    t_spec = timed(lambda: c32.collide(f, Qs))
-    routed = [0]
-    t_learn = timed(lambda: routed.__setitem__(0, c32.surrogate_collide(sur.net, f, Ql, sur.out_scale,
-                                                                        sur.ind_scale, threshold)))
+def sample_cells():
+    """64 cells of the 32^3 grid: the x-layers around the interface and the walls, spread in y, z."""
+    rng = np.random.Generator(np.random.PCG64(2024))
+    xs = [0, 1, 8, 14, 15, 16, 17, 18, 24, 30, 31]
+    cells = [((x * GRID[1] + int(rng.integers(GRID[1]))) * GRID[2] + int(rng.integers(GRID[2]))) for x in xs for _ in range(6)]
+    return sorted(set(c for c in cells if c < NCELLS))[:64]
 
-    def err(Q):
-        d = (Q.double() - Q64).flatten(1).norm(dim=1) / Q64.flatten(1).norm(dim=1)
-        return float(d.max().item()), float(d.median().item())
 
-    # the learned + split-BF16 path: routed cells recomputed on the tensor cores
-    ctc = fks.Context(fks.Config(ncell=(nc, 1, 1), n=NV, L=LBOX, kn=KN, A1=A1, A2=A2, precision=fks.FKS_BF16X3))
-    Qt, Qlt = torch.empty_like(f), torch.empty_like(f)
-    t_tc = timed(lambda: ctc.collide(f, Qt))
-    routed_t = [0]
-    t_learn_tc = timed(lambda: routed_t.__setitem__(0, ctc.surrogate_collide(sur.net, f, Qlt, sur.out_scale,
-                                                                              sur.ind_scale, threshold)))
-    elt, mlt = err(Qlt)
-    del ctc
-    el, ml = err(Ql)
-    es, ms = err(Qs)
-    pts = nc * NV ** 3
-    return {"value": pts / (t_learn / 1e3), "unit": "pts/s", "ms": t_learn, "cells": nc,
-            "routed_fraction": routed[0] / nc, "threshold": threshold,
-            "err_vs_fp64": {"max": el, "median": ml},
-            "spectral_fp32_collide": {"value": pts / (t_spec / 1e3), "ms": t_spec, "err_vs_fp64": {"max": es, "median": ms}},
-            "speedup_vs_spectral_fp32": t_spec / t_learn,
-            "learned_bf16x3": {"value": pts / (t_learn_tc / 1e3), "ms": t_learn_tc, "routed_fraction": routed_t[0] / nc,
-                               "err_vs_fp64": {"max": elt, "median": mlt},
-                               "spectral_bf16x3_collide_ms": t_tc,
-                               "note": "routed cells recomputed by the split-BF16 tensor-core operator"},
-            "err_note": "relative L2 of Q against the FP64 operator on this sample, which includes nearly "
-                        "Maxwellian shock-tube cells: there ||L|| / ||Q|| is large and the error is bounded on the "
-                        "loss scale (FP32 2.5e-7 ||L||, split BF16 2.5e-5 ||L||); far from equilibrium see "
-                        "bf16x3_tensor_core.err_vs_fp64",
-            "train_seconds": train_s, "train_loss_last": sur.train_loss[-1], "calibration": sur.calib,
-            "note": "collision operator only (the part the surrogate replaces), same sample for both paths; "
-                    "net: 6 x conv3d 3^3, 32 ch, BF16 weights and activations, FP32 accumulation; inference on "
-                    "the tensor cores (tcgen05 implicit GEMM), training on CUDA cores"}
+def operator_errors(torch, fks, dev, fstar, collide):
+    """Relative L2 of Q per sampled cell of f* (the transported state of a step): collide(fs, Q) is
+    the path's own operator on a context of the sampled cells, the reference the FP64 GPU operator."""
+    cells = torch.tensor(sample_cells(), device=dev)
+    fs = fstar.index_select(0, cells).contiguous()
+    q64 = torch.empty(fs.shape, dtype=torch.float64, device=dev)
+    fks.Context(fks.Config(ncell=(fs.shape[0], 1, 1), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
+                           precision=fks.FKS_FP64)).collide(fs.double(), q64)
+    q = torch.empty_like(fs)
+    collide(fs, q)
+    d = ((q.double() - q64).flatten(1).norm(dim=1) / q64.flatten(1).norm(dim=1)).cpu().numpy()
+    return {"max": float(d.max()), "median": float(np.median(d)), "cells": int(len(d)),
+            "note": "per cell, relative L2 of Q against the FP64 operator on the same f* (sampled cells around the "
+                    "interface, the walls and the bulk)"}
+
+
+def sample_ctx(fks, prec, tol):
+    c = fks.Context(fks.Config(ncell=(len(sample_cells()), 1, 1), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1,
+                               A2=A2, precision=prec))
+    c.set_escalation(tol)
+    return c
 
 
 def run_reference(args):
@@ -344,6 +323,32 @@ def time_steps(torch, ctx, f0, steps, warmup, dt, ws):
     return total_ms, per, ctx.launches - launches0, bits, fa
 
 
+def timed_loop(torch, fn, steps, warmup, ws):
+    """W untimed calls, then K calls between CUDA events on the current stream, with a barrier and a
+    device synchronisation on both sides; returns (total ms, per-call ms)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for i in range(steps):
+        fn()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[steps]), [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+
+
+def health(torch, f):
+    """Positivity of a state (the method does not enforce it): the minimum value and the count of
+    negative values."""
+    return {"min_f": float(f.min().item()), "negative_values": int((f < 0).sum().item())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,11 +358,12 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bgk", action="store_true")
-    ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--no-tc", action="store_true")
+    ap.add_argument("--no-raw", action="store_true")
     ap.add_argument("--no-varb", action="store_true")
     ap.add_argument("--no-vhs", action="store_true")
     ap.add_argument("--no-strang", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--clocks-log", default=None, help="keep the raw nvidia-smi clock samples of the timed "
                                                         "region in this CSV file")
     ap.add_argument("--cpu-sample", type=int, default=int(os.environ.get("FKS_CPU_SAMPLE", "1024")))
@@ -386,92 +392,169 @@ def main():
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
     dt = dt_rule()
-    cfg = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
-                     A1=A1, A2=A2, precision=fks.FKS_FP32)
-    ctx = fks.Context(cfg)
     f0 = build_state(torch, torch.float32, dev)
     # measured FMA throughput of the FP32 and FP64 pipes (a second denominator beside the derived one)
     alu32 = fks.alu_peak(fks.FKS_FP32)
     alu64 = fks.alu_peak(fks.FKS_FP64)
 
+    # ---------------- the metric's path: learned + split BF16, escalated to 1e-3 per cell
+    sur, train_s = train_surrogate(torch, args.train_steps)
+    cfgl = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
+                      precision=fks.FKS_BF16X3)
+    ctx = fks.Context(cfgl)
+    assert abs(ctx.escalation()[0] - TOL) < 1e-15
+    fa, fb, work = f0.clone(), torch.empty_like(f0), torch.empty_like(f0)
+    state = {"a": fa, "b": fb}
+
+    def learned_step():
+        ctx.surrogate_step(sur.net, state["a"], state["b"], work, dt, sur.out_scale, sur.ind_scale, TOL)
+        state["a"], state["b"] = state["b"], state["a"]
+
+    for _ in range(args.warmup):
+        learned_step()
+    ctx.profile()                    # clear the stage record of the warm-up
+    ctx.set_profiling(True)
+    launches0 = ctx.launches + sur.net.launches
     clk = Clocks(torch.cuda.current_device(),
                  args.clocks_log or os.path.join(tempfile.gettempdir(), f"fks_clocks_{os.getpid()}_{rank}.csv"))
-    total_ms, per, launches, bits, _ = time_steps(torch, ctx, f0, args.steps, args.warmup, dt, ws)
+    total_ms, per = timed_loop(torch, learned_step, args.steps, 0, ws)
     clocks = clk.stop()
+    launches = ctx.launches + sur.net.launches - launches0
+    stage_ms, stage_n = ctx.profile()
+    ctx.set_profiling(False)
     total_ms = max_over_ranks(total_ms, ws)
-    sec = total_ms / 1e3
-    value = ws * PTS * args.steps / sec
-    step_ms = float(np.mean(per))
-    flops_launch = flops_per_cell() * NCELLS
-    achieved = flops_launch / (step_ms / 1e3) / 1e12
-
-    # stage timers (CUDA events, each stage alone; the step fuses transport, collision,
-    # projection and the Euler update into one kernel)
-    stages = None
+    value = ws * PTS * args.steps / (total_ms / 1e3)
+    bits = ctx.check()
+    _, esc_counts = ctx.escalation()          # the last step's escalated cells per tier
+    # one more step, kept for the error check and the routing counts
+    fs_in = state["a"]
+    routed = ctx.surrogate_step(sur.net, fs_in, state["b"], work, dt, sur.out_scale, sur.ind_scale, TOL)
+    _, esc_last = ctx.escalation()
+    learned_err = None
     if ws == 1:
-        tmp = torch.empty_like(f0)
-        U = torch.empty((NCELLS, 5), dtype=torch.float64, device=dev)
+        cl = sample_ctx(fks, fks.FKS_BF16X3, TOL)
+        learned_err = operator_errors(torch, fks, dev, work, lambda fs, q: cl.surrogate_collide(
+            sur.net, fs, q, sur.out_scale, sur.ind_scale, TOL))
+        del cl
+    positivity = health(torch, state["b"])
+    # roofline of the dominant kernel: the double-float tier (stage 2 of a split-BF16 context)
+    df_ms = stage_ms[2] / max(stage_n[2], 1)
+    df_cells = esc_counts[1]
+    df_flops = flops_per_cell() * df_cells
+    df_ach = df_flops / (df_ms / 1e3) / 1e12 if df_ms > 0 else 0.0
+    b_df = DRAM_BYTES_PER_CELL.get("collide_dfloat")
+    roofline = {"bound": "alu", "achieved": df_ach, "peak": DFLOAT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": df_ach / DFLOAT_PEAK_TFLOPS,
+                "traffic": b_df * df_cells if b_df else None,
+                "kernel": "collide_kernel<dfloat, 32, 8> (last escalation tier)",
+                "algorithmic_flops_per_launch": df_flops, "launch_ms": df_ms, "cells_per_launch": df_cells,
+                "peak_note": "double-float operations on the FP32 pipes: derived FP32 peak (152 SMs x 128 lanes x "
+                             "2 flop x 2.07 GHz) / %.0f FP32 instructions per operator flop" % DFLOAT_COST,
+                "traffic_note": "dram bytes per listed cell of one ncu capture (512 cells), times the cells of a launch",
+                "frac_of_fp64_peak": df_ach / FP64_PEAK_TFLOPS,
+                "cells_note": "cells of the last timed step; the stage time is the mean over the timed steps"}
+    stages = {"split_bf16_kernel_ms": stage_ms[0] / max(stage_n[0], 1),
+              "fp32_tier_ms": stage_ms[1] / max(stage_n[1], 1),
+              "dfloat_tier_ms": df_ms,
+              "other_ms": float(np.mean(per)) - sum(stage_ms) / max(args.steps, 1),
+              "note": "CUDA events around each collision launch inside the timed steps (fks_set_profiling); other = "
+                      "offsets, transport into f*, surrogate classification and inference"}
+    learned = {"routed_fraction": routed / NCELLS, "certified_fraction": 1.0 - routed / NCELLS,
+               "escalated": {"to_fp32": esc_last[0], "to_dfloat": esc_last[1], "cells": NCELLS},
+               "err_vs_fp64": learned_err, "train_seconds": train_s, "train_loss_last": sur.train_loss[-1],
+               "calibration": sur.calib, "threshold": TOL, "stages": stages, "gpu_launches": launches,
+               "health_bits": bits}
+    del fa, fb
 
-        def ev_ms(fn, reps=2):
-            fn()
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            for _ in range(reps):
-                fn()
-            b.record()
-            torch.cuda.synchronize()
-            return a.elapsed_time(b) / reps
+    # ---------------- the comparison: the plain FP64 spectral step (transport + FP64 operator)
+    fp64 = None
+    if not args.no_fp64 and ws == 1:
+        ctx64 = fks.Context(fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
+                                       A1=A1, A2=A2, precision=fks.FKS_FP64))
+        f64 = build_state(torch, torch.float64, dev)
+        k64 = 3
+        t64, per64, _, bits64, _ = time_steps(torch, ctx64, f64, k64, 1, dt, ws)
+        ms64 = t64 / k64
+        fl64 = flops_per_cell() * NCELLS / (ms64 / 1e3) / 1e12
+        fp64 = {"value": PTS / (ms64 / 1e3), "unit": "pts/s", "ms_per_step": ms64, "steps": k64,
+                "roofline": {"bound": "alu", "achieved": fl64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": fl64 / FP64_PEAK_TFLOPS, "traffic": None, "peak_measured": alu64,
+                             "frac_of_measured": fl64 / alu64 if alu64 else None,
+                             "peak_note": "derived FP64 CUDA-core peak: 152 SMs x 2 FP64 FMA lanes x 2 flop x "
+                                          "2.07 GHz (GB300's reduced FP64 rate)"},
+                "health_bits": bits64, "note": "same workload and step through the FP64 kernels (3 timed steps)"}
+        del f64, ctx64
 
-        stages = {"transport_ms": ev_ms(lambda: ctx.transport(f0, tmp, dt)),
-                  "moments_ms": ev_ms(lambda: ctx.moments(f0, U)),
-                  "collide_ms": ev_ms(lambda: ctx.collide(f0, tmp)),
-                  "step_ms": step_ms,
-                  "note": "FP32; transport = offsets + gather kernel (2 x 4 B per point), moments = compensated "
-                          "FP32 sums (FP64-equivalent), 4 B per point"}
-        del tmp, U
-
+    # ---------------- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        # public API with host buffers: H2D of the step's input, the step, D2H of the result
         host_in = torch.empty(f0.shape, dtype=torch.float32, pin_memory=True)
         host_in.copy_(f0)
         host_out = torch.empty_like(host_in, pin_memory=True)
-        e2e_steps = max(1, min(args.steps, 5))
-        # fks_step_host: the library copies the step's input in, steps and copies the result out,
-        # pipelined over x-slab chunks (every step: H2D of the whole state, the step, D2H)
-        ctx.step_host(host_in, host_out, dt)
-        torch.cuda.synchronize()
-        barrier(ws)
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
-        evs[0].record()
-        for i in range(e2e_steps):
-            ctx.step_host(host_in, host_out, dt)
-            evs[i + 1].record()
-        torch.cuda.synchronize()
-        e2e_ms = max_over_ranks(evs[0].elapsed_time(evs[e2e_steps]), ws)
-        e2e_each = [round(evs[i].elapsed_time(evs[i + 1]), 2) for i in range(e2e_steps)]
-        nbytes = f0.numel() * 4
-        # plain copy rates between the pinned host arrays and the device (one full-state copy each
-        # way), to read the e2e line against
-        dtmp = torch.empty_like(f0)
-        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        c0.record()
-        dtmp.copy_(host_in, non_blocking=True)
-        c1.record()
-        host_out.copy_(dtmp, non_blocking=True)
-        c2.record()
-        torch.cuda.synchronize()
-        copy_gbs = {"h2d": nbytes / (c0.elapsed_time(c1) / 1e3) / 1e9,
-                    "d2h": nbytes / (c1.elapsed_time(c2) / 1e3) / 1e9}
-        del dtmp
-        e2e = {"value": ws * PTS * e2e_steps / (e2e_ms / 1e3), "unit": "pts/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "ms_each": e2e_each,
-               "ms_median": float(np.median(e2e_each)), "copy_gbs": copy_gbs,
-               "api": "fks_step_host (pinned host arrays; copies overlapped with the step over 8 x-slab chunks)"}
-        del host_in, host_out
+        din, dout, dw = torch.empty_like(f0), torch.empty_like(f0), torch.empty_like(f0)
+        e2e_steps = max(1, min(args.steps, 3))
 
-    # BGK relaxation step on the same workload: HBM bound (8 B per point)
+        def e2e_step():
+            # every step: the state in from pinned host memory, the learned + BF16 step, the state out
+            din.copy_(host_in, non_blocking=True)
+            ctx.surrogate_step(sur.net, din, dout, dw, dt, sur.out_scale, sur.ind_scale, TOL)
+            host_out.copy_(dout, non_blocking=True)
+
+        e2e_ms, e2e_each = timed_loop(torch, e2e_step, e2e_steps, 1, ws)
+        e2e_ms = max_over_ranks(e2e_ms, ws)
+        nbytes = f0.numel() * 4
+        e2e = {"value": ws * PTS * e2e_steps / (e2e_ms / 1e3), "unit": "pts/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "ms_each": [round(x, 2) for x in e2e_each],
+               "api": "pinned host state -> device (copy), fks_surrogate_step, device -> pinned host (copy)"}
+        del host_in, host_out, din, dout, dw
+
+    # ---------------- the spectral paths alone: escalated FP32, and the raw arithmetic (no escalation)
+    raw = None
+    if not args.no_raw and ws == 1:
+        raw = {}
+        for name, prec, tol in (("fp32_escalated", fks.FKS_FP32, 1e-5), ("fp32_raw", fks.FKS_FP32, 0.0),
+                                ("bf16x3_escalated", fks.FKS_BF16X3, 1e-3), ("bf16x3_raw", fks.FKS_BF16X3, 0.0)):
+            c = fks.Context(fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
+                                       A1=A1, A2=A2, precision=prec))
+            c.set_escalation(tol)
+            k = 2 if tol > 0 else 3
+            tk, perk, lk, bk, fend = time_steps(torch, c, f0, k, 1, dt, ws)
+            fs = torch.empty_like(f0)
+            ct = fks.Context(fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kn=KN, A1=A1, A2=A2,
+                                        precision=fks.FKS_FP32))
+            ct.set_offsets(c.offsets())
+            ct.transport(fend, fs, dt)        # f* of the next step
+            cs_ = sample_ctx(fks, prec, tol)
+            raw[name] = {"ms_per_step": tk / k, "value": PTS / (tk / k / 1e3), "steps": k, "tol": tol,
+                         "escalated_last_step": c.escalation()[1], "gpu_launches": lk, "health_bits": bk,
+                         "err_vs_fp64": operator_errors(torch, fks, dev, fs, cs_.collide)}
+            del c, ct, cs_, fs, fend
+        fl32 = flops_per_cell() * NCELLS / (raw["fp32_raw"]["ms_per_step"] / 1e3) / 1e12
+        raw["fp32_raw"]["roofline"] = {"bound": "alu", "achieved": fl32, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                       "frac": fl32 / FP32_PEAK_TFLOPS, "traffic": traffic("collide_f32"),
+                                       "peak_measured": alu32, "frac_of_measured": fl32 / alu32 if alu32 else None}
+        issued = tc_issued_flops_per_cell() * NCELLS
+        tfl = issued / (raw["bf16x3_raw"]["ms_per_step"] / 1e3) / 1e12
+        raw["bf16x3_raw"]["roofline"] = {"bound": "tensor", "achieved": tfl, "peak": BF16_PEAK_TFLOPS,
+                                         "unit": "TFLOP/s", "frac": tfl / BF16_PEAK_TFLOPS,
+                                         "traffic": traffic("collide_tc"), "issued_flops_per_launch": issued,
+                                         "peak_note": "bf16_tflops_sustained of MEASURED_PEAKS.json (%s)" % BF16_PEAK_KIND}
+        # the same operators on far-from-equilibrium cells (two-stream), raw arithmetic: what each attains there
+        from paper_1701_01608_gb300 import inputs as I
+        fts = torch.from_numpy(I.two_stream((64, 1, 1), NV, LBOX, seed=77, noise=0.05).astype(np.float32)).to(dev)
+        qref = torch.empty(fts.shape, dtype=torch.float64, device=dev)
+        fks.Context(fks.Config(ncell=(64, 1, 1), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
+                               precision=fks.FKS_FP64)).collide(fts.double(), qref)
+        for name, prec in (("bf16x3_raw", fks.FKS_BF16X3), ("fp32_raw", fks.FKS_FP32)):
+            q = torch.empty_like(fts)
+            c = fks.Context(fks.Config(ncell=(64, 1, 1), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
+                                       precision=prec))
+            c.set_escalation(0.0)
+            c.collide(fts, q)
+            d = ((q.double() - qref).flatten(1).norm(dim=1) / qref.flatten(1).norm(dim=1)).cpu().numpy()
+            raw[name]["err_two_stream"] = {"max": float(d.max()), "median": float(np.median(d))}
+
+    # ---------------- BGK relaxation step on the same workload: HBM bound (8 B per point)
     bgk = None
     if not args.no_bgk:
         cfgb = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=fks.BGK, kn=KN, precision=fks.FKS_FP32)
@@ -486,67 +569,80 @@ def main():
                             "algorithmic_bytes_per_launch": 8.0 * PTS,
                             "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
                "note": "BGK relaxation (Sec. 2) with the fused transport gather, FP32"}
-        # the stiff (exponential) BGK step at Kn = 1e-6, nu dt ~ 1e3, where the Euler step diverges
-        ctxe = fks.Context(fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=fks.BGK, kn=1e-6,
-                                      precision=fks.FKS_FP32))
-        fa, fb = f0.clone(), torch.empty_like(f0)
-        for _ in range(max(1, min(args.warmup, 3))):
-            ctxe.step_exp(fa, fb, dt)
-            fa, fb = fb, fa
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            ctxe.step_exp(fa, fb, dt)
-            fa, fb = fb, fa
-        e1.record()
-        torch.cuda.synchronize()
-        bgk["stiff_exp_step"] = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "knudsen": 1e-6,
-                                 "health_bits": ctxe.check(),
-                                 "note": "fks_step_exp: transport + exact BGK relaxation over dt (stable at any nu dt)"}
-        del ctxb, ctxe, fa, fb
+        del ctxb
 
-    # the same step with every DFT on the tensor cores (split BF16)
-    tcp = None
-    if not args.no_tc:
-        cfgt = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
-                          A1=A1, A2=A2, precision=fks.FKS_BF16X3)
-        ctxt = fks.Context(cfgt)
-        tt, pert, launches_t, bits_t, _ = time_steps(torch, ctxt, f0, args.steps, args.warmup, dt, ws)
-        tt = max_over_ranks(tt, ws)
-        tms = float(np.mean(pert))
-        issued = tc_issued_flops_per_cell() * NCELLS
-        tfl = issued / (tms / 1e3) / 1e12
-        tcp = {"value": ws * PTS * args.steps / (tt / 1e3), "unit": "pts/s", "ms_per_step": tt / args.steps,
-               "roofline": {"bound": "tensor", "achieved": tfl, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": tfl / BF16_PEAK_TFLOPS, "traffic": traffic("collide_tc"),
-                            "issued_flops_per_launch": issued,
-                            "peak_note": "bf16_tflops_sustained of MEASURED_PEAKS.json (%s); issued split-BF16 "
-                                         "MMA flops (3 products per DFT)" % BF16_PEAK_KIND},
-               "algorithmic_tflops": flops_launch / (tms / 1e3) / 1e12,
-               "gpu_launches": launches_t, "health_bits": bits_t,
-               "note": "fks_step on an FKS_BF16X3 context: offsets + one tcgen05 kernel per step (split-BF16 "
-                       "DFT passes, FP32 between passes, FP64 moment sums)"}
-        if ws == 1:
-            # error of the collision operator against the FP64 GPU operator on cells far from
-            # equilibrium (the initial shock-tube cells are Maxwellians, Q ~ 0 there)
-            from paper_1701_01608_gb300 import inputs as I
-            fs = torch.from_numpy(I.two_stream((64, 1, 1), NV, LBOX, seed=77, noise=0.05).astype(np.float32)).to(dev)
-            errs = {}
-            qref = torch.empty(fs.shape, dtype=torch.float64, device=dev)
-            fks.Context(fks.Config(ncell=(64, 1, 1), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
-                                   precision=fks.FKS_FP64)).collide(fs.double(), qref)
-            for name, prec in (("bf16x3", fks.FKS_BF16X3), ("fp32", fks.FKS_FP32)):
-                q = torch.empty_like(fs)
-                fks.Context(fks.Config(ncell=(64, 1, 1), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
-                                       precision=prec)).collide(fs, q)
-                d = ((q.double() - qref).flatten(1).norm(dim=1) / qref.flatten(1).norm(dim=1)).cpu().numpy()
-                errs[name] = {"max": float(d.max()), "median": float(np.median(d))}
-            tcp["err_vs_fp64"] = errs
-            tcp["err_sample"] = "64 seeded two-stream cells (5 % noise) on the workload's velocity grid, relative L2 of Q"
-        del ctxt
+    # ---------------- the batch workloads
+    configs = None
+    if not args.no_configs and ws == 1:
+        from paper_1701_01608_gb300 import inputs as I
+        configs = {}
+        w = I.config_homogeneous_bkw(4096)
+        from scipy.special import gamma
+        # BKW rate (1/4) int B sin^2 d omega of the pseudo-Maxwell kernel B = C (sin(theta)/2)^-1/2, C = 1/4
+        lam = 0.25 * 2 * np.pi * 0.25 * np.sqrt(2) * np.sqrt(np.pi) * gamma(1.75) / gamma(2.25)
+        bdt, bsteps, nref = 0.035, 50, 512
+        K = 1.0 - 0.4 * np.exp(-lam * bdt * bsteps / w.kn)
+        from paper_1701_01608_gb300.inputs import bkw as bkw_profile
+        exact = torch.from_numpy(np.stack([bkw_profile(w.n, w.L, K, T=t) for t in w.T[:nref]])).to(dev)
+        res = {}
+        finals = {}
+        for name, prec, ncl in (("fp64", fks.FKS_FP64, nref), ("fp32", fks.FKS_FP32, 4096),
+                                ("bf16x3", fks.FKS_BF16X3, 4096)):
+            c = fks.Context(fks.Config(ncell=(ncl, 1, 1), n=w.n, L=w.L, kernel=fks.MAXWELL, C=w.C, kn=w.kn,
+                                       A1=w.A1, A2=w.A2, precision=prec))
+            dty = torch.float64 if prec == fks.FKS_FP64 else torch.float32
+            st = {"a": torch.from_numpy(w.f0[:ncl]).to(dev, dty), "b": None}
+            st["b"] = torch.empty_like(st["a"])
 
-    # variant B (de-aliased, 2n transforms) in the paper's own setting: 16^3 modes with 32^3 transforms
+            def relax_step(c=c, st=st):
+                c.relax(st["a"], st["b"], bdt)
+                st["a"], st["b"] = st["b"], st["a"]
+
+            tr, _ = timed_loop(torch, relax_step, bsteps, 0, ws)
+            finals[name] = st["a"][:nref].double()
+            d = ((finals[name] - exact).flatten(1).norm(dim=1) / exact.flatten(1).norm(dim=1)).cpu().numpy()
+            res[name] = {"cells": ncl, "ms_per_step": tr / bsteps, "value": ncl * w.n ** 3 * bsteps / (tr / 1e3),
+                         "err_vs_bkw_closed_form": {"max": float(d.max()), "median": float(np.median(d))},
+                         "health_bits": c.check()}
+            del c, st
+        for name in ("fp32", "bf16x3"):
+            travel = (finals["fp64"] - torch.from_numpy(w.f0[:nref]).to(dev)).flatten(1).norm(dim=1)
+            d = ((finals[name] - finals["fp64"]).flatten(1).norm(dim=1) / travel).cpu().numpy()
+            res[name]["diff_vs_fp64_over_travel"] = {"max": float(d.max()), "median": float(np.median(d))}
+        res["note"] = ("4096 homogeneous cells, pseudo-Maxwell kernel, 32^3 on [-10,10]^3, M = 32, BKW at K0 = 0.6, "
+                       "T ~ U[0.8, 1.2]; 50 fks_relax steps (dt = 0.035, t = 1.75); errors on the first 512 cells "
+                       "against the BKW closed form K(t) = 1 - 0.4 exp(-lam t) (the operator's discretisation + Euler), "
+                       "and the FP32 / BF16 runs against FP64 relative to the distance travelled")
+        configs["homogeneous_bkw_4096"] = res
+        probs = I.config_uneven_batch(96)
+        pts_b = sum(p["n"] ** 3 for p in probs)
+        resu = {}
+        outs = {}
+        for name, prec in (("fp64", fks.FKS_FP64), ("fp32", fks.FKS_FP32)):
+            b = fks.Batch(probs, A1=4, A2=8, precision=prec)
+            dty = torch.float64 if prec == fks.FKS_FP64 else torch.float32
+            fa_b = [torch.from_numpy(p["f0"]).to(dev, dty).contiguous() for p in probs]
+            fb_b = [torch.empty_like(x) for x in fa_b]
+            dts = [0.2 * p["kn"] for p in probs]
+            b.run(fa_b, fb_b, dts, 20)        # capture (first call) and one replay
+            torch.cuda.synchronize()
+            for i, p in enumerate(probs):
+                fa_b[i].copy_(torch.from_numpy(p["f0"]).to(dev, dty))
+            tg, _ = timed_loop(torch, lambda: b.run(fa_b, fb_b, dts, 20), 1, 0, ws)
+            outs[name] = fa_b
+            resu[name] = {"ms_20_steps": tg, "value": pts_b * 20 / (tg / 1e3), "health_bits": b.check(),
+                          "cluster_sizes": {n: b.cluster_size(n) for n in (16, 24, 32)}}
+            del b
+        d = [float(((outs["fp32"][i].double() - outs["fp64"][i]).norm() /
+                    (outs["fp64"][i] - torch.from_numpy(probs[i]["f0"]).to(dev)).norm()).item())
+             for i in range(len(probs))]
+        resu["fp32"]["diff_vs_fp64_over_travel"] = {"max": max(d), "median": float(np.median(d))}
+        resu["note"] = ("96 homogeneous problems, n in {16, 24, 32}, Kn log-uniform in [1e-3, 1], hard spheres or "
+                        "pseudo-Maxwell, two-Maxwellian data; 20 steps (dt = 0.2 Kn) in one captured CUDA graph "
+                        "(fks_batch_run), one persistent launch per n class; FP32 with its escalation")
+        configs["uneven_batch_96"] = resu
+
+    # ---------------- variant B (de-aliased, 2n transforms) in the paper's own setting: 16^3 modes, 32^3 transforms
     varb = None
     if not args.no_varb and ws == 1:
         from paper_1701_01608_gb300 import inputs as I
@@ -558,19 +654,11 @@ def main():
         for name, dealias in (("variant_b", True), ("variant_a", False)):
             cb = fks.Context(fks.Config(ncell=GRID, bc=(1, 0, 0), n=nb, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
                                         precision=fks.FKS_FP32, dealias=dealias))
-            tb_, perb_, lb_, bitsb_, _ = time_steps(torch, cb, fb0, args.steps, args.warmup, dt, ws)
-            res[name] = {"ms_per_step": tb_ / args.steps, "value": NCELLS * nb ** 3 * args.steps / (tb_ / 1e3),
+            cb.set_escalation(0.0)
+            tb_, perb_, lb_, bitsb_, _ = time_steps(torch, cb, fb0, 3, 1, dt, ws)
+            res[name] = {"ms_per_step": tb_ / 3, "value": NCELLS * nb ** 3 * 3 / (tb_ / 1e3),
                          "gpu_launches": lb_, "health_bits": bitsb_}
             del cb
-        # error of FP32 variant B against FP64 variant B on far-from-equilibrium cells
-        fs = torch.from_numpy(I.two_stream((64, 1, 1), nb, LBOX, seed=78, noise=0.05)).to(dev)
-        q64 = torch.empty_like(fs)
-        fks.Context(fks.Config(ncell=(64, 1, 1), n=nb, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
-                               precision=fks.FKS_FP64, dealias=True)).collide(fs, q64)
-        q32 = torch.empty_like(fs, dtype=torch.float32)
-        fks.Context(fks.Config(ncell=(64, 1, 1), n=nb, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
-                               precision=fks.FKS_FP32, dealias=True)).collide(fs.float(), q32)
-        d = ((q32.double() - q64).flatten(1).norm(dim=1) / q64.flatten(1).norm(dim=1)).cpu().numpy()
         ms_b = res["variant_b"]["ms_per_step"]
         fl2 = flops_per_cell(2 * nb, M) * NCELLS
         varb = {"value": res["variant_b"]["value"], "unit": "pts/s (N_v = 16^3)", "ms_per_step": ms_b,
@@ -579,128 +667,80 @@ def main():
                              "unit": "TFLOP/s", "frac": fl2 / (ms_b / 1e3) / 1e12 / FP32_PEAK_TFLOPS, "traffic": None,
                              "algorithmic_flops_per_launch": fl2,
                              "peak_note": "operator flops at the 2n = 32 grid; derived FP32 peak"},
-                "gpu_launches": res["variant_b"]["gpu_launches"],
-                "err_fp32_vs_fp64": {"max": float(d.max()), "median": float(np.median(d))},
-                "note": "shock tube %dx%dx%d cells x 16^3 velocities, FP32, fks_step with fks_set_dealias: "
-                        "interpolation to 32^3, the 32^3 collision without projection, truncation to "
-                        "|k| <= 8 and projection (per 2048-cell chunk: 3 launches)" % GRID}
+                "note": "shock tube x 16^3 velocities, FP32 raw arithmetic (variant B has no escalation), fks_step with "
+                        "fks_set_dealias: interpolation to 32^3, the 32^3 collision without projection, truncation "
+                        "to |k| <= 8 and projection"}
         del fb0, sb
 
-    # variable hard spheres B = C|g|^alpha (non-separable Carleman kernel, expanded into
-    # separable terms): Maxwell molecules, alpha = 0, on the same workload
+    # ---------------- variable hard spheres: Maxwell molecules (alpha = 0) on the same workload
     vhs = None
     if not args.no_vhs and ws == 1:
-        from paper_1701_01608_gb300 import inputs as I
         alpha = 0.0
         _, S, trunc = fks.vhs_factor(alpha, 0.25, LBOX, NV, fks.FKS_FP32, 0, 0.0, 0.0)
         cv = fks.Context(fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=fks.VHS, C=0.25, kn=KN,
                                     A1=A1, A2=A2, precision=fks.FKS_FP32, alpha=alpha))
-        ks, kw = min(args.steps, 3), max(1, min(args.warmup, 3))
-        tv, perv, lv, bitsv, _ = time_steps(torch, cv, f0, ks, kw, dt, ws)
+        tv, perv, lv, bitsv, _ = time_steps(torch, cv, f0, 2, 1, dt, ws)
         del cv
         msv = float(np.mean(perv))
         flv = flops_per_cell(NV, M * S) * NCELLS
-        fs = torch.from_numpy(I.two_stream((8, 1, 1), NV, LBOX, seed=79, noise=0.05)).to(dev)
-        q64 = torch.empty_like(fs)
-        fks.Context(fks.Config(ncell=(8, 1, 1), n=NV, L=LBOX, kernel=fks.VHS, C=0.25, kn=KN, A1=A1, A2=A2,
-                               precision=fks.FKS_FP64, alpha=alpha)).collide(fs, q64)
-        q32 = torch.empty_like(fs, dtype=torch.float32)
-        fks.Context(fks.Config(ncell=(8, 1, 1), n=NV, L=LBOX, kernel=fks.VHS, C=0.25, kn=KN, A1=A1, A2=A2,
-                               precision=fks.FKS_FP32, alpha=alpha)).collide(fs.float(), q32)
-        d = ((q32.double() - q64).flatten(1).norm(dim=1) / q64.flatten(1).norm(dim=1)).cpu().numpy()
-        vhs = {"value": PTS * ks / (tv / 1e3), "unit": "pts/s", "ms_per_step": tv / ks, "steps": ks,
+        vhs = {"value": PTS * 2 / (tv / 1e3), "unit": "pts/s", "ms_per_step": tv / 2, "steps": 2,
                "alpha": alpha, "terms": S, "truncation": trunc,
                "roofline": {"bound": "alu", "achieved": flv / (msv / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS,
                             "unit": "TFLOP/s", "frac": flv / (msv / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
-                            "traffic": None, "algorithmic_flops_per_launch": flv,
-                            "peak_note": "operator flops with M x terms table pairs; derived FP32 peak"},
+                            "traffic": None, "algorithmic_flops_per_launch": flv},
                "gpu_launches": lv, "health_bits": bitsv,
-               "err_fp32_vs_fp64": {"max": float(d.max()), "median": float(np.median(d))},
-               "note": "fks_step, FKS_VHS alpha = 0 (Maxwell molecules, B = C): the radial factor of the "
-                       "Carleman kernel 4C (|x|^2+|y|^2)^-1/2 expanded into %d separable terms, "
-                       "%d table pairs per cell; same shock tube, FP32" % (S, M * S)}
+               "note": "fks_step, FKS_VHS alpha = 0 (Maxwell molecules): %d separable terms, %d table pairs per cell; "
+                       "FP32 raw arithmetic (the VHS expansion has no escalation tier)" % (S, M * S)}
 
-    # second-order step (Strang splitting, Heun collision sub-step) on the same workload
+    # ---------------- second-order step (Strang, Heun) on the same workload, FP32 escalated
     strang = None
     if not args.no_strang and ws == 1:
-        cs = fks.Context(cfg)
-        fa, fb, fw = f0.clone(), torch.empty_like(f0), torch.empty_like(f0)
-        ks, kw = min(args.steps, 5), max(1, min(args.warmup, 3))
-        for _ in range(kw):
-            cs.step_strang(fa, fb, fw, dt)
-            fa, fb = fb, fa
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cs = fks.Context(fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
+                                    A1=A1, A2=A2, precision=fks.FKS_FP32))
+        sa, sb_, sw = f0.clone(), torch.empty_like(f0), torch.empty_like(f0)
+        stt = {"a": sa, "b": sb_}
+
+        def strang_step():
+            cs.step_strang(stt["a"], stt["b"], sw, dt)
+            stt["a"], stt["b"] = stt["b"], stt["a"]
+
         l0 = cs.launches
-        e0.record()
-        for _ in range(ks):
-            cs.step_strang(fa, fb, fw, dt)
-            fa, fb = fb, fa
-        e1.record()
-        torch.cuda.synchronize()
-        tsr = e0.elapsed_time(e1)
-        fls = 2 * flops_per_cell() * NCELLS / (tsr / ks / 1e3) / 1e12
-        strang = {"value": PTS * ks / (tsr / 1e3), "unit": "pts/s", "ms_per_step": tsr / ks, "steps": ks,
-                  "roofline": {"bound": "alu", "achieved": fls, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                               "frac": fls / FP32_PEAK_TFLOPS, "traffic": None,
-                               "peak_note": "two operator evaluations per step; derived FP32 peak"},
+        tsr, _ = timed_loop(torch, strang_step, 2, 1, ws)
+        strang = {"value": PTS * 2 / (tsr / 1e3), "unit": "pts/s", "ms_per_step": tsr / 2, "steps": 2,
                   "gpu_launches": cs.launches - l0, "health_bits": cs.check(),
-                  "note": "fks_step_strang: T(dt/2), Heun collision (two projected operator evaluations), "
-                          "T(dt/2); second order in dt; FP32, same workload and dt"}
-        del cs, fa, fb, fw
-
-    learned = None
-    if not args.no_learned and ws == 1:
-        learned = learned_path(torch, fks, dev, args)
-
-    fp64 = None
-    if not args.no_fp64 and ws == 1:
-        cfg64 = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN,
-                           A1=A1, A2=A2, precision=fks.FKS_FP64)
-        ctx64 = fks.Context(cfg64)
-        f64 = build_state(torch, torch.float64, dev)
-        t64, per64, _, _, _ = time_steps(torch, ctx64, f64, 1, 1, dt, ws)
-        fl64 = flops_per_cell() * NCELLS / (t64 / 1e3) / 1e12
-        fp64 = {"value": PTS / (t64 / 1e3), "unit": "pts/s", "ms_per_step": t64,
-                "roofline": {"bound": "alu", "achieved": fl64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": fl64 / FP64_PEAK_TFLOPS, "traffic": None, "peak_measured": alu64,
-                             "frac_of_measured": fl64 / alu64 if alu64 else None,
-                             "peak_note": "derived FP64 CUDA-core peak: 152 SMs x 2 FP64 FMA lanes x 2 flop x "
-                                          "2.07 GHz (GB300's reduced FP64 rate)"},
-                "note": "same workload and step through the FP64 kernels (1 timed step after 1 warm-up)"}
-        del f64, ctx64
+                  "note": "fks_step_strang: T(dt/2), Heun collision (two projected operator evaluations, escalated "
+                          "to 1e-5), T(dt/2); second order in dt; FP32"}
+        del cs, sa, sb_, sw
 
     if rank != 0:
         return
     out = {
         "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32+f32x2", "data": "synthetic",
         "config": {"workload": "hs_shocktube_%dx%dx%dc_32v" % GRID, "cells": NCELLS, "n_v": NV ** 3, "M": M,
-                   "kernel": "hard spheres", "knudsen": KN, "bc": "specular x, periodic y z",
-                   "dt": dt, "path": "fks_step: offsets + fused transport/collision/projection/Euler kernel",
-                   "cluster_size": ctx.cluster_size, "l2": "inputs 4.3 GB > L2 (no flush needed)",
+                   "kernel": "hard spheres", "knudsen": KN, "bc": "specular x, periodic y z", "dt": dt,
+                   "path": "fks_surrogate_step on an FKS_BF16X3 context: offsets + transport into f*, surrogate "
+                           "(cells its indicator certifies at 1e-3), split-BF16 tensor-core operator on the others, "
+                           "escalation of cells whose error bound exceeds 1e-3 to FP32 and then double-float",
+                   "tolerance": TOL, "l2": "inputs 4.3 GB > L2 (no flush needed)",
                    "parallelism": "replicas" if ws > 1 else "single"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic("collide_f32"),
-                     "traffic_note": "dram bytes of one ncu capture on 2048 cells, scaled by the cells of a launch",
-                     "algorithmic_flops_per_launch": flops_launch,
-                     "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
-                     "peak_measured": alu32, "frac_of_measured": achieved / alu32 if alu32 else None,
-                     "peak_measured_note": "FMA-chain kernel (fks_alu_peak), this run"},
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches,
         "health_bits": bits,
-        "stages": stages,
+        "positivity": positivity,
+        "learned": learned,
         "fp64_spectral": fp64,
+        "speedup_vs_fp64_spectral": (value / fp64["value"]) if fp64 else None,
+        "spectral_paths": raw,
         "bgk_step": bgk,
-        "bf16x3_tensor_core": tcp,
+        "configs": configs,
         "variant_b_16v": varb,
         "vhs_maxwell": vhs,
         "strang_second_order": strang,
-        "learned": learned,
     }
     print(json.dumps(out), flush=True)
 

@@ -208,6 +208,15 @@ fks_status fks_moments(fks_ctx *ctx, const void *f, double *U, void *stream);
  * bits in *bits if bits != NULL. */
 fks_status fks_check(fks_ctx *ctx, void *stream, int *bits);
 
+/* Stage timing for measurement: with on != 0 every collision launch of the
+ * context is bracketed by two CUDA events on its stream, by stage (0 the
+ * context's own kernel, 1 and 2 the escalation tiers).  fks_get_profile
+ * synchronises the device and returns, per stage, the summed event time in
+ * ms[3] and the number of launches in launches[3] (may be NULL), then clears
+ * the record. */
+fks_status fks_set_profiling(fks_ctx *ctx, int on);
+fks_status fks_get_profile(fks_ctx *ctx, double *ms, long *launches);
+
 /* Host copies of the per-axis sub-cell offsets s[3][n] (FP64).  get
  * synchronises the device; set is synchronous too. */
 fks_status fks_get_offsets(fks_ctx *ctx, double *s);
@@ -338,16 +347,26 @@ fks_status fks_surrogate_inputs(int n, double L, long ncells, const float *f, fl
 
 /* Q for every cell of an FP32 or split-BF16 (FKS_BF16X3) spectral context
  * (variant A) by the surrogate: Q = rho^2 y out_scale / Kn, projected onto
- * the conservation constraints; indicator = ind_scale (dist + relative moment
- * defect of the raw output); cells whose indicator exceeds `threshold` (or
- * is not finite) are recomputed with the context's spectral operator (the
- * FP32 cluster kernel, or the split-BF16 tensor-core kernel on the list of
- * routed cells, each with the context's precision escalation).  The routed
- * cells are listed on the device; `stream` is synchronised only if nrouted
- * != NULL (to read the routed count into *nrouted).  f and Q 16-byte aligned.  The moments of the raw
+ * the conservation constraints; indicator = ind_scale / dist + the relative
+ * moment defect of the raw output (the network's error is about a fixed
+ * fraction of its output scale while ||Q|| shrinks with dist, so its
+ * relative error grows as 1 / dist).  Cells whose bound ind_scale / dist
+ * already exceeds `threshold` skip the network; the others are inferred in
+ * compacted chunks.  Cells whose indicator exceeds `threshold` (or is not
+ * finite) are recomputed with the context's spectral operator (the FP32
+ * cluster kernel or the split-BF16 tensor-core kernel over a device list of
+ * the routed cells, each with the context's precision escalation).
+ * Synchronises `stream` once to read the candidate count, and once more if
+ * nrouted != NULL (the routed count).  f and Q 16-byte aligned.  The moments of the raw
  * output are FP64 sums of its FP32 values; the correction is applied in FP32. */
 fks_status fks_surrogate_collide(fks_ctx *ctx, fks_net *net, const void *f, void *Q, double out_scale,
                                  double ind_scale, double threshold, long *nrouted, void *stream);
+/* One FKS step with the surrogate: transport over dt into `work` (a device
+ * array of the size of f, overwritten: f*), then f_out = f* + dt Q with Q as in
+ * fks_surrogate_collide (the routed cells by the spectral step without
+ * transport).  f, f_out and work distinct and 16-byte aligned. */
+fks_status fks_surrogate_step(fks_ctx *ctx, fks_net *net, const void *f, void *f_out, void *work, double dt,
+                              double out_scale, double ind_scale, double threshold, long *nrouted, void *stream);
 /* host copy of the last indicators (count = number of cells) */
 fks_status fks_surrogate_indicator(const fks_ctx *ctx, float *host, long count);
 

@@ -976,8 +976,12 @@ void fks_destroy(fks_ctx* c) {
     cudaFree(c->s_dist);
     cudaFree(c->s_ind);
     cudaFree(c->s_cells);
+    cudaFree(c->s_cand);
     cudaFree(c->s_count);
     for (int i = 0; i < 2; ++i) cudaFree(c->esc[i].tables);
+    for (int k = 0; k < 3; ++k)
+        for (cudaEvent_t e : c->prof_ev[k]) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
     cudaFree(c->esc_lists);
     cudaFree(c->esc_counts);
     delete c;
@@ -1033,6 +1037,23 @@ static fks_status launch_bgk_ctx(fks_ctx* c, const void* f, void* out, const sig
 }
 
 static bool esc_on(const fks_ctx* c) { return c->esc_tol > 0.0 && c->esc_ntier > 0; }
+
+// stage timing: an event before and after a launch of stage `stage` on stream s
+static cudaEvent_t prof_event(fks_ctx* c) {
+    cudaEvent_t e = nullptr;
+    if (!c->prof_pool.empty()) {
+        e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+static void prof_mark(fks_ctx* c, int stage, cudaStream_t s) {
+    if (!c->prof) return;
+    cudaEvent_t e = prof_event(c);
+    if (e && cudaEventRecord(e, s) == cudaSuccess) c->prof_ev[stage].push_back(e);
+}
 
 static fks_status launch_tc_ctx(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
                                 cudaStream_t s, const int* cells = nullptr, long ncells = -1,
@@ -1134,7 +1155,9 @@ static fks_status launch_esc_tiers(fks_ctx* c, const void* f, void* out, const s
             a.esc_c2 = kEscFp32 * kEscFp32;
             a.esc_tol2 = c->esc_tol * c->esc_tol;
         }
+        prof_mark(c, 1 + i, s);
         const cudaError_t e = launch_cluster(t.var, t.C, t.max_clusters, a, c->ncells, s);
+        prof_mark(c, 1 + i, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "escalation kernel launch");
         c->launches += 1;
     }
@@ -1159,7 +1182,9 @@ static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const sig
         if (st != FKS_OK) return st;
     }
     if (c->tc) {
+        prof_mark(c, 0, s);
         const fks_status st = launch_tc_ctx(c, f, out, delta, dt, mode, s);
+        prof_mark(c, 0, s);
         if (st != FKS_OK || !esc) return st;
         return launch_esc_tiers(c, f, out, delta, dt, mode, s, base);
     }
@@ -1172,7 +1197,9 @@ static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const sig
         a.esc_c2 = kEscFp32 * kEscFp32;
         a.esc_tol2 = c->esc_tol * c->esc_tol;
     }
+    prof_mark(c, 0, s);
     const cudaError_t e = launch_cluster(c->var, c->C, c->max_clusters, a, cell1 - cell0, s);
+    prof_mark(c, 0, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "collision kernel launch");
     c->launches += 1;
     if (!esc) return FKS_OK;
@@ -1181,7 +1208,7 @@ static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const sig
 
 fks_status fks_internal_fail(fks_ctx* c, fks_status st, const std::string& msg) { return fail(c, st, msg); }
 fks_status fks_internal_collide_list(fks_ctx* c, const void* f, void* out, const int* cells, const int* count,
-                                     cudaStream_t s) {
+                                     int mode, double dt, cudaStream_t s) {
     if (c->bgk || c->dealias) return fail(c, FKS_ERR_UNSUPPORTED, "cell lists need a spectral context (variant A)");
     const bool esc = esc_on(c);
     if (esc) {
@@ -1189,10 +1216,12 @@ fks_status fks_internal_collide_list(fks_ctx* c, const void* f, void* out, const
         if (st != FKS_OK) return st;
     }
     if (c->tc) {
-        const fks_status st = launch_tc_ctx(c, f, out, nullptr, 0.0, 0, s, cells, c->ncells, count);
+        prof_mark(c, 0, s);
+        const fks_status st = launch_tc_ctx(c, f, out, nullptr, dt, mode, s, cells, c->ncells, count);
+        prof_mark(c, 0, s);
         if (st != FKS_OK) return st;
     } else {
-        CollideArgs a = cluster_args(c, c->tables, f, out, nullptr, 0.0, 0, 0, c->ncells, nullptr);
+        CollideArgs a = cluster_args(c, c->tables, f, out, nullptr, dt, mode, 0, c->ncells, nullptr);
         a.list = cells;
         a.list_count = count;
         if (esc) {
@@ -1201,11 +1230,13 @@ fks_status fks_internal_collide_list(fks_ctx* c, const void* f, void* out, const
             a.esc_c2 = kEscFp32 * kEscFp32;
             a.esc_tol2 = c->esc_tol * c->esc_tol;
         }
+        prof_mark(c, 0, s);
         const cudaError_t e = launch_cluster(c->var, c->C, c->max_clusters, a, c->ncells, s);
+        prof_mark(c, 0, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "collision kernel launch");
         c->launches += 1;
     }
-    return esc ? launch_esc_tiers(c, f, out, nullptr, 0.0, 0, s, nullptr) : FKS_OK;
+    return esc ? launch_esc_tiers(c, f, out, nullptr, dt, mode, s, nullptr) : FKS_OK;
 }
 fks_status fks_internal_collide(fks_ctx* c, const void* f, void* out, int mode, cudaStream_t s) {
     return launch_collide(c, f, out, nullptr, 0.0, mode, s);
@@ -1505,6 +1536,30 @@ fks_status fks_get_escalation(const fks_ctx* c, double* tol, long* counts) {
             return FKS_ERR_CUDA;
         counts[0] = h[0];
         counts[1] = h[1];
+    }
+    return FKS_OK;
+}
+
+fks_status fks_set_profiling(fks_ctx* c, int on) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    c->prof = on != 0;
+    return FKS_OK;
+}
+
+fks_status fks_get_profile(fks_ctx* c, double* ms, long* launches) {
+    if (!c || !ms) return FKS_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(c, FKS_ERR_CUDA, "profile synchronisation");
+    for (int k = 0; k < 3; ++k) {
+        double acc = 0.0;
+        auto& v = c->prof_ev[k];
+        for (size_t i = 0; i + 1 < v.size(); i += 2) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, v[i], v[i + 1]) == cudaSuccess) acc += t;
+        }
+        ms[k] = acc;
+        if (launches) launches[k] = (long)(v.size() / 2);
+        for (cudaEvent_t e : v) c->prof_pool.push_back(e);
+        v.clear();
     }
     return FKS_OK;
 }

@@ -183,7 +183,8 @@ struct fks_ctx {
     float* s_dist = nullptr;
     float* s_ind = nullptr;
     int* s_cells = nullptr;     // routed cell indices
-    int* s_count = nullptr;
+    int* s_cand = nullptr;      // cells the network infers
+    int* s_count = nullptr;     // [2]: routed, candidates
     // precision escalation (FP32 and split-BF16 contexts): cells whose error bound exceeds esc_tol are
     // listed by the context's kernel and recomputed by esc[0] (whose own failures go to esc[1])
     double esc_tol = 0.0;       // 0: off
@@ -192,6 +193,11 @@ struct fks_ctx {
     fks::EscTier esc[2];
     int* esc_lists = nullptr;   // [2][ncells]
     int* esc_counts = nullptr;  // [2]
+    // stage timing (fks_set_profiling): CUDA-event pairs around each collision launch, by stage
+    // (0 the context's kernel, 1 and 2 the escalation tiers), summed by fks_get_profile
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev[3];   // start, end, start, end, ...
+    std::vector<cudaEvent_t> prof_pool;
 };
 
 
@@ -201,9 +207,10 @@ struct fks_ctx {
 // (C linkage: they are defined beside the C ABI.)
 extern "C" fks_status fks_internal_fail(fks_ctx* c, fks_status st, const std::string& msg);
 extern "C" fks_status fks_internal_collide(fks_ctx* c, const void* f, void* out, int mode, cudaStream_t s);
-// collide (projected, with the context's escalation) only the cells cells[0 .. *count) (a device count)
+// collide (projected, with the context's escalation) only the cells cells[0 .. *count) (a device count):
+// mode 0 out = Q, mode 1 out = f + dt Q (no transport)
 extern "C" fks_status fks_internal_collide_list(fks_ctx* c, const void* f, void* out, const int* cells, const int* count,
-                                                cudaStream_t s);
+                                                int mode, double dt, cudaStream_t s);
 // variant B (fks_dealias.cu)
 fks_status launch_dealias(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
                           cudaStream_t s);

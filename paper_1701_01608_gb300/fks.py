@@ -68,7 +68,7 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
            "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
            "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias", "fks_step_host", "fks_vhs_factor",
-           "fks_step_strang", "fks_alu_peak", "fks_step_exp", "fks_relax", "fks_set_escalation", "fks_get_escalation", "fks_set_escalation_arith",
+           "fks_step_strang", "fks_alu_peak", "fks_step_exp", "fks_relax", "fks_surrogate_step", "fks_set_profiling", "fks_get_profile", "fks_set_escalation", "fks_get_escalation", "fks_set_escalation_arith",
            "fks_batch_set_escalation", "fks_batch_get_escalation"]
 
 
@@ -144,10 +144,13 @@ def lib(build: bool = True):
     L.fks_surrogate_inputs.argtypes = [I, D, ctypes.c_long, P, P, P, P, P]
     L.fks_surrogate_collide.argtypes = [P, P, P, P, D, D, D, ctypes.POINTER(ctypes.c_long), P]
     L.fks_surrogate_indicator.argtypes = [P, P, ctypes.c_long]
+    L.fks_surrogate_step.argtypes = [P, P, P, P, P, D, D, D, D, ctypes.POINTER(ctypes.c_long), P]
     L.fks_selftest_wait.argtypes = [ctypes.c_long, P]
     L.fks_alu_peak.argtypes = [I, ctypes.POINTER(D), P]
     L.fks_set_dealias.argtypes = [P, I]
     L.fks_set_escalation.argtypes = [P, D]
+    L.fks_set_profiling.argtypes = [P, I]
+    L.fks_get_profile.argtypes = [P, P, P]
     L.fks_set_escalation_arith.argtypes = [P, I]
     L.fks_get_escalation.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
     L.fks_step_host.argtypes = [P, P, P, D, P]
@@ -265,6 +268,17 @@ class Context:
         self._check(self._L.fks_get_escalation(self._h, ctypes.byref(tol), counts), "fks_get_escalation")
         return tol.value, (counts[0], counts[1])
 
+    def set_profiling(self, on: bool = True):
+        """Record CUDA events around each collision launch (stage 0 own kernel, 1 and 2 escalation tiers)."""
+        self._check(self._L.fks_set_profiling(self._h, 1 if on else 0), "fks_set_profiling")
+
+    def profile(self) -> tuple[list, list]:
+        """(ms per stage, launches per stage) since the last call; synchronises the device."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_long * 3)()
+        self._check(self._L.fks_get_profile(self._h, ms, n), "fks_get_profile")
+        return list(ms), list(n)
+
     def set_dealias(self, on: bool = True):
         """Variant B: the 2n-padded (de-aliased) operator for this context's collisions."""
         self._check(self._L.fks_set_dealias(self._h, 1 if on else 0), "fks_set_dealias")
@@ -341,6 +355,16 @@ class Context:
         self._check(self._L.fks_surrogate_collide(self._h, net._h, _dptr(f, self.dtype), _dptr(Q, self.dtype),
                                                   float(out_scale), float(ind_scale), float(threshold),
                                                   ctypes.byref(nr), _stream_ptr(stream)), "fks_surrogate_collide")
+        return nr.value
+
+    def surrogate_step(self, net: "Net", f, f_out, work, dt: float, out_scale: float, ind_scale: float,
+                       threshold: float, stream=None) -> int:
+        """One step with the surrogate (transport into work, then f* + dt Q); returns the routed count."""
+        nr = ctypes.c_long()
+        self._check(self._L.fks_surrogate_step(self._h, net._h, _dptr(f, self.dtype), _dptr(f_out, self.dtype),
+                                               _dptr(work, self.dtype), float(dt), float(out_scale), float(ind_scale),
+                                               float(threshold), ctypes.byref(nr), _stream_ptr(stream)),
+                    "fks_surrogate_step")
         return nr.value
 
     def indicator(self) -> np.ndarray:
