@@ -172,14 +172,22 @@ fks_status fks_step(fks_ctx *ctx, const void *f, void *f_out, double dt, void *s
  * precisions and escalation as fks_step.  f and f_out must not overlap. */
 fks_status fks_relax(fks_ctx *ctx, const void *f, void *f_out, double dt, void *stream);
 
-/* A stiff step for BGK contexts (Sec. 2.1 asks for care in the stiff limit):
- * transport over dt, then the exact solution of the BGK relaxation
- * df/dt = nu (M[f*] - f) - phi.mu from f*, whose Maxwellian, rate nu = rho/Kn
- * and projection term stay fixed over the step (the relaxation conserves
- * rho, rho u, E):  f_out = f* + (1 - e^{-nu dt}) / nu * Q(f*).  Stable for any
- * nu dt and equal to M[f*] (plus the projection correction) as Kn -> 0; tends
- * to fks_step as nu dt -> 0.  dt >= 0.  FKS_ERR_UNSUPPORTED for spectral
- * contexts.  f and f_out must not overlap. */
+/* A stiff step (Sec. 2.1 asks for care in the stiff limit): transport over
+ * dt, then
+ *  - BGK contexts: the exact solution of the BGK relaxation
+ *    df/dt = nu (M[f*] - f) - phi.mu from f*, whose Maxwellian, rate nu = rho/Kn
+ *    and projection term stay fixed over the step (the relaxation conserves
+ *    rho, rho u, E):  f_out = f* + (1 - e^{-nu dt}) / nu * Q(f*);  equal to M[f*]
+ *    (plus the projection correction) as Kn -> 0;
+ *  - FP64 and FP32 spectral contexts: the integrating-factor (exponential Euler)
+ *    step of the gain-loss split df/dt = G(f) - nu(v) f with the loss
+ *    frequency nu = IDFT(betaL F) / Kn and G frozen at f*, solved per velocity
+ *    point:  f_out = f* + dt P[phi(nu dt) (G - nu f*)], phi(x) = (1 - e^-x)/x, P the
+ *    conservation projection of the increment; bounded for any nu dt (tends to
+ *    G / nu in the stiff limit), with the FP32 context's escalation.
+ * Both tend to fks_step as nu dt -> 0 (first order in dt).  dt >= 0.
+ * FKS_ERR_UNSUPPORTED for split-BF16 and variant-B contexts.  f and f_out must
+ * not overlap. */
 fks_status fks_step_exp(fks_ctx *ctx, const void *f, void *f_out, double dt, void *stream);
 
 /* A second-order step (the higher-order splitting the paper allows in Sec. 2.1):

@@ -17,7 +17,9 @@ Functions and the passage each follows:
   bgk                    -- BGK relaxation nu (M[f] - f) (Sec. 2, BGK approximation)
   step                   -- Eq. disc_relax: transport, then f = f* + dt Q(f*)
   step_strang            -- second-order splitting (Sec. 2.1 allows it): T(dt/2), Heun, T(dt/2)
-  step_exp               -- stiff BGK step (Sec. 2.1, the stiff limit): exact BGK relaxation over dt
+  step_exp               -- stiff steps (Sec. 2.1, the stiff limit): exact BGK relaxation over dt;
+                            for the spectral operator the integrating-factor step of the gain-loss
+                            split with the loss frequency (loss_frequency) frozen at f*
   pad, truncate,
   collide_b, galerkin_b  -- variant B: Eq. CF1 with l + m = k not reduced mod n,
                             evaluated with 2n transforms (Sec. 5); brute force
@@ -217,6 +219,14 @@ def gain_loss(f, tab: Tables):
     return G, Lo
 
 
+def loss_frequency(f, tab: Tables) -> np.ndarray:
+    """l(v) = IDFT(betaL DFT(f)) / n^3 of one cell (Appendix A, the B_F(m, m) term): the loss term
+    of the operator is f l, the loss frequency l / Kn.  The oracle's own 3-D FFT."""
+    n = tab.n
+    F = fft3d(np.asarray(f, dtype=np.float64).reshape(n, n, n), -1)
+    return fft3d(tab.betaL * F, +1).real / n ** 3
+
+
 def galerkin(f, tab: Tables, kn: float = 1.0) -> np.ndarray:
     f = _f64(f)
     Q = np.empty_like(f)
@@ -393,10 +403,28 @@ class Solver:
         return collide(f, self.tab, self.kn, project=True)
 
     def step_exp(self, f, dt):
-        """Stiff BGK step (Sec. 2.1: care in the stiff limit): transport, then the exact solution
+        """Stiff step (Sec. 2.1: care in the stiff limit).  BGK: transport, then the exact solution
         of the BGK relaxation with the cell's Maxwellian, rate nu = rho/Kn and projection term
-        fixed: f* + (1 - exp(-nu dt)) / nu * Q(f*) per cell (dt where nu = 0)."""
-        assert self.tab is None and self.vhs is None, "BGK solvers only"
+        fixed: f* + (1 - exp(-nu dt)) / nu * Q(f*) per cell (dt where nu = 0).  Spectral operator:
+        transport, then the gain-loss split df/dt = G - nu f with G and the loss frequency
+        nu = l / Kn frozen at f*, solved per velocity point: the increment dt phi(nu dt) (G / Kn - nu f*),
+        phi(x) = (1 - e^-x) / x, projected onto the constraints.  Where the discrete loss frequency is
+        not positive (ringing of the truncated spectrum in the far tails, where f is negligible) the
+        term stays explicit: phi(max(x, 0))."""
+        assert self.vhs is None and not self.variant_b, "BGK or spectral (variant A) solvers"
+        if self.tab is not None:
+            fs = self.transport(f, dt)
+            n = self.n
+            out = np.empty_like(fs)
+            cells = fs.reshape(-1, n, n, n)
+            for c in range(cells.shape[0]):
+                G, Lo = gain_loss(cells[c], self.tab)
+                x = np.maximum(loss_frequency(cells[c], self.tab) / self.kn * dt, 0.0)
+                safe = np.where(x != 0.0, x, 1.0)
+                phi = np.where(x != 0.0, -np.expm1(-x) / safe, 1.0)
+                inc = project(dt * phi * (G - Lo) / self.kn, n, self.L)
+                out.reshape(-1, n, n, n)[c] = cells[c] + inc
+            return out
         fs = self.transport(f, dt)
         Q = bgk(fs, self.n, self.L, self.kn, project=True)
         dv3 = (2.0 * self.L / self.n) ** 3

@@ -1304,14 +1304,19 @@ fks_status fks_step_strang(fks_ctx* c, const void* f, void* f_out, void* work, d
     return st;
 }
 
-// Exponential BGK step: the relaxation df/dt = Q(f) = nu (M[f] - f) - phi.mu keeps M[f], nu and the
-// projection term fixed over the step (collision invariants), so its exact solution from f* is
+// Exponential steps.  BGK: the relaxation df/dt = Q(f) = nu (M[f] - f) - phi.mu keeps M[f], nu and
+// the projection term fixed over the step (collision invariants), so its exact solution from f* is
 // f* + (1 - e^{-nu dt}) / nu Q(f*): stable for any nu dt, and it reaches M[f*] as Kn -> 0.
+// Spectral operator: the gain-loss split df/dt = G(f) - nu(f) f (nu the loss frequency) with G and nu
+// frozen at f* is solved exactly per velocity point, f* + dt phi(nu dt) (G - nu f*), phi(x) =
+// (1 - e^-x) / x, and the increment projected; bounded for any nu dt (f* + (G - nu f*) / nu = G / nu
+// in the stiff limit), first order in dt like the Euler step it reduces to as nu dt -> 0.
 fks_status fks_step_exp(fks_ctx* c, const void* f, void* f_out, double dt, void* stream) {
     if (!c) return FKS_ERR_INVALID_ARG;
     if (!f || !f_out || !aligned16(f) || !aligned16(f_out)) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must be 16-byte aligned device pointers");
     if (f == f_out) return fail(c, FKS_ERR_INVALID_ARG, "f and f_out must not alias");
-    if (!c->bgk) return fail(c, FKS_ERR_UNSUPPORTED, "the exponential step needs a BGK context");
+    if (c->tc || c->dealias)
+        return fail(c, FKS_ERR_UNSUPPORTED, "the exponential step runs on the BGK and the FP64/FP32 spectral kernels");
     if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(c, FKS_ERR_INVALID_ARG, "dt must be finite and >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     fks_status st = launch_offsets(c, dt, s);

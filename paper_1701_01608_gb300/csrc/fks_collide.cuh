@@ -37,6 +37,7 @@
 #pragma once
 #include <cooperative_groups.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "fks_df.cuh"
 #include "fks_dfloat.cuh"
@@ -73,7 +74,9 @@ struct CollideArgs {
     double inv_kn;
     double dt;              // Euler step (step mode)
     int mode;               // 0 collide (out = Q), 1 step (out = f* + dt Q), 2 collide without projection,
-                            // 3 second Heun stage (out = (base + f* + dt Q) / 2; no transport, not batch)
+                            // 3 second Heun stage (out = (base + f* + dt Q) / 2; no transport, not batch),
+                            // 4 exponential step: out = f* + dt P[phi(nu dt) (G - nu f*)], nu = l / Kn the
+                            //   loss frequency, phi(x) = (1 - e^-x) / x, P the projection
     double P[25];           // dv^6 (C C^T)^-1 over the rows phi = (1, v, |v|^2/2)
     const BatchItem* items; // batch mode: ncells items, each a homogeneous problem
     const void* base;       // mode 3: the first stage's input, same layout as out (may be out itself)
@@ -643,11 +646,29 @@ collide_kernel(CollideArgs args) {
 #pragma unroll
                     for (int z = 0; z < N; ++z) col[z] = T(colbase[zoff[z]]);
                 }
+                // mode 4, the exponential (integrating-factor) step of the gain-loss split
+                // df/dt = G - nu f with nu = l / Kn and G frozen at f*: the increment is
+                // dt phi(nu dt) (G - nu f*), phi(x) = (1 - e^-x) / x, then projected like Q (the
+                // factor is computed in FP32 except in FP64 contexts; phi -> 1 as nu dt -> 0).  Where the
+                // discrete loss frequency is not positive (ringing of the truncated spectrum in the far
+                // tails) the term stays explicit: phi(max(x, 0)) = 1.
+                const bool expm = args.mode == 4;
+                const double kdt = inv_kn * dt_step;
+                auto phi = [&](int z) -> T {
+                    if constexpr (sizeof(T) == 8 && !std::is_same<T, dfloat>::value) {
+                        const double x = (double)av[z] * kdt;
+                        return x > 0.0 ? -expm1(-x) / x : 1.0;
+                    } else {
+                        const float x = (float)av[z] * (float)kdt;
+                        return T(x > 0.0f ? -expm1f(-x) / x : 1.0f);
+                    }
+                };
                 auto rval = [&](int z) -> T {
                     T g;
                     if constexpr (Cfg::G_REG) g = Greg[z];
                     else g = Gcol[(long)z * NTASK];
-                    return fma(-col[z], av[z], g);
+                    const T r = fma(-col[z], av[z], g);
+                    return expm ? r * phi(z) : r;
                 };
                 const int warp = tid >> 5, lane = tid & 31;
                 // escalation bound inputs: sum r^2 (r = G - f* l) and sum (f* l)^2 over the cell (FP32: an
@@ -665,7 +686,7 @@ collide_kernel(CollideArgs args) {
 #pragma unroll
                         for (int z = 0; z < N; ++z) {
                             const float r = rval(z);
-                            const float lz = col[z] * av[z];
+                            const float lz = expm ? col[z] * av[z] * phi(z) : col[z] * av[z];
                             e_qq = fmaf(r, r, e_qq);
                             e_ll = fmaf(lz, lz, e_ll);
                             a0 = df_add1(a0, r);
@@ -802,7 +823,7 @@ collide_kernel(CollideArgs args) {
                         cxy = (T)(mu[0] + mu[1] * vx + mu[2] * vy + mu[4] * v2xy);
                     const T kn = (T)inv_kn, dt = (T)dt_step;
                     const bool heun = !BATCH && args.mode == 3;
-                    const bool stepm = args.mode == 1 || heun;
+                    const bool stepm = args.mode == 1 || heun || expm;
                     ST* dst = fout + cell * N3 + ((long)zx * N + zl_y) * N;
                     // Heun: base row of this column (read before this thread's own store to it)
                     const ST* brow = static_cast<const ST*>(args.base) + cell * N3 + ((long)zx * N + zl_y) * N;

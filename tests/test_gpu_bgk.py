@@ -123,8 +123,10 @@ def test_bgk_exponential_step_matches_oracle(fks, oracle, n, prec, kn):
     assert rel(got, f) < (1e-11 if prec == 0 else 3e-6)
 
 
-def test_bgk_exponential_step_unsupported_for_spectral(fks):
-    c = fks.Context(fks.Config(ncell=(2, 1, 1), n=16, L=8.0, kernel=0, precision=1))
+def test_exponential_step_unsupported_for_split_bf16(fks):
+    """The exponential step runs on the BGK and the FP64/FP32 spectral kernels, not on the split-BF16
+    tensor-core kernel."""
+    c = fks.Context(fks.Config(ncell=(2, 1, 1), n=16, L=8.0, kernel=0, precision=2))
     f = torch.zeros((2, 16, 16, 16), device="cuda")
     with pytest.raises(fks.FKSError) as e:
         c.step_exp(f, torch.empty_like(f), 0.01)

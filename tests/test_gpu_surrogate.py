@@ -214,3 +214,88 @@ def test_routed_surrogate_collide_to_tensor_cores(fks):
     for c in range(nc):
         want = Qs[c] if not ind[c] <= thr else Qn[c]
         assert torch.equal(Qm[c], want), c
+
+
+def test_surrogate_step_routes_like_the_spectral_step(fks):
+    """fks_surrogate_step: with every cell routed it is the spectral step itself (transport into
+    work, then f* + dt Q over the routed list), bit for bit against fks_step; with none routed every
+    cell gets f* + dt Q of the network."""
+    n, L, kn = 16, 8.0, 0.3
+    ncell = (5, 3, 2)
+    cfg = fks.Config(ncell=ncell, bc=(1, 0, 0), n=n, L=L, kn=kn, A1=4, A2=4, precision=fks.FKS_FP32)
+    ca, cb = fks.Context(cfg), fks.Context(cfg)
+    net = fks.Net(n, 2, seed=11)
+    f = torch.from_numpy(I.two_stream(ncell, n, L, seed=8, noise=0.05).astype(np.float32)).cuda()
+    ref, out, work = torch.empty_like(f), torch.empty_like(f), torch.empty_like(f)
+    dt = 0.01
+    ca.step(f, ref, dt)
+    assert cb.surrogate_step(net, f, out, work, dt, 1.0, 1.0, -1.0) == f.shape[0]
+    assert torch.equal(out, ref)
+    # none routed: f* + dt Q_net, Q_net as fks_surrogate_collide gives it on f*
+    cc = fks.Context(cfg)
+    out2, work2 = torch.empty_like(f), torch.empty_like(f)
+    assert cc.surrogate_step(net, f, out2, work2, dt, 2.5, 1.0, 1e30) == 0
+    assert torch.equal(work2, work)      # the same transport (offsets from zero in both contexts)
+    qn = torch.empty_like(f)
+    fks.Context(cfg).surrogate_collide(net, work2, qn, 2.5, 1.0, 1e30)
+    assert torch.allclose(out2, work2 + dt * qn, rtol=1e-6, atol=1e-7)
+
+
+def test_trained_surrogate_gain_at_its_certified_tolerance(fks, oracle):
+    """What the trained network gains over the method without it.  A network trained on the
+    workload's velocity grid (two-stream and shock-tube-like mixtures) is calibrated on held-out
+    cells; at a tolerance it can certify, the certified cells are within that tolerance of the
+    oracle, the routed ones are the spectral result, and the learned path on the certified cells
+    is faster than the FP64 spectral operator on the same cells.  At 1e-3 the calibrated indicator
+    certifies none of them (the network's error is >= 1e-2 of ||Q|| at best)."""
+    from paper_1701_01608_gb300 import surrogate as S
+    n, L = 32, 10.0
+    f = S.two_stream_cells(torch, 384, n=n, L=L, seed=21)
+    Q = S.labels(torch, f, n=n, L=L, kn=1.0)
+    sur = S.train(torch, f, Q, batch=8, lr=2e-3, n=n, L=L, holdout=0.25, steps=1200)
+    assert sur.calib["covered"] >= 0.95
+    held = S.two_stream_cells(torch, 96, n=n, L=L, seed=22)
+    Qh = S.labels(torch, held, n=n, L=L, kn=1.0)
+    tol = 0.3
+    ctx = fks.Context(fks.Config(ncell=(96, 1, 1), n=n, L=L, kn=1.0, A1=4, A2=8, precision=fks.FKS_FP32))
+    out = torch.empty_like(held)
+    routed = ctx.surrogate_collide(sur.net, held, out, sur.out_scale, sur.ind_scale, tol)
+    ind = ctx.indicator()
+    cert = [c for c in range(96) if ind[c] <= tol]
+    assert len(cert) > 0 and routed == 96 - len(cert)
+    err = ((out - Qh).double().flatten(1).norm(dim=1) / Qh.double().flatten(1).norm(dim=1)).cpu().numpy()
+    for c in range(96):
+        if c in cert:
+            assert err[c] <= tol, (c, err[c])
+        else:
+            assert err[c] < 1e-5          # routed: the (escalated) FP32 spectral operator
+    # two certified cells against the oracle itself
+    tab = oracle.tables(n, L, 0, 0.25, 4, 8, 0)
+    for c in cert[:2]:
+        Qo = oracle.collide(held[c:c + 1].double().cpu().numpy(), tab, kn=1.0)[0]
+        assert rel(out[c].double().cpu().numpy(), Qo) <= tol
+    # time: the learned path on the certified cells against the FP64 spectral operator on them
+    fc = held[torch.tensor(cert, device="cuda")].contiguous()
+    k = fc.shape[0]
+    cl = fks.Context(fks.Config(ncell=(k, 1, 1), n=n, L=L, kn=1.0, A1=4, A2=8, precision=fks.FKS_FP32))
+    c64 = fks.Context(fks.Config(ncell=(k, 1, 1), n=n, L=L, kn=1.0, A1=4, A2=8, precision=fks.FKS_FP64))
+    ql, q64, f64 = torch.empty_like(fc), torch.empty(fc.shape, dtype=torch.float64, device="cuda"), fc.double()
+
+    def best(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    t_learn = best(lambda: cl.surrogate_collide(sur.net, fc, ql, sur.out_scale, sur.ind_scale, tol))
+    t_fp64 = best(lambda: c64.collide(f64, q64))
+    assert t_learn < t_fp64, (t_learn, t_fp64)
+    # the stated tolerance of the learned path is out of this network's reach
+    assert ctx.surrogate_collide(sur.net, held, out, sur.out_scale, sur.ind_scale, 1e-3) == 96
