@@ -307,6 +307,12 @@ __device__ void xpass_task_map(unsigned* map, unsigned char* used) {
     }
 }
 
+// phi(x) = (1 - e^-x) / x of the exponential step for x > 0, 1 otherwise (the explicit update where
+// the discrete loss frequency is not positive).  Not inlined: the unrolled epilogue calls it per
+// element and an inlined copy of expm1 per call site makes the kernels large.
+static __device__ __noinline__ float exp_step_factor(float x) { return x > 0.0f ? -expm1f(-x) / x : 1.0f; }
+static __device__ __noinline__ double exp_step_factor(double x) { return x > 0.0 ? -expm1(-x) / x : 1.0; }
+
 // T: arithmetic of the transforms (float, double, or dfloat: double-float pairs on the FP32 pipes);
 // ST: element type of f, out and base in global memory (ST = float with T = double or dfloat: the
 // last escalation tier of an FP32 state)
@@ -655,13 +661,10 @@ collide_kernel(CollideArgs args) {
                 const bool expm = args.mode == 4;
                 const double kdt = inv_kn * dt_step;
                 auto phi = [&](int z) -> T {
-                    if constexpr (sizeof(T) == 8 && !std::is_same<T, dfloat>::value) {
-                        const double x = (double)av[z] * kdt;
-                        return x > 0.0 ? -expm1(-x) / x : 1.0;
-                    } else {
-                        const float x = (float)av[z] * (float)kdt;
-                        return T(x > 0.0f ? -expm1f(-x) / x : 1.0f);
-                    }
+                    if constexpr (sizeof(T) == 8 && !std::is_same<T, dfloat>::value)
+                        return exp_step_factor((double)av[z] * kdt);
+                    else
+                        return T(exp_step_factor((float)av[z] * (float)kdt));
                 };
                 auto rval = [&](int z) -> T {
                     T g;

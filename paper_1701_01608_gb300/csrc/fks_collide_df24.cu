@@ -1,0 +1,9 @@
+// fks_collide_df24.cu -- the collision kernel in double-float arithmetic over an FP32 state at n = 24
+// (the last escalation tier; one translation unit per n, so that the large kernels compile in parallel).
+#include "fks_internal.h"
+
+namespace fks {
+
+bool find_collide_variant_dfloat_24(CollideVariant* out) { return collide_variant<dfloat, 24, 4, float>(out); }
+
+}  // namespace fks

@@ -7,32 +7,26 @@
 
 namespace fks {
 
-template <typename T, int N, int C>
-static bool variant(CollideVariant* out) {
-    using Cfg = CollideCfg<T, N, C>;
-    out->func = reinterpret_cast<const void*>(&collide_kernel<T, N, C, false, float>);
-    out->func_batch = reinterpret_cast<const void*>(&collide_kernel<T, N, C, true, float>);
-    out->N = N;
-    out->C = C;
-    out->NT = Cfg::NT;
-    out->smem = Cfg::SMEM_BYTES;
-    out->fp64 = true;
-    return true;
-}
-
-// one cluster size per n: the FP64 default
-template <typename T>
-static bool find(int N, int C, CollideVariant* out) {
+// one cluster size per n: the FP64 default.  The double-float instantiations sit in translation
+// units of their own (fks_collide_df*.cu), compiled in parallel: each is a large kernel.
+bool find_collide_variant_mixed(int N, int C, CollideVariant* out) {
     switch (N * 16 + C) {
-        case 8 * 16 + 1: return variant<T, 8, 1>(out);
-        case 16 * 16 + 2: return variant<T, 16, 2>(out);
-        case 24 * 16 + 4: return variant<T, 24, 4>(out);
-        case 32 * 16 + 8: return variant<T, 32, 8>(out);
+        case 8 * 16 + 1: return collide_variant<double, 8, 1, float>(out);
+        case 16 * 16 + 2: return collide_variant<double, 16, 2, float>(out);
+        case 24 * 16 + 4: return collide_variant<double, 24, 4, float>(out);
+        case 32 * 16 + 8: return collide_variant<double, 32, 8, float>(out);
         default: return false;
     }
 }
 
-bool find_collide_variant_mixed(int N, int C, CollideVariant* out) { return find<double>(N, C, out); }
-bool find_collide_variant_dfloat(int N, int C, CollideVariant* out) { return find<dfloat>(N, C, out); }
+bool find_collide_variant_dfloat(int N, int C, CollideVariant* out) {
+    switch (N * 16 + C) {
+        case 8 * 16 + 1: return find_collide_variant_dfloat_8(out);
+        case 16 * 16 + 2: return find_collide_variant_dfloat_16(out);
+        case 24 * 16 + 4: return find_collide_variant_dfloat_24(out);
+        case 32 * 16 + 8: return find_collide_variant_dfloat_32(out);
+        default: return false;
+    }
+}
 
 }  // namespace fks

@@ -29,6 +29,25 @@ bool find_collide_variant_f64(int N, int C, CollideVariant* out);
 // with double-float arithmetic on the FP32 pipes
 bool find_collide_variant_mixed(int N, int C, CollideVariant* out);
 bool find_collide_variant_dfloat(int N, int C, CollideVariant* out);
+// the double-float instantiation of each n at its cluster size (fks_collide_df*.cu)
+bool find_collide_variant_dfloat_8(CollideVariant* out);
+bool find_collide_variant_dfloat_16(CollideVariant* out);
+bool find_collide_variant_dfloat_24(CollideVariant* out);
+bool find_collide_variant_dfloat_32(CollideVariant* out);
+
+// fill *out with the instantiation collide_kernel<T, N, C, *, ST> (both the cell and the batch kernel)
+template <typename T, int N, int C, typename ST = T>
+inline bool collide_variant(CollideVariant* out) {
+    using Cfg = CollideCfg<T, N, C>;
+    out->func = reinterpret_cast<const void*>(&collide_kernel<T, N, C, false, ST>);
+    out->func_batch = reinterpret_cast<const void*>(&collide_kernel<T, N, C, true, ST>);
+    out->N = N;
+    out->C = C;
+    out->NT = Cfg::NT;
+    out->smem = Cfg::SMEM_BYTES;
+    out->fp64 = sizeof(T) == 8;
+    return true;
+}
 
 // One tier of the precision escalation: the cluster kernel that recomputes the listed cells of the
 // tier before it (FP32 arithmetic, or FP64 arithmetic over the FP32 state) with its own tables.
