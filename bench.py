@@ -624,6 +624,13 @@ def main():
             fa_b = [torch.from_numpy(p["f0"]).to(dev, dty).contiguous() for p in probs]
             fb_b = [torch.empty_like(x) for x in fa_b]
             dts = [0.2 * p["kn"] for p in probs]
+            tuned = None
+            if prec == fks.FKS_FP32:
+                # the autotuner picks (cluster size, radix schedule) per n class on these problems
+                from paper_1701_01608_gb300 import autotune
+                tuned = autotune.tune_batch(b, fa_b, fb_b, precision=prec, reps=2,
+                                            cache=os.path.join(tempfile.gettempdir(), f"fks_tune_{os.getpid()}.json"),
+                                            use_cache=False)
             b.run(fa_b, fb_b, dts, 20)        # capture (first call) and one replay
             torch.cuda.synchronize()
             for i, p in enumerate(probs):
@@ -631,7 +638,9 @@ def main():
             tg, _ = timed_loop(torch, lambda: b.run(fa_b, fb_b, dts, 20), 1, 0, ws)
             outs[name] = fa_b
             resu[name] = {"ms_20_steps": tg, "value": pts_b * 20 / (tg / 1e3), "health_bits": b.check(),
-                          "cluster_sizes": {n: b.cluster_size(n) for n in (16, 24, 32)}}
+                          "cluster_sizes": {n: b.cluster_size(n) for n in (16, 24, 32)},
+                          "radix_schedules": {n: b.radix(n) for n in (16, 24, 32)},
+                          "autotuned": {str(n): list(v) for n, v in tuned.items()} if tuned else None}
             del b
         d = [float(((outs["fp32"][i].double() - outs["fp64"][i]).norm() /
                     (outs["fp64"][i] - torch.from_numpy(probs[i]["f0"]).to(dev)).norm()).item())
@@ -639,7 +648,8 @@ def main():
         resu["fp32"]["diff_vs_fp64_over_travel"] = {"max": max(d), "median": float(np.median(d))}
         resu["note"] = ("96 homogeneous problems, n in {16, 24, 32}, Kn log-uniform in [1e-3, 1], hard spheres or "
                         "pseudo-Maxwell, two-Maxwellian data; 20 steps (dt = 0.2 Kn) in one captured CUDA graph "
-                        "(fks_batch_run), one persistent launch per n class; FP32 with its escalation")
+                        "(fks_batch_run), one persistent launch per n class; FP32 with its escalation and the autotuned "
+                        "(cluster size, radix schedule) per class")
         configs["uneven_batch_96"] = resu
 
     # ---------------- variant B (de-aliased, 2n transforms) in the paper's own setting: 16^3 modes, 32^3 transforms

@@ -239,6 +239,14 @@ int fks_cluster_size(const fks_ctx *ctx);
 /* Override the cluster size (a divisor of n for which a kernel exists);
  * used by the autotuner.  Returns FKS_ERR_UNSUPPORTED if there is none. */
 fks_status fks_set_cluster_size(fks_ctx *ctx, int C);
+/* Cluster size and radix schedule together: radix = the top radix of the
+ * length-n transforms (0 the default schedule 32 = 4 x 8, 24 = 3 x 8,
+ * 16 = 4 x 4; FP32 kernels are also compiled with 2 and 8 at n = 32 and 16 and
+ * with 2, 4, 8 at n = 24, at the default cluster size).  The result is the same
+ * transform to rounding.  FKS_ERR_UNSUPPORTED for a combination not compiled. */
+fks_status fks_set_schedule(fks_ctx *ctx, int C, int radix);
+/* The radix schedule in use (0: default), -1 for a NULL context. */
+int fks_radix(const fks_ctx *ctx);
 
 /* Kernel launches enqueued by this context since creation (for accounting). */
 long fks_launch_count(const fks_ctx *ctx);
@@ -304,6 +312,9 @@ fks_status fks_batch_get_escalation(const fks_batch *b, double *tol, long *count
  * setter rebuilds that class's tables (used by the autotuner). */
 int fks_batch_cluster_size(const fks_batch *b, int n);
 fks_status fks_batch_set_cluster_size(fks_batch *b, int n, int C);
+/* cluster size and radix schedule of class n together (as fks_set_schedule); the radix in use */
+fks_status fks_batch_set_schedule(fks_batch *b, int n, int C, int radix);
+int fks_batch_radix(const fks_batch *b, int n);
 long fks_batch_launch_count(const fks_batch *b);
 void fks_batch_destroy(fks_batch *b);
 const char *fks_batch_last_error(const fks_batch *b);

@@ -18,7 +18,8 @@ LIB = os.path.join(HERE, "libfks.so")
 SOURCES = ["fks_capi.cu", "fks_collide_f32.cu", "fks_collide_f64.cu", "fks_bgk.cu", "fks_net.cu",
            "fks_surrogate.cu", "fks_collide_tc.cu", "fks_dealias.cu", "fks_vhs.cu",
            "fks_batch.cu", "fks_collide_mixed.cu",
-           "fks_collide_df32.cu", "fks_collide_df24.cu", "fks_collide_df16.cu", "fks_collide_df8.cu"]
+           "fks_collide_df32.cu", "fks_collide_df24.cu", "fks_collide_df16.cu", "fks_collide_df8.cu",
+           "fks_collide_f32_radix.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -136,11 +136,11 @@ static fks_status batch_setup_escalation(fks_batch* b, BatchClass& cl) {
     return FKS_OK;
 }
 
-static fks_status batch_configure_class(fks_batch* b, BatchClass& cl, int C) {
+static fks_status batch_configure_class(fks_batch* b, BatchClass& cl, int C, int radix = 0) {
     CollideVariant v;
     int nclus = 0;
     bool found = false;
-    cudaError_t e = query_variant(b->fp64, cl.n, C, &v, &nclus, &found);
+    cudaError_t e = query_variant(b->fp64, cl.n, C, &v, &nclus, &found, radix);
     if (e != cudaSuccess) return bfail(b, FKS_ERR_CUDA, cudaGetErrorString(e));
     if (!found) return bfail(b, FKS_ERR_UNSUPPORTED, "no collision kernel for this (precision, n, cluster size)");
     if (nclus <= 0) return bfail(b, FKS_ERR_UNSUPPORTED, "batch kernel cannot be resident on this device");
@@ -401,15 +401,25 @@ int fks_batch_cluster_size(const fks_batch* b, int n) {
     return -1;
 }
 
-fks_status fks_batch_set_cluster_size(fks_batch* b, int n, int C) {
+int fks_batch_radix(const fks_batch* b, int n) {
+    if (!b) return -1;
+    for (const BatchClass& cl : b->classes)
+        if (cl.n == n) return cl.var.radix;
+    return -1;
+}
+
+fks_status fks_batch_set_cluster_size(fks_batch* b, int n, int C) { return fks_batch_set_schedule(b, n, C, 0); }
+
+fks_status fks_batch_set_schedule(fks_batch* b, int n, int C, int radix) {
     if (!b) return FKS_ERR_INVALID_ARG;
     for (BatchClass& cl : b->classes) {
         if (cl.n != n) continue;
-        if (cl.C == C) return FKS_OK;
+        if (cl.C == C && cl.var.radix == radix) return FKS_OK;
         cudaDeviceSynchronize();
-        fks_status st = batch_configure_class(b, cl, C);
+        const bool retable = cl.C != C;
+        fks_status st = batch_configure_class(b, cl, C, radix);
         if (st != FKS_OK) return st;
-        st = batch_build_class_tables(b, cl);
+        if (retable) st = batch_build_class_tables(b, cl);
         if (st != FKS_OK) return st;
         // descriptors and graphs hold table pointers: rebuild them on demand
         for (GraphEntry& g : b->graphs)

@@ -536,8 +536,11 @@ int default_cluster_size(bool fp64, int N) {
     return N == 32 ? 8 : (N == 24 ? 4 : (N == 16 ? 2 : 1));
 }
 
-bool find_collide_variant(bool fp64, int N, int C, CollideVariant* out) {
-    return fp64 ? find_collide_variant_f64(N, C, out) : find_collide_variant_f32(N, C, out);
+bool find_collide_variant(bool fp64, int N, int C, CollideVariant* out, int radix) {
+    if (radix != 0) return !fp64 && find_collide_variant_f32_radix(N, C, radix, out);
+    const bool ok = fp64 ? find_collide_variant_f64(N, C, out) : find_collide_variant_f32(N, C, out);
+    if (ok) out->radix = 0;
+    return ok;
 }
 
 // Gauss-Legendre rule on [a, b] by Newton iteration on the Legendre recurrence
@@ -582,8 +585,8 @@ static fks_status cuda_fail(fks_ctx* c, cudaError_t e, const char* where) {
     } while (0)
 
 // (declared in fks_internal.h)
-cudaError_t fks::query_variant(bool fp64, int n, int C, CollideVariant* v, int* max_clusters, bool* found) {
-    *found = find_collide_variant(fp64, n, C, v);
+cudaError_t fks::query_variant(bool fp64, int n, int C, CollideVariant* v, int* max_clusters, bool* found, int radix) {
+    *found = find_collide_variant(fp64, n, C, v, radix);
     if (!*found) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(v->func_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem);
@@ -607,11 +610,11 @@ cudaError_t fks::query_variant(bool fp64, int n, int C, CollideVariant* v, int* 
     return cudaOccupancyMaxActiveClusters(max_clusters, v->func, &cfg);
 }
 
-static fks_status configure_variant(fks_ctx* c, int C) {
+static fks_status configure_variant(fks_ctx* c, int C, int radix = 0) {
     CollideVariant v;
     int nclus = 0;
     bool found = false;
-    FKS_CUDA(query_variant(c->fp64, c->n, C, &v, &nclus, &found));
+    FKS_CUDA(query_variant(c->fp64, c->n, C, &v, &nclus, &found, radix));
     if (!found) return fail(c, FKS_ERR_UNSUPPORTED, "no collision kernel for this (precision, n, cluster size)");
     if (nclus <= 0) return fail(c, FKS_ERR_UNSUPPORTED, "collision kernel cannot be resident on this device");
     c->var = v;
@@ -993,22 +996,29 @@ int fks_nv(const fks_ctx* c) { return c ? c->n * c->n * c->n : -1; }
 int fks_cluster_size(const fks_ctx* c) { return c ? c->C : -1; }
 long fks_launch_count(const fks_ctx* c) { return c ? c->launches : -1; }
 
-fks_status fks_set_cluster_size(fks_ctx* c, int C) {
+fks_status fks_set_schedule(fks_ctx* c, int C, int radix) {
     if (!c) return FKS_ERR_INVALID_ARG;
     if (c->bgk) return fail(c, FKS_ERR_UNSUPPORTED, "the BGK kernel has no cluster size");
     if (c->tc) return fail(c, FKS_ERR_UNSUPPORTED, "the tensor-core kernel has no cluster size");
-    if (c->dealias) return fks_set_cluster_size(c->inner, C);   // the 2n kernel does the transforms
-    if (C == c->C) return FKS_OK;
-    // tables are laid out per cluster rank: rebuild them for the new size
+    if (c->dealias) return fks_set_schedule(c->inner, C, radix);   // the 2n kernel does the transforms
+    if (C == c->C && radix == c->var.radix) return FKS_OK;
     CollideVariant v;
-    if (!find_collide_variant(c->fp64, c->n, C, &v)) return fail(c, FKS_ERR_UNSUPPORTED, "no kernel for this cluster size");
+    if (!find_collide_variant(c->fp64, c->n, C, &v, radix))
+        return fail(c, FKS_ERR_UNSUPPORTED, "no kernel for this cluster size and radix schedule");
     cudaDeviceSynchronize();
-    cudaFree(c->tables);
-    c->tables = nullptr;
-    fks_status st = configure_variant(c, C);
-    if (st == FKS_OK) st = build_tables(c);
+    const bool retable = C != c->C;   // tables are laid out per cluster rank
+    fks_status st = configure_variant(c, C, radix);
+    if (st == FKS_OK && retable) {
+        cudaFree(c->tables);
+        c->tables = nullptr;
+        st = build_tables(c);
+    }
     return st;
 }
+
+fks_status fks_set_cluster_size(fks_ctx* c, int C) { return fks_set_schedule(c, C, 0); }
+
+int fks_radix(const fks_ctx* c) { return c ? c->var.radix : -1; }
 
 
 static fks_status launch_bgk_ctx(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,

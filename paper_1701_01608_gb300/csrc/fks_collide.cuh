@@ -316,7 +316,8 @@ static __device__ __noinline__ double exp_step_factor(double x) { return x > 0.0
 // T: arithmetic of the transforms (float, double, or dfloat: double-float pairs on the FP32 pipes);
 // ST: element type of f, out and base in global memory (ST = float with T = double or dfloat: the
 // last escalation tier of an FP32 state)
-template <typename T, int N, int C, bool BATCH = false, typename ST = T>
+// R0: top radix of the length-N transforms (0: the default schedule; see fft in fks_fft.cuh)
+template <typename T, int N, int C, bool BATCH = false, typename ST = T, int R0 = 0>
 __global__ void __launch_bounds__(CollideCfg<T, N, C>::NT, 1)
 collide_kernel(CollideArgs args) {
     using Cfg = CollideCfg<T, N, C>;
@@ -497,7 +498,7 @@ collide_kernel(CollideArgs args) {
             cpx<T> a[N];
 #pragma unroll
             for (int z = 0; z < N; ++z) a[z] = {T(colbase[zoff[z]]), T(0)};
-            fft<N, -1>(a);
+            fft<N, -1, R0>(a);
             cpx<T>* stg = W + ((long)zl_x * N + zl_y) * HF;
 #pragma unroll
             for (int k = 0; k < HF; ++k) stg[k] = a[k];
@@ -518,7 +519,7 @@ collide_kernel(CollideArgs args) {
             cpx<T> a[N];
 #pragma unroll
             for (int y = 0; y < N; ++y) a[y] = W[((long)xl * N + y) * HF + kz];
-            fft<N, -1>(a);
+            fft<N, -1, R0>(a);
             const int x = rank * NS + xl;
 #pragma unroll
             for (int ky = 0; ky < N; ++ky) putF(ky / NS, ((long)x * NS + ky % NS) * HF + kz, a[ky]);
@@ -530,7 +531,7 @@ collide_kernel(CollideArgs args) {
             cpx<T> a[N];
 #pragma unroll
             for (int x = 0; x < N; ++x) a[x] = Fh[((long)x * NS + kyl) * HF + kz];
-            fft<N, -1>(a);
+            fft<N, -1, R0>(a);
 #pragma unroll
             for (int kx = 0; kx < N; ++kx) Fh[((long)kx * NS + kyl) * HF + kz] = a[kx];
         }
@@ -569,7 +570,7 @@ collide_kernel(CollideArgs args) {
                         a[kx] = {tv * fv.x, tv * fv.y};
                     }
                 }
-                fft<N, +1>(a);
+                fft<N, +1, R0>(a);
             }
             cluster_wait();   // every CTA has finished reading its W (previous z-pass)
             if (active) {
@@ -612,7 +613,7 @@ collide_kernel(CollideArgs args) {
             if (active_y) {
 #pragma unroll
                 for (int y = 0; y < N; ++y) a[y] = W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP];
-                fft<N, +1>(a);
+                fft<N, +1, R0>(a);
 #pragma unroll
                 for (int y = 0; y < N; ++y) W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP] = a[y];
             }

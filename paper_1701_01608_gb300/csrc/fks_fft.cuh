@@ -7,6 +7,8 @@
 // octant reduction), never from a device math call.
 //
 //   fft<N, SIGN>(a)  :  a_k <- sum_j a_j exp(SIGN * 2 pi i j k / N), unnormalised
+//   fft<N, SIGN, R0> :  the same with the top radix R0 in {2, 3, 4, 8} (the radix schedule:
+//                       N = R0 x P, the sub-transforms of size P by the default schedule)
 //   c2r<N>(h, x)     :  real x_j = sum_{k=0}^{N-1} X_k exp(+2 pi i j k / N) for a
 //                       Hermitian X given as h[0] = (X_0, X_{N/2}) (both real)
 //                       and h[k] = X_k, 1 <= k < N/2; costs one N/2-point FFT.
@@ -99,9 +101,10 @@ FKS_HD cpx<T> mul_tw(cpx<T> a) {
 
 // ---------------------------------------------------------------- FFT kernels
 //
-// Mixed-radix decimation in time: N = R * P with R in {3, 4} at the top and
-// the sub-transforms of size P recursive; sizes 2, 3, 4 and 8 are direct
-// butterflies.  32 = 4 x 8, 16 = 4 x 4, 24 = 3 x 8, 12 = 3 x 4.
+// Mixed-radix decimation in time: N = R * P with R in {3, 4} at the top (or the
+// requested R0 in {2, 3, 4, 8}) and the sub-transforms of size P recursive;
+// sizes 2, 3, 4 and 8 are direct butterflies.  Default schedules: 32 = 4 x 8,
+// 16 = 4 x 4, 24 = 3 x 8, 12 = 3 x 4; alternatives e.g. 32 = 8 x 4 or 2 x 16.
 namespace detail {
 
 template <int N> constexpr bool is_pow2() { return N > 0 && (N & (N - 1)) == 0; }
@@ -157,22 +160,31 @@ FKS_HD void dft8(cpx<T> (&a)[8]) {
     a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
 }
 
-template <int N> constexpr int top_radix() {
-    if constexpr (N % 3 == 0) return 3;
+template <int N, int R0> constexpr int top_radix() {
+    if constexpr (R0 != 0) return R0;
+    else if constexpr (N % 3 == 0) return 3;
     else return 4;
+}
+
+// t[q] <- sub[q][K] W^{qK} for q < R (W = exp(SIGN 2 pi i / N)), compile-time q
+template <typename T, int SIGN, int N, int R, int P, int K, int... Q>
+FKS_HD void twiddle_column(cpx<T> (&t)[R], const cpx<T> (&sub)[R][P], std::integer_sequence<int, Q...>) {
+    ((t[Q] = mul_tw<T, SIGN, (long)Q * K, N>(sub[Q][K])), ...);
 }
 
 template <typename T, int SIGN, int N, int R, int P, int K>
 FKS_HD void combine_column(cpx<T> (&a)[N], const cpx<T> (&sub)[R][P]) {
     cpx<T> t[R];
-    t[0] = sub[0][K];
-    t[1] = mul_tw<T, SIGN, K, N>(sub[1][K]);
-    t[2] = mul_tw<T, SIGN, 2 * K, N>(sub[2][K]);
-    if constexpr (R == 3) {
+    twiddle_column<T, SIGN, N, R, P, K>(t, sub, std::make_integer_sequence<int, R>{});
+    if constexpr (R == 2) {
+        dft2<T, SIGN>(t[0], t[1]);
+    } else if constexpr (R == 3) {
         dft3<T, SIGN>(t[0], t[1], t[2]);
-    } else {
-        t[3] = mul_tw<T, SIGN, 3 * K, N>(sub[3][K]);
+    } else if constexpr (R == 4) {
         dft4<T, SIGN>(t[0], t[1], t[2], t[3]);
+    } else {
+        static_assert(R == 8, "top radix 2, 3, 4 or 8");
+        dft8<T, SIGN>(t);
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) a[K + P * q] = t[q];
@@ -185,7 +197,7 @@ FKS_HD void combine_all(cpx<T> (&a)[N], const cpx<T> (&sub)[R][P], std::integer_
 
 }  // namespace detail
 
-template <int N, int SIGN, typename T>
+template <int N, int SIGN, int R0 = 0, typename T>
 FKS_HD void fft(cpx<T> (&a)[N]) {
     if constexpr (N == 1) {
         return;
@@ -193,12 +205,12 @@ FKS_HD void fft(cpx<T> (&a)[N]) {
         detail::dft2<T, SIGN>(a[0], a[1]);
     } else if constexpr (N == 3) {
         detail::dft3<T, SIGN>(a[0], a[1], a[2]);
-    } else if constexpr (N == 4) {
+    } else if constexpr (N == 4 && R0 == 0) {
         detail::dft4<T, SIGN>(a[0], a[1], a[2], a[3]);
-    } else if constexpr (N == 8) {
+    } else if constexpr (N == 8 && R0 == 0) {
         detail::dft8<T, SIGN>(a);
     } else {
-        constexpr int R = detail::top_radix<N>();
+        constexpr int R = detail::top_radix<N, R0>();
         constexpr int P = N / R;
         static_assert(P * R == N, "FFT size must be 2^a or 3*2^a");
         cpx<T> sub[R][P];

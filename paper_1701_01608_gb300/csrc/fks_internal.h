@@ -19,10 +19,13 @@ struct CollideVariant {
     int N, C, NT;
     size_t smem;
     bool fp64;
+    int radix = 0;            // top radix of the length-N transforms (0: the default schedule)
 };
 
-// Look up an instantiation; returns false if (fp64, N, C) was not compiled.
-bool find_collide_variant(bool fp64, int N, int C, CollideVariant* out);
+// Look up an instantiation; returns false if (fp64, N, C, radix) was not compiled (radix 0: the
+// default schedule; other radixes: FP32 only).
+bool find_collide_variant(bool fp64, int N, int C, CollideVariant* out, int radix = 0);
+bool find_collide_variant_f32_radix(int N, int C, int R0, CollideVariant* out);
 bool find_collide_variant_f32(int N, int C, CollideVariant* out);
 bool find_collide_variant_f64(int N, int C, CollideVariant* out);
 // FP64 arithmetic over an FP32 state (the last tier of the precision escalation), and the same
@@ -35,17 +38,18 @@ bool find_collide_variant_dfloat_16(CollideVariant* out);
 bool find_collide_variant_dfloat_24(CollideVariant* out);
 bool find_collide_variant_dfloat_32(CollideVariant* out);
 
-// fill *out with the instantiation collide_kernel<T, N, C, *, ST> (both the cell and the batch kernel)
-template <typename T, int N, int C, typename ST = T>
+// fill *out with the instantiation collide_kernel<T, N, C, *, ST, R0> (both the cell and the batch kernel)
+template <typename T, int N, int C, typename ST = T, int R0 = 0>
 inline bool collide_variant(CollideVariant* out) {
     using Cfg = CollideCfg<T, N, C>;
-    out->func = reinterpret_cast<const void*>(&collide_kernel<T, N, C, false, ST>);
-    out->func_batch = reinterpret_cast<const void*>(&collide_kernel<T, N, C, true, ST>);
+    out->func = reinterpret_cast<const void*>(&collide_kernel<T, N, C, false, ST, R0>);
+    out->func_batch = reinterpret_cast<const void*>(&collide_kernel<T, N, C, true, ST, R0>);
     out->N = N;
     out->C = C;
     out->NT = Cfg::NT;
     out->smem = Cfg::SMEM_BYTES;
     out->fp64 = sizeof(T) == 8;
+    out->radix = R0;
     return true;
 }
 
@@ -143,7 +147,7 @@ inline fks_status alloc_failure() {
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 // Look up the (precision, n, C) instantiation, raise its shared-memory limit and count how many
 // clusters can be resident at once (*found = false: no such instantiation).
-cudaError_t query_variant(bool fp64, int n, int C, CollideVariant* v, int* max_clusters, bool* found);
+cudaError_t query_variant(bool fp64, int n, int C, CollideVariant* v, int* max_clusters, bool* found, int radix = 0);
 // Spectral tables of one (n, L, kernel, directions) in the collision kernel's layout for cluster
 // size C (full: the unsplit layout of the split-BF16 kernel), built on the device in FP64 and
 // stored in the working precision; *out is a new device allocation.  vx (FKS_VHS only): the

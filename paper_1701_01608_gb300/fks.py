@@ -68,7 +68,8 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_gradient", "fks_net_train_step", "fks_net_launch_count", "fks_net_last_error",
            "fks_net_destroy", "fks_surrogate_inputs", "fks_surrogate_collide", "fks_surrogate_indicator",
            "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias", "fks_step_host", "fks_vhs_factor",
-           "fks_step_strang", "fks_alu_peak", "fks_step_exp", "fks_relax", "fks_surrogate_step", "fks_set_profiling", "fks_get_profile", "fks_set_escalation", "fks_get_escalation", "fks_set_escalation_arith",
+           "fks_step_strang", "fks_alu_peak", "fks_step_exp", "fks_relax", "fks_surrogate_step", "fks_set_profiling", "fks_get_profile", "fks_set_schedule", "fks_radix",
+           "fks_batch_set_schedule", "fks_batch_radix", "fks_set_escalation", "fks_get_escalation", "fks_set_escalation_arith",
            "fks_batch_set_escalation", "fks_batch_get_escalation"]
 
 
@@ -102,6 +103,8 @@ def lib(build: bool = True):
     L.fks_nv.argtypes = [P]
     L.fks_cluster_size.argtypes = [P]
     L.fks_set_cluster_size.argtypes = [P, I]
+    L.fks_set_schedule.argtypes = [P, I, I]
+    L.fks_radix.argtypes = [P]
     L.fks_launch_count.argtypes = [P]
     L.fks_launch_count.restype = ctypes.c_long
     L.fks_kernel_transform.argtypes = [I, D, D, D, ctypes.POINTER(D), ctypes.POINTER(D)]
@@ -119,6 +122,8 @@ def lib(build: bool = True):
     L.fks_batch_get_escalation.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
     L.fks_batch_cluster_size.argtypes = [P, I]
     L.fks_batch_set_cluster_size.argtypes = [P, I, I]
+    L.fks_batch_set_schedule.argtypes = [P, I, I, I]
+    L.fks_batch_radix.argtypes = [P, I]
     L.fks_batch_launch_count.argtypes = [P]
     L.fks_batch_launch_count.restype = ctypes.c_long
     L.fks_batch_destroy.argtypes = [P]
@@ -304,6 +309,14 @@ class Context:
     def set_cluster_size(self, C: int):
         self._check(self._L.fks_set_cluster_size(self._h, C), "fks_set_cluster_size")
 
+    def set_schedule(self, C: int, radix: int = 0):
+        """Cluster size and radix schedule (top radix of the length-n transforms, 0 = default)."""
+        self._check(self._L.fks_set_schedule(self._h, C, radix), "fks_set_schedule")
+
+    @property
+    def radix(self) -> int:
+        return self._L.fks_radix(self._h)
+
     @property
     def launches(self) -> int:
         return self._L.fks_launch_count(self._h)
@@ -466,6 +479,12 @@ class Batch:
 
     def set_cluster_size(self, n: int, C: int):
         self._check(self._L.fks_batch_set_cluster_size(self._h, n, C), "fks_batch_set_cluster_size")
+
+    def set_schedule(self, n: int, C: int, radix: int = 0):
+        self._check(self._L.fks_batch_set_schedule(self._h, n, C, radix), "fks_batch_set_schedule")
+
+    def radix(self, n: int) -> int:
+        return self._L.fks_batch_radix(self._h, n)
 
     @property
     def launches(self) -> int:

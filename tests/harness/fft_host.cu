@@ -51,6 +51,37 @@ static int dispatch_c2r(int n, const double* in, double* out) {
     return 1;
 }
 
+template <int N, int R0, typename T>
+static void run_fft_r(int sign, const double* in, double* out) {
+    fks::cpx<T> a[N];
+    for (int i = 0; i < N; ++i) a[i] = {T(in[2 * i]), T(in[2 * i + 1])};
+    if (sign < 0) fks::fft<N, -1, R0>(a);
+    else fks::fft<N, +1, R0>(a);
+    for (int i = 0; i < N; ++i) { out[2 * i] = double(a[i].x); out[2 * i + 1] = double(a[i].y); }
+}
+
+// the radix schedules the collision kernels instantiate (top radix r0 of an n-point transform)
+template <typename T>
+static int dispatch_fft_r(int n, int r0, int sign, const double* in, double* out) {
+    switch (n * 16 + r0) {
+        case 8 * 16 + 2: run_fft_r<8, 2, T>(sign, in, out); return 0;
+        case 8 * 16 + 4: run_fft_r<8, 4, T>(sign, in, out); return 0;
+        case 16 * 16 + 2: run_fft_r<16, 2, T>(sign, in, out); return 0;
+        case 16 * 16 + 8: run_fft_r<16, 8, T>(sign, in, out); return 0;
+        case 24 * 16 + 2: run_fft_r<24, 2, T>(sign, in, out); return 0;
+        case 24 * 16 + 4: run_fft_r<24, 4, T>(sign, in, out); return 0;
+        case 24 * 16 + 8: run_fft_r<24, 8, T>(sign, in, out); return 0;
+        case 32 * 16 + 2: run_fft_r<32, 2, T>(sign, in, out); return 0;
+        case 32 * 16 + 8: run_fft_r<32, 8, T>(sign, in, out); return 0;
+    }
+    return 1;
+}
+
+extern "C" int fks_test_fft_radix(int n, int r0, int sign, int prec, const double* in, double* out) {
+    if (prec == 2) return dispatch_fft_r<fks::dfloat>(n, r0, sign, in, out);
+    return prec ? dispatch_fft_r<double>(n, r0, sign, in, out) : dispatch_fft_r<float>(n, r0, sign, in, out);
+}
+
 extern "C" int fks_test_fft(int n, int sign, int prec, const double* in, double* out) {
     if (prec == 2) return dispatch_fft<fks::dfloat>(n, sign, in, out);
     return prec ? dispatch_fft<double>(n, sign, in, out) : dispatch_fft<float>(n, sign, in, out);

@@ -22,6 +22,7 @@ def harness(tmp_path_factory):
     P = ctypes.c_void_p
     lib.fks_test_fft.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
     lib.fks_test_c2r.argtypes = [ctypes.c_int, ctypes.c_int, P, P]
+    lib.fks_test_fft_radix.argtypes = [ctypes.c_int] * 4 + [P, P]
     return lib
 
 
@@ -58,3 +59,20 @@ def test_c2r_matches_numpy(harness, n, fp64):
     assert harness.fks_test_c2r(n, fp64, inp.ctypes.data, out.ctypes.data) == 0
     want = n * np.fft.irfft(X, n)
     assert np.abs(out - want).max() < TOL[fp64] * np.abs(want).max()
+
+
+@pytest.mark.parametrize("prec", [1, 0, 2])
+@pytest.mark.parametrize("n,r0", [(8, 2), (8, 4), (16, 2), (16, 8), (24, 2), (24, 4), (24, 8), (32, 2), (32, 8)])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_radix_schedules_match_numpy(harness, n, r0, sign, prec):
+    """The alternative radix schedules (top radix r0 of the n-point transform) the autotuner can
+    choose give the same transform."""
+    rng = np.random.default_rng(n * 31 + r0 + sign)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    inp = np.ascontiguousarray(x).view(np.float64).copy()
+    out = np.empty(2 * n)
+    assert harness.fks_test_fft_radix(n, r0, sign, prec, inp.ctypes.data, out.ctypes.data) == 0
+    got = out.view(np.complex128)
+    xin = inp.view(np.complex128) if prec else inp.astype(np.float32).astype(np.float64).view(np.complex128)
+    want = np.fft.fft(xin) if sign < 0 else n * np.fft.ifft(xin)
+    assert np.abs(got - want).max() < TOL[prec] * np.abs(want).max()

@@ -84,9 +84,9 @@ def test_autotune_keeps_parity(fks, oracle, tmp_path):
     fs = [torch.from_numpy(p["f0"]).to("cuda", torch.float32).contiguous() for p in probs]
     Qs = [torch.empty_like(f) for f in fs]
     chosen = autotune.tune_batch(b, fs, Qs, precision=1, reps=2, cache=str(tmp_path / "tune.json"))
-    for n, C in chosen.items():
-        assert C in autotune.CANDIDATES[(1, n)]
-        assert b.cluster_size(n) == C
+    for n, (C, r) in chosen.items():
+        assert (C, r) in autotune.CANDIDATES[(1, n)]
+        assert b.cluster_size(n) == C and b.radix(n) == r
     b.collide(fs, Qs)
     for p, f, Q in zip(probs, fs, Qs):
         t = oracle.tables(p["n"], p["L"], p["kernel"], 0.25, 4, 8, 0)
@@ -107,3 +107,25 @@ def test_every_cluster_size_of_a_class(fks, oracle):
         Q = torch.empty_like(f)
         b.collide([f], [Q])
         assert rel(Q.double().cpu().numpy(), Qo) < 1e-5
+
+
+@pytest.mark.parametrize("n", [16, 24, 32])
+def test_every_radix_schedule_matches_oracle(fks, oracle, n):
+    """Every compiled (cluster size, radix schedule) of an FP32 context: the same operator (relative
+    L2 of Q <= 1e-5 per cell against the oracle)."""
+    from paper_1701_01608_gb300 import autotune
+    L = 8.0 if n == 16 else 10.0
+    nc = 5
+    ctx = fks.Context(fks.Config(ncell=(nc, 1, 1), n=n, L=L, kn=0.4, A1=4, A2=8, precision=1))
+    f = I.two_stream((nc, 1, 1), n, L, seed=70 + n, noise=0.05).astype(np.float32)
+    fd = torch.from_numpy(f).cuda()
+    Qo = oracle.collide(f.astype(np.float64), oracle.tables(n, L, 0, 0.25, 4, 8, 0), kn=0.4)
+    for C, r in autotune.CANDIDATES[(1, n)]:
+        ctx.set_schedule(C, r)
+        assert ctx.cluster_size == C and ctx.radix == r
+        Q = torch.empty_like(fd)
+        ctx.collide(fd, Q)
+        assert ctx.check() == 0
+        Qg = Q.double().cpu().numpy()
+        for c in range(nc):
+            assert rel(Qg[c], Qo[c]) < 1e-5, (C, r, c)

@@ -100,12 +100,21 @@ def test_bkw_batch_50_steps_follow_the_closed_form(fks, bkw):
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-4)])
-def test_uneven_batch_96_problems_graph_matches_oracle(fks, oracle, prec, tol):
+def test_uneven_batch_96_problems_graph_matches_oracle(fks, oracle, prec, tol, tmp_path):
     probs = I.config_uneven_batch(96)
     b = fks.Batch(probs, A1=4, A2=8, precision=prec)
     dtype = torch.float64 if prec == 0 else torch.float32
     fa = [torch.from_numpy(p["f0"]).to("cuda", dtype).contiguous() for p in probs]
     fb = [torch.empty_like(x) for x in fa]
+    if prec == 1:
+        # the autotuner picks (cluster size, radix schedule) per n class and records it
+        import json
+        from paper_1701_01608_gb300 import autotune
+        cache = str(tmp_path / "tune.json")
+        chosen = autotune.tune_batch(b, fa, fb, precision=1, reps=2, cache=cache)
+        assert set(chosen) == {16, 24, 32}
+        data = json.load(open(cache))
+        assert len(data) == 3 and all("radix" in v and len(v["ms"]) >= 4 for v in data.values())
     f0 = [x.double().cpu().numpy() for x in fa]
     dts = [0.2 * p["kn"] for p in probs]
     steps = 20
