@@ -363,6 +363,7 @@ def main():
     ap.add_argument("--no-vhs", action="store_true")
     ap.add_argument("--no-strang", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the headline path (profiling runs only)")
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--clocks-log", default=None, help="keep the raw nvidia-smi clock samples of the timed "
                                                         "region in this CSV file")
@@ -398,73 +399,79 @@ def main():
     alu64 = fks.alu_peak(fks.FKS_FP64)
 
     # ---------------- the metric's path: learned + split BF16, escalated to 1e-3 per cell
-    sur, train_s = train_surrogate(torch, args.train_steps)
-    cfgl = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
-                      precision=fks.FKS_BF16X3)
-    ctx = fks.Context(cfgl)
-    assert abs(ctx.escalation()[0] - TOL) < 1e-15
-    fa, fb, work = f0.clone(), torch.empty_like(f0), torch.empty_like(f0)
-    state = {"a": fa, "b": fb}
+    # (--no-learned: profiling runs of the other lines; no headline value then)
+    value = total_ms = None
+    roofline = learned = positivity = clocks = None
+    launches = bits = 0
+    sur = ctx = None
+    if not args.no_learned:
+        sur, train_s = train_surrogate(torch, args.train_steps)
+        cfgl = fks.Config(ncell=GRID, bc=(1, 0, 0), n=NV, L=LBOX, kernel=0, C=0.25, kn=KN, A1=A1, A2=A2,
+                          precision=fks.FKS_BF16X3)
+        ctx = fks.Context(cfgl)
+        assert abs(ctx.escalation()[0] - TOL) < 1e-15
+        fa, fb, work = f0.clone(), torch.empty_like(f0), torch.empty_like(f0)
+        state = {"a": fa, "b": fb}
 
-    def learned_step():
-        ctx.surrogate_step(sur.net, state["a"], state["b"], work, dt, sur.out_scale, sur.ind_scale, TOL)
-        state["a"], state["b"] = state["b"], state["a"]
+        def learned_step():
+            ctx.surrogate_step(sur.net, state["a"], state["b"], work, dt, sur.out_scale, sur.ind_scale, TOL)
+            state["a"], state["b"] = state["b"], state["a"]
 
-    for _ in range(args.warmup):
-        learned_step()
-    ctx.profile()                    # clear the stage record of the warm-up
-    ctx.set_profiling(True)
-    launches0 = ctx.launches + sur.net.launches
-    clk = Clocks(torch.cuda.current_device(),
-                 args.clocks_log or os.path.join(tempfile.gettempdir(), f"fks_clocks_{os.getpid()}_{rank}.csv"))
-    total_ms, per = timed_loop(torch, learned_step, args.steps, 0, ws)
-    clocks = clk.stop()
-    launches = ctx.launches + sur.net.launches - launches0
-    stage_ms, stage_n = ctx.profile()
-    ctx.set_profiling(False)
-    total_ms = max_over_ranks(total_ms, ws)
-    value = ws * PTS * args.steps / (total_ms / 1e3)
-    bits = ctx.check()
-    _, esc_counts = ctx.escalation()          # the last step's escalated cells per tier
-    # one more step, kept for the error check and the routing counts
-    fs_in = state["a"]
-    routed = ctx.surrogate_step(sur.net, fs_in, state["b"], work, dt, sur.out_scale, sur.ind_scale, TOL)
-    _, esc_last = ctx.escalation()
-    learned_err = None
-    if ws == 1:
-        cl = sample_ctx(fks, fks.FKS_BF16X3, TOL)
-        learned_err = operator_errors(torch, fks, dev, work, lambda fs, q: cl.surrogate_collide(
-            sur.net, fs, q, sur.out_scale, sur.ind_scale, TOL))
-        del cl
-    positivity = health(torch, state["b"])
-    # roofline of the dominant kernel: the double-float tier (stage 2 of a split-BF16 context)
-    df_ms = stage_ms[2] / max(stage_n[2], 1)
-    df_cells = esc_counts[1]
-    df_flops = flops_per_cell() * df_cells
-    df_ach = df_flops / (df_ms / 1e3) / 1e12 if df_ms > 0 else 0.0
-    b_df = DRAM_BYTES_PER_CELL.get("collide_dfloat")
-    roofline = {"bound": "alu", "achieved": df_ach, "peak": DFLOAT_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": df_ach / DFLOAT_PEAK_TFLOPS,
-                "traffic": b_df * df_cells if b_df else None,
-                "kernel": "collide_kernel<dfloat, 32, 8> (last escalation tier)",
-                "algorithmic_flops_per_launch": df_flops, "launch_ms": df_ms, "cells_per_launch": df_cells,
-                "peak_note": "double-float operations on the FP32 pipes: derived FP32 peak (152 SMs x 128 lanes x "
-                             "2 flop x 2.07 GHz) / %.0f FP32 instructions per operator flop" % DFLOAT_COST,
-                "traffic_note": "dram bytes per listed cell of one ncu capture (512 cells), times the cells of a launch",
-                "frac_of_fp64_peak": df_ach / FP64_PEAK_TFLOPS,
-                "cells_note": "cells of the last timed step; the stage time is the mean over the timed steps"}
-    stages = {"split_bf16_kernel_ms": stage_ms[0] / max(stage_n[0], 1),
-              "fp32_tier_ms": stage_ms[1] / max(stage_n[1], 1),
-              "dfloat_tier_ms": df_ms,
-              "other_ms": float(np.mean(per)) - sum(stage_ms) / max(args.steps, 1),
-              "note": "CUDA events around each collision launch inside the timed steps (fks_set_profiling); other = "
-                      "offsets, transport into f*, surrogate classification and inference"}
-    learned = {"routed_fraction": routed / NCELLS, "certified_fraction": 1.0 - routed / NCELLS,
-               "escalated": {"to_fp32": esc_last[0], "to_dfloat": esc_last[1], "cells": NCELLS},
-               "err_vs_fp64": learned_err, "train_seconds": train_s, "train_loss_last": sur.train_loss[-1],
-               "calibration": sur.calib, "threshold": TOL, "stages": stages, "gpu_launches": launches,
-               "health_bits": bits}
-    del fa, fb
+        for _ in range(args.warmup):
+            learned_step()
+        ctx.profile()                    # clear the stage record of the warm-up
+        ctx.set_profiling(True)
+        launches0 = ctx.launches + sur.net.launches
+        clk = Clocks(torch.cuda.current_device(),
+                     args.clocks_log or os.path.join(tempfile.gettempdir(), f"fks_clocks_{os.getpid()}_{rank}.csv"))
+        total_ms, per = timed_loop(torch, learned_step, args.steps, 0, ws)
+        clocks = clk.stop()
+        launches = ctx.launches + sur.net.launches - launches0
+        stage_ms, stage_n = ctx.profile()
+        ctx.set_profiling(False)
+        total_ms = max_over_ranks(total_ms, ws)
+        value = ws * PTS * args.steps / (total_ms / 1e3)
+        bits = ctx.check()
+        _, esc_counts = ctx.escalation()          # the last step's escalated cells per tier
+        # one more step, kept for the error check and the routing counts
+        fs_in = state["a"]
+        routed = ctx.surrogate_step(sur.net, fs_in, state["b"], work, dt, sur.out_scale, sur.ind_scale, TOL)
+        _, esc_last = ctx.escalation()
+        learned_err = None
+        if ws == 1:
+            cl = sample_ctx(fks, fks.FKS_BF16X3, TOL)
+            learned_err = operator_errors(torch, fks, dev, work, lambda fs, q: cl.surrogate_collide(
+                sur.net, fs, q, sur.out_scale, sur.ind_scale, TOL))
+            del cl
+        positivity = health(torch, state["b"])
+        # roofline of the dominant kernel: the double-float tier (stage 2 of a split-BF16 context)
+        df_ms = stage_ms[2] / max(stage_n[2], 1)
+        df_cells = esc_counts[1]
+        df_flops = flops_per_cell() * df_cells
+        df_ach = df_flops / (df_ms / 1e3) / 1e12 if df_ms > 0 else 0.0
+        b_df = DRAM_BYTES_PER_CELL.get("collide_dfloat")
+        roofline = {"bound": "alu", "achieved": df_ach, "peak": DFLOAT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": df_ach / DFLOAT_PEAK_TFLOPS,
+                    "traffic": b_df * df_cells if b_df else None,
+                    "kernel": "collide_kernel<dfloat, 32, 8> (last escalation tier)",
+                    "algorithmic_flops_per_launch": df_flops, "launch_ms": df_ms, "cells_per_launch": df_cells,
+                    "peak_note": "double-float operations on the FP32 pipes: derived FP32 peak (152 SMs x 128 lanes x "
+                                 "2 flop x 2.07 GHz) / %.0f FP32 instructions per operator flop" % DFLOAT_COST,
+                    "traffic_note": "dram bytes per listed cell of one ncu capture (512 cells), times the cells of a launch",
+                    "frac_of_fp64_peak": df_ach / FP64_PEAK_TFLOPS,
+                    "cells_note": "cells of the last timed step; the stage time is the mean over the timed steps"}
+        stages = {"split_bf16_kernel_ms": stage_ms[0] / max(stage_n[0], 1),
+                  "fp32_tier_ms": stage_ms[1] / max(stage_n[1], 1),
+                  "dfloat_tier_ms": df_ms,
+                  "other_ms": float(np.mean(per)) - sum(stage_ms) / max(args.steps, 1),
+                  "note": "CUDA events around each collision launch inside the timed steps (fks_set_profiling); other = "
+                          "offsets, transport into f*, surrogate classification and inference"}
+        learned = {"routed_fraction": routed / NCELLS, "certified_fraction": 1.0 - routed / NCELLS,
+                   "escalated": {"to_fp32": esc_last[0], "to_dfloat": esc_last[1], "cells": NCELLS},
+                   "err_vs_fp64": learned_err, "train_seconds": train_s, "train_loss_last": sur.train_loss[-1],
+                   "calibration": sur.calib, "threshold": TOL, "stages": stages, "gpu_launches": launches,
+                   "health_bits": bits}
+        del fa, fb
 
     # ---------------- the comparison: the plain FP64 spectral step (transport + FP64 operator)
     fp64 = None
@@ -487,7 +494,7 @@ def main():
 
     # ---------------- end to end through the public API with host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.no_learned:
         host_in = torch.empty(f0.shape, dtype=torch.float32, pin_memory=True)
         host_in.copy_(f0)
         host_out = torch.empty_like(host_in, pin_memory=True)
@@ -726,7 +733,7 @@ def main():
         return
     out = {
         "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps if total_ms else None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32+f32x2", "data": "synthetic",
         "config": {"workload": "hs_shocktube_%dx%dx%dc_32v" % GRID, "cells": NCELLS, "n_v": NV ** 3, "M": M,
                    "kernel": "hard spheres", "knudsen": KN, "bc": "specular x, periodic y z", "dt": dt,
@@ -744,7 +751,7 @@ def main():
         "positivity": positivity,
         "learned": learned,
         "fp64_spectral": fp64,
-        "speedup_vs_fp64_spectral": (value / fp64["value"]) if fp64 else None,
+        "speedup_vs_fp64_spectral": (value / fp64["value"]) if (fp64 and value) else None,
         "spectral_paths": raw,
         "bgk_step": bgk,
         "configs": configs,

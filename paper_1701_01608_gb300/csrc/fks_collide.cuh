@@ -409,6 +409,10 @@ collide_kernel(CollideArgs args) {
     if (args.cell0 + cluster_id < end) fetch_tables(item_tables(item_at(args.cell0 + cluster_id)), 0);
     const int ncx = args.nc[0], ncy = args.nc[1], ncz = args.nc[2];
 
+    // the double-float instantiations (instruction-fetch bound: every inlined transform is long) share
+    // one call site of each transform between the passes of a direction
+    constexpr bool kCompact = std::is_same<T, dfloat>::value;
+
     // z-pass ownership: column (xl, y), x = rank*NS + xl (threads >= NTASK idle)
     const bool has_col = tid < NTASK;
     const int zl_x = has_col ? tid / N : 0, zl_y = tid % N;
@@ -544,104 +548,218 @@ collide_kernel(CollideArgs args) {
             // ---- x-pass: table product, pack kz'=0 with kz'=N/2, inverse FFT along kx
             const bool active = has_col && (!loss || x_tab == 0);
             const bool active_y = has_col && (!loss || t_tab == 0);
+            // the exchange after the x-pass stores (the same steps as the inline sequence below)
+            auto exchange = [&]() {
+                if constexpr (C > 1) {
+                    if (tid == 0) mbar_expect_tx(xbar, (C - 1) * Cfg::BLK_BYTES);
+                }
+                __syncthreads();
+                if constexpr (C > 1) {
+                    if (tid < C && tid != rank) {
+                        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                        const int dst = tid;
+                        const cpx<T>* src = S + (long)(dst < rank ? dst : dst - 1) * BLK;
+                        const uint32_t d =
+                            map_rank(smem_addr(W), dst) + (uint32_t)((long)rank * BLK * (long)sizeof(cpx<T>));
+                        const uint32_t bar = map_rank(smem_addr(xbar), dst);
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
+                            "r"(smem_addr(src)), "r"(Cfg::BLK_BYTES), "r"(bar)
+                            : "memory");
+                    }
+                }
+                if (tid == 0) {
+                    if (!loss) fetch_tables(tab, p + 1);
+                    else if (has_next) fetch_tables(item_tables(item_at(it + nclusters)), 0);
+                }
+                if constexpr (C > 1) {
+                    tmo |= !mbar_wait_bounded(xbar, xphase, args.flags, tmo ? 1L : (1L << 26));
+                    xphase ^= 1u;
+                }
+            };
             cpx<T> a[N];
-            if constexpr (Cfg::TAB_SMEM) {
-                tmo |= !mbar_wait_bounded(tbar, tphase, args.flags, tmo ? 1L : (1L << 26));   // table slab of direction p has landed
-                tphase ^= 1u;
-            }
-            if (active) {
-                const cpx<T>* fb = Fh + (long)x_kyl * HF;
-                const T* tslab = Cfg::TAB_SMEM ? Tb : tab + ((long)p * C + rank) * Cfg::TAB_ELEMS;
-                const T* tb = tslab + (long)x_tab * N * NS * HF + (long)x_kyl * HF;
-                if (x_pp == 0) {
-#pragma unroll
-                    for (int kx = 0; kx < N; ++kx) {
-                        const long o = (long)kx * NS * HF;
-                        const cpx<T> fv = fb[o], fn = fb[o + H];
-                        const T tv = tb[o], tn = tb[o + H];
-                        a[kx] = {tv * fv.x - tn * fn.y, tv * fv.y + tn * fn.x};   // tv fv + i tn fn
+            if constexpr (kCompact) {
+                // one call site of the length-N FFT serves the x-pass and the y-pass (ps = 0, 1): the
+                // double-float kernel is bound by instruction fetch, and each inlined transform is
+                // thousands of instructions
+#pragma unroll 1
+                for (int ps = 0; ps < 2; ++ps) {
+                    const bool act = ps == 0 ? active : active_y;
+                    if (ps == 0) {
+                        if constexpr (Cfg::TAB_SMEM) {
+                            tmo |= !mbar_wait_bounded(tbar, tphase, args.flags, tmo ? 1L : (1L << 26));
+                            tphase ^= 1u;
+                        }
                     }
-                } else {
+                    if (act) {
+                        if (ps == 0) {
+                            const cpx<T>* fb = Fh + (long)x_kyl * HF;
+                            const T* tslab = Cfg::TAB_SMEM ? Tb : tab + ((long)p * C + rank) * Cfg::TAB_ELEMS;
+                            const T* tb = tslab + (long)x_tab * N * NS * HF + (long)x_kyl * HF;
+                            if (x_pp == 0) {
 #pragma unroll
-                    for (int kx = 0; kx < N; ++kx) {
-                        const long o = (long)kx * NS * HF + x_pp;
-                        const cpx<T> fv = fb[o];
-                        const T tv = tb[o];
-                        a[kx] = {tv * fv.x, tv * fv.y};
+                                for (int kx = 0; kx < N; ++kx) {
+                                    const long o = (long)kx * NS * HF;
+                                    const cpx<T> fv = fb[o], fn = fb[o + H];
+                                    const T tv = tb[o], tn = tb[o + H];
+                                    a[kx] = {tv * fv.x - tn * fn.y, tv * fv.y + tn * fn.x};
+                                }
+                            } else {
+#pragma unroll
+                                for (int kx = 0; kx < N; ++kx) {
+                                    const long o = (long)kx * NS * HF + x_pp;
+                                    const cpx<T> fv = fb[o];
+                                    const T tv = tb[o];
+                                    a[kx] = {tv * fv.x, tv * fv.y};
+                                }
+                            }
+                        } else {
+#pragma unroll
+                            for (int y = 0; y < N; ++y) a[y] = W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP];
+                        }
+                        fft<N, +1, R0>(a);
+                    }
+                    if (ps == 0) {
+                        cluster_wait();   // every CTA has finished reading its W (previous z-pass)
+                        if (act) {
+#pragma unroll
+                            for (int x = 0; x < N; ++x) {
+                                const int dst = x / NS;
+                                const long o = widx(x_tab, x % NS, x_kyl, x_pp);
+                                if (dst == rank) W[(long)rank * BLK + o] = a[x];
+                                else S[(long)(dst < rank ? dst : dst - 1) * BLK + o] = a[x];
+                            }
+                        }
+                        exchange();
+                    } else if (act) {
+#pragma unroll
+                        for (int y = 0; y < N; ++y) W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP] = a[y];
                     }
                 }
-                fft<N, +1, R0>(a);
-            }
-            cluster_wait();   // every CTA has finished reading its W (previous z-pass)
-            if (active) {
-                // own block directly into W[rank], peers' blocks into staging
-#pragma unroll
-                for (int x = 0; x < N; ++x) {
-                    const int dst = x / NS;
-                    const long o = widx(x_tab, x % NS, x_kyl, x_pp);
-                    if (dst == rank) W[(long)rank * BLK + o] = a[x];
-                    else S[(long)(dst < rank ? dst : dst - 1) * BLK + o] = a[x];
+            } else {
+                if constexpr (Cfg::TAB_SMEM) {
+                    tmo |= !mbar_wait_bounded(tbar, tphase, args.flags, tmo ? 1L : (1L << 26));   // table slab of direction p has landed
+                    tphase ^= 1u;
                 }
-            }
-            if constexpr (C > 1) {
-                if (tid == 0) mbar_expect_tx(xbar, (C - 1) * Cfg::BLK_BYTES);
-            }
-            __syncthreads();   // this CTA's x-pass is complete: staging written, slab free
-            if constexpr (C > 1) {
-                // one thread per peer issues that peer's bulk copy (the copies start together)
-                if (tid < C && tid != rank) {
-                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                    const int dst = tid;
-                    const cpx<T>* src = S + (long)(dst < rank ? dst : dst - 1) * BLK;
-                    const uint32_t d = map_rank(smem_addr(W), dst) + (uint32_t)((long)rank * BLK * (long)sizeof(cpx<T>));
-                    const uint32_t bar = map_rank(smem_addr(xbar), dst);
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
-                        "r"(smem_addr(src)), "r"(Cfg::BLK_BYTES), "r"(bar)
-                        : "memory");
+                if (active) {
+                    const cpx<T>* fb = Fh + (long)x_kyl * HF;
+                    const T* tslab = Cfg::TAB_SMEM ? Tb : tab + ((long)p * C + rank) * Cfg::TAB_ELEMS;
+                    const T* tb = tslab + (long)x_tab * N * NS * HF + (long)x_kyl * HF;
+                    if (x_pp == 0) {
+    #pragma unroll
+                        for (int kx = 0; kx < N; ++kx) {
+                            const long o = (long)kx * NS * HF;
+                            const cpx<T> fv = fb[o], fn = fb[o + H];
+                            const T tv = tb[o], tn = tb[o + H];
+                            a[kx] = {tv * fv.x - tn * fn.y, tv * fv.y + tn * fn.x};   // tv fv + i tn fn
+                        }
+                    } else {
+    #pragma unroll
+                        for (int kx = 0; kx < N; ++kx) {
+                            const long o = (long)kx * NS * HF + x_pp;
+                            const cpx<T> fv = fb[o];
+                            const T tv = tb[o];
+                            a[kx] = {tv * fv.x, tv * fv.y};
+                        }
+                    }
+                    fft<N, +1, R0>(a);
                 }
-            }
-            if (tid == 0) {
-                if (!loss) fetch_tables(tab, p + 1);
-                else if (has_next) fetch_tables(item_tables(item_at(it + nclusters)), 0);
-            }
-            if constexpr (C > 1) {
-                tmo |= !mbar_wait_bounded(xbar, xphase, args.flags, tmo ? 1L : (1L << 26));   // every peer's block has landed
-                xphase ^= 1u;
-            }
-            // ---- y-pass in place
-            if (active_y) {
-#pragma unroll
-                for (int y = 0; y < N; ++y) a[y] = W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP];
-                fft<N, +1, R0>(a);
-#pragma unroll
-                for (int y = 0; y < N; ++y) W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP] = a[y];
+                cluster_wait();   // every CTA has finished reading its W (previous z-pass)
+                if (active) {
+                    // own block directly into W[rank], peers' blocks into staging
+    #pragma unroll
+                    for (int x = 0; x < N; ++x) {
+                        const int dst = x / NS;
+                        const long o = widx(x_tab, x % NS, x_kyl, x_pp);
+                        if (dst == rank) W[(long)rank * BLK + o] = a[x];
+                        else S[(long)(dst < rank ? dst : dst - 1) * BLK + o] = a[x];
+                    }
+                }
+                if constexpr (C > 1) {
+                    if (tid == 0) mbar_expect_tx(xbar, (C - 1) * Cfg::BLK_BYTES);
+                }
+                __syncthreads();   // this CTA's x-pass is complete: staging written, slab free
+                if constexpr (C > 1) {
+                    // one thread per peer issues that peer's bulk copy (the copies start together)
+                    if (tid < C && tid != rank) {
+                        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                        const int dst = tid;
+                        const cpx<T>* src = S + (long)(dst < rank ? dst : dst - 1) * BLK;
+                        const uint32_t d = map_rank(smem_addr(W), dst) + (uint32_t)((long)rank * BLK * (long)sizeof(cpx<T>));
+                        const uint32_t bar = map_rank(smem_addr(xbar), dst);
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
+                            "r"(smem_addr(src)), "r"(Cfg::BLK_BYTES), "r"(bar)
+                            : "memory");
+                    }
+                }
+                if (tid == 0) {
+                    if (!loss) fetch_tables(tab, p + 1);
+                    else if (has_next) fetch_tables(item_tables(item_at(it + nclusters)), 0);
+                }
+                if constexpr (C > 1) {
+                    tmo |= !mbar_wait_bounded(xbar, xphase, args.flags, tmo ? 1L : (1L << 26));   // every peer's block has landed
+                    xphase ^= 1u;
+                }
+                // ---- y-pass in place
+                if (active_y) {
+    #pragma unroll
+                    for (int y = 0; y < N; ++y) a[y] = W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP];
+                    fft<N, +1, R0>(a);
+    #pragma unroll
+                    for (int y = 0; y < N; ++y) W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP] = a[y];
+                }
             }
             __syncthreads();
             // ---- z-pass: C2R along z, products
             T av[N];
-            if (has_col) {
-                const cpx<T>* c0 = W + (long)z_src * BLK + widx(0, zl_x, z_kyl, 0);
-                cpx<T> h[H];
-#pragma unroll
-                for (int k = 0; k < H; ++k) h[k] = c0[k];
-                c2r<N>(h, av);
-            }
-            if (!loss) {
+            if constexpr (kCompact) {
+                // one call site of the C2R for both tables: table 0 into av, table 1 into bv and the gain
                 if (has_col) {
-                    const cpx<T>* c1 = W + (long)z_src * BLK + widx(1, zl_x, z_kyl, 0);
-                    cpx<T> h[H];
+#pragma unroll 1
+                    for (int tb = 0; tb < (loss ? 1 : 2); ++tb) {
+                        const cpx<T>* c0 = W + (long)z_src * BLK + widx(tb, zl_x, z_kyl, 0);
+                        cpx<T> h[H];
 #pragma unroll
-                    for (int k = 0; k < H; ++k) h[k] = c1[k];
-                    T bv[N];
-                    c2r<N>(h, bv);
+                        for (int k = 0; k < H; ++k) h[k] = c0[k];
+                        T bv[N];
+                        c2r<N>(h, bv);
+                        if (tb == 0) {
 #pragma unroll
-                    for (int z = 0; z < N; ++z) {
-                        if constexpr (Cfg::G_REG) Greg[z] = fma(av[z], bv[z], Greg[z]);
-                        else Gcol[(long)z * NTASK] += av[z] * bv[z];
+                            for (int z = 0; z < N; ++z) av[z] = bv[z];
+                        } else {
+#pragma unroll
+                            for (int z = 0; z < N; ++z) Gcol[(long)z * NTASK] += av[z] * bv[z];
+                        }
                     }
                 }
-                cluster_arrive();   // this CTA has finished with W (its accesses ordered before peers' copies)
+                if (!loss) cluster_arrive();
+            } else {
+                if (has_col) {
+                    const cpx<T>* c0 = W + (long)z_src * BLK + widx(0, zl_x, z_kyl, 0);
+                    cpx<T> h[H];
+#pragma unroll
+                    for (int k = 0; k < H; ++k) h[k] = c0[k];
+                    c2r<N>(h, av);
+                }
+                if (!loss) {
+                    if (has_col) {
+                        const cpx<T>* c1 = W + (long)z_src * BLK + widx(1, zl_x, z_kyl, 0);
+                        cpx<T> h[H];
+#pragma unroll
+                        for (int k = 0; k < H; ++k) h[k] = c1[k];
+                        T bv[N];
+                        c2r<N>(h, bv);
+#pragma unroll
+                        for (int z = 0; z < N; ++z) {
+                            if constexpr (Cfg::G_REG) Greg[z] = fma(av[z], bv[z], Greg[z]);
+                            else Gcol[(long)z * NTASK] += av[z] * bv[z];
+                        }
+                    }
+                    cluster_arrive();   // this CTA has finished with W (its accesses ordered before peers' copies)
+                }
+            }
+            if (!loss) {
             } else {
                 // loss: r = G - f* l by one fused multiply-add (the product is exact,
                 // one rounding of the difference: relative to r itself), Q = r / Kn;
