@@ -181,6 +181,63 @@ __device__ __forceinline__ float2 df_shfl_xor(float2 v, int off) {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off));
 }
 
+// ---- transforms split over a pair of lanes (2t, 2t + 1) of a warp --------------------------
+// The double-float instantiations split every length-N transform of a pencil over G = 2 threads:
+// half the registers and half the transform code per thread and twice the warps per SM (with one
+// thread per pencil the double-float kernel is bound by instruction fetch, one warp per scheduler).
+__device__ __forceinline__ float pair_xchg(float v, unsigned mask) { return __shfl_xor_sync(mask, v, 1); }
+__device__ __forceinline__ double pair_xchg(double v, unsigned mask) { return __shfl_xor_sync(mask, v, 1); }
+__device__ __forceinline__ dfloat pair_xchg(dfloat v, unsigned mask) {
+    return dfloat(pair_xchg(v.hi, mask), pair_xchg(v.lo, mask));
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> pair_xchg(cpx<T> v, unsigned mask) {
+    return {pair_xchg(v.x, mask), pair_xchg(v.y, mask)};
+}
+
+// element index held in local slot m after fft_split by thread g of G: G = 1, m itself; G = 2,
+// the outputs k and k + N/2 of the last radix-2 combination with k = (m mod N/4) + g N/4
+template <int N, int G>
+__device__ __forceinline__ int split_out(int m, int g) {
+    if constexpr (G == 1) return m;
+    else return m % (N / 4) + g * (N / 4) + (m / (N / 4)) * (N / 2);
+}
+
+namespace detail {
+// output pair k = M + g N/4 of the radix-2 combination X_k = y0_k + W^k y1_k, X_{k+N/2} = y0_k - W^k y1_k
+// (W = exp(SIGN 2 pi i / N), y_g the half-length transform of the samples x_{2j+g}); thread 0 holds y0,
+// thread 1 y1, and each sends the partner the half it combines
+template <typename T, int SIGN, int N, int M>
+__device__ __forceinline__ void split_combine(cpx<T> (&a)[N / 2], bool g1, unsigned mask) {
+    constexpr int Q = N / 4;
+    const cpx<T> recv = pair_xchg(g1 ? a[M] : a[M + Q], mask);
+    const cpx<T> u = g1 ? recv : a[M];
+    cpx<T> v = mul_tw<T, SIGN, M, N>(g1 ? a[M + Q] : recv);
+    const cpx<T> vq = mul_si<T, SIGN>(v);   // W^{N/4} = SIGN i for thread 1's k = M + N/4
+    v = g1 ? vq : v;
+    a[M] = cadd(u, v);
+    a[M + Q] = csub(u, v);
+}
+template <typename T, int SIGN, int N, int... M>
+__device__ __forceinline__ void split_combine_all(cpx<T> (&a)[N / 2], bool g1, unsigned mask,
+                                                  std::integer_sequence<int, M...>) {
+    (split_combine<T, SIGN, N, M>(a, g1, mask), ...);
+}
+}  // namespace detail
+
+// fft<N, SIGN> of a pencil spread over G threads: thread g holds a[j] = x_{jG+g} (j < N/G) and ends
+// with a[m] = X_{split_out<N, G>(m, g)}; mask names the pair's two lanes (both call it together)
+template <int N, int SIGN, int G, int R0, typename T>
+__device__ __forceinline__ void fft_split(cpx<T> (&a)[N / G], int g, unsigned mask) {
+    if constexpr (G == 1) {
+        fft<N, SIGN, R0>(a);
+    } else {
+        static_assert(G == 2 && N % 4 == 0, "a pencil is split over one pair of lanes");
+        fft<N / 2, SIGN>(a);
+        detail::split_combine_all<T, SIGN, N>(a, g != 0, mask, std::make_integer_sequence<int, N / 4>{});
+    }
+}
+
 // cell index -> (cx, cy, cz) in 32-bit unsigned arithmetic (a context holds fewer
 // than 2^31 cells; 64-bit division is a long emulated sequence, run by every thread)
 __device__ __forceinline__ void cell_coords(long cell, int ncy, int ncz, int& cx, int& cy, int& cz) {
@@ -240,7 +297,10 @@ struct CollideCfg {
     static constexpr int HF = H + 1;          // kz' planes of f^ (odd row stride)
     static constexpr int HP = H + 1;          // row stride of W (odd)
     static constexpr int NTASK = N * N / C;   // pencils / columns per pass per CTA
-    static constexpr int NT = (NTASK + 31) / 32 * 32;   // threads per CTA (whole warps)
+    // threads per pencil: double-float transforms are split over a pair of lanes (fft_split)
+    static constexpr int G = std::is_same<T, dfloat>::value ? 2 : 1;
+    static constexpr int NE = N / G;          // pencil elements per thread
+    static constexpr int NT = (NTASK * G + 31) / 32 * 32;   // threads per CTA (whole warps)
     static constexpr bool G_REG = sizeof(T) == 4;       // FP32: gain accumulator in registers
     static constexpr long FH_ELEMS = (long)N * NS * HF;  // f^ slab [N kx][NS kyl][HF]
     // W: C source blocks, each [2 tab][NS xl][NS kyl][HP]   (cpx<T>)
@@ -358,7 +418,8 @@ collide_kernel(CollideArgs args) {
     // store v at element idx of the f^ slab of CTA dst
     auto putF = [&](int dst, long idx, cpx<T> v) {
         if constexpr (C == 1) Fh[idx] = v;
-        else st_cluster(Frank[dst] + (uint32_t)(idx * (long)sizeof(cpx<T>)), v);
+        else if constexpr (Cfg::G == 1) st_cluster(Frank[dst] + (uint32_t)(idx * (long)sizeof(cpx<T>)), v);
+        else st_cluster(map_rank(smem_addr(Fh), dst) + (uint32_t)(idx * (long)sizeof(cpx<T>)), v);   // dst per lane
     };
 
     // per-item data: the cells of one problem, or (batch) one problem per item
@@ -413,21 +474,29 @@ collide_kernel(CollideArgs args) {
     // one call site of each transform between the passes of a direction
     constexpr bool kCompact = std::is_same<T, dfloat>::value;
 
-    // z-pass ownership: column (xl, y), x = rank*NS + xl (threads >= NTASK idle)
-    const bool has_col = tid < NTASK;
-    const int zl_x = has_col ? tid / N : 0, zl_y = tid % N;
+    // pencil task of this thread and its part g of the pencil (G threads per pencil: the pair's
+    // lanes 2t, 2t + 1; element j of a pencil is loaded by part j mod G, outputs are at split_out)
+    constexpr int G = Cfg::G, NE = Cfg::NE;
+    const int task = G == 1 ? tid : tid / G;
+    const int g = G == 1 ? 0 : tid % G;
+    const unsigned pmask = G == 1 ? 0xffffffffu : 3u << (tid & 30);
+    auto zz = [g](int m) { return split_out<N, G>(m, g); };   // element of output slot m
+
+    // z-pass ownership: column (xl, y), x = rank*NS + xl (tasks >= NTASK idle)
+    const bool has_col = task < NTASK;
+    const int zl_x = has_col ? task / N : 0, zl_y = task % N;
     const int zx = rank * NS + zl_x;
     const int z_src = zl_y / NS, z_kyl = zl_y % NS;   // where column y sits in W
-    T* Gcol = Gs + tid;   // FP64: element z at Gcol[z * NTASK]
+    T* Gcol = Gs + task;   // FP64: element z at Gcol[z * NTASK]
 
     // y-pass task (tab, xl, plane), plane fastest
-    const int t_tab = tid / (NS * H);
-    const int t_rem = tid % (NS * H);
+    const int t_tab = task / (NS * H);
+    const int t_rem = task % (NS * H);
     const int t_xl = t_rem / H;
     const int t_pp = t_rem % H;
     // x-pass task (tab, kyl, plane) from the lane map (built before the first cluster barrier)
-    const unsigned xm = tid < NTASK ? xmap[tid] : 0u;
-    const int x_tab = tid < NTASK ? (int)(xm >> 16) : 2;
+    const unsigned xm = task < NTASK ? xmap[task] : 0u;
+    const int x_tab = task < NTASK ? (int)(xm >> 16) : 2;
     const int x_kyl = (int)((xm >> 8) & 255u);
     const int x_pp = (int)(xm & 255u);
     // offset of (tab, xl, kyl, plane) inside a W block
@@ -499,16 +568,19 @@ collide_kernel(CollideArgs args) {
         // ---------------- forward transform -----------------------------
         // F1: z-R2C of this CTA's columns; staging = W as [xl][y][HF]
         if (has_col) {
-            cpx<T> a[N];
+            cpx<T> a[NE];
 #pragma unroll
-            for (int z = 0; z < N; ++z) a[z] = {T(colbase[zoff[z]]), T(0)};
-            fft<N, -1, R0>(a);
+            for (int j = 0; j < NE; ++j) a[j] = {T(colbase[zoff[j * G + g]]), T(0)};
+            fft_split<N, -1, G, R0>(a, g, pmask);
             cpx<T>* stg = W + ((long)zl_x * N + zl_y) * HF;
 #pragma unroll
-            for (int k = 0; k < HF; ++k) stg[k] = a[k];
+            for (int m = 0; m < NE; ++m) {
+                const int k = zz(m);
+                if (G == 1 ? m < HF : k < HF) stg[k] = a[m];
+            }
             if constexpr (!Cfg::G_REG) {
 #pragma unroll
-                for (int z = 0; z < N; ++z) Gcol[(long)z * NTASK] = T(0);
+                for (int m = 0; m < NE; ++m) Gcol[(long)zz(m) * NTASK] = T(0);
             }
         }
         T Greg[Cfg::G_REG ? N : 1];
@@ -518,26 +590,29 @@ collide_kernel(CollideArgs args) {
         }
         __syncthreads();
         // F2 + F3: y-FFT of (xl, kz') pencils, scatter to the ky owner (pre-x-FFT, x in place of kx)
-        if (tid < NS * HF) {
-            const int xl = tid / HF, kz = tid % HF;
-            cpx<T> a[N];
+        if (task < NS * HF) {
+            const int xl = task / HF, kz = task % HF;
+            cpx<T> a[NE];
 #pragma unroll
-            for (int y = 0; y < N; ++y) a[y] = W[((long)xl * N + y) * HF + kz];
-            fft<N, -1, R0>(a);
+            for (int j = 0; j < NE; ++j) a[j] = W[((long)xl * N + (j * G + g)) * HF + kz];
+            fft_split<N, -1, G, R0>(a, g, pmask);
             const int x = rank * NS + xl;
 #pragma unroll
-            for (int ky = 0; ky < N; ++ky) putF(ky / NS, ((long)x * NS + ky % NS) * HF + kz, a[ky]);
+            for (int m = 0; m < NE; ++m) {
+                const int ky = zz(m);
+                putF(ky / NS, ((long)x * NS + ky % NS) * HF + kz, a[m]);
+            }
         }
         cluster_sync_all();
         // F4: x-FFT of (kyl, kz') pencils in place
-        if (tid < NS * HF) {
-            const int kyl = tid / HF, kz = tid % HF;
-            cpx<T> a[N];
+        if (task < NS * HF) {
+            const int kyl = task / HF, kz = task % HF;
+            cpx<T> a[NE];
 #pragma unroll
-            for (int x = 0; x < N; ++x) a[x] = Fh[((long)x * NS + kyl) * HF + kz];
-            fft<N, -1, R0>(a);
+            for (int j = 0; j < NE; ++j) a[j] = Fh[((long)(j * G + g) * NS + kyl) * HF + kz];
+            fft_split<N, -1, G, R0>(a, g, pmask);
 #pragma unroll
-            for (int kx = 0; kx < N; ++kx) Fh[((long)kx * NS + kyl) * HF + kz] = a[kx];
+            for (int m = 0; m < NE; ++m) Fh[((long)zz(m) * NS + kyl) * HF + kz] = a[m];
         }
         __syncthreads();
 
@@ -577,19 +652,53 @@ collide_kernel(CollideArgs args) {
                     xphase ^= 1u;
                 }
             };
-            cpx<T> a[N];
+            cpx<T> a[NE];
+            T av[NE];   // loss direction: the loss frequency l at the elements zz(m) of this thread's column
             if constexpr (kCompact) {
-                // one call site of the length-N FFT serves the x-pass and the y-pass (ps = 0, 1): the
-                // double-float kernel is bound by instruction fetch, and each inlined transform is
+                // z-pass input of the two tables' columns packed as one complex sequence: Z_k = X_k + i Y_k
+                // (X, Y the Hermitian spectra of table 0 and 1, stored as X_0 + i X_{N/2}, X_1 .. X_{N/2-1});
+                // its transform holds the two real C2R results as real and imaginary parts.  The loss
+                // direction transforms table 0 alone (Y = 0).
+                auto load_z = [&](bool two) {
+                    const cpx<T>* c0 = W + (long)z_src * BLK + widx(0, zl_x, z_kyl, 0);
+                    const cpx<T>* c1 = W + (long)z_src * BLK + widx(1, zl_x, z_kyl, 0);
+#pragma unroll
+                    for (int j = 0; j < NE; ++j) {
+                        const int k = j * G + g;
+                        const int kk = k <= H ? k : N - k;
+                        const int e = kk == H ? 0 : kk;
+                        const cpx<T> x0 = c0[e];
+                        const cpx<T> x1 = two ? c1[e] : cpx<T>{T(0), T(0)};
+                        cpx<T> X, Y;
+                        if (kk == 0) {
+                            X = {x0.x, T(0)};
+                            Y = {x1.x, T(0)};
+                        } else if (kk == H) {
+                            X = {x0.y, T(0)};
+                            Y = {x1.y, T(0)};
+                        } else if (k < H) {
+                            X = x0;
+                            Y = x1;
+                        } else {
+                            X = {x0.x, -x0.y};
+                            Y = {x1.x, -x1.y};
+                        }
+                        a[j] = {X.x - Y.y, X.y + Y.x};
+                    }
+                };
+                // one call site of the length-N transform serves the x-, y- and z-passes (ps = 0, 1, 2):
+                // the double-float kernel is bound by instruction fetch, and each inlined transform is
                 // thousands of instructions
 #pragma unroll 1
-                for (int ps = 0; ps < 2; ++ps) {
-                    const bool act = ps == 0 ? active : active_y;
+                for (int ps = 0; ps < (loss ? 2 : 3); ++ps) {
+                    const bool act = ps == 0 ? active : (ps == 1 ? active_y : has_col);
                     if (ps == 0) {
                         if constexpr (Cfg::TAB_SMEM) {
                             tmo |= !mbar_wait_bounded(tbar, tphase, args.flags, tmo ? 1L : (1L << 26));
                             tphase ^= 1u;
                         }
+                    } else if (ps == 2) {
+                        __syncthreads();   // the y-pass results are in W
                     }
                     if (act) {
                         if (ps == 0) {
@@ -598,42 +707,68 @@ collide_kernel(CollideArgs args) {
                             const T* tb = tslab + (long)x_tab * N * NS * HF + (long)x_kyl * HF;
                             if (x_pp == 0) {
 #pragma unroll
-                                for (int kx = 0; kx < N; ++kx) {
-                                    const long o = (long)kx * NS * HF;
+                                for (int j = 0; j < NE; ++j) {
+                                    const long o = (long)(j * G + g) * NS * HF;
                                     const cpx<T> fv = fb[o], fn = fb[o + H];
                                     const T tv = tb[o], tn = tb[o + H];
-                                    a[kx] = {tv * fv.x - tn * fn.y, tv * fv.y + tn * fn.x};
+                                    a[j] = {tv * fv.x - tn * fn.y, tv * fv.y + tn * fn.x};
                                 }
                             } else {
 #pragma unroll
-                                for (int kx = 0; kx < N; ++kx) {
-                                    const long o = (long)kx * NS * HF + x_pp;
+                                for (int j = 0; j < NE; ++j) {
+                                    const long o = (long)(j * G + g) * NS * HF + x_pp;
                                     const cpx<T> fv = fb[o];
                                     const T tv = tb[o];
-                                    a[kx] = {tv * fv.x, tv * fv.y};
+                                    a[j] = {tv * fv.x, tv * fv.y};
                                 }
                             }
-                        } else {
+                        } else if (ps == 1) {
 #pragma unroll
-                            for (int y = 0; y < N; ++y) a[y] = W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP];
+                            for (int j = 0; j < NE; ++j) {
+                                const int y = j * G + g;
+                                a[j] = W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP];
+                            }
+                        } else {
+                            load_z(true);
                         }
-                        fft<N, +1, R0>(a);
+                        fft_split<N, +1, G, R0>(a, g, pmask);
                     }
                     if (ps == 0) {
                         cluster_wait();   // every CTA has finished reading its W (previous z-pass)
                         if (act) {
 #pragma unroll
-                            for (int x = 0; x < N; ++x) {
+                            for (int m = 0; m < NE; ++m) {
+                                const int x = zz(m);
                                 const int dst = x / NS;
                                 const long o = widx(x_tab, x % NS, x_kyl, x_pp);
-                                if (dst == rank) W[(long)rank * BLK + o] = a[x];
-                                else S[(long)(dst < rank ? dst : dst - 1) * BLK + o] = a[x];
+                                if (dst == rank) W[(long)rank * BLK + o] = a[m];
+                                else S[(long)(dst < rank ? dst : dst - 1) * BLK + o] = a[m];
                             }
                         }
                         exchange();
-                    } else if (act) {
+                    } else if (ps == 1) {
+                        if (act) {
 #pragma unroll
-                        for (int y = 0; y < N; ++y) W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP] = a[y];
+                            for (int m = 0; m < NE; ++m) {
+                                const int y = zz(m);
+                                W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP] = a[m];
+                            }
+                        }
+                    } else {
+                        if (act) {
+#pragma unroll
+                            for (int m = 0; m < NE; ++m) Gcol[(long)zz(m) * NTASK] += a[m].x * a[m].y;
+                        }
+                        cluster_arrive();   // this CTA has finished with W (its accesses ordered before peers' copies)
+                    }
+                }
+                if (loss) {
+                    __syncthreads();
+                    if (has_col) {
+                        load_z(false);
+                        fft_split<N, +1, G, R0>(a, g, pmask);
+#pragma unroll
+                        for (int m = 0; m < NE; ++m) av[m] = a[m].x;
                     }
                 }
             } else {
@@ -709,32 +844,8 @@ collide_kernel(CollideArgs args) {
     #pragma unroll
                     for (int y = 0; y < N; ++y) W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP] = a[y];
                 }
-            }
-            __syncthreads();
-            // ---- z-pass: C2R along z, products
-            T av[N];
-            if constexpr (kCompact) {
-                // one call site of the C2R for both tables: table 0 into av, table 1 into bv and the gain
-                if (has_col) {
-#pragma unroll 1
-                    for (int tb = 0; tb < (loss ? 1 : 2); ++tb) {
-                        const cpx<T>* c0 = W + (long)z_src * BLK + widx(tb, zl_x, z_kyl, 0);
-                        cpx<T> h[H];
-#pragma unroll
-                        for (int k = 0; k < H; ++k) h[k] = c0[k];
-                        T bv[N];
-                        c2r<N>(h, bv);
-                        if (tb == 0) {
-#pragma unroll
-                            for (int z = 0; z < N; ++z) av[z] = bv[z];
-                        } else {
-#pragma unroll
-                            for (int z = 0; z < N; ++z) Gcol[(long)z * NTASK] += av[z] * bv[z];
-                        }
-                    }
-                }
-                if (!loss) cluster_arrive();
-            } else {
+                __syncthreads();
+                // ---- z-pass: C2R along z, products
                 if (has_col) {
                     const cpx<T>* c0 = W + (long)z_src * BLK + widx(0, zl_x, z_kyl, 0);
                     cpx<T> h[H];
@@ -766,10 +877,10 @@ collide_kernel(CollideArgs args) {
                 // the five moments of Q from three sums per column
                 const double vx = vel(zx), vy = vel(zl_y);
                 const double v2xy = 0.5 * (vx * vx + vy * vy);
-                T col[N];
+                T col[NE];   // f* at the elements zz(m) of this thread's column
                 if (has_col) {
 #pragma unroll
-                    for (int z = 0; z < N; ++z) col[z] = T(colbase[zoff[z]]);
+                    for (int m = 0; m < NE; ++m) col[m] = T(colbase[zoff[zz(m)]]);
                 }
                 // mode 4, the exponential (integrating-factor) step of the gain-loss split
                 // df/dt = G - nu f with nu = l / Kn and G frozen at f*: the increment is
@@ -779,18 +890,19 @@ collide_kernel(CollideArgs args) {
                 // tails) the term stays explicit: phi(max(x, 0)) = 1.
                 const bool expm = args.mode == 4;
                 const double kdt = inv_kn * dt_step;
-                auto phi = [&](int z) -> T {
+                // slot m of this thread's column (element zz(m))
+                auto phi = [&](int m) -> T {
                     if constexpr (sizeof(T) == 8 && !std::is_same<T, dfloat>::value)
-                        return exp_step_factor((double)av[z] * kdt);
+                        return exp_step_factor((double)av[m] * kdt);
                     else
-                        return T(exp_step_factor((float)av[z] * (float)kdt));
+                        return T(exp_step_factor((float)av[m] * (float)kdt));
                 };
-                auto rval = [&](int z) -> T {
-                    T g;
-                    if constexpr (Cfg::G_REG) g = Greg[z];
-                    else g = Gcol[(long)z * NTASK];
-                    const T r = fma(-col[z], av[z], g);
-                    return expm ? r * phi(z) : r;
+                auto rval = [&](int m) -> T {
+                    T gz;
+                    if constexpr (Cfg::G_REG) gz = Greg[m];
+                    else gz = Gcol[(long)zz(m) * NTASK];
+                    const T r = fma(-col[m], av[m], gz);
+                    return expm ? r * phi(m) : r;
                 };
                 const int warp = tid >> 5, lane = tid & 31;
                 // escalation bound inputs: sum r^2 (r = G - f* l) and sum (f* l)^2 over the cell (FP32: an
@@ -806,9 +918,10 @@ collide_kernel(CollideArgs args) {
                     if (has_col) {
                         float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0;
 #pragma unroll
-                        for (int z = 0; z < N; ++z) {
-                            const float r = rval(z);
-                            const float lz = expm ? col[z] * av[z] * phi(z) : col[z] * av[z];
+                        for (int m = 0; m < NE; ++m) {
+                            const int z = zz(m);
+                            const float r = rval(m);
+                            const float lz = expm ? col[m] * av[m] * phi(m) : col[m] * av[m];
                             e_qq = fmaf(r, r, e_qq);
                             e_ll = fmaf(lz, lz, e_ll);
                             a0 = df_add1(a0, r);
@@ -860,8 +973,9 @@ collide_kernel(CollideArgs args) {
                     if (has_col) {
                         double s0 = 0.0, sz = 0.0, szz = 0.0;
 #pragma unroll
-                        for (int z = 0; z < N; ++z) {
-                            const double r = (double)rval(z);
+                        for (int m = 0; m < NE; ++m) {
+                            const int z = zz(m);
+                            const double r = (double)rval(m);
                             s0 += r;
                             sz = fma(r, vzt[z], sz);
                             szz = fma(r, vz2t[z], szz);
@@ -950,14 +1064,20 @@ collide_kernel(CollideArgs args) {
                     // Heun: base row of this column (read before this thread's own store to it)
                     const ST* brow = static_cast<const ST*>(args.base) + cell * N3 + ((long)zx * N + zl_y) * N;
                     bool bad = false, neg = false;
-                    constexpr int V = 16 / sizeof(ST);
+                    // 16-byte vectors of the row where this thread's elements run in whole vectors
+                    // (G = 2: runs of N/4 consecutive elements), single elements otherwise
+                    constexpr int VW = 16 / sizeof(ST);
+                    constexpr int V = (G == 1 || (N / 4) % VW == 0) ? VW : 1;
                     static_assert((N * sizeof(ST)) % 16 == 0, "rows are whole 16-byte vectors");
 #pragma unroll
-                    for (int z0 = 0; z0 < N; z0 += V) {
+                    for (int m0 = 0; m0 < NE; m0 += V) {
+                        const int z0 = zz(m0);
                         ST res[V];
                         T bv[V];
                         if (heun) {
-                            if constexpr (sizeof(ST) == 4) {
+                            if constexpr (V == 1) {
+                                bv[0] = T(brow[z0]);
+                            } else if constexpr (sizeof(ST) == 4) {
                                 const float4 w = *reinterpret_cast<const float4*>(brow + z0);
                                 bv[0] = T(w.x); bv[1] = T(w.y); bv[2] = T(w.z); bv[3] = T(w.w);
                             } else {
@@ -968,14 +1088,16 @@ collide_kernel(CollideArgs args) {
 #pragma unroll
                         for (int j = 0; j < V; ++j) {
                             const int z = z0 + j;
-                            const T q = fma(rval(z), kn, -(cxy + czt[z]));
-                            T o = stepm ? fma(dt, q, col[z]) : q;
+                            const T q = fma(rval(m0 + j), kn, -(cxy + czt[z]));
+                            T o = stepm ? fma(dt, q, col[m0 + j]) : q;
                             if (heun) o = T(0.5) * (o + bv[j]);
                             res[j] = ST(o);
                             bad |= !isfinite(res[j]);
                             neg |= stepm && (res[j] < ST(0));
                         }
-                        if constexpr (sizeof(ST) == 4)
+                        if constexpr (V == 1)
+                            dst[z0] = res[0];
+                        else if constexpr (sizeof(ST) == 4)
                             *reinterpret_cast<float4*>(dst + z0) = make_float4(res[0], res[1], res[2], res[3]);
                         else
                             *reinterpret_cast<double2*>(dst + z0) = make_double2(res[0], res[1]);

@@ -25,6 +25,10 @@ namespace fks {
 
 template <typename T> struct cpx { T x, y; };
 
+// Arithmetic types whose products cost several sums (double-float pairs): an eighth-turn twiddle
+// is then taken as one sum scaled by 1/sqrt 2 instead of four products.
+template <typename T> struct costly_mul { static constexpr bool value = false; };
+
 template <typename T> FKS_HD cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T> FKS_HD cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
 template <typename T> FKS_HD cpx<T> cmul(cpx<T> a, cpx<T> b) {
@@ -91,9 +95,17 @@ FKS_HD cpx<T> mul_tw(cpx<T> a) {
         // odd multiple of an eighth turn: (+-1 +- i)/sqrt 2
         constexpr detail::SC sc = detail::sincos_frac(K, LEN);
         const T h = T(0.707106781186547524400844362104849039);
-        const T cr = sc.c > 0 ? h : -h;
-        const T ci = (SIGN * sc.s) > 0 ? h : -h;
-        return {cr * a.x - ci * a.y, cr * a.y + ci * a.x};
+        if constexpr (costly_mul<T>::value) {
+            // (sr + i si) h a with sr, si = +-1: the sums first, then two products
+            constexpr bool pr = sc.c > 0, pi = (SIGN * sc.s) > 0;
+            const T re = pr ? (pi ? a.x - a.y : a.x + a.y) : (pi ? -(a.x + a.y) : a.y - a.x);
+            const T im = pr ? (pi ? a.y + a.x : a.y - a.x) : (pi ? a.x - a.y : -(a.x + a.y));
+            return {h * re, h * im};
+        } else {
+            const T cr = sc.c > 0 ? h : -h;
+            const T ci = (SIGN * sc.s) > 0 ? h : -h;
+            return {cr * a.x - ci * a.y, cr * a.y + ci * a.x};
+        }
     } else {
         return cmul(a, twiddle<T, SIGN, K, LEN>());
     }

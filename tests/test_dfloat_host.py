@@ -26,13 +26,14 @@ def _build(tmp, src_text=None):
         inc = str(d)
     out = str(tmp / ("libdd_planted.so" if src_text else "libdd.so"))
     cmd = ["nvcc", "-std=c++17", "-O2", "-Xcompiler", "-fPIC,-ffp-contract=off", "-shared",
-           "--expt-relaxed-constexpr", "-I", inc, src, "-o", out]
+           "--expt-relaxed-constexpr", "-I", inc, "-I", CSRC, src, "-o", out]
     subprocess.run(cmd, check=True, capture_output=True)
     lib = ctypes.CDLL(out)
     F = ctypes.c_float
     for fn in ("fks_test_dd_add", "fks_test_dd_mul"):
         getattr(lib, fn).argtypes = [F, F, F, F, ctypes.c_void_p]
     lib.fks_test_dd_from_double.argtypes = [ctypes.c_double, ctypes.c_void_p]
+    lib.fks_test_dd_dot2.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     return lib
 
 
@@ -105,6 +106,52 @@ def test_product_within_relative_bound(lib):
         p = exact(a) * exact(b)
         assert abs(exact(r) - p) <= Fraction(2) ** -45 * abs(p), (a, b, r)
         assert normalised(r)
+
+
+def dot2(fn, a, b, c, d):
+    inp = np.array([*a, *b, *c, *d], dtype=np.float32)
+    out = np.zeros(2, dtype=np.float32)
+    fn(inp.ctypes.data, out.ctypes.data)
+    return float(out[0]), float(out[1])
+
+
+def dot2_cases(seed, n=400):
+    """(a, b, c, d) with a b + c d generic, cancelling (c d = -a b up to the low parts) or lopsided."""
+    rng = np.random.default_rng(seed)
+    for i in range(n):
+        a = pair(rng, 10.0 ** rng.uniform(-2, 2))
+        b = pair(rng, 10.0 ** rng.uniform(-2, 2))
+        kind = i % 3
+        if kind == 0:
+            c, d = pair(rng, 10.0 ** rng.uniform(-2, 2)), pair(rng, 10.0 ** rng.uniform(-2, 2))
+        elif kind == 1:   # complex product with a twiddle of modulus one: near cancellation
+            c, d = (-a[0], float(np.float32(a[1] * rng.uniform(-1, 1)))), b
+        else:
+            c, d = pair(rng, 1e-5), pair(rng)
+        yield a, b, c, d
+
+
+def test_dot2_within_normwise_bound(lib):
+    """The fused a b + c d of the complex products: error below 2^-45 (|a b| + |c d|), normalised."""
+    for a, b, c, d in dot2_cases(6):
+        r = dot2(lib.fks_test_dd_dot2, a, b, c, d)
+        ab, cd = exact(a) * exact(b), exact(c) * exact(d)
+        assert abs(exact(r) - (ab + cd)) <= Fraction(2) ** -45 * (abs(ab) + abs(cd)), (a, b, c, d, r)
+        assert normalised(r), (a, b, c, d, r)
+
+
+def test_planted_mistake_breaks_dot2_bound(tmp_path):
+    """Without the cross terms of the low parts the dot product is only single precision."""
+    text = open(os.path.join(CSRC, "fks_dfloat.cuh")).read()
+    planted = text.replace("    t = fmaf(a.lo, b.hi, t);\n", "")
+    assert planted != text
+    bad = _build(tmp_path, planted)
+    worst = Fraction(0)
+    for a, b, c, d in dot2_cases(7, 100):
+        r = dot2(bad.fks_test_dd_dot2, a, b, c, d)
+        ab, cd = exact(a) * exact(b), exact(c) * exact(d)
+        worst = max(worst, abs(exact(r) - (ab + cd)) / (abs(ab) + abs(cd)))
+    assert worst > Fraction(2) ** -40
 
 
 def test_from_double(lib):
