@@ -148,9 +148,27 @@ fks_status fks_set_escalation(fks_ctx *ctx, double tol);
  * 1/64 of the FP32 rate).  Rebuilds that tier's tables; synchronises the
  * device.  FKS_ERR_UNSUPPORTED on contexts without tiers. */
 fks_status fks_set_escalation_arith(fks_ctx *ctx, int arith);
+/* Direct routes to the last escalation tier, on by default (on != 0) for
+ * contexts with tiers (FKS_ERR_UNSUPPORTED otherwise):
+ *  - FKS_BF16X3: a cell whose FP32 bound must also exceed tol (the split-BF16
+ *    kernel's own estimates of ||Q|| and ||L|| show c_32 ||L|| / Kn > tol ||Q||
+ *    whatever the FP32 tier computes, c_32 = 5e-7, the split-BF16 error
+ *    allowed for) is listed for the last tier at once instead of passing
+ *    through the FP32 tier.  The last tier recomputes from f*, so the results
+ *    are identical either way; only the FP32 tier's work changes.
+ *  - fks_surrogate_step / fks_surrogate_collide: the classification before
+ *    inference sends a cell whose distance from its local Maxwellian
+ *    d = ||f* - M|| / ||M|| is below 0.1 c_32 / tol straight to the last tier
+ *    (near equilibrium ||L|| / ||Q|| >= 0.1 / d: measured 1.2 .. 2.6 times 1/d
+ *    off equilibrium, far more at exact Maxwellians), skipping the context's
+ *    own kernel; results are identical wherever that bound holds, and a cell
+ *    where it did not would get the last tier's (more accurate) result.
+ * Off: every escalated cell passes through every tier. */
+fks_status fks_set_escalation_direct(fks_ctx *ctx, int on);
 /* The tolerance in force and, if counts != NULL, the cells sent to each tier
- * (counts[0]: first tier, counts[1]: second) by the last collision or step
- * call (synchronous device read). */
+ * (counts[0]: first tier, counts[1]: second, including the cells a split-BF16
+ * kernel listed for it directly) by the last collision or step call
+ * (synchronous device read). */
 fks_status fks_get_escalation(const fks_ctx *ctx, double *tol, long *counts);
 
 /* Exact shift transport over time dt (Sec. 2.1): advances the generic-cell

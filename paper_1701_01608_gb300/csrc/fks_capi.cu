@@ -1075,6 +1075,17 @@ static fks_status launch_tc_ctx(fks_ctx* c, const void* f, void* out, const sign
         l.esc_count = c->esc_counts;
         l.esc_c2 = kEscBf16 * kEscBf16;
         l.esc_tol2 = c->esc_tol * c->esc_tol;
+        // A cell whose FP32 bound must exceed the tolerance is listed for the last tier at once: with
+        // |q_b - q| <= c_b l and |q_32 - q| <= c_32 l (q = ||Q_proj||, l = ||L|| / Kn; b: this kernel,
+        // 32: the FP32 tier), c_32 l > tol q_32 holds whenever (c_32 - tol (c_b + c_32)) l > tol q_b;
+        // 0.9 of that constant covers the tiers' different estimates of ||L||.  The last tier
+        // recomputes from f*, so the results are those of the route through the FP32 tier.
+        const double cd = 0.9 * (kEscFp32 - c->esc_tol * (kEscBf16 + kEscFp32));
+        if (c->esc_direct && c->esc_ntier == 2 && cd > 0.0) {
+            l.esc_last_list = c->esc_lists + c->ncells;
+            l.esc_last_count = c->esc_counts + 1;
+            l.esc_last_c2 = cd * cd;
+        }
     }
     l.f = f;
     l.out = out;
@@ -1217,11 +1228,26 @@ static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const sig
 }
 
 fks_status fks_internal_fail(fks_ctx* c, fks_status st, const std::string& msg) { return fail(c, st, msg); }
+fks_status fks_internal_last_tier_route(fks_ctx* c, cudaStream_t s, int** list, int** count, double* d_max) {
+    *list = nullptr;
+    *count = nullptr;
+    *d_max = 0.0;
+    if (!esc_on(c)) return FKS_OK;
+    const fks_status st = reset_esc(c, s);
+    if (st != FKS_OK) return st;
+    const int last = c->esc_ntier - 1;
+    *list = c->esc_lists + (long)last * c->ncells;
+    *count = c->esc_counts + last;
+    // the FP32 bound is the binding one (the split-BF16 bound is 30x looser)
+    if (c->esc_direct) *d_max = kKappaDist * kEscFp32 / c->esc_tol;
+    return FKS_OK;
+}
+
 fks_status fks_internal_collide_list(fks_ctx* c, const void* f, void* out, const int* cells, const int* count,
-                                     int mode, double dt, cudaStream_t s) {
+                                     int mode, double dt, cudaStream_t s, int keep_counts) {
     if (c->bgk || c->dealias) return fail(c, FKS_ERR_UNSUPPORTED, "cell lists need a spectral context (variant A)");
     const bool esc = esc_on(c);
-    if (esc) {
+    if (esc && !keep_counts) {
         const fks_status st = reset_esc(c, s);
         if (st != FKS_OK) return st;
     }
@@ -1540,6 +1566,13 @@ fks_status fks_set_escalation_arith(fks_ctx* c, int arith) {
     cudaDeviceSynchronize();
     c->esc_arith = arith;
     return setup_escalation(c);   // rebuilds the tiers (the last one in the new arithmetic)
+}
+
+fks_status fks_set_escalation_direct(fks_ctx* c, int on) {
+    if (!c) return FKS_ERR_INVALID_ARG;
+    if (c->esc_ntier < 1) return fail(c, FKS_ERR_UNSUPPORTED, "direct routing needs a context with escalation tiers");
+    c->esc_direct = on != 0;
+    return FKS_OK;
 }
 
 fks_status fks_get_escalation(const fks_ctx* c, double* tol, long* counts) {

@@ -96,6 +96,12 @@ struct CollideArgs {
 // (FP32 ~2.4e-7, split BF16 ~5e-6 of ||L|| on near-equilibrium and two-stream cells).
 constexpr double kEscFp32 = 5e-7;
 constexpr double kEscBf16 = 1.5e-5;
+// Lower bound of (||L|| / ||Q||) d near equilibrium, d = ||f - M|| / ||M|| (M the Maxwellian of f's
+// moments): Q ~ L_M (f - M) + Q(M) with ||L_M h|| of the order of the loss frequency times ||h||, so the
+// product is of order one; measured 1.2 .. 2.6 on shock-tube cells with d from 2e-4 to 0.4 and far
+// above one for the (near-)exact Maxwellians.  A tenfold margin: a cell with d < kKappaDist c / tol
+// fails the bound c ||L|| / Kn <= tol ||Q|| of a tier with constant c.
+constexpr double kKappaDist = 0.1;
 
 __device__ __forceinline__ void cluster_arrive() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
@@ -181,60 +187,89 @@ __device__ __forceinline__ float2 df_shfl_xor(float2 v, int off) {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off));
 }
 
-// ---- transforms split over a pair of lanes (2t, 2t + 1) of a warp --------------------------
-// The double-float instantiations split every length-N transform of a pencil over G = 2 threads:
-// half the registers and half the transform code per thread and twice the warps per SM (with one
-// thread per pencil the double-float kernel is bound by instruction fetch, one warp per scheduler).
-__device__ __forceinline__ float pair_xchg(float v, unsigned mask) { return __shfl_xor_sync(mask, v, 1); }
-__device__ __forceinline__ double pair_xchg(double v, unsigned mask) { return __shfl_xor_sync(mask, v, 1); }
-__device__ __forceinline__ dfloat pair_xchg(dfloat v, unsigned mask) {
-    return dfloat(pair_xchg(v.hi, mask), pair_xchg(v.lo, mask));
+// ---- transforms split over G = 2 or 4 consecutive lanes of a warp -------------------------
+// The double-float instantiations split every length-N transform of a pencil over G threads: 1/G of
+// the registers and about 1/G of the transform code per thread and G times the warps per SM (with
+// one thread per pencil the double-float kernel is bound by instruction fetch, one warp per
+// scheduler).
+__device__ __forceinline__ float lane_xchg(float v, unsigned mask, int d) { return __shfl_xor_sync(mask, v, d); }
+__device__ __forceinline__ double lane_xchg(double v, unsigned mask, int d) { return __shfl_xor_sync(mask, v, d); }
+__device__ __forceinline__ dfloat lane_xchg(dfloat v, unsigned mask, int d) {
+    return dfloat(lane_xchg(v.hi, mask, d), lane_xchg(v.lo, mask, d));
 }
 template <typename T>
-__device__ __forceinline__ cpx<T> pair_xchg(cpx<T> v, unsigned mask) {
-    return {pair_xchg(v.x, mask), pair_xchg(v.y, mask)};
+__device__ __forceinline__ cpx<T> lane_xchg(cpx<T> v, unsigned mask, int d) {
+    return {lane_xchg(v.x, mask, d), lane_xchg(v.y, mask, d)};
 }
 
-// element index held in local slot m after fft_split by thread g of G: G = 1, m itself; G = 2,
-// the outputs k and k + N/2 of the last radix-2 combination with k = (m mod N/4) + g N/4
+// element index held in local slot m after fft_split by thread g = sum_b g_b 2^b of G: G = 1, m
+// itself; otherwise the outputs k and k + N/2 of the last radix-2 combination, with
+// k = (m mod N/2G) + (N/2G) (g_{r-1} + 2 g_{r-2} + ... + 2^{r-1} g_0), G = 2^r (bit-reversed part)
 template <int N, int G>
 __device__ __forceinline__ int split_out(int m, int g) {
-    if constexpr (G == 1) return m;
-    else return m % (N / 4) + g * (N / 4) + (m / (N / 4)) * (N / 2);
+    if constexpr (G == 1) {
+        return m;
+    } else {
+        constexpr int Q = N / (2 * G);
+        int rev = 0;
+#pragma unroll
+        for (int b = 1; b < G; b <<= 1) rev = (rev << 1) | ((g & b) ? 1 : 0);
+        return m % Q + rev * Q + (m / Q) * (N / 2);
+    }
 }
 
 namespace detail {
-// output pair k = M + g N/4 of the radix-2 combination X_k = y0_k + W^k y1_k, X_{k+N/2} = y0_k - W^k y1_k
-// (W = exp(SIGN 2 pi i / N), y_g the half-length transform of the samples x_{2j+g}); thread 0 holds y0,
-// thread 1 y1, and each sends the partner the half it combines
-template <typename T, int SIGN, int N, int M>
-__device__ __forceinline__ void split_combine(cpx<T> (&a)[N / 2], bool g1, unsigned mask) {
-    constexpr int Q = N / 4;
-    const cpx<T> recv = pair_xchg(g1 ? a[M] : a[M + Q], mask);
-    const cpx<T> u = g1 ? recv : a[M];
-    cpx<T> v = mul_tw<T, SIGN, M, N>(g1 ? a[M + Q] : recv);
-    const cpx<T> vq = mul_si<T, SIGN>(v);   // W^{N/4} = SIGN i for thread 1's k = M + N/4
-    v = g1 ? vq : v;
+// output pair k = kb(M) of the last radix-2 combination X_k = E_k + W^k O_k, X_{k+N/2} = E_k - W^k O_k
+// (W = exp(SIGN 2 pi i / N); E, O the half-length transforms of the even and odd samples): the
+// lane with bit D clear holds E, its partner (lane ^ D) holds O at the same indices; each keeps one
+// half of the M slots and sends the partner the other half.  Slot M < L/2 of the E lane and slot
+// M + L/2 of the O lane combine; the index of slot M is M + base, base = Q (bit-reversed higher part)
+// with the O lane's extra N/4 (W^{N/4} = SIGN i) and the higher parts' extra N/8 (an eighth turn).
+template <typename T, int SIGN, int N, int L, int M>
+__device__ __forceinline__ void split_combine(cpx<T> (&a)[L], bool odd, bool eighth, unsigned mask, int d) {
+    constexpr int H2 = L / 2;
+    const cpx<T> recv = lane_xchg(odd ? a[M] : a[M + H2], mask, d);
+    const cpx<T> u = odd ? recv : a[M];
+    cpx<T> v = mul_tw<T, SIGN, M, N>(odd ? a[M + H2] : recv);
+    if constexpr (N % 8 == 0 && L * 2 < N) {
+        const cpx<T> ve = mul_tw<T, SIGN, N / 8, N>(v);   // the part's eighth turn (G = 4)
+        v = eighth ? ve : v;
+    }
+    const cpx<T> vq = mul_si<T, SIGN>(v);   // W^{N/4} = SIGN i for the odd lane's slots
+    v = odd ? vq : v;
     a[M] = cadd(u, v);
-    a[M + Q] = csub(u, v);
+    a[M + H2] = csub(u, v);
 }
-template <typename T, int SIGN, int N, int... M>
-__device__ __forceinline__ void split_combine_all(cpx<T> (&a)[N / 2], bool g1, unsigned mask,
+template <typename T, int SIGN, int N, int L, int... M>
+__device__ __forceinline__ void split_combine_all(cpx<T> (&a)[L], bool odd, bool eighth, unsigned mask, int d,
                                                   std::integer_sequence<int, M...>) {
-    (split_combine<T, SIGN, N, M>(a, g1, mask), ...);
+    (split_combine<T, SIGN, N, L, M>(a, odd, eighth, mask, d), ...);
 }
 }  // namespace detail
 
-// fft<N, SIGN> of a pencil spread over G threads: thread g holds a[j] = x_{jG+g} (j < N/G) and ends
-// with a[m] = X_{split_out<N, G>(m, g)}; mask names the pair's two lanes (both call it together)
+// fft<N, SIGN> of a pencil spread over G consecutive lanes: thread g holds a[j] = x_{jG+g} (j < N/G)
+// and ends with a[m] = X_{split_out<N, G>(m, g)}; mask names the pencil's lanes (they call it
+// together).  G = 2: both halves transform their samples (decimation in time) and combine; G = 4:
+// the even lanes (bit 0 clear) transform the even samples as a 2-lane split over lane bit 1, the odd
+// lanes the odd samples, then one combination across lane bit 0.
 template <int N, int SIGN, int G, int R0, typename T>
 __device__ __forceinline__ void fft_split(cpx<T> (&a)[N / G], int g, unsigned mask) {
     if constexpr (G == 1) {
         fft<N, SIGN, R0>(a);
-    } else {
-        static_assert(G == 2 && N % 4 == 0, "a pencil is split over one pair of lanes");
+    } else if constexpr (G == 2) {
+        static_assert(N % 4 == 0, "a pencil split over two lanes");
         fft<N / 2, SIGN>(a);
-        detail::split_combine_all<T, SIGN, N>(a, g != 0, mask, std::make_integer_sequence<int, N / 4>{});
+        detail::split_combine_all<T, SIGN, N, N / 2>(a, g != 0, false, mask, 1,
+                                                      std::make_integer_sequence<int, N / 4>{});
+    } else {
+        static_assert(G == 4 && N % 8 == 0, "a pencil split over two or four lanes");
+        // half-length transform of this lane's parity class over lane bit 1 (partner lane ^ 2)
+        fft<N / 4, SIGN>(a);
+        detail::split_combine_all<T, SIGN, N / 2, N / 4>(a, (g & 2) != 0, false, mask, 2,
+                                                          std::make_integer_sequence<int, N / 8>{});
+        // across lane bit 0 (partner lane ^ 1): slot indices k = M + (N/8) g1 (+ N/4 for the odd lane)
+        detail::split_combine_all<T, SIGN, N, N / 4>(a, (g & 1) != 0, (g & 2) != 0, mask, 1,
+                                                      std::make_integer_sequence<int, N / 8>{});
     }
 }
 
@@ -297,7 +332,7 @@ struct CollideCfg {
     static constexpr int HF = H + 1;          // kz' planes of f^ (odd row stride)
     static constexpr int HP = H + 1;          // row stride of W (odd)
     static constexpr int NTASK = N * N / C;   // pencils / columns per pass per CTA
-    // threads per pencil: double-float transforms are split over a pair of lanes (fft_split)
+    // threads per pencil: double-float transforms are split over consecutive lanes (fft_split)
     static constexpr int G = std::is_same<T, dfloat>::value ? 2 : 1;
     static constexpr int NE = N / G;          // pencil elements per thread
     static constexpr int NT = (NTASK * G + 31) / 32 * 32;   // threads per CTA (whole warps)
@@ -314,7 +349,10 @@ struct CollideCfg {
     // table slab of one direction: [2 tab][N kx][NS kyl][HF]   (T)
     static constexpr long TAB_ELEMS = 2L * N * NS * HF;
     static constexpr unsigned TAB_BYTES = (unsigned)(sizeof(T) * TAB_ELEMS);
-    static constexpr long G_ELEMS = G_REG ? 0 : (long)NTASK * N;    // FP64 gain [N z][NTASK]
+    // gain accumulator [N z][GSTR] (FP64, double-float): split pencils pad the row by one element so
+    // that the lanes of a pencil, N/(2G) rows apart, fall on different banks
+    static constexpr int GSTR = NTASK + (G > 1 ? 1 : 0);
+    static constexpr long G_ELEMS = G_REG ? 0 : (long)GSTR * N;
     static constexpr size_t SMEM_BASE = sizeof(cpx<T>) * (FH_ELEMS + W_ELEMS + S_ELEMS) + sizeof(T) * G_ELEMS +
                                         sizeof(double) * (8 + (NT / 32) * 7 + 8 + 2 * N) + sizeof(float) * (4 * N + 8) +
                                         sizeof(T) * N + sizeof(long) * N + 2 * sizeof(uint64_t) + 3 * N + 4 * NT + 64;
@@ -327,6 +365,7 @@ struct CollideCfg {
                                          sizeof(float) * (4 * N + 8) + sizeof(T) * N + sizeof(long) * N +
                                          2 * sizeof(uint64_t) + 3 * N + 4 * NT + 64;
     static_assert(N % C == 0, "cluster size must divide N");
+    static_assert(G == 1 || NTASK % 8 == 0, "split pencils permute their tasks in groups of 8");
     static_assert(TAB_BYTES % 16 == 0 && BLK_BYTES % 16 == 0, "bulk copies move whole 16-byte units");
     static_assert(STG_ELEMS <= W_ELEMS, "forward staging fits in W");
 };
@@ -396,7 +435,7 @@ collide_kernel(CollideArgs args) {
     cpx<T>* W = Fh + Cfg::FH_ELEMS;                                    // [C src][block]
     cpx<T>* S = W + Cfg::W_ELEMS;                                      // [C-1][block] staging
     T* Tb = reinterpret_cast<T*>(S + Cfg::S_ELEMS);                   // table slab
-    T* Gs = Tb + Cfg::TB_ELEMS;                                        // FP64 gain [N z][NTASK]
+    T* Gs = Tb + Cfg::TB_ELEMS;                                        // FP64 gain [N z][GSTR]
     double* red = reinterpret_cast<double*>(Gs + Cfg::G_ELEMS);       // [8] own partials
     double* redw = red + 8;                                            // [NT/32][7]
     double* mu = redw + (NT / 32) * 7;                                 // [8] correction coefficients, [7] escalation
@@ -474,24 +513,31 @@ collide_kernel(CollideArgs args) {
     // one call site of each transform between the passes of a direction
     constexpr bool kCompact = std::is_same<T, dfloat>::value;
 
-    // pencil task of this thread and its part g of the pencil (G threads per pencil: the pair's
-    // lanes 2t, 2t + 1; element j of a pencil is loaded by part j mod G, outputs are at split_out)
+    // pencil task of this thread and its part g of the pencil (G threads per pencil: lanes
+    // Gt .. Gt + G - 1; element j of a pencil is loaded by part j mod G, outputs are at split_out)
     constexpr int G = Cfg::G, NE = Cfg::NE;
     const int task = G == 1 ? tid : tid / G;
     const int g = G == 1 ? 0 : tid % G;
-    const unsigned pmask = G == 1 ? 0xffffffffu : 3u << (tid & 30);
+    const unsigned pmask = G == 1 ? 0xffffffffu : ((1u << G) - 1u) << (tid & (32 - G));   // the pencil's lanes
     auto zz = [g](int m) { return split_out<N, G>(m, g); };   // element of output slot m
+
+    // split pencils: the y- and z-pass tasks are permuted within groups of 8 (even members first), so
+    // that the four pencils of a shared-memory phase take every other plane (column) and the pair's
+    // lanes, one element apart, fall on different banks
+    auto perm8 = [](int t) { const int q = t & 7; return (t & ~7) | (q < 4 ? 2 * q : 2 * q - 7); };
+    const int ztask = G == 2 ? perm8(task) : task;
+    constexpr int GSTR = Cfg::GSTR;
 
     // z-pass ownership: column (xl, y), x = rank*NS + xl (tasks >= NTASK idle)
     const bool has_col = task < NTASK;
-    const int zl_x = has_col ? task / N : 0, zl_y = task % N;
+    const int zl_x = has_col ? ztask / N : 0, zl_y = ztask % N;
     const int zx = rank * NS + zl_x;
     const int z_src = zl_y / NS, z_kyl = zl_y % NS;   // where column y sits in W
-    T* Gcol = Gs + task;   // FP64: element z at Gcol[z * NTASK]
+    T* Gcol = Gs + task;   // FP64: element z at Gcol[z * GSTR]
 
     // y-pass task (tab, xl, plane), plane fastest
-    const int t_tab = task / (NS * H);
-    const int t_rem = task % (NS * H);
+    const int t_tab = ztask / (NS * H);
+    const int t_rem = ztask % (NS * H);
     const int t_xl = t_rem / H;
     const int t_pp = t_rem % H;
     // x-pass task (tab, kyl, plane) from the lane map (built before the first cluster barrier)
@@ -580,7 +626,7 @@ collide_kernel(CollideArgs args) {
             }
             if constexpr (!Cfg::G_REG) {
 #pragma unroll
-                for (int m = 0; m < NE; ++m) Gcol[(long)zz(m) * NTASK] = T(0);
+                for (int m = 0; m < NE; ++m) Gcol[(long)zz(m) * GSTR] = T(0);
             }
         }
         T Greg[Cfg::G_REG ? N : 1];
@@ -757,7 +803,7 @@ collide_kernel(CollideArgs args) {
                     } else {
                         if (act) {
 #pragma unroll
-                            for (int m = 0; m < NE; ++m) Gcol[(long)zz(m) * NTASK] += a[m].x * a[m].y;
+                            for (int m = 0; m < NE; ++m) Gcol[(long)zz(m) * GSTR] += a[m].x * a[m].y;
                         }
                         cluster_arrive();   // this CTA has finished with W (its accesses ordered before peers' copies)
                     }
@@ -864,7 +910,7 @@ collide_kernel(CollideArgs args) {
 #pragma unroll
                         for (int z = 0; z < N; ++z) {
                             if constexpr (Cfg::G_REG) Greg[z] = fma(av[z], bv[z], Greg[z]);
-                            else Gcol[(long)z * NTASK] += av[z] * bv[z];
+                            else Gcol[(long)z * GSTR] += av[z] * bv[z];
                         }
                     }
                     cluster_arrive();   // this CTA has finished with W (its accesses ordered before peers' copies)
@@ -900,7 +946,7 @@ collide_kernel(CollideArgs args) {
                 auto rval = [&](int m) -> T {
                     T gz;
                     if constexpr (Cfg::G_REG) gz = Greg[m];
-                    else gz = Gcol[(long)zz(m) * NTASK];
+                    else gz = Gcol[(long)zz(m) * GSTR];
                     const T r = fma(-col[m], av[m], gz);
                     return expm ? r * phi(m) : r;
                 };
@@ -1065,9 +1111,9 @@ collide_kernel(CollideArgs args) {
                     const ST* brow = static_cast<const ST*>(args.base) + cell * N3 + ((long)zx * N + zl_y) * N;
                     bool bad = false, neg = false;
                     // 16-byte vectors of the row where this thread's elements run in whole vectors
-                    // (G = 2: runs of N/4 consecutive elements), single elements otherwise
+                    // (split pencils: runs of N / 2G consecutive elements), single elements otherwise
                     constexpr int VW = 16 / sizeof(ST);
-                    constexpr int V = (G == 1 || (N / 4) % VW == 0) ? VW : 1;
+                    constexpr int V = (G == 1 || (N / (2 * G)) % VW == 0) ? VW : 1;
                     static_assert((N * sizeof(ST)) % 16 == 0, "rows are whole 16-byte vectors");
 #pragma unroll
                     for (int m0 = 0; m0 < NE; m0 += V) {

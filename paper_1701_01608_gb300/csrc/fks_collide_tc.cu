@@ -220,6 +220,9 @@ struct Args {
     int* esc_list;              // precision escalation (as in the cluster kernel): cells whose bound
     int* esc_count;             //   esc_c ||L|| / Kn exceeds esc_tol ||Q|| are listed here, not written
     double esc_c2, esc_tol2;
+    int* esc_last_list;         //   cells beyond the next tier's reach (bound with esc_last_c2) go to
+    int* esc_last_count;        //   the last tier's list instead (nullptr: all to esc_list)
+    double esc_last_c2;
     int nc[3], bc[3];
     int M;
     double L, inv_kn, dt;
@@ -617,15 +620,18 @@ __global__ void __launch_bounds__(NTH, 1) collide_tc_kernel(const __grid_constan
             mu[tid] = m[tid];
             if (tid == 0) {
                 // ||Q_proj||^2 = ||Q||^2 - mu . s (s = the moment sums of Q)
-                bool esc = false;
+                bool esc = false, last = false;
                 if (a.esc_list) {
                     double ms = 0.0;
                     for (int i = 0; i < 5; ++i) ms += m[i] * tot[i];
                     const double qp = tot[6] - ms, k2 = a.inv_kn * a.inv_kn;
-                    esc = a.esc_c2 * k2 * tot[5] > a.esc_tol2 * (qp > 0.0 ? qp : 0.0);
+                    const double rhs = a.esc_tol2 * (qp > 0.0 ? qp : 0.0);
+                    esc = a.esc_c2 * k2 * tot[5] > rhs;
+                    last = esc && a.esc_last_list && a.esc_last_c2 * k2 * tot[5] > rhs;
                 }
                 s_esc = esc ? 1 : 0;
-                if (esc) a.esc_list[atomicAdd(a.esc_count, 1)] = (int)cell;
+                if (last) a.esc_last_list[atomicAdd(a.esc_last_count, 1)] = (int)cell;
+                else if (esc) a.esc_list[atomicAdd(a.esc_count, 1)] = (int)cell;
             }
         }
         __syncthreads();
@@ -751,6 +757,9 @@ cudaError_t launch_collide_tc(int n, const TcLaunch& l, cudaStream_t s) {
     a.esc_count = l.esc_count;
     a.esc_c2 = l.esc_c2;
     a.esc_tol2 = l.esc_tol2;
+    a.esc_last_list = l.esc_last_list;
+    a.esc_last_count = l.esc_last_count;
+    a.esc_last_c2 = l.esc_last_c2;
     for (int i = 0; i < 3; ++i) {
         a.nc[i] = l.nc[i];
         a.bc[i] = l.bc[i];

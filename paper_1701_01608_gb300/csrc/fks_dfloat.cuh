@@ -77,6 +77,13 @@ struct dfloat {
         const float2 r = dd_fast_two_sum(p, e);
         return dfloat(r.x, r.y);
     }
+    // sum without the final renormalisation (|lo| up to ulp(hi) + |a.lo| + |b.lo|): for a sum whose
+    // only use is another sum, which renormalises (the normwise error bound is unchanged in order)
+    friend FKS_DD_HD dfloat add_lazy(dfloat a, dfloat b) {
+        const float2 s = dd_two_sum(a.hi, b.hi);
+        return dfloat(s.x, FKS_DADD(s.y, FKS_DADD(a.lo, b.lo)));
+    }
+    friend FKS_DD_HD dfloat sub_lazy(dfloat a, dfloat b) { return add_lazy(a, dfloat(-b.hi, -b.lo)); }
     friend FKS_DD_HD dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
     friend FKS_DD_HD dfloat& operator-=(dfloat& a, dfloat b) { return a = a - b; }
     friend FKS_DD_HD dfloat& operator*=(dfloat& a, dfloat b) { return a = a * b; }

@@ -35,6 +35,12 @@ template <typename T> FKS_HD cpx<T> cmul(cpx<T> a, cpx<T> b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 template <typename T> FKS_HD cpx<T> cscale(cpx<T> a, T s) { return {a.x * s, a.y * s}; }
+// sums that feed only further sums: a type may leave them unnormalised (double-float pairs skip the
+// final renormalisation, see fks_dfloat.cuh); plain sums otherwise
+template <typename T> FKS_HD T add_lazy(T a, T b) { return a + b; }
+template <typename T> FKS_HD T sub_lazy(T a, T b) { return a - b; }
+template <typename T> FKS_HD cpx<T> cadd_lazy(cpx<T> a, cpx<T> b) { return {add_lazy(a.x, b.x), add_lazy(a.y, b.y)}; }
+template <typename T> FKS_HD cpx<T> csub_lazy(cpx<T> a, cpx<T> b) { return {sub_lazy(a.x, b.x), sub_lazy(a.y, b.y)}; }
 
 // ---------------------------------------------------------------- constexpr trig
 namespace detail {
@@ -137,8 +143,9 @@ FKS_HD cpx<T> mul_si(cpx<T> a) {
 
 template <typename T, int SIGN>
 FKS_HD void dft4(cpx<T>& a0, cpx<T>& a1, cpx<T>& a2, cpx<T>& a3) {
-    const cpx<T> s02 = cadd(a0, a2), d02 = csub(a0, a2);
-    const cpx<T> s13 = cadd(a1, a3), d13 = mul_si<T, SIGN>(csub(a1, a3));
+    // first level: sums of sums, which may stay unnormalised
+    const cpx<T> s02 = cadd_lazy(a0, a2), d02 = csub_lazy(a0, a2);
+    const cpx<T> s13 = cadd_lazy(a1, a3), d13 = mul_si<T, SIGN>(csub_lazy(a1, a3));
     a0 = cadd(s02, s13);
     a2 = csub(s02, s13);
     a1 = cadd(d02, d13);

@@ -99,6 +99,11 @@ struct TcLaunch {
     int* esc_list = nullptr;    // precision escalation output (see CollideArgs)
     int* esc_count = nullptr;
     double esc_c2 = 0.0, esc_tol2 = 0.0;
+    // cells whose bound with esc_last_c2 exceeds the tolerance go straight to the last tier's list
+    // (the FP32 tier would list them again); nullptr: every escalated cell goes to esc_list
+    int* esc_last_list = nullptr;
+    int* esc_last_count = nullptr;
+    double esc_last_c2 = 0.0;
     int nc[3], bc[3];
     int M;
     double L, inv_kn, dt;
@@ -213,6 +218,7 @@ struct fks_ctx {
     double esc_tol = 0.0;       // 0: off
     int esc_ntier = 0;
     int esc_arith = FKS_FP32X2; // arithmetic of the last tier: FKS_FP32X2 or FKS_FP64
+    bool esc_direct = true;     // split BF16: cells beyond the FP32 tier's reach go straight to the last tier
     fks::EscTier esc[2];
     int* esc_lists = nullptr;   // [2][ncells]
     int* esc_counts = nullptr;  // [2]
@@ -232,8 +238,15 @@ extern "C" fks_status fks_internal_fail(fks_ctx* c, fks_status st, const std::st
 extern "C" fks_status fks_internal_collide(fks_ctx* c, const void* f, void* out, int mode, cudaStream_t s);
 // collide (projected, with the context's escalation) only the cells cells[0 .. *count) (a device count):
 // mode 0 out = Q, mode 1 out = f + dt Q (no transport)
+// keep_counts: the escalation counts were reset by fks_internal_last_tier_route before a classification
+// that listed cells for the last tier (the tiers then add to that list)
 extern "C" fks_status fks_internal_collide_list(fks_ctx* c, const void* f, void* out, const int* cells, const int* count,
-                                                int mode, double dt, cudaStream_t s);
+                                                int mode, double dt, cudaStream_t s, int keep_counts);
+// Before a classification of the cells (surrogate step): resets the escalation counts on s and returns
+// the last tier's device list and count and the distance from equilibrium d = ||f - M|| / ||M|| below
+// which a cell certainly fails every earlier tier (d_max = 0: no such route; list = nullptr: no tiers).
+// A cell with d < d_max goes straight to the last tier: near equilibrium ||L|| / ||Q|| >= kKappaDist / d.
+extern "C" fks_status fks_internal_last_tier_route(fks_ctx* c, cudaStream_t s, int** list, int** count, double* d_max);
 // variant B (fks_dealias.cu)
 fks_status launch_dealias(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
                           cudaStream_t s);

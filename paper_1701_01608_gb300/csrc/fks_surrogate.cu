@@ -222,13 +222,19 @@ __global__ void __launch_bounds__(BS) output_kernel(int n, double L, long c0, lo
 
 // split the cells by the indicator's lower bound ind_scale / d (known before inference): over the
 // threshold (or not finite) -> route list (their indicator is that bound), else -> candidate list
+//   d < d_last: straight to the last escalation tier's list (last, count *nlast; *ndirect counts them)
 __global__ void classify_kernel(long ncells, const float* __restrict__ dist, double ind_scale, float threshold,
                                 float* __restrict__ ind, int* __restrict__ route, int* __restrict__ nroute,
-                                int* __restrict__ cand, int* __restrict__ ncand) {
+                                int* __restrict__ cand, int* __restrict__ ncand, double d_last,
+                                int* __restrict__ last, int* __restrict__ nlast, int* __restrict__ ndirect) {
     for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncells; c += (long)gridDim.x * blockDim.x) {
         const double d = (double)dist[c];
         const float lb = (float)(ind_scale / (d > 1e-30 ? d : 1e-30));
-        if (!(lb <= threshold)) {
+        if (d < d_last) {
+            ind[c] = lb;
+            last[atomicAdd(nlast, 1)] = (int)c;
+            atomicAdd(ndirect, 1);
+        } else if (!(lb <= threshold)) {
             ind[c] = lb;
             route[atomicAdd(nroute, 1)] = (int)c;
         } else {
@@ -265,7 +271,7 @@ static fks_status surrogate_run(fks_ctx* c, fks_net* net, const float* fs, float
     // per-context surrogate workspace: rho, distance, indicator, routed and candidate lists, two counts
     if (!c->s_rho) {
         if (cudaMalloc(&c->s_rho, sizeof(double) * nc) != cudaSuccess || cudaMalloc(&c->s_dist, sizeof(float) * nc) ||
-            cudaMalloc(&c->s_ind, sizeof(float) * nc) || cudaMalloc(&c->s_count, 2 * sizeof(int)) ||
+            cudaMalloc(&c->s_ind, sizeof(float) * nc) || cudaMalloc(&c->s_count, 3 * sizeof(int)) ||
             cudaMalloc(&c->s_cells, sizeof(int) * (nc > 0 ? nc : 1)) ||
             cudaMalloc(&c->s_cand, sizeof(int) * (nc > 0 ? nc : 1))) {
             c->err = "surrogate workspace";
@@ -278,13 +284,20 @@ static fks_status surrogate_run(fks_ctx* c, fks_net* net, const float* fs, float
         c->err = "surrogate inference workspace";
         return FKS_ERR_OOM;
     }
-    if (cudaMemsetAsync(c->s_count, 0, 2 * sizeof(int), s) != cudaSuccess) return FKS_ERR_CUDA;
+    if (cudaMemsetAsync(c->s_count, 0, 3 * sizeof(int), s) != cudaSuccess) return FKS_ERR_CUDA;
+    // the escalation lists start here: cells that certainly fail every earlier tier (d below the
+    // route's bound) go straight to the last tier
+    int *last = nullptr, *nlast = nullptr;
+    double d_last = 0.0;
+    fks_status st0 = fks_internal_last_tier_route(c, s, &last, &nlast, &d_last);
+    if (st0 != FKS_OK) return st0;
     // 1. rho and d of every cell; the cells whose bound ind_scale / d already exceeds the threshold
     //    are routed without inference
     const long gridc = nc < 152L * 8 ? nc : 152L * 8;
     surr::inputs_kernel<<<(unsigned)gridc, surr::BS, 0, s>>>(n, c->vbox.L, 0, nc, fs, nullptr, c->s_rho, c->s_dist);
     surr::classify_kernel<<<256, 256, 0, s>>>(nc, c->s_dist, ind_scale, (float)threshold, c->s_ind, c->s_cells,
-                                             c->s_count, c->s_cand, c->s_count + 1);
+                                             c->s_count, c->s_cand, c->s_count + 1, last ? d_last : 0.0, last, nlast,
+                                             c->s_count + 2);
     c->launches += 2;
     // 2. the candidates in chunks of B (their count read back: one synchronisation)
     int ncand = 0;
@@ -306,14 +319,14 @@ static fks_status surrogate_run(fks_ctx* c, fks_net* net, const float* fs, float
     }
     // 3. the context's spectral operator (projected, with its precision escalation) on the routed
     //    cells; the kernels read the routed count on the device
-    const fks_status st = fks_internal_collide_list(c, fs, out, c->s_cells, c->s_count, mode, dt, s);
+    const fks_status st = fks_internal_collide_list(c, fs, out, c->s_cells, c->s_count, mode, dt, s, last != nullptr);
     if (st != FKS_OK) return st;
     if (nrouted) {
-        int count = 0;
-        if (cudaMemcpyAsync(&count, c->s_count, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        int count[3] = {0, 0, 0};
+        if (cudaMemcpyAsync(count, c->s_count, sizeof(count), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return FKS_ERR_CUDA;
-        *nrouted = count;
+        *nrouted = count[0] + count[2];   // to the spectral operator, directly or through its first kernel
     }
     return cudaGetLastError() == cudaSuccess ? FKS_OK : FKS_ERR_CUDA;
 }

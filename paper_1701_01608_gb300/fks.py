@@ -70,7 +70,7 @@ EXPORTS = ["fks_init", "fks_collide", "fks_transport", "fks_step", "fks_moments"
            "fks_net_infer", "fks_net_check", "fks_selftest_wait", "fks_set_dealias", "fks_step_host", "fks_vhs_factor",
            "fks_step_strang", "fks_alu_peak", "fks_step_exp", "fks_relax", "fks_surrogate_step", "fks_set_profiling", "fks_get_profile", "fks_set_schedule", "fks_radix",
            "fks_batch_set_schedule", "fks_batch_radix", "fks_set_escalation", "fks_get_escalation", "fks_set_escalation_arith",
-           "fks_batch_set_escalation", "fks_batch_get_escalation"]
+           "fks_batch_set_escalation", "fks_batch_get_escalation", "fks_set_escalation_direct"]
 
 
 def lib(build: bool = True):
@@ -157,6 +157,7 @@ def lib(build: bool = True):
     L.fks_set_profiling.argtypes = [P, I]
     L.fks_get_profile.argtypes = [P, P, P]
     L.fks_set_escalation_arith.argtypes = [P, I]
+    L.fks_set_escalation_direct.argtypes = [P, I]
     L.fks_get_escalation.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
     L.fks_step_host.argtypes = [P, P, P, D, P]
     L.fks_destroy.argtypes = [P]
@@ -265,6 +266,12 @@ class Context:
     def set_escalation_arith(self, arith: int):
         """Arithmetic of the last escalation tier: FKS_FP32X2 (double-float, default) or FKS_FP64."""
         self._check(self._L.fks_set_escalation_arith(self._h, int(arith)), "fks_set_escalation_arith")
+
+    def set_escalation_direct(self, on: bool):
+        """Direct routes to the last escalation tier (default on): split-BF16 cells beyond the FP32
+        tier's reach, and in the surrogate step cells this close to equilibrium that every earlier
+        tier must fail them (identical results, less work)."""
+        self._check(self._L.fks_set_escalation_direct(self._h, int(bool(on))), "fks_set_escalation_direct")
 
     def escalation(self) -> tuple[float, tuple[int, int]]:
         """(tolerance, cells sent to the first and second tier by the last collision or step)."""

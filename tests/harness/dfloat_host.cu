@@ -28,6 +28,15 @@ int fks_test_dd_dot2(const float* abcd, float* out) {
     return 0;
 }
 
+// (a + b) + (c - d) with the two inner sums left unnormalised (the first level of a radix-4 butterfly)
+int fks_test_dd_lazy4(const float* abcd, float* out) {
+    const fks::dfloat a(abcd[0], abcd[1]), b(abcd[2], abcd[3]), c(abcd[4], abcd[5]), d(abcd[6], abcd[7]);
+    const fks::dfloat r = add_lazy(a, b) + sub_lazy(c, d);
+    out[0] = r.hi;
+    out[1] = r.lo;
+    return 0;
+}
+
 int fks_test_dd_from_double(double d, float* out) {
     const fks::dfloat r(d);
     out[0] = r.hi;

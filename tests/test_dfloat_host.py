@@ -34,6 +34,7 @@ def _build(tmp, src_text=None):
         getattr(lib, fn).argtypes = [F, F, F, F, ctypes.c_void_p]
     lib.fks_test_dd_from_double.argtypes = [ctypes.c_double, ctypes.c_void_p]
     lib.fks_test_dd_dot2.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.fks_test_dd_lazy4.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     return lib
 
 
@@ -137,6 +138,17 @@ def test_dot2_within_normwise_bound(lib):
         r = dot2(lib.fks_test_dd_dot2, a, b, c, d)
         ab, cd = exact(a) * exact(b), exact(c) * exact(d)
         assert abs(exact(r) - (ab + cd)) <= Fraction(2) ** -45 * (abs(ab) + abs(cd)), (a, b, c, d, r)
+        assert normalised(r), (a, b, c, d, r)
+
+
+def test_unnormalised_inner_sums_keep_the_normwise_bound(lib):
+    """(a + b) + (c - d) with the inner sums left unnormalised: error below 2^-44 of the sum of the
+    magnitudes (cancelling, lopsided and generic operands), the result normalised."""
+    for (a, b), (c, d) in zip(cases(8), cases(9)):
+        r = dot2(lib.fks_test_dd_lazy4, a, b, c, d)
+        want = exact(a) + exact(b) + exact(c) - exact(d)
+        mag = abs(exact(a)) + abs(exact(b)) + abs(exact(c)) + abs(exact(d))
+        assert abs(exact(r) - want) <= Fraction(2) ** -44 * mag, (a, b, c, d, r)
         assert normalised(r), (a, b, c, d, r)
 
 

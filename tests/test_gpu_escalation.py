@@ -96,6 +96,55 @@ def test_near_equilibrium_cells_meet_plain_bound(fks, shock_cells, prec, tol, ar
     assert torch.equal(Q2, torch.from_numpy(Qg.astype(np.float32)).cuda())
 
 
+def test_direct_route_to_last_tier_is_identical(fks, shock_cells):
+    """Split BF16 at 1e-3: cells whose FP32 bound must exceed the tolerance (the split-BF16 kernel's own
+    estimates of ||Q|| and ||L||, its error allowed for) go straight to the last tier.  The results equal
+    those of the route through the FP32 tier bit for bit; the last tier receives the same number of
+    cells, the FP32 tier fewer (the exact Maxwellians skip it)."""
+    f32, Qo, kappa = shock_cells
+    nc = f32.shape[0]
+    ctx = make_ctx(fks, nc, 2)
+    fd = torch.from_numpy(f32).cuda()
+    Qa, Qb = torch.empty_like(fd), torch.empty_like(fd)
+    ctx.collide(fd, Qa)
+    direct = ctx.escalation()[1]
+    ctx.set_escalation_direct(False)
+    ctx.collide(fd, Qb)
+    through = ctx.escalation()[1]
+    assert ctx.check() == 0
+    assert torch.equal(Qa, Qb)
+    assert direct[1] == through[1] > 0
+    assert direct[0] < through[0]
+    ctx.set_escalation_direct(True)
+    ctx.collide(fd, Qb)
+    assert torch.equal(Qa, Qb) and ctx.escalation()[1] == direct
+
+
+def test_direct_route_from_the_classification_is_identical(fks, shock_cells):
+    """The surrogate's classification sends cells with d = ||f - M|| / ||M|| below 0.1 c_32 / tol
+    (5e-5 at 1e-3: the exact Maxwellians and the 1e-5 perturbation) straight to the last tier, past
+    the split-BF16 kernel.  Every cell is routed (random network, indicator scale 1); the results
+    equal those of the route through every tier bit for bit and meet the bound against the oracle."""
+    f32, Qo, kappa = shock_cells
+    nc = f32.shape[0]
+    net = fks.Net(N, 2, seed=5)
+    fd = torch.from_numpy(f32).cuda()
+    outs, counts = [], []
+    for direct in (True, False):
+        ctx = make_ctx(fks, nc, 2)
+        ctx.set_escalation_direct(direct)
+        out = torch.empty_like(fd)
+        assert ctx.surrogate_collide(net, fd, out, 1.0, 1.0, BF16_REL) == nc
+        assert ctx.check() == 0
+        outs.append(out)
+        counts.append(ctx.escalation()[1])
+    assert torch.equal(outs[0], outs[1])
+    assert counts[0][1] == counts[1][1] > 0
+    assert counts[0][0] < counts[1][0]
+    for c in range(nc):
+        assert rel(outs[0][c].double().cpu().numpy(), Qo[c]) < BF16_REL, (c, kappa[c])
+
+
 def test_escalated_step_fp32(fks, oracle, tab, shock_cells):
     """One fused transport + collision step of the 32-cell tube after 4 oracle steps: the
     increment f_out - f* against dt Q of the oracle, per cell, up to the FP32 rounding of the
