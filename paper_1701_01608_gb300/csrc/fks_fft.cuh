@@ -104,8 +104,8 @@ FKS_HD cpx<T> mul_tw(cpx<T> a) {
         if constexpr (costly_mul<T>::value) {
             // (sr + i si) h a with sr, si = +-1: the sums first, then two products
             constexpr bool pr = sc.c > 0, pi = (SIGN * sc.s) > 0;
-            const T re = pr ? (pi ? a.x - a.y : a.x + a.y) : (pi ? -(a.x + a.y) : a.y - a.x);
-            const T im = pr ? (pi ? a.y + a.x : a.y - a.x) : (pi ? a.x - a.y : -(a.x + a.y));
+            const T re = pr ? (pi ? sub_lazy(a.x, a.y) : add_lazy(a.x, a.y)) : (pi ? -add_lazy(a.x, a.y) : sub_lazy(a.y, a.x));
+            const T im = pr ? (pi ? add_lazy(a.y, a.x) : sub_lazy(a.y, a.x)) : (pi ? sub_lazy(a.x, a.y) : -add_lazy(a.x, a.y));
             return {h * re, h * im};
         } else {
             const T cr = sc.c > 0 ? h : -h;
@@ -129,7 +129,7 @@ template <int N> constexpr bool is_pow2() { return N > 0 && (N & (N - 1)) == 0; 
 
 template <typename T, int SIGN>
 FKS_HD void dft2(cpx<T>& a0, cpx<T>& a1) {
-    const cpx<T> s = cadd(a0, a1), d = csub(a0, a1);
+    const cpx<T> s = cadd_lazy(a0, a1), d = csub_lazy(a0, a1);
     a0 = s;
     a1 = d;
 }
@@ -143,25 +143,26 @@ FKS_HD cpx<T> mul_si(cpx<T> a) {
 
 template <typename T, int SIGN>
 FKS_HD void dft4(cpx<T>& a0, cpx<T>& a1, cpx<T>& a2, cpx<T>& a3) {
-    // first level: sums of sums, which may stay unnormalised
+    // every butterfly sum may stay unnormalised: its uses are sums and products (which take an
+    // unnormalised operand); the caller renormalises the transform's outputs where it needs them
     const cpx<T> s02 = cadd_lazy(a0, a2), d02 = csub_lazy(a0, a2);
     const cpx<T> s13 = cadd_lazy(a1, a3), d13 = mul_si<T, SIGN>(csub_lazy(a1, a3));
-    a0 = cadd(s02, s13);
-    a2 = csub(s02, s13);
-    a1 = cadd(d02, d13);
-    a3 = csub(d02, d13);
+    a0 = cadd_lazy(s02, s13);
+    a2 = csub_lazy(s02, s13);
+    a1 = cadd_lazy(d02, d13);
+    a3 = csub_lazy(d02, d13);
 }
 
 template <typename T, int SIGN>
 FKS_HD void dft3(cpx<T>& a0, cpx<T>& a1, cpx<T>& a2) {
     const T c = T(-0.5);
     const T s = T(SIGN) * T(0.866025403784438646763723170752936183);   // sin(2 pi / 3)
-    const cpx<T> sum = cadd(a1, a2), dif = csub(a1, a2);
+    const cpx<T> sum = cadd_lazy(a1, a2), dif = csub_lazy(a1, a2);
     const cpx<T> m = {a0.x + c * sum.x, a0.y + c * sum.y};
     const cpx<T> r = {-s * dif.y, s * dif.x};
-    a0 = cadd(a0, sum);
-    a1 = cadd(m, r);
-    a2 = csub(m, r);
+    a0 = cadd_lazy(a0, sum);
+    a1 = cadd_lazy(m, r);
+    a2 = csub_lazy(m, r);
 }
 
 template <typename T, int SIGN>
@@ -173,10 +174,10 @@ FKS_HD void dft8(cpx<T> (&a)[8]) {
     o1 = mul_tw<T, SIGN, 1, 8>(o1);
     o2 = mul_tw<T, SIGN, 2, 8>(o2);
     o3 = mul_tw<T, SIGN, 3, 8>(o3);
-    a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
-    a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
-    a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
-    a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
+    a[0] = cadd_lazy(e0, o0); a[4] = csub_lazy(e0, o0);
+    a[1] = cadd_lazy(e1, o1); a[5] = csub_lazy(e1, o1);
+    a[2] = cadd_lazy(e2, o2); a[6] = csub_lazy(e2, o2);
+    a[3] = cadd_lazy(e3, o3); a[7] = csub_lazy(e3, o3);
 }
 
 template <int N, int R0> constexpr int top_radix() {
