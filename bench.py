@@ -470,7 +470,7 @@ def main():
                    "escalated": {"to_fp32": esc_last[0], "to_dfloat": esc_last[1], "cells": NCELLS},
                    "err_vs_fp64": learned_err, "train_seconds": train_s, "train_loss_last": sur.train_loss[-1],
                    "calibration": sur.calib, "threshold": TOL, "stages": stages, "gpu_launches": launches,
-                   "health_bits": bits}
+                   "health_bits": bits, "ms_each": [round(x, 2) for x in per]}
         del fa, fb
 
     # ---------------- the comparison: the plain FP64 spectral step (transport + FP64 operator)
@@ -509,14 +509,25 @@ def main():
             host[1].copy_(dout, non_blocking=True)
             host.reverse()
 
-        e2e_ms, e2e_each = timed_loop(torch, e2e_step, e2e_steps, 1, ws)
+        e2e_step()                       # warm-up
+        torch.cuda.synchronize()
+        ctx.profile()                    # clear the stage record
+        ctx.set_profiling(True)
+        e2e_ms, e2e_each = timed_loop(torch, e2e_step, e2e_steps, 0, ws)
+        e_ms, e_n = ctx.profile()
+        ctx.set_profiling(False)
         e2e_ms = max_over_ranks(e2e_ms, ws)
         nbytes = f0.numel() * 4
         e2e = {"value": ws * PTS * e2e_steps / (e2e_ms / 1e3), "unit": "pts/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "ms_each": [round(x, 2) for x in e2e_each],
                "api": "pinned host state -> device (copy), fks_surrogate_step, device -> pinned host (copy); the "
                       "state advances on the host from the device loop's last state",
-               "escalated_last_step": ctx.escalation()[1]}
+               "escalated_last_step": ctx.escalation()[1],
+               "stages_ms_per_step": {"split_bf16_kernel": e_ms[0] / e2e_steps, "fp32_tier": e_ms[1] / e2e_steps,
+                                      "dfloat_tier": e_ms[2] / e2e_steps,
+                                      "rest": float(np.mean(e2e_each)) - sum(e_ms) / e2e_steps,
+                                      "note": "library stage timers over the timed steps; rest = the copies, "
+                                              "offsets, transport, classification and host synchronisation"}}
         del host, din, dout, dw
 
     # ---------------- the spectral paths alone: escalated FP32, and the raw arithmetic (no escalation)
