@@ -341,8 +341,13 @@ struct CollideCfg {
     // W: C source blocks, each [2 tab][NS xl][NS kyl][HP]   (cpx<T>)
     static constexpr long BLK = 2L * NS * NS * HP;
     static constexpr long BLK_STRIDE = BLK + best_block_pad<(int)sizeof(cpx<T>)>(N, NS, HP, BLK);
-    static constexpr long W_ELEMS = (long)C * BLK_STRIDE;
-    static constexpr long S_ELEMS = (long)(C - 1) * BLK_STRIDE;   // staging for the peers' blocks
+    // split pencils (double-float): the x-pass stores its outputs straight into the owner CTAs' W (DSMEM),
+    // W double-buffered by direction parity, one cluster barrier per direction, no staging blocks;
+    // otherwise W single, the peers' blocks staged in S and moved by bulk copies
+    static constexpr bool XDIRECT = G > 1;
+    static constexpr long W_ONE = (long)C * BLK_STRIDE;                 // one W buffer
+    static constexpr long W_ELEMS = (XDIRECT ? 2 : 1) * W_ONE;
+    static constexpr long S_ELEMS = XDIRECT ? 0 : (long)(C - 1) * BLK_STRIDE;   // staging for the peers' blocks
     static constexpr unsigned BLK_BYTES = (unsigned)(sizeof(cpx<T>) * BLK);
     // forward-transform staging [NS xl][N y][HF] reuses W
     static constexpr long STG_ELEMS = (long)NS * N * HF;
@@ -367,7 +372,7 @@ struct CollideCfg {
     static_assert(N % C == 0, "cluster size must divide N");
     static_assert(G == 1 || NTASK % 8 == 0, "split pencils permute their tasks in groups of 8");
     static_assert(TAB_BYTES % 16 == 0 && BLK_BYTES % 16 == 0, "bulk copies move whole 16-byte units");
-    static_assert(STG_ELEMS <= W_ELEMS, "forward staging fits in W");
+    static_assert(STG_ELEMS <= W_ONE, "forward staging fits in W");
 };
 
 // Lane assignment of the x-pass tasks (tab, kyl, plane).  Tasks of the packed
@@ -663,9 +668,13 @@ collide_kernel(CollideArgs args) {
         __syncthreads();
 
         // ---------------- gain and loss ---------------------------------
-        cluster_arrive();   // matches the wait before the first x-pass exchange (W staging reads done)
+        // staged exchange: matches the wait before the first x-pass exchange (W staging reads done); the
+        // direct stores need none (the forward transform's cluster barrier freed W)
+        if constexpr (!Cfg::XDIRECT) cluster_arrive();
         for (int p = 0; p <= args.M; ++p) {
             const bool loss = (p == args.M);
+            // this direction's W (direct stores: the buffer of its parity, last read by direction p - 2)
+            cpx<T>* const Wp = W + (Cfg::XDIRECT ? (long)(p & 1) * Cfg::W_ONE : 0L);
             // ---- x-pass: table product, pack kz'=0 with kz'=N/2, inverse FFT along kx
             const bool active = has_col && (!loss || x_tab == 0);
             const bool active_y = has_col && (!loss || t_tab == 0);
@@ -706,8 +715,8 @@ collide_kernel(CollideArgs args) {
                 // its transform holds the two real C2R results as real and imaginary parts.  The loss
                 // direction transforms table 0 alone (Y = 0).
                 auto load_z = [&](bool two) {
-                    const cpx<T>* c0 = W + (long)z_src * BLK + widx(0, zl_x, z_kyl, 0);
-                    const cpx<T>* c1 = W + (long)z_src * BLK + widx(1, zl_x, z_kyl, 0);
+                    const cpx<T>* c0 = Wp + (long)z_src * BLK + widx(0, zl_x, z_kyl, 0);
+                    const cpx<T>* c1 = Wp + (long)z_src * BLK + widx(1, zl_x, z_kyl, 0);
 #pragma unroll
                     for (int j = 0; j < NE; ++j) {
                         const int k = j * G + g;
@@ -772,7 +781,7 @@ collide_kernel(CollideArgs args) {
 #pragma unroll
                             for (int j = 0; j < NE; ++j) {
                                 const int y = j * G + g;
-                                a[j] = W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP];
+                                a[j] = Wp[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP];
                             }
                         } else {
                             load_z(true);
@@ -780,24 +789,45 @@ collide_kernel(CollideArgs args) {
                         fft_split<N, +1, G, R0>(a, g, pmask);
                     }
                     if (ps == 0) {
-                        cluster_wait();   // every CTA has finished reading its W (previous z-pass)
-                        if (act) {
+                        if constexpr (Cfg::XDIRECT) {
+                            // straight into block `rank` of the owner's W (this direction's buffer), then
+                            // one cluster barrier: every CTA's outputs are in place
+                            if (act) {
+                                const uint32_t wsrc = smem_addr(Wp + (long)rank * BLK);
 #pragma unroll
-                            for (int m = 0; m < NE; ++m) {
-                                const int x = zz(m);
-                                const int dst = x / NS;
-                                const long o = widx(x_tab, x % NS, x_kyl, x_pp);
-                                if (dst == rank) W[(long)rank * BLK + o] = a[m];
-                                else S[(long)(dst < rank ? dst : dst - 1) * BLK + o] = a[m];
+                                for (int m = 0; m < NE; ++m) {
+                                    const int x = zz(m);
+                                    const long o = widx(x_tab, x % NS, x_kyl, x_pp);
+                                    st_cluster(map_rank(wsrc + (uint32_t)(o * (long)sizeof(cpx<T>)), x / NS), a[m]);
+                                }
                             }
+                            cluster_arrive();
+                            cluster_wait();
+                            // the table slab has been read by every thread: the next one (staged tables)
+                            if (tid == 0) {
+                                if (!loss) fetch_tables(tab, p + 1);
+                                else if (has_next) fetch_tables(item_tables(item_at(it + nclusters)), 0);
+                            }
+                        } else {
+                            cluster_wait();   // every CTA has finished reading its W (previous z-pass)
+                            if (act) {
+#pragma unroll
+                                for (int m = 0; m < NE; ++m) {
+                                    const int x = zz(m);
+                                    const int dst = x / NS;
+                                    const long o = widx(x_tab, x % NS, x_kyl, x_pp);
+                                    if (dst == rank) W[(long)rank * BLK + o] = a[m];
+                                    else S[(long)(dst < rank ? dst : dst - 1) * BLK + o] = a[m];
+                                }
+                            }
+                            exchange();
                         }
-                        exchange();
                     } else if (ps == 1) {
                         if (act) {
 #pragma unroll
                             for (int m = 0; m < NE; ++m) {
                                 const int y = zz(m);
-                                W[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP] = a[m];
+                                Wp[ybase + (long)(y / NS) * BLK + (long)(y % NS) * HP] = a[m];
                             }
                         }
                     } else {
@@ -805,7 +835,8 @@ collide_kernel(CollideArgs args) {
 #pragma unroll
                             for (int m = 0; m < NE; ++m) Gcol[(long)zz(m) * GSTR] += a[m].x * a[m].y;
                         }
-                        cluster_arrive();   // this CTA has finished with W (its accesses ordered before peers' copies)
+                        // staged exchange: this CTA has finished with W (its accesses ordered before peers' copies)
+                        if constexpr (!Cfg::XDIRECT) cluster_arrive();
                     }
                 }
                 if (loss) {

@@ -2,7 +2,8 @@
 
 compute-sanitizer's race and sync checks are not available here, so each kernel's protocol is written
 out as the sequence of barriers, mbarrier waits, bulk copies and shared-memory accesses that its code
-executes (csrc/fks_collide.cuh: collide_kernel; csrc/fks_bgk.cu: bgk_cluster_kernel) and run under many
+executes (csrc/fks_collide.cuh: collide_kernel, its staged and its split-pencil exchange;
+csrc/fks_bgk.cu: bgk_cluster_kernel) and run under many
 seeded schedules by a vector-clock model (tests/harness/protocol_model.py).  The written-out
 protocols follow the kernels statement by statement; each test also plants a plausible mistake
 (a barrier dropped or moved) and checks that the model reports it, so that a model too weak to see a
@@ -95,6 +96,68 @@ def collide_program(c, i, C, cells, M, mutate=None):
     return P
 
 
+def collide_direct_program(c, i, C, cells, M, tables=True, mutate=None):
+    """collide_kernel, split-pencil path (double-float): forward transform as above, then per direction p
+    the x-pass stores straight into block c of every CTA's W[p mod 2] (DSMEM), one cluster barrier, the
+    next table slab (staged tables only), y-pass in place, z-pass; no staging blocks, no bulk copies.
+    Locations: ('W', cta, buffer, source slot), ('Fh', cta), ('Tb', cta), ('red', cta)."""
+    P = []
+    acc = lambda loc, k, e, s: P.append(("acc", loc, k, e, s))
+    t0 = i == 0
+    nbuf = 1 if mutate == "single_w_buffer" else 2
+    if t0 and cells and tables:
+        P.append(("tma", (cells[0], 0)))
+    P += [("carrive",), ("cwait",)]
+    for ci, cell in enumerate(cells):
+        nxt = cells[ci + 1] if ci + 1 < len(cells) else None
+        P.append(("sync",))
+        for s in range(C):                    # F1: staging in the first W buffer
+            acc(("W", c, 0, s), "w", ("F", cell), "F1")
+        P.append(("sync",))
+        for s in range(C):
+            acc(("W", c, 0, s), "r", ("F", cell), "F2")
+        for d in range(C):
+            acc(("Fh", d), "w", ("F", cell), "F2")
+        P += [("carrive",), ("cwait",)]
+        acc(("Fh", c), "r", ("F", cell), "F4")
+        acc(("Fh", c), "w", ("F", cell), "F4")
+        P.append(("sync",))
+        for p in range(M + 1):
+            loss = p == M
+            b = p % nbuf
+            if tables:
+                P.append(("twait",))
+                acc(("Tb", c), "r", ("slab", (cell, p)), "x")
+            acc(("Fh", c), "r", ("F", cell), "x")
+            for d in range(C):                # block c of every CTA's W[b]
+                acc(("W", d, b, c), "w", ("dir", cell, p), "x")
+            if mutate != "no_barrier_after_stores":
+                P += [("carrive",), ("cwait",)]
+            if tables and t0:
+                if not loss:
+                    P.append(("tma", (cell, p + 1)))
+                elif nxt is not None:
+                    P.append(("tma", (nxt, 0)))
+            for s in range(C):
+                acc(("W", c, b, s), "r", ("dir", cell, p), "y")
+                acc(("W", c, b, s), "w", ("dir", cell, p), "y")
+            P.append(("sync",))
+            for s in range(C):
+                acc(("W", c, b, s), "r", ("dir", cell, p), "z")
+            if mutate == "no_barrier_after_stores":
+                P += [("carrive",), ("cwait",)]   # the same barrier count, too late
+            if loss:
+                P.append(("sync",))
+                if t0:
+                    acc(("red", c), "w", ("cell", cell), "ep")
+                P += [("carrive",), ("cwait",)]
+                if t0:
+                    for d in range(C):
+                        acc(("red", d), "r", ("cell", cell), "ep2")
+                P += [("carrive",), ("cwait",)]
+    return P
+
+
 def bgk_program(c, i, CL, cells, mutate=None):
     """bgk_cluster_kernel<float, 32, 4>: per cell the gather tables, the loads, the moment partials
     (warp partials in redw, the CTA's in red[parity]), the cluster barrier, warp 0's serial phase
@@ -148,6 +211,20 @@ def test_collide_protocol_model_sees_planted_mistakes(mutate):
     cells = [0, 1]
     bad = _failures(lambda c, i: collide_program(c, i, 4, cells, 2, mutate), 4, seeds=30)
     assert len(bad) >= 25, mutate
+
+
+@pytest.mark.parametrize("tables", [True, False])
+@pytest.mark.parametrize("C,M,ncells", [(1, 2, 2), (2, 1, 3), (4, 3, 2), (8, 2, 2)])
+def test_collide_direct_protocol_is_race_and_deadlock_free(C, M, ncells, tables):
+    cells = list(range(ncells))
+    bad = _failures(lambda c, i: collide_direct_program(c, i, C, cells, M, tables), C, seeds=60)
+    assert not bad, bad[0]
+
+
+@pytest.mark.parametrize("mutate", ["single_w_buffer", "no_barrier_after_stores"])
+def test_collide_direct_protocol_model_sees_planted_mistakes(mutate):
+    bad = _failures(lambda c, i: collide_direct_program(c, i, 4, [0, 1], 3, True, mutate), 4, seeds=30)
+    assert len(bad) >= 25, (mutate, len(bad))
 
 
 @pytest.mark.parametrize("ncells", [1, 2, 5])
