@@ -148,8 +148,10 @@ fks_status fks_set_escalation(fks_ctx *ctx, double tol);
  * 1/64 of the FP32 rate).  Rebuilds that tier's tables; synchronises the
  * device.  FKS_ERR_UNSUPPORTED on contexts without tiers. */
 fks_status fks_set_escalation_arith(fks_ctx *ctx, int arith);
-/* Direct routes to the last escalation tier, on by default (on != 0) for
- * contexts with tiers (FKS_ERR_UNSUPPORTED otherwise):
+/* Direct routes to the last escalation tier of the bound above (the loss term
+ * L of the gain-loss split of Appendix A against ||Q||), on by default
+ * (on != 0) for contexts with tiers (FKS_ERR_UNSUPPORTED otherwise,
+ * FKS_ERR_INVALID_ARG for a NULL ctx; takes effect from the next call):
  *  - FKS_BF16X3: a cell whose FP32 bound must also exceed tol (the split-BF16
  *    kernel's own estimates of ||Q|| and ||L|| show c_32 ||L|| / Kn > tol ||Q||
  *    whatever the FP32 tier computes, c_32 = 5e-7, the split-BF16 error
