@@ -65,7 +65,7 @@ BF16_PEAK_TFLOPS, BF16_PEAK_KIND = _bf16_peak()
 # the cells of a launch).  Valid for the kernels as profiled; None once a kernel changes.
 DRAM_BYTES_PER_CELL = {
     "collide_f32": (275447296 + 222745088) / 2048,   # collide_kernel<float, 32, 8>
-    "collide_dfloat": (76990720 + 25570560) / 512,   # collide_kernel<dfloat, 32, 8, false, float> (512 listed cells, pair-split)
+    "collide_dfloat": (76821760 + 26061824) / 512,   # collide_kernel<dfloat, 32, 8, false, float> (512 listed cells, pair-split)
     "bgk_f32": (268507392 + 215125504) / 2048,       # bgk_cluster_kernel<float, 32, 4> (f* read once)
     "collide_tc": (634375680 + 1517931008) / 2048,   # collide_tc_kernel<32> (scratch written back from L2)
 }

@@ -218,3 +218,45 @@ def test_last_tier_alone_matches_oracle(fks, oracle, arith, n):
     for c in range(nc):
         # the result is stored in FP32: its rounding (6e-8 relative) is the floor
         assert rel(Q[c].double().cpu().numpy(), Qo[c]) < 2e-7, c
+
+
+def test_full_size_learned_step_sampled(fks, oracle):
+    """The benchmark's step at its full size and launch configuration: 32^3 cells x 32^3 velocities of the
+    shock tube (left rho = 1, T = 1; right rho = 0.125, T = 0.8; specular x walls), fks_surrogate_step on
+    a split-BF16 context at 1e-3 (the classification, its direct route, the split-BF16 kernel, the FP32
+    and double-float tiers).  Sampled cells (the walls, the bulk on both sides, the interface) against
+    f* (transport, bit-exact) plus dt Q of the oracle, up to the FP32 rounding of the stored state."""
+    w = I.config_shock_tube(ncell=(1, 1, 1))        # parameters only
+    w.ncell = (32, 32, 32)
+    cfg = fks.Config(ncell=w.ncell, bc=w.bc, n=w.n, L=w.L, kernel=w.kernel, kn=w.kn, A1=w.A1, A2=w.A2,
+                     precision=fks.FKS_BF16X3)
+    ctx = fks.Context(cfg)
+    states, which = I.shock_tube_states(w.n, w.L, 32)
+    st = torch.from_numpy(states).float().cuda()
+    f0 = st.index_select(0, torch.from_numpy(np.repeat(which, 1024)).cuda()).contiguous()
+    out, work = torch.empty_like(f0), torch.empty_like(f0)
+    net = fks.Net(w.n, 8, seed=4)
+    dt = 1e-3
+    for _ in range(24):                          # the interface spreads over a few cells
+        ctx.surrogate_step(net, f0, out, work, dt, 1.0, 1.0, BF16_REL)
+        f0, out = out, f0
+    ct = fks.Context(fks.Config(ncell=w.ncell, bc=w.bc, n=w.n, L=w.L, kn=w.kn, A1=w.A1, A2=w.A2,
+                                precision=fks.FKS_FP32))
+    ct.set_offsets(ctx.offsets())                # the same particle offsets: f* of the checked step
+    assert ctx.surrogate_step(net, f0, out, work, dt, 1.0, 1.0, BF16_REL) == f0.shape[0]
+    assert ctx.check() & 1 == 0
+    counts = ctx.escalation()[1]
+    assert counts[1] > 16384                     # the bulk's exact Maxwellians reach the last tier
+    fs = torch.empty_like(f0)
+    ct.transport(f0, fs, dt)
+    assert torch.equal(fs, work)
+    # walls, bulk on both sides, the interface region (x = 14 .. 17)
+    sample = [0, 5 * 1024 + 17, 14 * 1024 + 9, 15 * 1024 + 31, 16 * 1024 + 5 * 32 + 7, 17 * 1024 + 2,
+              26 * 1024 + 3, 32767]
+    tab = oracle.tables(32, w.L, 0, 0.25, w.A1, w.A2, 0)
+    fsh = fs[sample].double().cpu().numpy()
+    Qo = oracle.collide(fsh, tab, kn=w.kn, project=True)
+    got = out[sample].double().cpu().numpy()
+    for i in range(len(sample)):
+        err = np.linalg.norm(got[i] - fsh[i] - dt * Qo[i])
+        assert err <= BF16_REL * np.linalg.norm(dt * Qo[i]) + 2.0 ** -24 * np.linalg.norm(got[i]) * 1.5, sample[i]
