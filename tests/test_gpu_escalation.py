@@ -260,3 +260,14 @@ def test_full_size_learned_step_sampled(fks, oracle):
     for i in range(len(sample)):
         err = np.linalg.norm(got[i] - fsh[i] - dt * Qo[i])
         assert err <= BF16_REL * np.linalg.norm(dt * Qo[i]) + 2.0 ** -24 * np.linalg.norm(got[i]) * 1.5, sample[i]
+
+
+def test_direct_route_error_behaviour(fks):
+    """fks_set_escalation_direct needs a context with escalation tiers: FP64 contexts have none."""
+    c64 = fks.Context(fks.Config(ncell=(2, 1, 1), n=16, L=8.0, kn=0.1, A1=4, A2=4, precision=fks.FKS_FP64))
+    with pytest.raises(fks.FKSError) as e:
+        c64.set_escalation_direct(True)
+    assert e.value.status == 2   # FKS_ERR_UNSUPPORTED
+    c32 = fks.Context(fks.Config(ncell=(2, 1, 1), n=16, L=8.0, kn=0.1, A1=4, A2=4, precision=fks.FKS_FP32))
+    c32.set_escalation_direct(False)
+    c32.set_escalation_direct(True)
