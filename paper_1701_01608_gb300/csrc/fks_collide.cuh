@@ -34,6 +34,10 @@
 // thread per peer then moves that peer's staged block with a bulk copy (TMA,
 // shared::cta -> shared::cluster) that completes on the receiving CTA's
 // mbarrier (issued by one thread in sequence they cost 5 % of the kernel).
+// The double-float instantiations (pencils split over lane pairs) store their
+// x-pass outputs straight into block `rank` of every owner's W instead, with W
+// double-buffered by direction parity, so one cluster barrier per direction
+// orders both the stores and the reuse of the buffer (no staging, no copies).
 #pragma once
 #include <cooperative_groups.h>
 #include <cstdint>
