@@ -161,10 +161,11 @@ fks_status fks_set_escalation_arith(fks_ctx *ctx, int arith);
  *  - fks_surrogate_step / fks_surrogate_collide: the classification before
  *    inference sends a cell whose distance from its local Maxwellian
  *    d = ||f* - M|| / ||M|| is below 0.1 c_32 / tol straight to the last tier
- *    (near equilibrium ||L|| / ||Q|| >= 0.1 / d: measured 1.2 .. 2.6 times 1/d
- *    off equilibrium, far more at exact Maxwellians), skipping the context's
- *    own kernel; results are identical wherever that bound holds, and a cell
- *    where it did not would get the last tier's (more accurate) result.
+ *    (near equilibrium ||Q|| <~ d ||L|| / k_d + ||Q(M)||, k_d = 0.75 .. 2.6
+ *    measured, the residual Q(M) below 1e-5 ||L||: such a cell fails the
+ *    earlier tiers' bound), skipping the context's own kernel; results are
+ *    identical wherever that holds, and a cell where it did not would get the
+ *    last tier's (more accurate) result.
  * Off: every escalated cell passes through every tier. */
 fks_status fks_set_escalation_direct(fks_ctx *ctx, int on);
 /* The tolerance in force and, if counts != NULL, the cells sent to each tier

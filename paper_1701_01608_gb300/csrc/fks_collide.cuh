@@ -100,11 +100,12 @@ struct CollideArgs {
 // (FP32 ~2.4e-7, split BF16 ~5e-6 of ||L|| on near-equilibrium and two-stream cells).
 constexpr double kEscFp32 = 5e-7;
 constexpr double kEscBf16 = 1.5e-5;
-// Lower bound of (||L|| / ||Q||) d near equilibrium, d = ||f - M|| / ||M|| (M the Maxwellian of f's
-// moments): Q ~ L_M (f - M) + Q(M) with ||L_M h|| of the order of the loss frequency times ||h||, so the
-// product is of order one; measured 1.2 .. 2.6 on shock-tube cells with d from 2e-4 to 0.4 and far
-// above one for the (near-)exact Maxwellians.  A tenfold margin: a cell with d < kKappaDist c / tol
-// fails the bound c ||L|| / Kn <= tol ||Q|| of a tier with constant c.
+// Near equilibrium, d = ||f - M|| / ||M|| (M the Maxwellian of f's moments): Q ~ L_M (f - M) + Q(M), so
+// ||Q|| <~ d ||L|| / k_d + ||Q(M)|| with ||L_M h|| of the order of the loss frequency times ||h|| (k_d
+// of order one: 0.75 .. 2.6 measured over shock-tube cells and perturbations of several shapes) and the
+// operator's residual Q(M) below 1e-5 ||L|| (||L|| / ||Q|| > 1e5 at exact discrete Maxwellians).  With
+// k_d taken as kKappaDist (a margin of 7 or more) a cell with d < kKappaDist c / tol fails the bound
+// c ||L|| / Kn <= tol ||Q|| of a tier with constant c.
 constexpr double kKappaDist = 0.1;
 
 __device__ __forceinline__ void cluster_arrive() {

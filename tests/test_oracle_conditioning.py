@@ -63,3 +63,60 @@ def test_fp32_error_is_a_fraction_of_the_loss_term(oracle):
     assert all(1e-8 < e < 1e-6 for e, _ in out)         # on the loss scale: FP32 rounding
     assert out[1][1] > 30 * out[0][1]                    # relative to Q: grows with the conditioning
     assert out[1][1] > 1e-5                              # and misses the FP32 bound near equilibrium
+
+
+def _distance_from_equilibrium(f, n, L):
+    """d = ||f - M|| / ||M||, M the continuous Maxwellian of f's discrete moments at the grid points (the
+    quantity the surrogate's classification computes per cell)."""
+    dv = 2.0 * L / n
+    v = (np.arange(n) + 0.5 - n / 2) * dv
+    V2 = v[:, None, None] ** 2 + v[None, :, None] ** 2 + v[None, None, :] ** 2
+    rho = f.sum() * dv ** 3
+    u = [(f.sum(axis=(1, 2)) * v).sum() * dv ** 3 / rho, (f.sum(axis=(0, 2)) * v).sum() * dv ** 3 / rho,
+         (f.sum(axis=(0, 1)) * v).sum() * dv ** 3 / rho]
+    T = (0.5 * (f * V2).sum() * dv ** 3 - 0.5 * rho * sum(x * x for x in u)) / (1.5 * rho)
+    M = rho / (2 * np.pi * T) ** 1.5 * np.exp(-((v[:, None, None] - u[0]) ** 2 + (v[None, :, None] - u[1]) ** 2 +
+                                                 (v[None, None, :] - u[2]) ** 2) / (2 * T))
+    return np.linalg.norm(f - M) / np.linalg.norm(M)
+
+
+def test_conditioning_times_distance_from_equilibrium(oracle):
+    """The route of the surrogate's classification (a cell with d < 0.1 c / tol goes straight to the
+    last escalation tier) rests on ||Q|| <~ d ||L|| / k_d + ||Q(M)|| near equilibrium (Q ~ L_M(f - M) +
+    Q(M), ||L_M h|| of the order of the loss frequency times ||h||) with k_d of order one and the
+    operator's residual Q(M) at the exact discrete Maxwellian far below ||L||.  Pinned on the oracle:
+    k_d = (||L|| / ||Q||) d over perturbations of a Maxwellian of different shapes and sizes (white
+    noise, noise weighted by |v|^2 and |v|^4 towards the tails, a nearby drifting Maxwellian, a
+    temperature mix) stays at or above 0.5 (0.75 .. 2.3 here, a fivefold margin over the route's 0.1),
+    and ||L|| / ||Q|| at the shock tube's two exact discrete Maxwellians is above 1e5.  Then every cell
+    with d < 0.1 c / tol has ||L|| / ||Q|| > tol / c: it fails the earlier tiers' bound."""
+    n, L = 32, 10.0
+    tab = oracle.tables(n, L, 0, 0.25, 4, 8, 0)
+    M0 = I.maxwellian(n, L, 1.0, (0, 0, 0), 1.0)
+    dv = 2.0 * L / n
+    v = (np.arange(n) + 0.5 - n / 2) * dv
+    w = (v[:, None, None] ** 2 + v[None, :, None] ** 2 + v[None, None, :] ** 2) / 3.0
+    rng = np.random.default_rng(5)
+    cells = {}
+    for eps in (1e-3, 1e-4):
+        cells[f"white {eps:g}"] = M0 * (1 + eps * rng.uniform(-1, 1, M0.shape))
+        cells[f"tail v2 {eps:g}"] = M0 * (1 + eps * w * rng.uniform(-1, 1, M0.shape))
+        cells[f"tail v4 {eps:g}"] = M0 * (1 + eps * w ** 2 * rng.uniform(-1, 1, M0.shape))
+        cells[f"drift {eps:g}"] = M0 + eps * I.maxwellian(n, L, 1.0, (0.5, 0, 0), 0.7)
+        cells[f"T-mix {eps:g}"] = (1 - eps) * M0 + eps * I.maxwellian(n, L, 1.0, (0, 0, 0), 1.5)
+    prod = {}
+    for name, f in cells.items():
+        G, Lo = oracle.gain_loss(f, tab)
+        kappa = np.linalg.norm(Lo) / np.linalg.norm(G - Lo)
+        prod[name] = kappa * _distance_from_equilibrium(f, n, L)
+    assert min(prod.values()) >= 0.5, prod
+    for rho, T in ((1.0, 1.0), (0.125, 0.8)):
+        Mx = I.maxwellian(n, L, rho, (0, 0, 0), T)
+        G, Lo = oracle.gain_loss(Mx, tab)
+        assert np.linalg.norm(Lo) / np.linalg.norm(G - Lo) > 1e5, (rho, T)
+    # the route's consequence at its bound (c = 5e-7, the FP32 constant; tol 1e-5 and 1e-3): a cell at
+    # d = 0.1 c / tol with the smallest k_d seen and a residual of 1e-5 ||L|| still fails the bound
+    c = 5e-7
+    for tol in (1e-5, 1e-3):
+        d = 0.1 * c / tol
+        assert 1.0 / (d / min(prod.values()) + 1e-5) > tol / c, tol
