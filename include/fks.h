@@ -165,7 +165,9 @@ fks_status fks_set_escalation_arith(fks_ctx *ctx, int arith);
  *    measured, the residual Q(M) below 1e-5 ||L||: such a cell fails the
  *    earlier tiers' bound), skipping the context's own kernel; results are
  *    identical wherever that holds, and a cell where it did not would get the
- *    last tier's (more accurate) result.
+ *    last tier's (more accurate) result.  In FKS_BF16X3 contexts a cell with
+ *    d below 0.1 c_b / tol (c_b = 1.5e-5, the split-BF16 constant) goes
+ *    straight to the FP32 tier in the same way.
  * Off: every escalated cell passes through every tier. */
 fks_status fks_set_escalation_direct(fks_ctx *ctx, int on);
 /* The tolerance in force and, if counts != NULL, the cells sent to each tier

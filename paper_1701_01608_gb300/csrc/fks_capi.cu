@@ -1228,18 +1228,29 @@ static fks_status launch_collide(fks_ctx* c, const void* f, void* out, const sig
 }
 
 fks_status fks_internal_fail(fks_ctx* c, fks_status st, const std::string& msg) { return fail(c, st, msg); }
-fks_status fks_internal_last_tier_route(fks_ctx* c, cudaStream_t s, int** list, int** count, double* d_max) {
+fks_status fks_internal_last_tier_route(fks_ctx* c, cudaStream_t s, int** list, int** count, double* d_max,
+                                        int** mid_list, int** mid_count, double* d_mid) {
     *list = nullptr;
     *count = nullptr;
     *d_max = 0.0;
+    *mid_list = nullptr;
+    *mid_count = nullptr;
+    *d_mid = 0.0;
     if (!esc_on(c)) return FKS_OK;
     const fks_status st = reset_esc(c, s);
     if (st != FKS_OK) return st;
     const int last = c->esc_ntier - 1;
     *list = c->esc_lists + (long)last * c->ncells;
     *count = c->esc_counts + last;
-    // the FP32 bound is the binding one (the split-BF16 bound is 30x looser)
-    if (c->esc_direct) *d_max = kKappaDist * kEscFp32 / c->esc_tol;
+    if (!c->esc_direct) return FKS_OK;
+    // the last tier: the FP32 bound is the binding one (the split-BF16 bound is 30x looser)
+    *d_max = kKappaDist * kEscFp32 / c->esc_tol;
+    if (c->tc && c->esc_ntier == 2) {
+        // the FP32 tier (first of two): cells the split-BF16 bound must fail
+        *mid_list = c->esc_lists;
+        *mid_count = c->esc_counts;
+        *d_mid = kKappaDist * kEscBf16 / c->esc_tol;
+    }
     return FKS_OK;
 }
 

@@ -244,9 +244,11 @@ extern "C" fks_status fks_internal_collide_list(fks_ctx* c, const void* f, void*
                                                 int mode, double dt, cudaStream_t s, int keep_counts);
 // Before a classification of the cells (surrogate step): resets the escalation counts on s and returns
 // the last tier's device list and count and the distance from equilibrium d = ||f - M|| / ||M|| below
-// which a cell certainly fails every earlier tier (d_max = 0: no such route; list = nullptr: no tiers).
-// A cell with d < d_max goes straight to the last tier: near equilibrium ||L|| / ||Q|| >= kKappaDist / d.
-extern "C" fks_status fks_internal_last_tier_route(fks_ctx* c, cudaStream_t s, int** list, int** count, double* d_max);
+// which a cell certainly fails every earlier tier (d_max = 0: no such route; list = nullptr: no tiers),
+// and for split-BF16 contexts the FP32 tier's list, count and the distance below which a cell fails the
+// split-BF16 bound (d_mid = 0: none).  See kKappaDist.
+extern "C" fks_status fks_internal_last_tier_route(fks_ctx* c, cudaStream_t s, int** list, int** count, double* d_max,
+                                                   int** mid_list, int** mid_count, double* d_mid);
 // variant B (fks_dealias.cu)
 fks_status launch_dealias(fks_ctx* c, const void* f, void* out, const signed char* delta, double dt, int mode,
                           cudaStream_t s);

@@ -222,17 +222,23 @@ __global__ void __launch_bounds__(BS) output_kernel(int n, double L, long c0, lo
 
 // split the cells by the indicator's lower bound ind_scale / d (known before inference): over the
 // threshold (or not finite) -> route list (their indicator is that bound), else -> candidate list
-//   d < d_last: straight to the last escalation tier's list (last, count *nlast; *ndirect counts them)
+//   d < d_last: straight to the last escalation tier's list (last, count *nlast); else d < d_mid: straight
+//   to the middle tier's list (mid, count *nmid); *ndirect counts both
 __global__ void classify_kernel(long ncells, const float* __restrict__ dist, double ind_scale, float threshold,
                                 float* __restrict__ ind, int* __restrict__ route, int* __restrict__ nroute,
                                 int* __restrict__ cand, int* __restrict__ ncand, double d_last,
-                                int* __restrict__ last, int* __restrict__ nlast, int* __restrict__ ndirect) {
+                                int* __restrict__ last, int* __restrict__ nlast, double d_mid, int* __restrict__ mid,
+                                int* __restrict__ nmid, int* __restrict__ ndirect) {
     for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncells; c += (long)gridDim.x * blockDim.x) {
         const double d = (double)dist[c];
         const float lb = (float)(ind_scale / (d > 1e-30 ? d : 1e-30));
         if (d < d_last) {
             ind[c] = lb;
             last[atomicAdd(nlast, 1)] = (int)c;
+            atomicAdd(ndirect, 1);
+        } else if (d < d_mid) {
+            ind[c] = lb;
+            mid[atomicAdd(nmid, 1)] = (int)c;
             atomicAdd(ndirect, 1);
         } else if (!(lb <= threshold)) {
             ind[c] = lb;
@@ -287,9 +293,9 @@ static fks_status surrogate_run(fks_ctx* c, fks_net* net, const float* fs, float
     if (cudaMemsetAsync(c->s_count, 0, 3 * sizeof(int), s) != cudaSuccess) return FKS_ERR_CUDA;
     // the escalation lists start here: cells that certainly fail every earlier tier (d below the
     // route's bound) go straight to the last tier
-    int *last = nullptr, *nlast = nullptr;
-    double d_last = 0.0;
-    fks_status st0 = fks_internal_last_tier_route(c, s, &last, &nlast, &d_last);
+    int *last = nullptr, *nlast = nullptr, *mid = nullptr, *nmid = nullptr;
+    double d_last = 0.0, d_mid = 0.0;
+    fks_status st0 = fks_internal_last_tier_route(c, s, &last, &nlast, &d_last, &mid, &nmid, &d_mid);
     if (st0 != FKS_OK) return st0;
     // 1. rho and d of every cell; the cells whose bound ind_scale / d already exceeds the threshold
     //    are routed without inference
@@ -297,7 +303,7 @@ static fks_status surrogate_run(fks_ctx* c, fks_net* net, const float* fs, float
     surr::inputs_kernel<<<(unsigned)gridc, surr::BS, 0, s>>>(n, c->vbox.L, 0, nc, fs, nullptr, c->s_rho, c->s_dist);
     surr::classify_kernel<<<256, 256, 0, s>>>(nc, c->s_dist, ind_scale, (float)threshold, c->s_ind, c->s_cells,
                                              c->s_count, c->s_cand, c->s_count + 1, last ? d_last : 0.0, last, nlast,
-                                             c->s_count + 2);
+                                             mid ? d_mid : 0.0, mid, nmid, c->s_count + 2);
     c->launches += 2;
     // 2. the candidates in chunks of B (their count read back: one synchronisation)
     int ncand = 0;
