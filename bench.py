@@ -31,9 +31,10 @@ NCELLS = NX ** 3
 PTS = NCELLS * NV ** 3
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA lanes x FMA x max SM clock (1.26 TFLOP/s)
-# double-float arithmetic on the FP32 pipes: a complex butterfly (4 real products, 6 real sums:
-# 10 FP32 flops) costs 4 x 8 + 6 x 11 = 98 FP32 instructions in pairs -> ~10 per operator flop
-DFLOAT_COST = 10.0
+# double-float arithmetic on the FP32 pipes as the kernel implements it: a complex butterfly (one complex
+# product = 4 real products and 2 sums, two complex sums = 4 sums: 10 FP32 flops) costs 2 x 19 (two fused
+# dot products) + 4 x 8 (unnormalised sums) = 70 FP32 instructions in pairs -> 7 per operator flop
+DFLOAT_COST = 7.0
 DFLOAT_PEAK_TFLOPS = FP32_PEAK_TFLOPS / DFLOAT_COST
 TOL = 1e-3   # the metric's bound: relative L2 of Q per cell against the FP64 operator
 
