@@ -32,10 +32,11 @@ PTS = NCELLS * NV ** 3
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA lanes x FMA x max SM clock (1.26 TFLOP/s)
 # double-float arithmetic on the FP32 pipes as the kernel implements it: a complex butterfly (one complex
-# product = 4 real products and 2 sums, two complex sums = 4 sums: 10 FP32 flops) costs 2 x 19 (two fused
-# dot products) + 4 x 8 (unnormalised sums) = 70 FP32 instructions in pairs -> 7 per operator flop
+# product = 4 real products and 2 sums, two complex sums = 4 sums: 10 flops) costs 2 x 19 (two fused dot
+# products) + 4 x 8 (unnormalised sums) = 70 FP32 instructions in pairs -> 7 per operator flop.  The FP32
+# pipes issue FP32_PEAK_TFLOPS / 2 instructions per second (an FMA counts two flops in the peak).
 DFLOAT_COST = 7.0
-DFLOAT_PEAK_TFLOPS = FP32_PEAK_TFLOPS / DFLOAT_COST
+DFLOAT_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 2.0 / DFLOAT_COST
 TOL = 1e-3   # the metric's bound: relative L2 of Q per cell against the FP64 operator
 
 
@@ -456,8 +457,8 @@ def main():
                     "traffic": b_df * df_cells if b_df else None,
                     "kernel": "collide_kernel<dfloat, 32, 8> (last escalation tier)",
                     "algorithmic_flops_per_launch": df_flops, "launch_ms": df_ms, "cells_per_launch": df_cells,
-                    "peak_note": "double-float operations on the FP32 pipes: derived FP32 peak (152 SMs x 128 lanes x "
-                                 "2 flop x 2.07 GHz) / %.0f FP32 instructions per operator flop" % DFLOAT_COST,
+                    "peak_note": "double-float operations on the FP32 pipes: FP32 instruction rate (152 SMs x 128 "
+                                 "lanes x 2.07 GHz) / %.0f FP32 instructions per operator flop" % DFLOAT_COST,
                     "traffic_note": "dram bytes per listed cell of one ncu capture (512 cells), times the cells of a launch",
                     "frac_of_fp64_peak": df_ach / FP64_PEAK_TFLOPS,
                     "cells_note": "cells of the last timed step; the stage time is the mean over the timed steps"}
